@@ -1,0 +1,433 @@
+/*
+ * FP64 CPU oracle for the FREDEC periodogram hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file; only the tests, the package smoke check and the bench's
+ * CPU-baseline leg do.  It shares no code, header, table or constant with the
+ * CUDA library.
+ *
+ * Every quantity is computed from its plain definition: for each model the
+ * design matrix is built explicitly and the weighted least-squares problem is
+ * solved by Householder QR (no normal equations, no Cholesky, no reuse between
+ * frequencies).  Single-threaded, double precision throughout.
+ *
+ * Definitions followed (Baluev, "FREDEC", Section 2 and Section 3):
+ *   data x_i at times t_i with weights w_i = 1/sigma_i^2             (Sect. 2)
+ *   <phi> = sum_i w_i phi(t_i)                                        (Sect. 2)
+ *   chi2(theta, f) = <(x - mu)^2>                                     (Sect. 2)
+ *   H_n : mu = c + sum_k a_k cos(2 pi f_k t) + b_k sin(2 pi f_k t)    (Eq. Hn)
+ *   l_n(f) = min_theta chi2                                           (Sect. 2)
+ *   relative statistic with base frequencies f' held fixed and joint linear
+ *   refit (Eq. zpowrel): here in the known-noise difference form
+ *       z(f) = ( l(f') - l(f', f) ) / 2
+ *   local refinement of the frequencies (Sect. 3, Eq. lsqf): Gauss-Newton
+ *   on f with the linear parameters refitted at every step.
+ *
+ * Column dropping: a column whose norm after the previous reflections is at
+ * most ORACLE_DROPTOL times its own original norm is treated as linearly
+ * dependent and left out (the residual is then the minimum-norm least-squares
+ * residual).  The paper is silent on degenerate columns (f = 0, f equal to a
+ * base frequency); this is the reading taken.
+ *
+ * Parity pins: every function is pinned by tests that use an independent
+ * route (closed forms, library least squares, invariants, finite differences,
+ * an independent nonlinear solver); see the "not gpu" tests.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_DROPTOL 1e-7
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0   /* 0 = correct oracle; >0 plants one known mistake (tests only) */
+#endif
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* sin and cos of 2*pi*f*t.  The product f*t is split into its rounded value and
+ * its exact rounding error (fma), the nearest integer number of turns is removed
+ * (exactly), and libm is called on the remaining angle in [-pi, pi]. */
+static void trig(double f, double t, double *c, double *s)
+{
+    double x = f * t;
+    double e = fma(f, t, -x);
+    double r = (x - nearbyint(x)) + e;
+#if ORACLE_MUTANT == 2
+    r = -r;    /* planted: wrong sign of the phase of every column */
+#endif
+    double a = TWO_PI * r;
+    *c = cos(a);
+    *s = sin(a);
+}
+
+static double weight(double sigma)
+{
+#if ORACLE_MUTANT == 1
+    (void)sigma;
+    return 1.0;   /* planted: weights ignored */
+#else
+    return 1.0 / (sigma * sigma);
+#endif
+}
+
+/*
+ * Householder QR least squares (Golub & Van Loan, Sect. 5.1-5.3), no pivoting.
+ *   A : N x m, column-major (leading dimension N); overwritten.
+ *   b : N; overwritten by Q^T b.
+ *   x : m coefficients (0 for dropped columns), may be NULL.
+ *   ratio : m, remaining-norm / original-norm of each column when it was
+ *           processed (1 = orthogonal to the previous ones), may be NULL.
+ * Returns the residual sum of squares min_x ||b - A x||^2.
+ */
+static double hh_lsq(double *A, double *b, int64_t N, int m, double *x, double *ratio)
+{
+    double orig[128];
+    int rowof[128];
+    int64_t r = 0;
+    for (int k = 0; k < m; ++k) {
+        double s = 0.0;
+        const double *a = A + (size_t)k * N;
+        for (int64_t i = 0; i < N; ++i) s += a[i] * a[i];
+        orig[k] = sqrt(s);
+    }
+    for (int k = 0; k < m; ++k) {
+        double *a = A + (size_t)k * N;
+        double s = 0.0;
+        for (int64_t i = r; i < N; ++i) s += a[i] * a[i];
+        double sig = sqrt(s);
+        double rat = orig[k] > 0.0 ? sig / orig[k] : 0.0;
+        if (ratio) ratio[k] = rat;
+        if (r >= N || orig[k] == 0.0 || rat <= ORACLE_DROPTOL) {
+            rowof[k] = -1;
+            continue;
+        }
+        double x0 = a[r];
+        double alpha = x0 >= 0.0 ? -sig : sig;
+        double v0 = x0 - alpha;
+        double vtv = 2.0 * sig * (sig + fabs(x0));
+        double beta = 2.0 / vtv;
+        /* v = (v0, a[r+1..N-1]) ; apply H = I - beta v v^T to later columns and b */
+        for (int j = k + 1; j <= m; ++j) {
+            double *c = (j < m) ? A + (size_t)j * N : b;
+            double d = v0 * c[r];
+            for (int64_t i = r + 1; i < N; ++i) d += a[i] * c[i];
+            d *= beta;
+            c[r] -= d * v0;
+            for (int64_t i = r + 1; i < N; ++i) c[i] -= d * a[i];
+        }
+        a[r] = alpha;
+        /* keep v below the diagonal is not needed: only R and Q^T b are used */
+        rowof[k] = (int)r;
+        ++r;
+    }
+    double chi2 = 0.0;
+    for (int64_t i = r; i < N; ++i) chi2 += b[i] * b[i];
+    if (x) {
+        for (int k = m - 1; k >= 0; --k) {
+            if (rowof[k] < 0) { x[k] = 0.0; continue; }
+            int64_t rk = rowof[k];
+            double acc = b[rk];
+            for (int j = k + 1; j < m; ++j)
+                if (rowof[j] >= 0) acc -= A[(size_t)j * N + rk] * x[j];
+            x[k] = acc / A[(size_t)k * N + rk];
+        }
+    }
+    return chi2;
+}
+
+/* Fill the weighted design matrix of the model
+ *   [1, cos 2pi g_0 t, sin 2pi g_0 t, ..., cos 2pi g_{n-1} t, sin 2pi g_{n-1} t]
+ * (Eq. Hn) scaled row-wise by sqrt(w_i), and b = sqrt(w_i) x_i. */
+static void design(const double *t, const double *y, const double *sigma, int64_t N,
+                   const double *g, int n, double *A, double *b)
+{
+    for (int64_t i = 0; i < N; ++i) {
+        double sw = sqrt(weight(sigma[i]));
+#if ORACLE_MUTANT == 3
+        A[i] = 0.0;   /* planted: the free constant c of Eq. H0 is missing */
+#else
+        A[i] = sw;
+#endif
+        for (int k = 0; k < n; ++k) {
+            double c, s;
+            trig(g[k], t[i], &c, &s);
+            A[(size_t)(1 + 2 * k) * N + i] = sw * c;
+            A[(size_t)(2 + 2 * k) * N + i] = sw * s;
+        }
+        if (b) b[i] = sw * y[i];
+    }
+}
+
+/* l(g) = min over the linear parameters of chi2 for the model with the n
+ * frequencies g (Sect. 2).  Optional: coefficients theta (2n+1, order
+ * [c, a_0, b_0, a_1, b_1, ...]) and the unweighted residual x_i - mu(t_i). */
+static double model_fit(const double *t, const double *y, const double *sigma, int64_t N,
+                        const double *g, int n, double *theta, double *ratio, double *resid)
+{
+    int m = 2 * n + 1;
+    double *A = (double *)malloc(sizeof(double) * (size_t)N * m);
+    double *b = (double *)malloc(sizeof(double) * (size_t)N);
+    double th[128];
+    design(t, y, sigma, N, g, n, A, b);
+    double chi2 = hh_lsq(A, b, N, m, th, ratio);
+    if (theta) memcpy(theta, th, sizeof(double) * m);
+    if (resid) {
+        for (int64_t i = 0; i < N; ++i) {
+            double mu = th[0];
+            for (int k = 0; k < n; ++k) {
+                double c, s;
+                trig(g[k], t[i], &c, &s);
+                mu += th[1 + 2 * k] * c + th[2 + 2 * k] * s;
+            }
+            resid[i] = y[i] - mu;
+        }
+    }
+    free(A);
+    free(b);
+    return chi2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Residual periodogram (Eq. zpowrel, difference form).                       */
+
+/*
+ * For every trial frequency f_j the model [base model, cos 2pi f_j t,
+ * sin 2pi f_j t] is fitted jointly (the base amplitudes are refitted; the base
+ * frequencies stay fixed) and
+ *     z_j = ( chi2_base - chi2_j ) / 2 .
+ * Outputs: z (nf); chi2_base (1) may be NULL; coef (2*nf: a_j, b_j, the
+ * coefficients of cos and sin of the trial frequency in raw time t) may be
+ * NULL; ratio (nf: min over the two trial columns of remaining/original norm)
+ * may be NULL.
+ */
+int oracle_periodogram(const double *t, const double *y, const double *sigma, int64_t N,
+                       const double *base, int n_base, const double *fgrid, int64_t nf,
+                       double *z, double *chi2_base, double *coef, double *ratio)
+{
+    if (N <= 0 || n_base < 0 || n_base > 40 || nf < 0) return 1;
+    double *g = (double *)malloc(sizeof(double) * (n_base + 1));
+    for (int k = 0; k < n_base; ++k) g[k] = base[k];
+    double l0 = model_fit(t, y, sigma, N, g, n_base, NULL, NULL, NULL);
+    if (chi2_base) *chi2_base = l0;
+    double th[128], rat[128];
+    for (int64_t j = 0; j < nf; ++j) {
+        g[n_base] = fgrid[j];
+        double l1 = model_fit(t, y, sigma, N, g, n_base + 1, th, rat, NULL);
+        z[j] = 0.5 * (l0 - l1);
+        if (coef) {
+            coef[2 * j] = th[2 * n_base + 1];
+            coef[2 * j + 1] = th[2 * n_base + 2];
+        }
+        if (ratio) {
+            double a = rat[2 * n_base + 1], bb = rat[2 * n_base + 2];
+            ratio[j] = a < bb ? a : bb;
+        }
+    }
+    free(g);
+    return 0;
+}
+
+/*
+ * dz/df_j for the residual periodogram.  By the envelope theorem (the linear
+ * parameters are at their optimum) only the explicit frequency dependence of
+ * the model matters:
+ *     dz/df = -1/2 d chi2/df = sum_i w_i r_i dmu/df(t_i),
+ *     dmu/df = 2 pi t (-a sin 2pi f t + b cos 2pi f t),
+ * with r the residual of the full fit and (a, b) its coefficients at f.
+ */
+int oracle_periodogram_grad(const double *t, const double *y, const double *sigma, int64_t N,
+                            const double *base, int n_base, const double *fgrid, int64_t nf,
+                            double *dzdf)
+{
+    if (N <= 0 || n_base < 0 || n_base > 40 || nf < 0) return 1;
+    double *g = (double *)malloc(sizeof(double) * (n_base + 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double th[128];
+    for (int k = 0; k < n_base; ++k) g[k] = base[k];
+    for (int64_t j = 0; j < nf; ++j) {
+        g[n_base] = fgrid[j];
+        model_fit(t, y, sigma, N, g, n_base + 1, th, NULL, r);
+        double a = th[2 * n_base + 1], b = th[2 * n_base + 2], acc = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double c, s;
+            trig(fgrid[j], t[i], &c, &s);
+            acc += weight(sigma[i]) * r[i] * TWO_PI * t[i] * (-a * s + b * c);
+        }
+        dzdf[j] = acc;
+    }
+    free(g);
+    free(r);
+    return 0;
+}
+
+/*
+ * Vector-Jacobian product of the periodogram with respect to the data:
+ *     dL/dy_i = sum_j v_j dz_j/dy_i,   dz_j/dy_i = w_i ( mu_j(t_i) - mu_base(t_i) ),
+ * (again the envelope theorem: d chi2/dy_i = 2 w_i r_i at the optimum), where
+ * mu_j is the fitted model with trial frequency f_j and mu_base the base fit.
+ */
+int oracle_periodogram_vjp(const double *t, const double *y, const double *sigma, int64_t N,
+                           const double *base, int n_base, const double *fgrid, int64_t nf,
+                           const double *v, double *dldy)
+{
+    if (N <= 0 || n_base < 0 || n_base > 40 || nf < 0) return 1;
+    double *g = (double *)malloc(sizeof(double) * (n_base + 1));
+    double *rb = (double *)malloc(sizeof(double) * (size_t)N);
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int k = 0; k < n_base; ++k) g[k] = base[k];
+    model_fit(t, y, sigma, N, g, n_base, NULL, NULL, rb);
+    for (int64_t i = 0; i < N; ++i) dldy[i] = 0.0;
+    for (int64_t j = 0; j < nf; ++j) {
+        if (v[j] == 0.0) continue;
+        g[n_base] = fgrid[j];
+        model_fit(t, y, sigma, N, g, n_base + 1, NULL, NULL, r);
+        for (int64_t i = 0; i < N; ++i) dldy[i] += v[j] * (rb[i] - r[i]);   /* mu_j - mu_b */
+    }
+    for (int64_t i = 0; i < N; ++i) dldy[i] *= weight(sigma[i]);
+    free(g);
+    free(rb);
+    free(r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Frequency tuples on a constant base (Sect. 2, Phase 2 of Sect. 4).         */
+
+/* l_0: chi2 of the constant-only model H_0 (Eq. H0). */
+double oracle_l0(const double *t, const double *y, const double *sigma, int64_t N)
+{
+    return model_fit(t, y, sigma, N, NULL, 0, NULL, NULL, NULL);
+}
+
+/* l(S) for one tuple of m frequencies (model H_m, Eq. Hn). theta may be NULL. */
+double oracle_tuple_l(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *freqs, int m, double *theta)
+{
+    return model_fit(t, y, sigma, N, freqs, m, theta, NULL, NULL);
+}
+
+/*
+ * Many tuples in CSR layout: tuple k holds freqs[off[k] .. off[k+1]).
+ * z_k = (l_0 - l_k)/2.  l0_out may be NULL.
+ */
+int oracle_tuple_eval(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *freqs, const int64_t *off, int64_t n_tuples,
+                      double *z, double *l0_out)
+{
+    if (N <= 0 || n_tuples < 0) return 1;
+    double l0 = oracle_l0(t, y, sigma, N);
+    if (l0_out) *l0_out = l0;
+    for (int64_t k = 0; k < n_tuples; ++k) {
+        int m = (int)(off[k + 1] - off[k]);
+        if (m < 0 || m > 60) return 1;
+        z[k] = 0.5 * (l0 - oracle_tuple_l(t, y, sigma, N, freqs + off[k], m, NULL));
+    }
+    return 0;
+}
+
+/*
+ * All subtuples of a pool of n frequencies (Phase 2 forward cascade):
+ * l_table[mask] = l of the tuple {pool[k] : bit k of mask set}, l_table[0] = l_0.
+ */
+int oracle_pool_table(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *pool, int n, double *l_table)
+{
+    if (N <= 0 || n < 0 || n > 24) return 1;
+    double g[64];
+    for (uint64_t mask = 0; mask < (1ull << n); ++mask) {
+        int m = 0;
+        for (int k = 0; k < n; ++k)
+            if (mask >> k & 1) g[m++] = pool[k];
+        l_table[mask] = oracle_tuple_l(t, y, sigma, N, g, m, NULL);
+    }
+    return 0;
+}
+
+/*
+ * z and its gradient for CSR tuples: dz/df_k = sum_i w_i r_i 2 pi t_i
+ * (-a_k sin 2pi f_k t_i + b_k cos 2pi f_k t_i), r the residual of the tuple fit.
+ */
+int oracle_tuple_grad(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *freqs, const int64_t *off, int64_t n_tuples,
+                      double *z, double *dzdf)
+{
+    if (N <= 0 || n_tuples < 0) return 1;
+    double l0 = oracle_l0(t, y, sigma, N);
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double th[128];
+    for (int64_t k = 0; k < n_tuples; ++k) {
+        const double *g = freqs + off[k];
+        int m = (int)(off[k + 1] - off[k]);
+        double l = model_fit(t, y, sigma, N, g, m, th, NULL, r);
+        z[k] = 0.5 * (l0 - l);
+        for (int q = 0; q < m; ++q) {
+            double a = th[1 + 2 * q], b = th[2 + 2 * q], acc = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double c, s;
+                trig(g[q], t[i], &c, &s);
+                acc += weight(sigma[i]) * r[i] * TWO_PI * t[i] * (-a * s + b * c);
+            }
+            dzdf[off[k] + q] = acc;
+        }
+    }
+    free(r);
+    return 0;
+}
+
+/*
+ * Local refinement of one tuple (Sect. 3, Eq. lsqf): Gauss-Newton on the
+ * frequencies.  Each iteration refits the linear parameters at the current f,
+ * linearises the model in xi = (theta, f) with the frequency columns
+ *     d mu / d f_k = 2 pi t (-a_k sin 2pi f_k t + b_k cos 2pi f_k t),
+ * solves the linear least-squares step for (dtheta, df) by QR, and moves f by
+ * df.  If the step does not lower chi2 it is halved (up to 40 times).
+ * Stops when max_k |df_k| * span(t) < tol or after max_iter iterations; the
+ * final l is the chi2 of the linear refit at the final f.
+ * freqs is updated in place.  Returns the number of iterations (>= 0) or -1.
+ */
+int oracle_tuple_refine(const double *t, const double *y, const double *sigma, int64_t N,
+                        double *freqs, int m, int max_iter, double tol, double *l_out)
+{
+    if (N <= 0 || m < 0 || m > 40) return -1;
+    int p = 2 * m + 1, q = 3 * m + 1;
+    double th[256], xi[256];
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *J = (double *)malloc(sizeof(double) * (size_t)N * q);
+    double *rb = (double *)malloc(sizeof(double) * (size_t)N);
+    double *trial = (double *)malloc(sizeof(double) * (m + 1));
+    double tmin = t[0], tmax = t[0];
+    for (int64_t i = 0; i < N; ++i) { if (t[i] < tmin) tmin = t[i]; if (t[i] > tmax) tmax = t[i]; }
+    double span = tmax - tmin > 0 ? tmax - tmin : 1.0;
+    double l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r);
+    int it = 0;
+    for (; it < max_iter && m > 0; ++it) {
+        design(t, y, sigma, N, freqs, m, J, NULL);
+        for (int k = 0; k < m; ++k) {
+            double a = th[1 + 2 * k], b = th[2 + 2 * k];
+            for (int64_t i = 0; i < N; ++i) {
+                double c, s;
+                trig(freqs[k], t[i], &c, &s);
+                J[(size_t)(p + k) * N + i] = sqrt(weight(sigma[i])) * TWO_PI * t[i] * (-a * s + b * c);
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) rb[i] = sqrt(weight(sigma[i])) * r[i];
+        hh_lsq(J, rb, N, q, xi, NULL);
+        double step = 1.0, dmax = 0.0, lnew = l;
+        for (int k = 0; k < m; ++k) if (fabs(xi[p + k]) > dmax) dmax = fabs(xi[p + k]);
+        int accepted = 0;
+        for (int h = 0; h < 40; ++h, step *= 0.5) {
+            for (int k = 0; k < m; ++k) trial[k] = freqs[k] + step * xi[p + k];
+            lnew = model_fit(t, y, sigma, N, trial, m, NULL, NULL, NULL);
+            if (lnew <= l) { accepted = 1; break; }
+        }
+        if (!accepted) break;
+        for (int k = 0; k < m; ++k) freqs[k] = trial[k];
+        l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r);
+        if (step * dmax * span < tol) { ++it; break; }
+    }
+    if (l_out) *l_out = l;
+    free(r); free(J); free(rb); free(trial);
+    return it;
+}
