@@ -1,0 +1,283 @@
+/*
+ * fredec.h -- C ABI of the B300 (sm_103a) FREDEC hot-path library, libfredec.so.
+ *
+ * What it computes (Baluev, "Detecting multiple periodicities ... II. Frequency
+ * Decomposer", Sections 2-5):
+ *
+ *   Data: N observations (t_i, y_i) with uncertainties sigma_i; weights
+ *   w_i = 1/sigma_i^2 (Section 2: the noise variance is kappa/w_i).
+ *   Weighted sum <phi> = sum_i w_i phi(t_i)  (Section 2).
+ *   Model H_n (Eq. Hn): mu(t) = c + sum_k a_k cos(2 pi f_k t) + b_k sin(2 pi f_k t).
+ *   l(f) = min over (c, a, b) of <(y - mu)^2>  (Section 2).
+ *
+ *   Residual periodogram (Eq. zpowrel with the base tuple f' held fixed and the
+ *   base amplitudes refitted jointly), in the known-noise difference form:
+ *       z(f) = ( l(f') - l(f', f) ) / 2 ,
+ *   evaluated on a trial-frequency grid.  The base model is the constant plus
+ *   n_base fixed sinusoids.  f is in cycles per unit of t (omega = 2 pi f).
+ *
+ *   Tuples on a constant base (Section 2 and Phase 2 of Section 4):
+ *       z_S = ( l_0 - l(S) ) / 2   for a frequency tuple S, l_0 = l of H_0.
+ *   Local refinement (Section 3, Eq. lsqf): Gauss-Newton steps in the
+ *   frequencies with the linear parameters refitted at each step.
+ *
+ * Conventions shared by all entry points
+ *   - Return value: a fredec_status.  On any error nothing is written to the
+ *     outputs of the host-pointer variants, and fredec_last_error() returns a
+ *     message (thread-local, valid until the next call on the same thread).
+ *   - Ownership: the caller owns every buffer.  The library keeps no pointer
+ *     after a call returns (plans are the documented exception).
+ *   - Host-pointer variants are synchronous and validate all values.
+ *   - _dev variants take device pointers and a CUDA stream (cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  They are stream-ordered:
+ *     they return after enqueueing work, and the caller keeps the buffers alive
+ *     until the stream has completed.  Sizes are validated on the host; values
+ *     (sigma > 0, finite data) are not read back -- invalid values give
+ *     non-finite outputs, not an error code.  Scratch memory is taken from the
+ *     stream-ordered allocator (cudaMallocAsync) on the same stream.
+ *   - Precision: FREDEC_FP64 computes everything in double precision.
+ *     FREDEC_MIXED keeps phases (as exact 64-bit fixed-point turns), the
+ *     re-seeding of the sin/cos recurrence, the base fit and every solve in
+ *     FP64, and accumulates the trigonometric sums in FP32 with blocked
+ *     summation; bins whose 2x2 system is ill-conditioned are re-evaluated
+ *     in FP64 (see fredec_opts.flag_tau).
+ *   - Degenerate trial columns (f = 0, f equal to a base frequency): a new
+ *     column whose norm after projection on the previous columns is below
+ *     1e-7 of its own norm is dropped (minimum-norm least squares); z is then
+ *     the contribution of the remaining column, or 0.
+ */
+#ifndef FREDEC_H
+#define FREDEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FREDEC_MAX_NBASE 12   /* base sinusoids (p = 2*n_base + 1 <= 25)          */
+#define FREDEC_MAX_TUPLE 20   /* frequencies per tuple for eval/grad/refine       */
+#define FREDEC_MAX_POOL  24   /* pool size for the all-subtuple table (2^24 rows) */
+#define FREDEC_MAX_TOPK  64
+
+typedef enum {
+    FREDEC_OK = 0,
+    FREDEC_EINVAL = 1,     /* bad sizes or values                                */
+    FREDEC_ENOMEM = 2,     /* device allocation failed                           */
+    FREDEC_ECUDA = 3,      /* a CUDA call failed (message has the CUDA error)    */
+    FREDEC_ESINGULAR = 4,  /* the base model's normal matrix is singular         */
+    FREDEC_ETIMEOUT = 5    /* a bounded device wait gave up                      */
+} fredec_status;
+
+enum { FREDEC_FP64 = 0, FREDEC_MIXED = 1 };
+
+typedef struct fredec_opts {
+    int32_t precision;  /* FREDEC_FP64 (default) or FREDEC_MIXED                   */
+    int32_t topk;       /* number of local maxima of z to report, 0..64 (default 0) */
+    int32_t fpt;        /* frequencies per thread; 0 = tuned or built-in default    */
+    int32_t warps;      /* warps per CTA (point splits); 0 = tuned or default       */
+    double  flag_tau;   /* MIXED: a bin is recomputed in FP64 when a pivot of its
+                           2x2 system falls below flag_tau times its column norm.
+                           0 = default (0.05); negative = never recompute.          */
+} fredec_opts;
+
+/* Fill *o with the defaults (FP64, no top-k, tuned launch shape). */
+void fredec_opts_init(fredec_opts *o);
+
+/* ------------------------------------------------------------------------ */
+/* Residual periodogram                                                      */
+
+/*
+ * z_out[j] = z(f_grid[j]) for j < nf, FP64, host pointers.
+ *   t, y, sigma : N observations (sigma > 0, all finite), any time order.
+ *   base_freqs  : n_base fixed base frequencies (0 <= n_base <= FREDEC_MAX_NBASE;
+ *                 may be NULL when n_base == 0).  N must be >= 2*n_base + 3.
+ *   f_grid      : nf >= 0 finite trial frequencies.  Uniform grids
+ *                 (f_j = f_0 + j*df to 8 ulps) use the rotation recurrence;
+ *                 other grids use a per-term phase (slower).
+ * Errors: EINVAL (sizes/values), ESINGULAR (base normal matrix singular, e.g.
+ * duplicate base frequencies), ENOMEM, ECUDA.
+ */
+int fredec_periodogram(const double *t, const double *y, const double *sigma, int64_t N,
+                       const double *base_freqs, int32_t n_base,
+                       const double *f_grid, int64_t nf, double *z_out);
+
+/*
+ * As fredec_periodogram with options and extra outputs (each may be NULL):
+ *   info_out[3]   : chi2_base = l(f'), W = sum of weights, t_c = the time origin
+ *                   used for the coefficients below.
+ *   topk_idx_out  : opts->topk grid indices of the largest local maxima of z
+ *                   (z_j > z_{j-1} and z_j >= z_{j+1}; an end point counts when it
+ *                   exceeds its one neighbour), by decreasing z, ties to the lower
+ *                   index; -1 where fewer maxima exist.
+ *   coef_out[2nf] : (a_j, b_j), the fitted amplitudes of cos and sin of
+ *                   2 pi f_j (t - t_c) in the joint fit (needed by the VJP).
+ */
+int fredec_periodogram_ex(const double *t, const double *y, const double *sigma, int64_t N,
+                          const double *base_freqs, int32_t n_base,
+                          const double *f_grid, int64_t nf, const fredec_opts *opts,
+                          double *z_out, double *info_out, int64_t *topk_idx_out,
+                          double *coef_out);
+
+/*
+ * Device-pointer, stream-ordered variant on the uniform grid f_j = f0 + j*df,
+ * j = 0..nf-1.  All array arguments are device pointers (base_freqs too);
+ * outputs as in fredec_periodogram_ex (info_out, topk_idx_out, coef_out may be
+ * NULL).
+ */
+int fredec_periodogram_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                           const double *base_freqs, int32_t n_base,
+                           double f0, double df, int64_t nf, const fredec_opts *opts,
+                           double *z_out, double *info_out, int64_t *topk_idx_out,
+                           double *coef_out, void *stream);
+
+/*
+ * Vector-Jacobian product of the periodogram with respect to the data y
+ * (the adjoint of the map y -> z on a fixed uniform grid):
+ *   dldy_out[i] = sum_j v_j dz_j/dy_i = w_i sum_j v_j ( mu_j(t_i) - mu_base(t_i) ),
+ * where mu_j is the fit with trial frequency f_j (envelope theorem: the linear
+ * parameters are optimal, so only the explicit y dependence of chi2 counts).
+ * coef and info are the coef_out / info_out of the forward call on the same
+ * inputs (precision of the forward call).  Device pointers, stream-ordered.
+ */
+int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                               const double *base_freqs, int32_t n_base,
+                               double f0, double df, int64_t nf,
+                               const double *coef, const double *info, const double *v,
+                               int32_t precision, double *dldy_out, void *stream);
+
+/* Host-pointer variant of the VJP on a uniform grid (recomputes the forward). */
+int fredec_periodogram_vjp(const double *t, const double *y, const double *sigma, int64_t N,
+                           const double *base_freqs, int32_t n_base,
+                           double f0, double df, int64_t nf, const double *v,
+                           int32_t precision, double *dldy_out);
+
+/* ------------------------------------------------------------------------ */
+/* Frequency tuples on a constant base                                       */
+
+/*
+ * z_out[k] = (l_0 - l(S_k))/2 for n_tuples tuples in CSR layout: tuple k holds
+ * tuple_freqs[tuple_offsets[k] .. tuple_offsets[k+1]) (0..FREDEC_MAX_TUPLE
+ * frequencies; offsets nondecreasing, offsets[0] = 0).  l0_out (may be NULL)
+ * receives l_0.  FP64 sums and solves.  Host pointers.
+ */
+int fredec_tuple_eval(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
+                      double *z_out, double *l0_out);
+
+/*
+ * All 2^n_pool subtuples of a candidate pool (Phase 2, Section 4):
+ * l_table[mask] = l of the tuple {pool[k] : bit k of mask}; l_table[0] = l_0.
+ * n_pool <= FREDEC_MAX_POOL.  One FP64 Gram of the pool's 2 n_pool + 1 columns,
+ * then one Cholesky per mask.  Host pointers.
+ */
+int fredec_pool_subtuples_eval(const double *t, const double *y, const double *sigma, int64_t N,
+                               const double *pool, int32_t n_pool, double *l_table);
+
+/*
+ * z and its gradient with respect to the tuple frequencies (CSR layout as in
+ * fredec_tuple_eval):  dz/df_k = sum_i w_i r_i 2 pi t_i (-a_k sin + b_k cos),
+ * r the residual of the tuple's fit.  dz_df_out has the layout of tuple_freqs.
+ * precision selects FP64 or FP32-accumulated sums (solves always FP64).
+ */
+int fredec_tuple_grad(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
+                      int32_t precision, double *z_out, double *dz_df_out);
+
+/*
+ * Local refinement of every tuple (Section 3): up to max_iter Gauss-Newton
+ * steps on the frequencies, each solving the extended system of Eq. lsqf by
+ * extending the Cholesky factor of the linear normal matrix; a step that does
+ * not lower l is halved.  Stops when max_k |df_k| * span(t) < tol.
+ * tuple_freqs (CSR as above) is updated in place; l_out[k] = l at the final
+ * frequencies; iters_out[k] (may be NULL) = iterations used.
+ */
+int fredec_tuple_refine(const double *t, const double *y, const double *sigma, int64_t N,
+                        double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
+                        int32_t max_iter, double tol, int32_t precision,
+                        double *l_out, int32_t *iters_out);
+
+/* ------------------------------------------------------------------------ */
+/* Batched residual periodograms (many series, one persistent launch)        */
+
+/*
+ * n_series independent series in CSR layout (host pointers):
+ *   observations of series s: t/y/sigma[obs_offsets[s] .. obs_offsets[s+1])
+ *   base frequencies:          base_freqs[base_offsets[s] .. base_offsets[s+1])
+ *   uniform grid:              f0[s] + j*df[s], j < nf[s]
+ *   output:                    z_out[z_offsets[s] .. z_offsets[s] + nf[s])
+ *   topk_idx_out (may be NULL): n_series * opts->topk indices.
+ * All series go through one batched prep and one persistent periodogram
+ * kernel with a device work queue.
+ */
+int fredec_periodogram_batch(const double *t, const double *y, const double *sigma,
+                             const int64_t *obs_offsets, int64_t n_series,
+                             const double *base_freqs, const int64_t *base_offsets,
+                             const double *f0, const double *df, const int64_t *nf,
+                             const int64_t *z_offsets, const fredec_opts *opts,
+                             double *z_out, int64_t *topk_idx_out);
+
+/*
+ * A batch plan: device-resident inputs plus the captured CUDA graph of
+ * prep -> persistent periodogram -> FP64 re-evaluation -> top-k.  The plan
+ * copies the host inputs once (same layout as fredec_periodogram_batch) and
+ * keeps them; run replays the graph on a stream and leaves z and top-k in
+ * device buffers owned by the plan.
+ */
+typedef struct fredec_batch_plan fredec_batch_plan;
+
+int fredec_batch_plan_create(fredec_batch_plan **plan,
+                             const double *t, const double *y, const double *sigma,
+                             const int64_t *obs_offsets, int64_t n_series,
+                             const double *base_freqs, const int64_t *base_offsets,
+                             const double *f0, const double *df, const int64_t *nf,
+                             const int64_t *z_offsets, const fredec_opts *opts);
+int fredec_batch_plan_run(fredec_batch_plan *plan, void *stream);
+/* Device pointers to the plan's outputs (valid until destroy). */
+int fredec_batch_plan_outputs(fredec_batch_plan *plan, double **z_dev, int64_t **topk_dev,
+                              int64_t *z_total, int64_t *terms);
+/* Copy the outputs to host buffers (synchronous). Either may be NULL. */
+int fredec_batch_plan_download(fredec_batch_plan *plan, double *z_out, int64_t *topk_idx_out);
+void fredec_batch_plan_destroy(fredec_batch_plan *plan);
+
+/* ------------------------------------------------------------------------ */
+/* Launch-shape autotuner                                                    */
+
+/*
+ * Time the compiled launch shapes (frequencies per thread, warps per CTA) for a
+ * periodogram with this base size, N and nf on synthetic inputs, and remember
+ * the fastest for later calls with the same (precision, n_base, N bucket,
+ * nf bucket).  If the environment variable FREDEC_TUNE_CACHE names a file,
+ * the table is loaded from it at first use and rewritten after each tuning.
+ * best_fpt / best_warps (may be NULL) receive the winner.
+ */
+int fredec_tune(int32_t precision, int32_t n_base, int64_t N, int64_t nf,
+                int32_t *best_fpt, int32_t *best_warps);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement support (no counterpart in the paper)                        */
+
+/*
+ * When both are non-NULL CUDA events (cudaEvent_t as void*), every following
+ * periodogram call on this host thread records ev_start immediately before and
+ * ev_stop immediately after its main periodogram kernel, on the call's stream;
+ * NULL, NULL switches this off.  The library does not own the events.
+ */
+int fredec_profile_events(void *ev_start, void *ev_stop);
+
+/*
+ * Measured whole-GPU pipe rates of the current device (lane operations per
+ * second): out[0] FP32 FMA, out[1] FP64 FMA, out[2] MUFU sine.  Synchronous;
+ * runs three short microbenchmark kernels.
+ */
+int fredec_pipe_peaks(double *out);
+
+/* ------------------------------------------------------------------------ */
+const char *fredec_last_error(void);
+const char *fredec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FREDEC_H */

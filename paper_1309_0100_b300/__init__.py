@@ -1,0 +1,388 @@
+"""B300-native FREDEC hot path: residual and multifrequency periodograms.
+
+A thin Python binding of libfredec.so (C ABI declared in include/fredec.h).
+This module only marshals arguments: every step of the computation runs in
+the library's CUDA kernels.  numpy arrays go through the host-pointer entry
+points; CUDA torch tensors through the stream-ordered ``*_dev`` entry points
+on torch's current stream.
+
+If the shared library has not been built, every call raises: there is no
+CPU fallback.  Build it with ``python -m paper_1309_0100_b300._build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
+    "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
+    "tuple_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
+]
+
+FP64 = 0
+MIXED = 1
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfredec.so")
+
+_c_dp = ctypes.POINTER(ctypes.c_double)
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+
+
+class FredecError(RuntimeError):
+    STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESINGULAR", 5: "ETIMEOUT"}
+
+    def __init__(self, code: int, msg: str):
+        self.code = code
+        self.status = self.STATUS.get(code, str(code))
+        super().__init__(f"fredec {self.status}: {msg}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("topk", ctypes.c_int32), ("fpt", ctypes.c_int32),
+                ("warps", ctypes.c_int32), ("flag_tau", ctypes.c_double)]
+
+
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libfredec.so (raises if it was not built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise FredecError(3, f"{LIB_PATH} is missing: build it with python -m paper_1309_0100_b300._build")
+    L = ctypes.CDLL(LIB_PATH)
+    d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "fredec_opts_init": (None, [ctypes.POINTER(Opts)]),
+        "fredec_last_error": (ctypes.c_char_p, []),
+        "fredec_version": (ctypes.c_char_p, []),
+        "fredec_periodogram": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, _c_dp, i64, _c_dp]),
+        "fredec_periodogram_ex": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, _c_dp, i64,
+                                                 ctypes.POINTER(Opts), _c_dp, _c_dp, _c_i64p, _c_dp]),
+        "fredec_periodogram_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64, ctypes.POINTER(Opts),
+                                                  _vp, _vp, _vp, _vp, _vp]),
+        "fredec_periodogram_vjp_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64, _vp, _vp, _vp, i32,
+                                                      _vp, _vp]),
+        "fredec_periodogram_vjp": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, d, d, i64, _c_dp, i32,
+                                                  _c_dp]),
+        "fredec_tuple_eval": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, _c_dp, _c_dp]),
+        "fredec_pool_subtuples_eval": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, _c_dp]),
+        "fredec_tuple_grad": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, i32, _c_dp, _c_dp]),
+        "fredec_tuple_refine": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, i32, d, i32, _c_dp,
+                                               _c_i32p]),
+        "fredec_periodogram_batch": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, _c_i64p, i64, _c_dp, _c_i64p, _c_dp, _c_dp,
+                                                    _c_i64p, _c_i64p, ctypes.POINTER(Opts), _c_dp, _c_i64p]),
+        "fredec_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _c_dp, _c_dp, _c_dp, _c_i64p, i64, _c_dp,
+                                                    _c_i64p, _c_dp, _c_dp, _c_i64p, _c_i64p, ctypes.POINTER(Opts)]),
+        "fredec_batch_plan_run": (ctypes.c_int, [_vp, _vp]),
+        "fredec_batch_plan_outputs": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_i64p,
+                                                     _c_i64p]),
+        "fredec_batch_plan_download": (ctypes.c_int, [_vp, _c_dp, _c_i64p]),
+        "fredec_batch_plan_destroy": (None, [_vp]),
+        "fredec_tune": (ctypes.c_int, [i32, i32, i64, i64, _c_i32p, _c_i32p]),
+        "fredec_profile_events": (ctypes.c_int, [_vp, _vp]),
+        "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib_handle = L
+    return L
+
+
+def version() -> str:
+    return lib().fredec_version().decode()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise FredecError(rc, lib().fredec_last_error().decode())
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _p(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_c_dp)
+    if a.dtype == np.int64:
+        return a.ctypes.data_as(_c_i64p)
+    if a.dtype == np.int32:
+        return a.ctypes.data_as(_c_i32p)
+    raise TypeError(a.dtype)
+
+
+def _prec(precision) -> int:
+    if isinstance(precision, str):
+        return {"fp64": FP64, "mixed": MIXED}[precision.lower()]
+    return int(precision)
+
+
+def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0) -> Opts:
+    o = Opts()
+    lib().fredec_opts_init(ctypes.byref(o))
+    o.precision = _prec(precision)
+    o.topk = int(topk)
+    o.fpt = int(fpt)
+    o.warps = int(warps)
+    o.flag_tau = float(flag_tau)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Residual periodogram
+
+def periodogram(t, y, sigma, base_freqs, f_grid, *, precision=FP64, topk=0, want_coef=False, want_info=False,
+                fpt=0, warps=0, flag_tau=0.0):
+    """z(f) for every trial frequency (host arrays in, host arrays out).
+
+    Returns z, or a tuple (z, [topk_idx], [info], [coef]) when extras are
+    requested.  info = (chi2_base, sum of weights, time origin t_c); coef
+    (nf, 2) = fitted amplitudes of cos/sin of 2 pi f (t - t_c).
+    """
+    t, y, sigma, f = map(_f64, (t, y, sigma, f_grid))
+    base = _f64(base_freqs)
+    nf = f.size
+    z = np.empty(nf)
+    top = np.empty(max(int(topk), 1), dtype=np.int64) if topk else None
+    info = np.empty(3) if want_info else None
+    coef = np.empty((nf, 2)) if want_coef else None
+    o = _opts(precision, topk, fpt, warps, flag_tau)
+    _check(lib().fredec_periodogram_ex(_p(t), _p(y), _p(sigma), t.size, _p(base) if base.size else None, base.size,
+                                       _p(f), nf, ctypes.byref(o), _p(z), _p(info), _p(top), _p(coef)))
+    if not (topk or want_info or want_coef):
+        return z
+    out = [z]
+    if topk:
+        out.append(top[:topk])
+    if want_info:
+        out.append(info)
+    if want_coef:
+        out.append(coef)
+    return tuple(out)
+
+
+def _dptr(x) -> int:
+    return 0 if x is None else int(x.data_ptr())
+
+
+def _stream(torch, stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def periodogram_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, precision=FP64, topk=0,
+                    want_coef=False, fpt=0, warps=0, flag_tau=0.0, out=None, stream=None):
+    """Device path on the uniform grid f_j = f0 + j df (torch CUDA tensors,
+    float64, contiguous).  Enqueued on torch's current stream (or ``stream``).
+    Returns dict with z, info (3), and optionally topk (int64) and coef."""
+    import torch
+    dev = t.device
+    for x in (t, y, sigma, base_freqs):
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("periodogram_dev wants contiguous float64 CUDA tensors")
+    z = out if out is not None else torch.empty(nf, dtype=torch.float64, device=dev)
+    info = torch.empty(3, dtype=torch.float64, device=dev)
+    top = torch.empty(max(topk, 1), dtype=torch.int64, device=dev) if topk else None
+    coef = torch.empty((nf, 2), dtype=torch.float64, device=dev) if want_coef else None
+    o = _opts(precision, topk, fpt, warps, flag_tau)
+    _check(lib().fredec_periodogram_dev(_dptr(t), _dptr(y), _dptr(sigma), t.numel(),
+                                        _dptr(base_freqs) if base_freqs.numel() else None, base_freqs.numel(),
+                                        float(f0), float(df), int(nf), ctypes.byref(o), _dptr(z), _dptr(info),
+                                        _dptr(top), _dptr(coef), _stream(torch, stream)))
+    res = {"z": z, "info": info}
+    if topk:
+        res["topk"] = top[:topk]
+    if want_coef:
+        res["coef"] = coef
+    return res
+
+
+def periodogram_vjp_dev(t, y, sigma, base_freqs, f0, df, nf, coef, info, v, *, precision=FP64, out=None,
+                        stream=None):
+    """dL/dy = sum_j v_j dz_j/dy on the device (inputs from a forward call)."""
+    import torch
+    g = out if out is not None else torch.empty_like(y)
+    _check(lib().fredec_periodogram_vjp_dev(_dptr(t), _dptr(y), _dptr(sigma), t.numel(),
+                                            _dptr(base_freqs) if base_freqs.numel() else None, base_freqs.numel(),
+                                            float(f0), float(df), int(nf), _dptr(coef), _dptr(info), _dptr(v),
+                                            _prec(precision), _dptr(g), _stream(torch, stream)))
+    return g
+
+
+def periodogram_vjp(t, y, sigma, base_freqs, f0, df, nf, v, *, precision=FP64):
+    t, y, sigma, base, v = map(_f64, (t, y, sigma, base_freqs, v))
+    g = np.empty(t.size)
+    _check(lib().fredec_periodogram_vjp(_p(t), _p(y), _p(sigma), t.size, _p(base) if base.size else None, base.size,
+                                        float(f0), float(df), int(nf), _p(v), _prec(precision), _p(g)))
+    return g
+
+
+# ---------------------------------------------------------------------------
+# Tuples
+
+def _csr(tuples: Sequence[Sequence[float]]):
+    off = np.zeros(len(tuples) + 1, dtype=np.int64)
+    for k, tp in enumerate(tuples):
+        off[k + 1] = off[k] + len(tp)
+    flat = np.concatenate([np.asarray(tp, dtype=np.float64) for tp in tuples]) if off[-1] else np.zeros(1)
+    return np.ascontiguousarray(flat), off
+
+
+def tuple_eval(t, y, sigma, tuples):
+    """z_k = (l_0 - l(S_k))/2 for each tuple (constant base). Returns (z, l0)."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    flat, off = _csr(tuples)
+    z = np.empty(max(len(tuples), 1))
+    l0 = np.empty(1)
+    _check(lib().fredec_tuple_eval(_p(t), _p(y), _p(sigma), t.size, _p(flat), _p(off), len(tuples), _p(z), _p(l0)))
+    return z[:len(tuples)], float(l0[0])
+
+
+def pool_subtuples_eval(t, y, sigma, pool):
+    """l_table[mask] for all subsets of the pool (entry 0 = l_0)."""
+    t, y, sigma, pool = map(_f64, (t, y, sigma, pool))
+    out = np.empty(1 << pool.size)
+    _check(lib().fredec_pool_subtuples_eval(_p(t), _p(y), _p(sigma), t.size, _p(pool), pool.size, _p(out)))
+    return out
+
+
+def tuple_grad(t, y, sigma, tuples, *, precision=FP64):
+    """(z, dz/df flattened in tuple order)."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    flat, off = _csr(tuples)
+    z = np.empty(max(len(tuples), 1))
+    g = np.empty(max(int(off[-1]), 1))
+    _check(lib().fredec_tuple_grad(_p(t), _p(y), _p(sigma), t.size, _p(flat), _p(off), len(tuples),
+                                   _prec(precision), _p(z), _p(g)))
+    return z[:len(tuples)], g[:int(off[-1])]
+
+
+def tuple_refine(t, y, sigma, tuples, *, max_iter=20, tol=1e-9, precision=FP64):
+    """Gauss-Newton refinement of every tuple.  Returns (list of refined
+    frequency arrays, l, iterations)."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    flat, off = _csr(tuples)
+    flat = flat.copy()
+    n = len(tuples)
+    l = np.empty(max(n, 1))
+    it = np.empty(max(n, 1), dtype=np.int32)
+    _check(lib().fredec_tuple_refine(_p(t), _p(y), _p(sigma), t.size, _p(flat), _p(off), n, int(max_iter),
+                                     float(tol), _prec(precision), _p(l), _p(it)))
+    return [flat[off[k]:off[k + 1]].copy() for k in range(n)], l[:n], it[:n]
+
+
+# ---------------------------------------------------------------------------
+# Batches
+
+def _batch_arrays(series):
+    """CSR arrays from a list of objects with t, y, sigma, base_freqs, grid(f0, df, nf)."""
+    obs = np.zeros(len(series) + 1, dtype=np.int64)
+    bo = np.zeros(len(series) + 1, dtype=np.int64)
+    zo = np.zeros(len(series) + 1, dtype=np.int64)
+    for k, s in enumerate(series):
+        obs[k + 1] = obs[k] + s.t.size
+        bo[k + 1] = bo[k] + len(s.base_freqs)
+        zo[k + 1] = zo[k] + s.grid.nf
+    cat = lambda xs: np.ascontiguousarray(np.concatenate(xs)) if len(xs) else np.zeros(1)
+    t = cat([s.t for s in series])
+    y = cat([s.y for s in series])
+    sg = cat([s.sigma for s in series])
+    base = cat([np.asarray(s.base_freqs, dtype=np.float64) for s in series]) if bo[-1] else np.zeros(1)
+    f0 = _f64([s.grid.f0 for s in series])
+    df = _f64([s.grid.df for s in series])
+    nf = _i64([s.grid.nf for s in series])
+    return t, y, sg, obs, base, bo, f0, df, nf, zo
+
+
+def periodogram_batch(series, *, precision=FP64, topk=0, flag_tau=0.0):
+    """One call for many series (objects with t, y, sigma, base_freqs, grid).
+    Returns (z_concat, z_offsets, topk (n_series, k) or None)."""
+    t, y, sg, obs, base, bo, f0, df, nf, zo = _batch_arrays(series)
+    z = np.empty(max(int(zo[-1]), 1))
+    top = np.empty(max(len(series) * topk, 1), dtype=np.int64) if topk else None
+    o = _opts(precision, topk, 0, 0, flag_tau)
+    _check(lib().fredec_periodogram_batch(_p(t), _p(y), _p(sg), _p(obs), len(series), _p(base), _p(bo), _p(f0),
+                                          _p(df), _p(nf), _p(zo[:-1].copy()), ctypes.byref(o), _p(z), _p(top)))
+    return z[:int(zo[-1])], zo, (top.reshape(len(series), topk) if topk else None)
+
+
+class BatchPlan:
+    """Device-resident batch with a captured CUDA graph (see fredec.h)."""
+
+    def __init__(self, series, *, precision=FP64, topk=0, flag_tau=0.0):
+        t, y, sg, obs, base, bo, f0, df, nf, zo = _batch_arrays(series)
+        self.n_series = len(series)
+        self.topk = topk
+        self.z_offsets = zo
+        self._h = _vp()
+        o = _opts(precision, topk, 0, 0, flag_tau)
+        _check(lib().fredec_batch_plan_create(ctypes.byref(self._h), _p(t), _p(y), _p(sg), _p(obs), len(series),
+                                              _p(base), _p(bo), _p(f0), _p(df), _p(nf), _p(zo[:-1].copy()),
+                                              ctypes.byref(o)))
+        zp, tp = _vp(), _vp()
+        ztot, terms = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().fredec_batch_plan_outputs(self._h, ctypes.byref(zp), ctypes.byref(tp), ctypes.byref(ztot),
+                                               ctypes.byref(terms)))
+        self.z_total = ztot.value
+        self.terms = terms.value
+        self.z_ptr = zp.value
+        self.topk_ptr = tp.value
+
+    def run(self, stream=None):
+        import torch
+        _check(lib().fredec_batch_plan_run(self._h, _stream(torch, stream)))
+
+    def download(self):
+        z = np.empty(max(self.z_total, 1))
+        top = np.empty(max(self.n_series * self.topk, 1), dtype=np.int64)
+        _check(lib().fredec_batch_plan_download(self._h, _p(z), _p(top) if self.topk else None))
+        return z[:self.z_total], (top.reshape(self.n_series, self.topk) if self.topk else None)
+
+    def close(self):
+        if self._h:
+            lib().fredec_batch_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def profile_events(ev_start=None, ev_stop=None):
+    """Record torch.cuda.Event pairs around the main periodogram kernel of the
+    following calls on this thread (None, None switches it off)."""
+    h = lambda e: None if e is None else ctypes.c_void_p(int(e.cuda_event))
+    _check(lib().fredec_profile_events(h(ev_start), h(ev_stop)))
+
+
+def pipe_peaks():
+    """Measured FP32 FMA, FP64 FMA and MUFU sine lane-op rates (per second)."""
+    out = np.empty(3)
+    _check(lib().fredec_pipe_peaks(_p(out)))
+    return {"ffma_per_s": out[0], "dfma_per_s": out[1], "mufu_per_s": out[2]}
+
+
+def tune(precision, n_base, N, nf):
+    """Time the compiled launch shapes and remember the best; returns (fpt, warps)."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().fredec_tune(_prec(precision), int(n_base), int(N), int(nf), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

@@ -1,0 +1,381 @@
+// Public C ABI (include/fredec.h): validation, workspace and the single-series
+// periodogram pipeline  prep -> periodogram -> FP64 re-evaluation -> top-k.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fredec_internal.cuh"
+
+namespace fredec {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+// Keep freed blocks cached in the device's default stream-ordered pool so that
+// repeated calls do not return memory to the driver (once per device).
+static void keep_pool_cached() {
+    static thread_local int done_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+    done_dev = dev;
+}
+
+int DevBuf::alloc(size_t n, cudaStream_t s) {
+    stream = s;
+    bytes = n;
+    if (n == 0) return FREDEC_OK;
+    keep_pool_cached();
+    cudaError_t e = cudaMallocAsync(&ptr, n, s);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        (void)cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? FREDEC_ENOMEM : FREDEC_ECUDA,
+                    std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    }
+    return FREDEC_OK;
+}
+DevBuf::~DevBuf() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+size_t pgram_smem(int p, int prec, int F, int warps);
+
+// ---------------------------------------------------------------------------
+// Small device helpers for the pipeline
+
+namespace {
+
+__global__ void init_series_kernel(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int32_t *chunk_series,
+                                   int64_t nchunks, uint32_t *flag_words, int64_t nflag, int32_t *flag_count,
+                                   int32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *desc = v;
+        for (int k = 0; k < 6; ++k) state->counter[k] = 0;
+        state->status = FREDEC_OK;
+        if (flag_count) *flag_count = 0;
+        if (err) *err = FREDEC_OK;
+    }
+    for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
+    if (flag_words)
+        for (int64_t q = i; q < nflag; q += (int64_t)gridDim.x * blockDim.x) flag_words[q] = 0u;
+}
+
+__global__ void info_kernel(const SeriesState *state, double *info) {
+    info[0] = state->chi2;
+    info[1] = state->W;
+    info[2] = state->tc;
+}
+
+__global__ void nan_fill_if_failed(const SeriesState *state, double *z, int64_t nf) {
+    if (state->status == FREDEC_OK) return;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x)
+        z[j] = NAN;
+}
+
+bool finite_all(const double *a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// Workspace of one single-series periodogram call.
+struct SingleWork {
+    SeriesDesc *desc;
+    SeriesState *state;
+    int32_t *chunk_series;
+    double *partials;
+    double *psi;
+    void *rec;       // records of the main precision
+    void *rec64;     // FP64 records for re-evaluation (mixed) or == rec (FP64)
+    uint32_t *flag_words;
+    int32_t *flag_list;
+    int32_t *flag_count;
+    int32_t *err;
+    int64_t nchunks, nflag;
+};
+
+int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
+                     int precision, void *rec64, cudaStream_t st);
+
+// The device pipeline for one series on a uniform grid.  All pointers device.
+static int periodogram_core(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
+                            int nb, double f0, double df, int64_t nf, const fredec_opts &o, double *z,
+                            double *info, int64_t *topk, double *coef, cudaStream_t st, DevBuf &ws,
+                            SingleWork &w) {
+    const int p = 2 * nb + 1;
+    const int prec = o.precision;
+    const double tau = o.flag_tau == 0.0 ? 0.05 : o.flag_tau;
+    const bool fix = prec == FREDEC_MIXED && tau >= 0.0;
+    const int64_t nchunks = (N + PREP_THREADS - 1) / PREP_THREADS;
+    const int fpt64 = fixup_fpt(p);
+    const int64_t nflag = fix ? (nf + 32LL * fpt64 - 1) / (32LL * fpt64) : 0;
+    const size_t rb = (size_t)rec_bytes(p, prec);
+    const size_t rb64 = (size_t)rec_bytes(p, FREDEC_FP64);
+    // carve one allocation
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
+    const size_t o_desc = take(sizeof(SeriesDesc)), o_state = take(sizeof(SeriesState));
+    const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
+    const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * rb);
+    const size_t o_rec64 = fix ? take(N * rb64) : 0;
+    const size_t o_fw = take(nflag * 4 + 4), o_fl = take(nflag * 4 + 4), o_fc = take(4), o_err = take(4);
+    if (int rc = ws.alloc(off, st)) return rc;
+    unsigned char *b = ws.as<unsigned char>();
+    w.desc = (SeriesDesc *)(b + o_desc);
+    w.state = (SeriesState *)(b + o_state);
+    w.chunk_series = (int32_t *)(b + o_cs);
+    w.partials = (double *)(b + o_part);
+    w.psi = (double *)(b + o_psi);
+    w.rec = b + o_rec;
+    w.rec64 = fix ? (void *)(b + o_rec64) : (prec == FREDEC_FP64 ? w.rec : nullptr);
+    w.flag_words = fix ? (uint32_t *)(b + o_fw) : nullptr;
+    w.flag_list = fix ? (int32_t *)(b + o_fl) : nullptr;
+    w.flag_count = (int32_t *)(b + o_fc);
+    w.err = (int32_t *)(b + o_err);
+    w.nchunks = nchunks;
+    w.nflag = nflag;
+
+    SeriesDesc d{};
+    d.f0 = f0;
+    d.df = df;
+    d.nf = nf;
+    d.N = (int32_t)N;
+    d.nb = nb;
+    d.p = p;
+    d.nchunks = (int32_t)nchunks;
+    init_series_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (std::max(nchunks, nflag) + 255) / 256)), 256, 0,
+                         st>>>(w.desc, d, w.state, w.chunk_series, nchunks, w.flag_words, nflag, w.flag_count, w.err);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+
+    PrepPlan pp;
+    pp.S = 1;
+    pp.nchunks = nchunks;
+    pp.pmax = p;
+    pp.desc = w.desc;
+    pp.state = w.state;
+    pp.chunk_series = w.chunk_series;
+    pp.partials = w.partials;
+    pp.psi = w.psi;
+    pp.rec = w.rec;
+    if (int rc = run_prep_records(pp, t, y, sigma, base, prec, fix ? w.rec64 : nullptr, st)) return rc;
+
+    PgramShape shape;
+    if (o.fpt > 0 || o.warps > 0) {
+        shape = default_shape(prec, p, N, nf);
+        if (o.fpt > 0) shape.fpt = o.fpt;
+        if (o.warps > 0) shape.warps = o.warps;
+    } else if (!tuned_shape(prec, p, N, nf, &shape)) {
+        shape = default_shape(prec, p, N, nf);
+    }
+    if (nf > 0) {
+        if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_words,
+                                  w.flag_list, w.flag_count, w.err, st))
+            return rc;
+        if (fix) {
+            if (int rc = launch_fixup(w.desc, w.state, w.rec64, p, (int)N, nf, fpt64, w.flag_list, w.flag_count,
+                                      nflag, z, coef, w.err, st))
+                return rc;
+        }
+        nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
+        if (topk && o.topk > 0)
+            if (int rc = launch_topk_single(z, nf, o.topk, topk, st)) return rc;
+    }
+    if (info) info_kernel<<<1, 1, 0, st>>>(w.state, info);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
+// Host-side checks shared by the entry points.
+static int check_opts(const fredec_opts *o, fredec_opts *out) {
+    fredec_opts_init(out);
+    if (o) *out = *o;
+    if (out->precision != FREDEC_FP64 && out->precision != FREDEC_MIXED)
+        return fail(FREDEC_EINVAL, "opts.precision must be FREDEC_FP64 or FREDEC_MIXED");
+    if (out->topk < 0 || out->topk > FREDEC_MAX_TOPK) return fail(FREDEC_EINVAL, "opts.topk must be in 0..64");
+    if (out->fpt < 0 || out->warps < 0 || out->warps > 8) return fail(FREDEC_EINVAL, "bad opts.fpt / opts.warps");
+    if (!std::isfinite(out->flag_tau)) return fail(FREDEC_EINVAL, "opts.flag_tau must be finite");
+    return FREDEC_OK;
+}
+
+static int check_sizes(int64_t N, int32_t n_base, int64_t nf) {
+    if (n_base < 0 || n_base > FREDEC_MAX_NBASE) return fail(FREDEC_EINVAL, "n_base must be in 0..FREDEC_MAX_NBASE");
+    if (N < 2LL * n_base + 3) return fail(FREDEC_EINVAL, "N must be at least 2*n_base + 3");
+    if (N > (1LL << 31) - 1) return fail(FREDEC_EINVAL, "N too large");
+    if (nf < 0 || nf > (1LL << 31) - 1) return fail(FREDEC_EINVAL, "nf must be in 0..2^31-1");
+    return FREDEC_OK;
+}
+
+static int check_series_host(const double *t, const double *y, const double *sigma, int64_t N,
+                             const double *base, int32_t nb) {
+    if (!t || !y || !sigma || (nb > 0 && !base)) return fail(FREDEC_EINVAL, "null input pointer");
+    if (!finite_all(t, N) || !finite_all(y, N)) return fail(FREDEC_EINVAL, "t and y must be finite");
+    for (int64_t i = 0; i < N; ++i)
+        if (!(sigma[i] > 0.0) || !std::isfinite(sigma[i])) return fail(FREDEC_EINVAL, "sigma must be finite and > 0");
+    if (nb > 0 && !finite_all(base, nb)) return fail(FREDEC_EINVAL, "base frequencies must be finite");
+    return FREDEC_OK;
+}
+
+// Uniform-grid detection: f_j = f0 + j*df within 8 ulps of max |f|.
+static bool grid_uniform(const double *f, int64_t nf, double *f0, double *df) {
+    if (nf <= 0) { *f0 = 0.0; *df = 0.0; return true; }
+    *f0 = f[0];
+    *df = nf > 1 ? (f[nf - 1] - f[0]) / (double)(nf - 1) : 0.0;
+    double fmax = 0.0;
+    for (int64_t j = 0; j < nf; ++j) fmax = std::max(fmax, std::fabs(f[j]));
+    const double tol = 8.0 * std::ldexp(1.0, std::ilogb(fmax > 0 ? fmax : 1.0) - 52);
+    for (int64_t j = 0; j < nf; ++j)
+        if (std::fabs(f[j] - (*f0 + (double)j * *df)) > tol) return false;
+    return true;
+}
+
+struct HostStream {
+    cudaStream_t s = nullptr;
+    int make() {
+        FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        return FREDEC_OK;
+    }
+    ~HostStream() {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+// Read back status words after a synchronous host call.
+static int finish_host(cudaStream_t st, const SeriesState *state, const int32_t *err) {
+    FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t status = FREDEC_OK, e = FREDEC_OK;
+    if (state) FREDEC_CUDA_TRY(cudaMemcpy(&status, &state->status, 4, cudaMemcpyDeviceToHost));
+    if (err) FREDEC_CUDA_TRY(cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost));
+    if (status == FREDEC_ESINGULAR)
+        return fail(FREDEC_ESINGULAR, "the base model's normal matrix is singular (duplicate base frequencies?)");
+    if (e == FREDEC_ETIMEOUT) return fail(FREDEC_ETIMEOUT, "a bounded device wait gave up");
+    return FREDEC_OK;
+}
+
+int generic_grid_periodogram(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
+                             int nb, const double *f_grid_dev, int64_t nf, int precision, double *z, double *coef,
+                             double *info, cudaStream_t st, SeriesState **state_out, DevBuf &ws);
+
+}  // namespace fredec
+
+using namespace fredec;
+
+extern "C" {
+
+void fredec_opts_init(fredec_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FREDEC_FP64;
+}
+
+const char *fredec_last_error(void) { return g_last_error.c_str(); }
+const char *fredec_version(void) { return "fredec-b300 0.1 (sm_103a)"; }
+
+int fredec_periodogram_dev(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
+                           int32_t n_base, double f0, double df, int64_t nf, const fredec_opts *opts, double *z_out,
+                           double *info_out, int64_t *topk_idx_out, double *coef_out, void *stream) {
+    fredec_opts o;
+    if (int rc = check_opts(opts, &o)) return rc;
+    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || (nf > 0 && !z_out))
+        return fail(FREDEC_EINVAL, "null pointer argument");
+    if (!std::isfinite(f0) || !std::isfinite(df)) return fail(FREDEC_EINVAL, "f0 and df must be finite");
+    DevBuf ws;
+    SingleWork w;
+    return periodogram_core(t, y, sigma, N, base_freqs, n_base, f0, df, nf, o, z_out, info_out, topk_idx_out,
+                            coef_out, (cudaStream_t)stream, ws, w);
+}
+
+int fredec_periodogram_ex(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
+                          int32_t n_base, const double *f_grid, int64_t nf, const fredec_opts *opts, double *z_out,
+                          double *info_out, int64_t *topk_idx_out, double *coef_out) {
+    fredec_opts o;
+    if (int rc = check_opts(opts, &o)) return rc;
+    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (int rc = check_series_host(t, y, sigma, N, base_freqs, n_base)) return rc;
+    if (nf > 0 && (!f_grid || !z_out)) return fail(FREDEC_EINVAL, "null f_grid or z_out");
+    if (nf > 0 && !finite_all(f_grid, nf)) return fail(FREDEC_EINVAL, "trial frequencies must be finite");
+    double f0, df;
+    const bool uniform = grid_uniform(f_grid, nf, &f0, &df);
+    HostStream hs;
+    if (int rc = hs.make()) return rc;
+    cudaStream_t st = hs.s;
+    const int nb = n_base;
+    const int k = o.topk;
+    int rc = FREDEC_OK;
+    {
+        DevBuf io;
+        const size_t nin = 3 * N + nb + (uniform ? 0 : nf);
+        const size_t bytes = nin * 8 + (size_t)nf * 8 + 3 * 8 + (size_t)k * 8 + (coef_out ? 16 * nf : 0) + 64;
+        if ((rc = io.alloc(bytes, st))) return rc;
+        double *d = io.as<double>();
+        double *dt = d, *dy = d + N, *ds = d + 2 * N, *db = d + 3 * N, *dfg = db + nb;
+        double *dz = dfg + (uniform ? 0 : nf), *dinfo = dz + nf, *dcoef = dinfo + 3;
+        int64_t *dtop = (int64_t *)(dcoef + (coef_out ? 2 * nf : 0));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(dt, t, N * 8, cudaMemcpyHostToDevice, st));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(dy, y, N * 8, cudaMemcpyHostToDevice, st));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(ds, sigma, N * 8, cudaMemcpyHostToDevice, st));
+        if (nb) FREDEC_CUDA_TRY(cudaMemcpyAsync(db, base_freqs, nb * 8, cudaMemcpyHostToDevice, st));
+        DevBuf ws;
+        const SeriesState *state = nullptr;
+        const int32_t *err = nullptr;
+        if (uniform) {
+            SingleWork w;
+            rc = periodogram_core(dt, dy, ds, N, db, nb, f0, df, nf, o, dz, dinfo, k ? dtop : nullptr,
+                                  coef_out ? dcoef : nullptr, st, ws, w);
+            state = w.state;
+            err = w.err;
+        } else {
+            FREDEC_CUDA_TRY(cudaMemcpyAsync(dfg, f_grid, nf * 8, cudaMemcpyHostToDevice, st));
+            SeriesState *sp = nullptr;
+            rc = generic_grid_periodogram(dt, dy, ds, N, db, nb, dfg, nf, o.precision, dz, coef_out ? dcoef : nullptr,
+                                          dinfo, st, &sp, ws);
+            state = sp;
+            if (!rc && k) rc = launch_topk_single(dz, nf, k, dtop, st);
+        }
+        if (rc) {
+            cudaStreamSynchronize(st);
+            return rc;
+        }
+        if ((rc = finish_host(st, state, err))) return rc;
+        if (nf) FREDEC_CUDA_TRY(cudaMemcpy(z_out, dz, nf * 8, cudaMemcpyDeviceToHost));
+        if (info_out) FREDEC_CUDA_TRY(cudaMemcpy(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost));
+        if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpy(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost));
+        if (coef_out && nf) FREDEC_CUDA_TRY(cudaMemcpy(coef_out, dcoef, 16 * nf, cudaMemcpyDeviceToHost));
+    }
+    FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+    return FREDEC_OK;
+}
+
+int fredec_periodogram(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
+                       int32_t n_base, const double *f_grid, int64_t nf, double *z_out) {
+    return fredec_periodogram_ex(t, y, sigma, N, base_freqs, n_base, f_grid, nf, nullptr, z_out, nullptr, nullptr,
+                                 nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of libfredec.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/fredec.h"
+
+namespace fredec {
+
+// ---------------------------------------------------------------------------
+// Limits and layout constants
+
+constexpr int PMAX = 2 * FREDEC_MAX_NBASE + 1;      // base columns (constant + cos/sin pairs)
+constexpr int NTRI = PMAX * (PMAX + 1) / 2;         // packed lower triangle
+constexpr int PREP_THREADS = 128;                    // one point per thread per prep chunk
+constexpr int TILE_POINTS = 128;                     // observation records per smem tile
+constexpr double DROP2 = 1e-14;                      // squared column-drop ratio (1e-7)^2
+
+// Record widths.  Mixed records (32-bit words):
+//   [0..1] phase A = frac(f0 t') as u64 turns, [2..3] phase B = frac(df t'),
+//   [4] cos(2 pi df t'), [5] sin(2 pi df t'), [6] w, [7] w r, [8..8+p) w psi_k.
+// FP64 records (64-bit words): [0] A, [1] B, [2] cos, [3] sin, [4] w, [5] w r,
+//   [6..6+p) w psi_k.  Both are padded to a multiple of 16 bytes.
+__host__ __device__ constexpr int rec32_words(int p) { return 8 + 4 * ((p + 3) / 4); }
+__host__ __device__ constexpr int rec64_words(int p) { return 6 + 2 * ((p + 1) / 2); }
+__host__ __device__ constexpr int rec_bytes(int p, int prec) {
+    return prec == FREDEC_MIXED ? 4 * rec32_words(p) : 8 * rec64_words(p);
+}
+
+// Per-series description (host-built, device-resident).
+struct SeriesDesc {
+    int64_t obs_off;     // into t, y, sigma
+    int64_t base_off;    // into base frequencies
+    int64_t rec_off;     // into the record buffer, bytes
+    int64_t rec64_off;   // into the extra FP64 record buffer (mixed with re-evaluation), bytes
+    int64_t psi_off;     // into the psi scratch, doubles (p*N per series)
+    int64_t z_off;       // into z (and 2*z_off into coef)
+    int64_t chunk_off;   // first prep chunk of this series
+    int64_t flag_off;    // first FP64 re-evaluation flag word of this series
+    double f0, df;       // uniform grid f_j = f0 + j df
+    int64_t nf;
+    int32_t N, nb, nchunks, p;
+};
+
+// Per-series results of the prep kernels.
+struct SeriesState {
+    double W;            // sum of weights (FP64)
+    double Wf;           // sum of FP32-rounded weights (what the mixed kernel integrates)
+    double tc;           // time origin
+    double chi2;         // l(f') of the base model
+    double Swt;          // sum w t (scratch)
+    double L1[NTRI];     // Cholesky factor of the raw base Gram
+    double L2[NTRI];     // Cholesky factor of the second (re-orthogonalisation) Gram
+    double a[PMAX];      // coefficients of y on the orthonormal base columns
+    double a2[PMAX];     // second-pass correction
+    int32_t status;      // FREDEC_OK or FREDEC_ESINGULAR
+    uint32_t counter[6]; // last-block-done counters (reset by the finishing block)
+};
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+#define FREDEC_CUDA_TRY(expr)                                                        \
+    do {                                                                             \
+        cudaError_t e_ = (expr);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return ::fredec::fail(FREDEC_ECUDA, std::string(#expr) + ": " +         \
+                                                     cudaGetErrorString(e_));        \
+    } while (0)
+
+// Workspace from the stream-ordered allocator; freed on destruction.
+struct DevBuf {
+    void *ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t bytes = 0;
+    int alloc(size_t n, cudaStream_t s);
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+    ~DevBuf();
+};
+
+// ---------------------------------------------------------------------------
+// Prep (prep.cu)
+
+struct PrepPlan {
+    int S = 0;                 // series
+    int64_t nchunks = 0;       // total prep chunks
+    int pmax = 1;
+    SeriesDesc *desc = nullptr;      // device [S]
+    SeriesState *state = nullptr;    // device [S]
+    int32_t *chunk_series = nullptr; // device [nchunks]
+    double *partials = nullptr;      // device [nchunks * NPART(pmax)]
+    double *psi = nullptr;           // device scratch
+    void *rec = nullptr;             // device records
+};
+int prep_npart(int pmax);
+// Enqueue the prep kernels (uniform grids).  Writes state[] and records.
+int launch_prep(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
+                const double *base, int precision, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Periodogram kernels (pgram.cu)
+
+struct PgramShape { int fpt; int warps; };
+PgramShape default_shape(int precision, int p, int64_t N, int64_t nf);
+bool shape_supported(int precision, int p, int fpt);
+// Single-series launch: z (and optional coef) for all nf grid points.
+int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev,
+                 const void *rec, int p, int N, int64_t nf, PgramShape shape, double flag_tau,
+                 double *z, double *coef, uint32_t *flag_bytes, int32_t *flag_list,
+                 int32_t *flag_count, int32_t *err, cudaStream_t st);
+// FP64 re-evaluation of the listed FP64 blocks.
+int launch_fixup(const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec64, int p,
+                 int N, int64_t nf, int fpt64, const int32_t *flag_list, const int32_t *flag_count,
+                 int64_t max_items, double *z, double *coef, int32_t *err, cudaStream_t st);
+int fixup_fpt(int p);
+
+// Top-k local maxima (topk.cu); segmented over series.
+int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S, int k,
+                int64_t *idx_out, cudaStream_t st);
+int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st);
+
+// VJP (vjp.cu)
+int launch_vjp(const SeriesDesc *desc_dev, const SeriesState *state_dev, const double *t,
+               const double *sigma, const double *psi, int p, int N, double f0, double df, int64_t nf,
+               const double *coef, const double *v, int precision, double *dldy, cudaStream_t st);
+
+// Tuples (tuple.cu)
+int tuple_eval_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                   const double *freqs, const int64_t *off, int64_t n_tuples, int max_m,
+                   double *z, double *l0, cudaStream_t st);
+int pool_table_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                   const double *pool, int n_pool, double *l_table, cudaStream_t st);
+int tuple_grad_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                   const double *freqs, const int64_t *off, int64_t n_tuples, int max_m,
+                   int precision, double *z, double *dzdf, cudaStream_t st);
+int tuple_refine_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                     double *freqs, const int64_t *off, int64_t n_tuples, int max_m,
+                     int max_iter, double tol, int precision, double *l_out, int32_t *iters,
+                     cudaStream_t st);
+
+// Tuning table (tune.cu)
+bool tuned_shape(int precision, int p, int64_t N, int64_t nf, PgramShape *out);
+
+int sm_count();
+// Events recorded around the main periodogram kernel (fredec_profile_events).
+void set_profile_events(cudaEvent_t a, cudaEvent_t b);
+void profile_events(cudaEvent_t *a, cudaEvent_t *b);
+
+}  // namespace fredec

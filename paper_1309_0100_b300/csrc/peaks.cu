@@ -1,0 +1,99 @@
+// Pipe-throughput microbenchmarks: FP32 FMA, FP64 FMA and MUFU sin/cos
+// instruction rates of the whole GPU, for the roofline denominators of the
+// ALU-bound kernels.  Each thread runs 8 independent dependency chains so the
+// pipes, not latency, limit the rate.
+#include <algorithm>
+
+#include "fredec_internal.cuh"
+
+namespace {
+
+constexpr int ITERS = 4096;
+
+__global__ void __launch_bounds__(256) ffma_loop(float *out, float a, float b) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3f + k;
+    for (int i = 0; i < ITERS; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 12345.678f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) dfma_loop(double *out, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < ITERS / 16; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 12345.678) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) mufu_loop(float *out) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3f + k * 0.1f;
+    for (int i = 0; i < ITERS / 8; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __sinf(x[k]);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 12345.678f) out[0] = s;
+}
+
+}  // namespace
+
+using namespace fredec;
+
+// out[0] = FP32 FMA/s, out[1] = FP64 FMA/s, out[2] = MUFU sin/s (lane operations).
+extern "C" int fredec_pipe_peaks(double *out) {
+    if (!out) return fail(FREDEC_EINVAL, "null out");
+    const int blocks = sm_count() * 8;
+    const double threads = (double)blocks * 256;
+    float *dummy;
+    FREDEC_CUDA_TRY(cudaMalloc(&dummy, 64));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms;
+    double best[3] = {0, 0, 0};
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0);
+        ffma_loop<<<blocks, 256>>>(dummy, 0.999f, 1e-3f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        best[0] = std::max(best[0], threads * 8.0 * ITERS / (ms * 1e-3));
+        cudaEventRecord(e0);
+        dfma_loop<<<blocks, 256>>>((double *)dummy, 0.999, 1e-3);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        best[1] = std::max(best[1], threads * 8.0 * (ITERS / 16) / (ms * 1e-3));
+        cudaEventRecord(e0);
+        mufu_loop<<<blocks, 256>>>(dummy);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        best[2] = std::max(best[2], threads * 8.0 * (ITERS / 8) / (ms * 1e-3));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dummy);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k < 3; ++k) out[k] = best[k];
+    return FREDEC_OK;
+}
+
+extern "C" int fredec_profile_events(void *ev_start, void *ev_stop) {
+    set_profile_events((cudaEvent_t)ev_start, (cudaEvent_t)ev_stop);
+    return FREDEC_OK;
+}

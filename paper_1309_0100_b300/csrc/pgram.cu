@@ -1,0 +1,140 @@
+// Dispatch of the periodogram kernels over (precision, base size P,
+// frequencies per thread F).  The kernels themselves are in pgram_impl.cuh and
+// are instantiated per P in pgram_p*.cu.
+#include <algorithm>
+
+#include "fpt_options.h"
+#include "pgram_impl.cuh"
+
+namespace fredec {
+
+static thread_local cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
+void set_profile_events(cudaEvent_t a, cudaEvent_t b) { g_ev0 = a; g_ev1 = b; }
+void profile_events(cudaEvent_t *a, cudaEvent_t *b) { *a = g_ev0; *b = g_ev1; }
+
+#define FREDEC_DECL_P(P)                                                                              \
+    int launch_pgram_p##P(int, int, const PgramParams &, int64_t, int, int, int, cudaStream_t);     \
+    size_t smem_pgram_p##P(int, int, int);
+FREDEC_DECL_P(1) FREDEC_DECL_P(3) FREDEC_DECL_P(5) FREDEC_DECL_P(7) FREDEC_DECL_P(9) FREDEC_DECL_P(11)
+FREDEC_DECL_P(13) FREDEC_DECL_P(15) FREDEC_DECL_P(17) FREDEC_DECL_P(19) FREDEC_DECL_P(21)
+FREDEC_DECL_P(23) FREDEC_DECL_P(25)
+#undef FREDEC_DECL_P
+
+static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, int list_mode,
+                    int grid_override, cudaStream_t st) {
+    switch (p) {
+#define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, list_mode, grid_override, st);
+        C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
+#undef C
+    }
+    return -1;
+}
+
+size_t pgram_smem(int p, int prec, int F, int warps) {
+    switch (p) {
+#define C(P) case P: return smem_pgram_p##P(prec, F, warps);
+        C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
+#undef C
+    }
+    return 0;
+}
+
+static const FptOptions *options_for(int p) {
+    for (const auto &o : kFptOptions)
+        if (o.p == p) return &o;
+    return nullptr;
+}
+
+bool shape_supported(int precision, int p, int fpt) {
+    const FptOptions *o = options_for(p);
+    if (!o) return false;
+    const int *v = precision == FREDEC_MIXED ? o->mixed : o->fp64;
+    const int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
+    for (int i = 0; i < n; ++i)
+        if (v[i] == fpt) return true;
+    return false;
+}
+
+int compiled_fpts(int precision, int p, int *out) {
+    const FptOptions *o = options_for(p);
+    if (!o) return 0;
+    const int *v = precision == FREDEC_MIXED ? o->mixed : o->fp64;
+    const int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
+    for (int i = 0; i < n; ++i) out[i] = v[i];
+    return n;
+}
+
+// Built-in default: the largest compiled F (fewest re-seeds) and 4 warps,
+// reduced when the grid would not fill the GPU once.
+PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
+    PgramShape s{1, 4};
+    const FptOptions *o = options_for(p);
+    if (!o) return s;
+    const int *v = precision == FREDEC_MIXED ? o->mixed : o->fp64;
+    const int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
+    s.fpt = v[n - 1];
+    const int64_t want = 2LL * sm_count();
+    for (int i = n - 1; i > 0; --i) {
+        if ((nf + 32LL * v[i] - 1) / (32LL * v[i]) >= want) break;
+        s.fpt = v[i - 1];
+    }
+    if (N < 256) s.warps = 2;
+    return s;
+}
+
+int fixup_fpt(int p) {
+    const FptOptions *o = options_for(p);
+    return o ? o->fp64[0] : 1;
+}
+
+int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,
+                 int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef,
+                 uint32_t *flag_words, int32_t *flag_list, int32_t *flag_count, int32_t *err, cudaStream_t st) {
+    (void)N;
+    if (!shape_supported(precision, p, shape.fpt))
+        return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, frequencies per thread)");
+    if (shape.warps < 1 || shape.warps > 8) return fail(FREDEC_EINVAL, "warps per CTA must be in 1..8");
+    PgramParams prm{};
+    prm.desc = desc_dev;
+    prm.state = state_dev;
+    prm.rec = (const unsigned char *)rec;
+    prm.z = z;
+    prm.coef = coef;
+    prm.flag_tau = (precision == FREDEC_MIXED && flag_words) ? flag_tau : -1.0;
+    prm.flag_words = flag_words;
+    prm.flag_list = flag_list;
+    prm.flag_count = flag_count;
+    prm.fpt64 = fixup_fpt(p);
+    prm.err = err;
+    const int64_t nblocks = (nf + 32LL * shape.fpt - 1) / (32LL * shape.fpt);
+    cudaEvent_t e0, e1;
+    profile_events(&e0, &e1);
+    if (e0) cudaEventRecord(e0, st);
+    const int rc = dispatch(p, precision, shape.fpt, prm, nblocks, shape.warps, 0, 0, st);
+    if (e1) cudaEventRecord(e1, st);
+    return rc < 0 ? fail(FREDEC_EINVAL, "kernel dispatch failed") : rc;
+}
+
+int launch_fixup(const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec64, int p, int N,
+                 int64_t nf, int fpt64, const int32_t *flag_list, const int32_t *flag_count, int64_t max_items,
+                 double *z, double *coef, int32_t *err, cudaStream_t st) {
+    (void)N;
+    (void)nf;
+    PgramParams prm{};
+    prm.desc = desc_dev;
+    prm.state = state_dev;
+    prm.rec = (const unsigned char *)rec64;
+    prm.z = z;
+    prm.coef = coef;
+    prm.flag_tau = -1.0;
+    prm.fpt64 = fpt64;
+    prm.err = err;
+    prm.items = flag_list;
+    prm.item_count = flag_count;
+    prm.use_rec64_off = 1;
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 2LL * sm_count());
+    const int rc = dispatch(p, FREDEC_FP64, fpt64, prm, 0, 4, 1, grid, st);
+    return rc < 0 ? fail(FREDEC_EINVAL, "fixup dispatch failed") : rc;
+}
+
+}  // namespace fredec

@@ -1,0 +1,359 @@
+// Residual-periodogram kernels (the hot loop).  Included by the per-P
+// instantiation units and by the batched persistent kernels.
+//
+// Paper: Section 5 (GPU parallelization) spends >90% of the time in the
+// trigonometric averages of Eq. avrg1; the observation series is preloaded in
+// fast shared memory and every thread evaluates the same averages for its own
+// frequency.  Per trial frequency f (omega = 2 pi f, c = cos omega t',
+// s = sin omega t', t' = t - t_c) the kernel accumulates the 2P+4 weighted sums
+//     V_c[k] = <psi_k c>, V_s[k] = <psi_k s>   (k < P, psi = orthonormal base)
+//     R_c = <r c>, R_s = <r s>                  (r = base residual)
+//     CC = <c^2>, CS = <c s>                    (<s^2> = <1> - CC, Eq. idn)
+// and solves the 2x2 Schur complement of the extended normal matrix (the
+// incremental Cholesky extension of Section 3):
+//     S = [[CC, CS], [CS, W - CC]] - V^T V,  z = 1/2 rho^T S^{-1} rho,
+//     rho = (R_c, R_s).
+//
+// Decomposition: a CTA owns 32*F consecutive grid frequencies (lane l owns
+// F consecutive ones) and its warps split the observations; records are
+// staged tile by tile in shared memory with TMA bulk copies (double buffer,
+// mbarrier completion, bounded waits).  Along the grid, cos/sin are advanced
+// by the rotation e^{i 2 pi df t'} (a complex multiply), re-seeded for every
+// point at each thread's first frequency from the exact fixed-point phase.
+#pragma once
+
+#include "device_util.cuh"
+#include "fredec_internal.cuh"
+
+namespace fredec {
+
+constexpr int FLUSH_POINTS = 256;   // mixed: FP32 partials are flushed to shared sums every 256 points
+
+struct PgramParams {
+    const SeriesDesc *desc;
+    const SeriesState *state;
+    const unsigned char *rec;   // record buffer base (series offsets in desc)
+    double *z;                  // output base (series offsets in desc)
+    double *coef;               // optional (a_j, b_j) output, same offsets * 2
+    double flag_tau;            // mixed: FP64 re-evaluation threshold (< 0: never)
+    uint32_t *flag_words;       // mixed: one word per FP64 block, set when requested
+    int32_t *flag_list;         // mixed: compacted FP64 block requests (series-local block ids)
+    int32_t *flag_count;
+    int fpt64;                  // frequencies per thread of the FP64 re-evaluation kernel
+    int32_t *err;               // FREDEC_ETIMEOUT on a bounded-wait timeout
+    const int32_t *items;       // list mode: block ids to process
+    const int32_t *item_count;  // list mode: number of ids
+    int use_rec64_off;          // records are the extra FP64 records (read at desc.rec64_off)
+};
+
+template <int PREC> struct AccT;
+template <> struct AccT<FREDEC_MIXED> { using T = float; };
+template <> struct AccT<FREDEC_FP64> { using T = double; };
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <int PREC, int P, int F>
+struct PgramLayout {
+    static constexpr int Q = 2 * P + 4;
+    static constexpr int RB = rec_bytes(P, PREC);
+    static constexpr size_t TILE_BYTES = (size_t)TILE_POINTS * RB;
+    static constexpr size_t OFF_TILES = 128;
+    static constexpr size_t OFF_RED = OFF_TILES + 2 * TILE_BYTES;
+    static __host__ __device__ size_t red_bytes(int nw) {
+        return (size_t)nw * Q * F * 32 * sizeof(typename AccT<PREC>::T);
+    }
+    static __host__ __device__ size_t off_table(int nw) { return align_up(OFF_RED + red_bytes(nw), 16); }
+    static __host__ __device__ size_t smem_bytes(int nw) {
+        return off_table(nw) + (PREC == FREDEC_FP64 ? sizeof(SeedTable) : 0);
+    }
+};
+
+// Per-frequency 2x2 solve in FP64.  Returns z; writes the joint-fit
+// coefficients of cos/sin (a, b) and the smaller pivot ratio (1 = orthogonal
+// to the base, 0 = dependent).
+__device__ __forceinline__ double solve2(double CC, double CS, double SS, double vcc, double vcs,
+                                         double vss, double Rc, double Rs, double *pa, double *pb,
+                                         double *pr) {
+    const double S11 = CC - vcc, S12 = CS - vcs, S22 = SS - vss;
+    const bool kc = S11 > DROP2 * CC && CC > 0.0;
+    double a = 0.0, b = 0.0, z = 0.0, r1 = kc ? S11 / CC : 0.0, r2;
+    if (kc) {
+        const double l21 = S12 / S11;
+        const double S22p = S22 - S12 * l21;
+        r2 = SS > 0.0 ? S22p / SS : 0.0;
+        if (S22p > DROP2 * SS && SS > 0.0) {
+            const double y1 = Rc * rsqrt(S11);
+            const double y2 = (Rs - l21 * Rc) * rsqrt(S22p);
+            z = 0.5 * (y1 * y1 + y2 * y2);
+            b = (Rs - l21 * Rc) / S22p;
+            a = (Rc - S12 * b) / S11;
+        } else {
+            z = 0.5 * Rc * Rc / S11;
+            a = Rc / S11;
+        }
+    } else {
+        r2 = SS > 0.0 ? S22 / SS : 0.0;
+        if (S22 > DROP2 * SS && SS > 0.0) {
+            z = 0.5 * Rs * Rs / S22;
+            b = Rs / S22;
+        }
+    }
+    *pa = a;
+    *pb = b;
+    *pr = fmin(fmin(r1, r2), fmin(CC, SS) / (CC + SS));
+    return z;
+}
+
+// ---------------------------------------------------------------------------
+// Inner loops: one observation record against this thread's F frequencies.
+
+template <int P, int F>
+__device__ __forceinline__ void mixed_point(const uint4 *__restrict__ r4, uint32_t j0,
+                                            float (&acc)[F][2 * P + 4]) {
+    const uint4 h = r4[0];
+    const float4 m = *reinterpret_cast<const float4 *>(r4 + 1);
+    float u[4 * ((P + 3) / 4)];
+#pragma unroll
+    for (int q4 = 0; q4 < (P + 3) / 4; ++q4) {
+        const float4 v = reinterpret_cast<const float4 *>(r4 + 2)[q4];
+        u[4 * q4] = v.x;
+        u[4 * q4 + 1] = v.y;
+        u[4 * q4 + 2] = v.z;
+        u[4 * q4 + 3] = v.w;
+    }
+    const uint64_t A = ((uint64_t)h.y << 32) | h.x;
+    const uint64_t B = ((uint64_t)h.w << 32) | h.z;
+    const uint64_t ph = A + (uint64_t)j0 * B;          // exact phase (turns * 2^64) at f_{j0}
+    const float ang = (float)(int32_t)(ph >> 32) * TWO_PI_OVER_2_32;
+    float s, c;
+    __sincosf(ang, &s, &c);
+    const float cr = m.x, sr = m.y, w = m.z, wr = m.w;
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+        const float wc = w * c;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            acc[k][q] = fmaf(u[q], c, acc[k][q]);
+            acc[k][P + q] = fmaf(u[q], s, acc[k][P + q]);
+        }
+        acc[k][2 * P] = fmaf(wr, c, acc[k][2 * P]);
+        acc[k][2 * P + 1] = fmaf(wr, s, acc[k][2 * P + 1]);
+        acc[k][2 * P + 2] = fmaf(wc, c, acc[k][2 * P + 2]);
+        acc[k][2 * P + 3] = fmaf(wc, s, acc[k][2 * P + 3]);
+        if (k + 1 < F) {
+            const float cn = fmaf(c, cr, -s * sr);
+            s = fmaf(s, cr, c * sr);
+            c = cn;
+        }
+    }
+}
+
+template <int P, int F>
+__device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const SeedTable &tab, uint32_t j0,
+                                           double (&acc)[F][2 * P + 4]) {
+    const ulonglong2 h = *reinterpret_cast<const ulonglong2 *>(r2);
+    const double2 rot = r2[1];
+    const double2 ww = r2[2];
+    double u[2 * ((P + 1) / 2)];
+#pragma unroll
+    for (int q2 = 0; q2 < (P + 1) / 2; ++q2) {
+        const double2 v = r2[3 + q2];
+        u[2 * q2] = v.x;
+        u[2 * q2 + 1] = v.y;
+    }
+    const uint64_t ph = h.x + (uint64_t)j0 * h.y;
+    double s, c;
+    seed_from_table(tab, ph, &s, &c);
+    const double cr = rot.x, sr = rot.y, w = ww.x, wr = ww.y;
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+        const double wc = w * c;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            acc[k][q] = fma(u[q], c, acc[k][q]);
+            acc[k][P + q] = fma(u[q], s, acc[k][P + q]);
+        }
+        acc[k][2 * P] = fma(wr, c, acc[k][2 * P]);
+        acc[k][2 * P + 1] = fma(wr, s, acc[k][2 * P + 1]);
+        acc[k][2 * P + 2] = fma(wc, c, acc[k][2 * P + 2]);
+        acc[k][2 * P + 3] = fma(wc, s, acc[k][2 * P + 3]);
+        if (k + 1 < F) {
+            const double cn = fma(c, cr, -s * sr);
+            s = fma(s, cr, c * sr);
+            c = cn;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One CTA-block of 32*F frequencies of one series.
+// use[2]: per-buffer mbarrier phase counters, identical in all threads.
+
+template <int PREC, int P, int F>
+__device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
+                                            int64_t blk, unsigned char *smem, uint32_t (&use)[2]) {
+    using L = PgramLayout<PREC, P, F>;
+    using T = typename AccT<PREC>::T;
+    constexpr int Q = L::Q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *tiles = smem + L::OFF_TILES;
+    T *red = reinterpret_cast<T *>(smem + L::OFF_RED);
+    const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + L::off_table(nw));
+
+    const int N = d.N;
+    const int64_t jblock = blk * 32 * F;
+    const uint32_t j0 = (uint32_t)(jblock + lane * F);
+    const unsigned char *src = prm.rec + (prm.use_rec64_off ? d.rec64_off : d.rec_off);
+    const int ntiles = (N + TILE_POINTS - 1) / TILE_POINTS;
+
+    __syncthreads();   // previous block's epilogue is done with red / tiles
+    for (int q = lane; q < Q * F * 32; q += 32) red[(size_t)warp * Q * F * 32 + q] = T(0);
+    if (tid == 0) {
+        for (int k = 0; k < 2 && k < ntiles; ++k) {
+            const unsigned n = (unsigned)min(TILE_POINTS, N - k * TILE_POINTS);
+            mbar_arrive_expect_tx(&bars[k], n * L::RB);
+            bulk_g2s(tiles + k * L::TILE_BYTES, src + (size_t)k * L::TILE_BYTES, n * L::RB, &bars[k]);
+        }
+    }
+
+    T acc[F][Q];
+#pragma unroll
+    for (int k = 0; k < F; ++k)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[k][q] = T(0);
+
+    auto flush = [&]() {
+        T *mine = red + (size_t)warp * Q * F * 32;
+#pragma unroll
+        for (int k = 0; k < F; ++k)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                mine[(q * F + k) * 32 + lane] += acc[k][q];
+                acc[k][q] = T(0);
+            }
+    };
+
+    int since = 0;
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int b = tile & 1;
+        if (!mbar_wait_bounded(&bars[b], use[b] & 1u)) {
+            if (lane == 0) atomicExch(prm.err, FREDEC_ETIMEOUT);
+        }
+        ++use[b];
+        const int n = min(TILE_POINTS, N - tile * TILE_POINTS);
+        const unsigned char *tb = tiles + b * L::TILE_BYTES;
+        for (int i = warp; i < n; i += nw) {
+            if constexpr (PREC == FREDEC_MIXED) {
+                mixed_point<P, F>(reinterpret_cast<const uint4 *>(tb + (size_t)i * L::RB), j0, acc);
+                if (++since == FLUSH_POINTS) {
+                    flush();
+                    since = 0;
+                }
+            } else {
+                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, acc);
+            }
+        }
+        __syncthreads();   // all warps are done with buffer b
+        if (tid == 0 && tile + 2 < ntiles) {
+            const unsigned nn = (unsigned)min(TILE_POINTS, N - (tile + 2) * TILE_POINTS);
+            mbar_arrive_expect_tx(&bars[b], nn * L::RB);
+            bulk_g2s(tiles + b * L::TILE_BYTES, src + (size_t)(tile + 2) * L::TILE_BYTES, nn * L::RB, &bars[b]);
+        }
+    }
+    flush();
+    __syncthreads();
+
+    // Epilogue: combine the warps' partial sums in FP64 and solve per frequency.
+    const double W = (PREC == FREDEC_MIXED) ? st.Wf : st.W;
+    const int64_t nf = d.nf;
+    const bool mixed_flags = (PREC == FREDEC_MIXED) && prm.flag_tau >= 0.0;
+    for (int fs = tid; fs < 32 * F; fs += blockDim.x) {
+        const int k = fs >> 5, ln = fs & 31;
+        const int64_t j = jblock + (int64_t)ln * F + k;
+        if (j >= nf) continue;
+        double S[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double sq = 0.0;
+            for (int w = 0; w < nw; ++w) sq += (double)red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
+            S[q] = sq;
+        }
+        double vcc = 0.0, vcs = 0.0, vss = 0.0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            vcc = fma(S[q], S[q], vcc);
+            vcs = fma(S[q], S[P + q], vcs);
+            vss = fma(S[P + q], S[P + q], vss);
+        }
+        const double CC = S[2 * P + 2], CS = S[2 * P + 3];
+        double a, bb, ratio;
+        const double zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
+        prm.z[d.z_off + j] = zz;
+        if (prm.coef) {
+            prm.coef[2 * (d.z_off + j)] = a;
+            prm.coef[2 * (d.z_off + j) + 1] = bb;
+        }
+        if (mixed_flags && ratio < prm.flag_tau) {
+            const int64_t fb = j / (32 * prm.fpt64);
+            if (atomicExch(&prm.flag_words[d.flag_off + fb], 1u) == 0u) {
+                const int32_t at = atomicAdd(prm.flag_count, 1);
+                prm.flag_list[at] = (int32_t)fb;
+            }
+        }
+    }
+}
+
+template <int PREC, int P, int F>
+__device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
+    using L = PgramLayout<PREC, P, F>;
+    if (threadIdx.x == 0) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    if constexpr (PREC == FREDEC_FP64)
+        fill_seed_table(*reinterpret_cast<SeedTable *>(smem + L::off_table(blockDim.x >> 5)));
+    __syncthreads();
+}
+
+// Grid kernel: one CTA per block of the single series desc[0], or (list mode)
+// a persistent grid over prm.items.
+template <int PREC, int P, int F>
+__global__ void __launch_bounds__(256, 1) pgram_kernel(PgramParams prm, int list_mode) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    pgram_cta_init<PREC, P, F>(smem);
+    const SeriesDesc d = prm.desc[0];
+    const SeriesState &st = prm.state[0];
+    if (st.status != FREDEC_OK) return;
+    uint32_t use[2] = {0u, 0u};
+    if (!list_mode) {
+        pgram_block<PREC, P, F>(prm, d, st, blockIdx.x, smem, use);
+    } else {
+        const int32_t n = *prm.item_count;
+        for (int32_t it = blockIdx.x; it < n; it += gridDim.x)
+            pgram_block<PREC, P, F>(prm, d, st, prm.items[it], smem, use);
+    }
+}
+
+template <int PREC, int P, int F>
+int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, int list_mode, int grid_override,
+                   cudaStream_t st) {
+    using L = PgramLayout<PREC, P, F>;
+    const size_t smem = L::smem_bytes(warps);
+    auto kern = pgram_kernel<PREC, P, F>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+    const int64_t grid = list_mode ? grid_override : nblocks;
+    if (grid <= 0) return FREDEC_OK;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(prm, list_mode);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram launch: ") + cudaGetErrorString(e));
+    return FREDEC_OK;
+}
+
+template <int PREC, int P, int F>
+size_t pgram_smem_t(int warps) { return PgramLayout<PREC, P, F>::smem_bytes(warps); }
+
+}  // namespace fredec

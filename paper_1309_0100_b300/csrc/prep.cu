@@ -1,0 +1,325 @@
+// Prep of one or many series (FP64): weights w = 1/sigma^2, time origin t_c,
+// the base model's columns orthonormalised in the weighted inner product
+// <phi> = sum w phi (two rounds of Cholesky-QR), the base fit l(f') and the
+// per-point records that the periodogram kernels stream.
+//
+// Paper: the base model is H_m with fixed frequencies f' (Eq. Hn); its linear
+// fit is the Cholesky solve of Section 3 (Q = L L^T, a = L^{-1} g).  Here the
+// factor is applied to the columns themselves (psi = L^{-1} phi), so that the
+// per-frequency solve becomes the incremental two-row extension of L described
+// for Q_f in Section 3.  The normalisations of Section 4.1 (Eq. idn) are used
+// in the form that matters for the kernels: centred time, and
+// <sin^2> = <1> - <cos^2>.
+//
+// Every kernel works on chunks of PREP_THREADS points of one series (one point
+// per thread).  Each chunk writes partial sums; the last chunk of a series to
+// finish (atomic counter) reduces them in chunk order, so results do not
+// depend on scheduling.
+#include "device_util.cuh"
+#include "fredec_internal.cuh"
+
+namespace fredec {
+
+int prep_npart(int pmax) { return pmax * (pmax + 1) / 2 + pmax + 4; }
+int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
+                     const double *base, int precision, void *rec64, cudaStream_t st);
+
+namespace {
+
+struct PrepArgs {
+    const SeriesDesc *desc;
+    SeriesState *state;
+    const int32_t *chunk_series;
+    double *partials;
+    int npart;
+    double *psi;
+    unsigned char *rec;
+    unsigned char *rec64;   // optional extra FP64 records (mixed runs with FP64 re-evaluation)
+    const double *t, *y, *sigma, *base;
+    int precision;
+};
+
+// Reduce nv per-thread values over the CTA and store them as this chunk's
+// partials.  vals may live in local memory.
+__device__ void store_partials(const PrepArgs &a, int64_t chunk, const double *vals, int nv, double *sm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nv; ++q) {
+        const double v = warp_sum_d(vals[q]);
+        if (lane == 0) sm[wid * (NTRI + PMAX + 4) + q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sm[w * (NTRI + PMAX + 4) + q];
+        a.partials[chunk * a.npart + q] = s;
+    }
+}
+
+// Last-block-done: returns true in exactly one CTA of the series (the last to
+// arrive), after all partials of the series are visible.
+__device__ bool arrive_last(SeriesState &st, int which, int nchunks) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&st.counter[which], 1u);
+        last = (prev == (unsigned)nchunks - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Sum of partial q over the series' chunks, in chunk order.
+__device__ double sum_partial(const PrepArgs &a, const SeriesDesc &d, int q) {
+    double s = 0.0;
+    for (int c = 0; c < d.nchunks; ++c) s += __ldcg(&a.partials[(d.chunk_off + c) * a.npart + q]);
+    return s;
+}
+
+__device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &d, double tp, double *phi) {
+    phi[0] = 1.0;
+    for (int k = 0; k < d.nb; ++k) {
+        const double g = a.base[d.base_off + k];
+        const uint64_t ph = frac_turns_u64(g, tp);
+        double s, c;
+        sincos_turns_d(ph, &s, &c);
+        phi[1 + 2 * k] = c;
+        phi[2 + 2 * k] = s;
+    }
+}
+
+extern __shared__ double prep_sm[];
+
+// K1: sum w, sum w t  ->  W, t_c.
+__global__ void __launch_bounds__(PREP_THREADS) prep_k1(PrepArgs a) {
+    const int64_t chunk = blockIdx.x;
+    const int s = a.chunk_series[chunk];
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (i < d.N) {
+        const double sg = a.sigma[d.obs_off + i];
+        const double w = 1.0 / (sg * sg);
+        v[0] = w;
+        v[1] = w * a.t[d.obs_off + i];
+    }
+    store_partials(a, chunk, v, 2, prep_sm);
+    if (arrive_last(st, 0, d.nchunks)) {
+        if (threadIdx.x == 0) {
+            const double W = sum_partial(a, d, 0), Swt = sum_partial(a, d, 1);
+            st.W = W;
+            st.Swt = Swt;
+            st.tc = rint(Swt / W);
+            st.status = FREDEC_OK;
+            st.counter[0] = 0;
+        }
+    }
+}
+
+// K2: raw base columns phi(t'), Gram Q1 = <phi phi^T>  ->  L1 = chol(Q1).
+__global__ void __launch_bounds__(PREP_THREADS) prep_k2(PrepArgs a) {
+    const int64_t chunk = blockIdx.x;
+    const int s = a.chunk_series[chunk];
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.p;
+    const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
+    double phi[PMAX], v[NTRI];
+    for (int q = 0; q < p * (p + 1) / 2; ++q) v[q] = 0.0;
+    if (i < d.N) {
+        const double sg = a.sigma[d.obs_off + i];
+        const double w = 1.0 / (sg * sg);
+        const double tp = a.t[d.obs_off + i] - st.tc;
+        base_basis(a, d, tp, phi);
+        for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * d.N + i] = phi[q];
+        for (int r = 0; r < p; ++r)
+            for (int c = 0; c <= r; ++c) v[tri(r, c)] = w * phi[r] * phi[c];
+    }
+    store_partials(a, chunk, v, p * (p + 1) / 2, prep_sm);
+    if (arrive_last(st, 1, d.nchunks)) {
+        for (int q = threadIdx.x; q < p * (p + 1) / 2; q += blockDim.x) st.L1[q] = sum_partial(a, d, q);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!chol_packed(st.L1, p, 1e-12)) st.status = FREDEC_ESINGULAR;
+            st.counter[1] = 0;
+        }
+    }
+}
+
+// K3: psi1 = L1^{-1} phi, Gram Q2 = <psi1 psi1^T>, <psi1 y>  ->  L2, a = L2^{-1}<psi1 y>.
+__global__ void __launch_bounds__(PREP_THREADS) prep_k3(PrepArgs a) {
+    const int64_t chunk = blockIdx.x;
+    const int s = a.chunk_series[chunk];
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.p, nt = p * (p + 1) / 2;
+    const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
+    double x[PMAX], v[NTRI + PMAX];
+    for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
+    if (i < d.N && st.status == FREDEC_OK) {
+        const double sg = a.sigma[d.obs_off + i];
+        const double w = 1.0 / (sg * sg);
+        const double yi = a.y[d.obs_off + i];
+        for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * d.N + i];
+        forward_packed(st.L1, x, p);
+        for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * d.N + i] = x[q];
+        for (int r = 0; r < p; ++r)
+            for (int c = 0; c <= r; ++c) v[tri(r, c)] = w * x[r] * x[c];
+        for (int q = 0; q < p; ++q) v[nt + q] = w * x[q] * yi;
+    }
+    store_partials(a, chunk, v, nt + p, prep_sm);
+    if (arrive_last(st, 2, d.nchunks)) {
+        for (int q = threadIdx.x; q < nt + p; q += blockDim.x) {
+            const double sq = sum_partial(a, d, q);
+            if (q < nt) st.L2[q] = sq; else st.a[q - nt] = sq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (st.status == FREDEC_OK) {
+                if (!chol_packed(st.L2, p, 1e-12)) st.status = FREDEC_ESINGULAR;
+                else forward_packed(st.L2, st.a, p);
+            }
+            st.counter[2] = 0;
+        }
+    }
+}
+
+// K4: psi = L2^{-1} psi1 (final orthonormal columns), r = y - a^T psi,
+// <psi r>  ->  a2 (second-pass coefficients; tiny).
+__global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
+    const int64_t chunk = blockIdx.x;
+    const int s = a.chunk_series[chunk];
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.p;
+    const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
+    double x[PMAX], v[PMAX];
+    for (int q = 0; q < p; ++q) v[q] = 0.0;
+    if (i < d.N && st.status == FREDEC_OK) {
+        const double sg = a.sigma[d.obs_off + i];
+        const double w = 1.0 / (sg * sg);
+        double r = a.y[d.obs_off + i];
+        for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * d.N + i];
+        forward_packed(st.L2, x, p);
+        for (int q = 0; q < p; ++q) {
+            a.psi[d.psi_off + (int64_t)q * d.N + i] = x[q];
+            r -= st.a[q] * x[q];
+        }
+        for (int q = 0; q < p; ++q) v[q] = w * x[q] * r;
+    }
+    store_partials(a, chunk, v, p, prep_sm);
+    if (arrive_last(st, 3, d.nchunks)) {
+        for (int q = threadIdx.x; q < p; q += blockDim.x) st.a2[q] = sum_partial(a, d, q);
+        __syncthreads();
+        if (threadIdx.x == 0) st.counter[3] = 0;
+    }
+}
+
+// K5: final residual r2 = y - (a + a2)^T psi, records for the grid, chi2 and
+// the sum of the weights as the mixed kernel sees them.
+__global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
+    const int64_t chunk = blockIdx.x;
+    const int s = a.chunk_series[chunk];
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.p;
+    const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (i < d.N && st.status == FREDEC_OK) {
+        const double sg = a.sigma[d.obs_off + i];
+        const double w = 1.0 / (sg * sg);
+        const double tp = a.t[d.obs_off + i] - st.tc;
+        double r = a.y[d.obs_off + i];
+        double u[PMAX];
+        for (int q = 0; q < p; ++q) {
+            const double ps = a.psi[d.psi_off + (int64_t)q * d.N + i];
+            r -= (st.a[q] + st.a2[q]) * ps;
+            u[q] = w * ps;
+        }
+        const uint64_t A = frac_turns_u64(d.f0, tp);
+        const uint64_t B = frac_turns_u64(d.df, tp);
+        double sr, cr;
+        sincos_turns_d(B, &sr, &cr);
+        const float wf = (float)w;
+        v[0] = w * r * r;
+        v[1] = (double)wf;
+        if (a.precision == FREDEC_MIXED) {
+            uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + i * rec32_words(p);
+            R[0] = (uint32_t)A;
+            R[1] = (uint32_t)(A >> 32);
+            R[2] = (uint32_t)B;
+            R[3] = (uint32_t)(B >> 32);
+            float *Rf = (float *)R;
+            Rf[4] = (float)cr;
+            Rf[5] = (float)sr;
+            Rf[6] = wf;
+            Rf[7] = (float)(w * r);
+            for (int q = 0; q < p; ++q) Rf[8 + q] = (float)u[q];
+            for (int q = 8 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
+        }
+        unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : a.rec64;
+        if (r64) {
+            const int64_t off64 = a.precision == FREDEC_FP64 ? d.rec_off : d.rec64_off;
+            uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p);
+            R[0] = A;
+            R[1] = B;
+            double *Rd = (double *)R;
+            Rd[2] = cr;
+            Rd[3] = sr;
+            Rd[4] = w;
+            Rd[5] = w * r;
+            for (int q = 0; q < p; ++q) Rd[6 + q] = u[q];
+            for (int q = 6 + p; q < rec64_words(p); ++q) Rd[q] = 0.0;
+        }
+    }
+    store_partials(a, chunk, v, 2, prep_sm);
+    if (arrive_last(st, 4, d.nchunks)) {
+        if (threadIdx.x == 0) {
+            st.chi2 = sum_partial(a, d, 0);
+            st.Wf = sum_partial(a, d, 1);
+            st.counter[4] = 0;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_prep(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
+                const double *base, int precision, cudaStream_t st) {
+    return run_prep_records(pp, t, y, sigma, base, precision, nullptr, st);
+}
+
+// As launch_prep; rec64 (optional) also receives FP64 records at each series'
+// rec64_off.
+int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
+                     const double *base, int precision, void *rec64, cudaStream_t st) {
+    PrepArgs a;
+    a.rec64 = (unsigned char *)rec64;
+    a.desc = pp.desc;
+    a.state = pp.state;
+    a.chunk_series = pp.chunk_series;
+    a.partials = pp.partials;
+    a.npart = prep_npart(pp.pmax);
+    a.psi = pp.psi;
+    a.rec = (unsigned char *)pp.rec;
+    a.t = t;
+    a.y = y;
+    a.sigma = sigma;
+    a.base = base;
+    a.precision = precision;
+    if (pp.nchunks <= 0) return FREDEC_OK;
+    const size_t smem = sizeof(double) * (PREP_THREADS / 32) * (NTRI + PMAX + 4);
+    const dim3 grid((unsigned)pp.nchunks);
+    prep_k1<<<grid, PREP_THREADS, smem, st>>>(a);
+    prep_k2<<<grid, PREP_THREADS, smem, st>>>(a);
+    prep_k3<<<grid, PREP_THREADS, smem, st>>>(a);
+    prep_k4<<<grid, PREP_THREADS, smem, st>>>(a);
+    prep_k5<<<grid, PREP_THREADS, smem, st>>>(a);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
+}  // namespace fredec
