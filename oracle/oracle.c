@@ -79,9 +79,14 @@ static double weight(double sigma)
  *   x : m coefficients (0 for dropped columns), may be NULL.
  *   ratio : m, remaining-norm / original-norm of each column when it was
  *           processed (1 = orthogonal to the previous ones), may be NULL.
+ *   comp : m, the squared component of Q^T b along the orthonormal direction
+ *          that column k adds (0 for a dropped column), may be NULL.  Adding
+ *          column k to the model lowers the residual sum of squares by exactly
+ *          comp[k], so a difference of two nested fits is a sum of comp[]
+ *          entries; summing them avoids subtracting two large chi2 values.
  * Returns the residual sum of squares min_x ||b - A x||^2.
  */
-static double hh_lsq(double *A, double *b, int64_t N, int m, double *x, double *ratio)
+static double hh_lsq(double *A, double *b, int64_t N, int m, double *x, double *ratio, double *comp)
 {
     double orig[128];
     int rowof[128];
@@ -101,6 +106,7 @@ static double hh_lsq(double *A, double *b, int64_t N, int m, double *x, double *
         if (ratio) ratio[k] = rat;
         if (r >= N || orig[k] == 0.0 || rat <= ORACLE_DROPTOL) {
             rowof[k] = -1;
+            if (comp) comp[k] = 0.0;
             continue;
         }
         double x0 = a[r];
@@ -119,6 +125,7 @@ static double hh_lsq(double *A, double *b, int64_t N, int m, double *x, double *
         }
         a[r] = alpha;
         /* keep v below the diagonal is not needed: only R and Q^T b are used */
+        if (comp) comp[k] = b[r] * b[r];
         rowof[k] = (int)r;
         ++r;
     }
@@ -162,16 +169,17 @@ static void design(const double *t, const double *y, const double *sigma, int64_
 
 /* l(g) = min over the linear parameters of chi2 for the model with the n
  * frequencies g (Sect. 2).  Optional: coefficients theta (2n+1, order
- * [c, a_0, b_0, a_1, b_1, ...]) and the unweighted residual x_i - mu(t_i). */
+ * [c, a_0, b_0, a_1, b_1, ...]), the unweighted residual x_i - mu(t_i) and
+ * the per-column chi2 reductions comp (see hh_lsq). */
 static double model_fit(const double *t, const double *y, const double *sigma, int64_t N,
-                        const double *g, int n, double *theta, double *ratio, double *resid)
+                        const double *g, int n, double *theta, double *ratio, double *resid, double *comp)
 {
     int m = 2 * n + 1;
     double *A = (double *)malloc(sizeof(double) * (size_t)N * m);
     double *b = (double *)malloc(sizeof(double) * (size_t)N);
     double th[128];
     design(t, y, sigma, N, g, n, A, b);
-    double chi2 = hh_lsq(A, b, N, m, th, ratio);
+    double chi2 = hh_lsq(A, b, N, m, th, ratio, comp);
     if (theta) memcpy(theta, th, sizeof(double) * m);
     if (resid) {
         for (int64_t i = 0; i < N; ++i) {
@@ -197,6 +205,9 @@ static double model_fit(const double *t, const double *y, const double *sigma, i
  * sin 2pi f_j t] is fitted jointly (the base amplitudes are refitted; the base
  * frequencies stay fixed) and
  *     z_j = ( chi2_base - chi2_j ) / 2 .
+ * The QR of [base | trial] starts with the base columns, so chi2_base - chi2_j
+ * equals the sum of the two trial columns' comp[] terms; that sum is what is
+ * returned (same quantity, without cancelling two large chi2 values).
  * Outputs: z (nf); chi2_base (1) may be NULL; coef (2*nf: a_j, b_j, the
  * coefficients of cos and sin of the trial frequency in raw time t) may be
  * NULL; ratio (nf: min over the two trial columns of remaining/original norm)
@@ -209,13 +220,13 @@ int oracle_periodogram(const double *t, const double *y, const double *sigma, in
     if (N <= 0 || n_base < 0 || n_base > 40 || nf < 0) return 1;
     double *g = (double *)malloc(sizeof(double) * (n_base + 1));
     for (int k = 0; k < n_base; ++k) g[k] = base[k];
-    double l0 = model_fit(t, y, sigma, N, g, n_base, NULL, NULL, NULL);
+    double l0 = model_fit(t, y, sigma, N, g, n_base, NULL, NULL, NULL, NULL);
     if (chi2_base) *chi2_base = l0;
-    double th[128], rat[128];
+    double th[128], rat[128], comp[128];
     for (int64_t j = 0; j < nf; ++j) {
         g[n_base] = fgrid[j];
-        double l1 = model_fit(t, y, sigma, N, g, n_base + 1, th, rat, NULL);
-        z[j] = 0.5 * (l0 - l1);
+        model_fit(t, y, sigma, N, g, n_base + 1, th, rat, NULL, comp);
+        z[j] = 0.5 * (comp[2 * n_base + 1] + comp[2 * n_base + 2]);
         if (coef) {
             coef[2 * j] = th[2 * n_base + 1];
             coef[2 * j + 1] = th[2 * n_base + 2];
@@ -248,7 +259,7 @@ int oracle_periodogram_grad(const double *t, const double *y, const double *sigm
     for (int k = 0; k < n_base; ++k) g[k] = base[k];
     for (int64_t j = 0; j < nf; ++j) {
         g[n_base] = fgrid[j];
-        model_fit(t, y, sigma, N, g, n_base + 1, th, NULL, r);
+        model_fit(t, y, sigma, N, g, n_base + 1, th, NULL, r, NULL);
         double a = th[2 * n_base + 1], b = th[2 * n_base + 2], acc = 0.0;
         for (int64_t i = 0; i < N; ++i) {
             double c, s;
@@ -277,12 +288,12 @@ int oracle_periodogram_vjp(const double *t, const double *y, const double *sigma
     double *rb = (double *)malloc(sizeof(double) * (size_t)N);
     double *r = (double *)malloc(sizeof(double) * (size_t)N);
     for (int k = 0; k < n_base; ++k) g[k] = base[k];
-    model_fit(t, y, sigma, N, g, n_base, NULL, NULL, rb);
+    model_fit(t, y, sigma, N, g, n_base, NULL, NULL, rb, NULL);
     for (int64_t i = 0; i < N; ++i) dldy[i] = 0.0;
     for (int64_t j = 0; j < nf; ++j) {
         if (v[j] == 0.0) continue;
         g[n_base] = fgrid[j];
-        model_fit(t, y, sigma, N, g, n_base + 1, NULL, NULL, r);
+        model_fit(t, y, sigma, N, g, n_base + 1, NULL, NULL, r, NULL);
         for (int64_t i = 0; i < N; ++i) dldy[i] += v[j] * (rb[i] - r[i]);   /* mu_j - mu_b */
     }
     for (int64_t i = 0; i < N; ++i) dldy[i] *= weight(sigma[i]);
@@ -298,14 +309,25 @@ int oracle_periodogram_vjp(const double *t, const double *y, const double *sigma
 /* l_0: chi2 of the constant-only model H_0 (Eq. H0). */
 double oracle_l0(const double *t, const double *y, const double *sigma, int64_t N)
 {
-    return model_fit(t, y, sigma, N, NULL, 0, NULL, NULL, NULL);
+    return model_fit(t, y, sigma, N, NULL, 0, NULL, NULL, NULL, NULL);
 }
 
 /* l(S) for one tuple of m frequencies (model H_m, Eq. Hn). theta may be NULL. */
 double oracle_tuple_l(const double *t, const double *y, const double *sigma, int64_t N,
                       const double *freqs, int m, double *theta)
 {
-    return model_fit(t, y, sigma, N, freqs, m, theta, NULL, NULL);
+    return model_fit(t, y, sigma, N, freqs, m, theta, NULL, NULL, NULL);
+}
+
+/* z(S) = (l_0 - l(S))/2 computed as half the sum of the comp[] terms of every
+ * column after the constant (the QR starts with the constant column). */
+static double tuple_z(const double *t, const double *y, const double *sigma, int64_t N,
+                      const double *freqs, int m, double *theta, double *resid)
+{
+    double comp[128], z = 0.0;
+    model_fit(t, y, sigma, N, freqs, m, theta, NULL, resid, comp);
+    for (int k = 1; k < 2 * m + 1; ++k) z += comp[k];
+    return 0.5 * z;
 }
 
 /*
@@ -322,7 +344,7 @@ int oracle_tuple_eval(const double *t, const double *y, const double *sigma, int
     for (int64_t k = 0; k < n_tuples; ++k) {
         int m = (int)(off[k + 1] - off[k]);
         if (m < 0 || m > 60) return 1;
-        z[k] = 0.5 * (l0 - oracle_tuple_l(t, y, sigma, N, freqs + off[k], m, NULL));
+        z[k] = tuple_z(t, y, sigma, N, freqs + off[k], m, NULL, NULL);
     }
     return 0;
 }
@@ -354,14 +376,12 @@ int oracle_tuple_grad(const double *t, const double *y, const double *sigma, int
                       double *z, double *dzdf)
 {
     if (N <= 0 || n_tuples < 0) return 1;
-    double l0 = oracle_l0(t, y, sigma, N);
     double *r = (double *)malloc(sizeof(double) * (size_t)N);
     double th[128];
     for (int64_t k = 0; k < n_tuples; ++k) {
         const double *g = freqs + off[k];
         int m = (int)(off[k + 1] - off[k]);
-        double l = model_fit(t, y, sigma, N, g, m, th, NULL, r);
-        z[k] = 0.5 * (l0 - l);
+        z[k] = tuple_z(t, y, sigma, N, g, m, th, r);
         for (int q = 0; q < m; ++q) {
             double a = th[1 + 2 * q], b = th[2 + 2 * q], acc = 0.0;
             for (int64_t i = 0; i < N; ++i) {
@@ -400,7 +420,7 @@ int oracle_tuple_refine(const double *t, const double *y, const double *sigma, i
     double tmin = t[0], tmax = t[0];
     for (int64_t i = 0; i < N; ++i) { if (t[i] < tmin) tmin = t[i]; if (t[i] > tmax) tmax = t[i]; }
     double span = tmax - tmin > 0 ? tmax - tmin : 1.0;
-    double l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r);
+    double l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r, NULL);
     int it = 0;
     for (; it < max_iter && m > 0; ++it) {
         design(t, y, sigma, N, freqs, m, J, NULL);
@@ -413,18 +433,18 @@ int oracle_tuple_refine(const double *t, const double *y, const double *sigma, i
             }
         }
         for (int64_t i = 0; i < N; ++i) rb[i] = sqrt(weight(sigma[i])) * r[i];
-        hh_lsq(J, rb, N, q, xi, NULL);
+        hh_lsq(J, rb, N, q, xi, NULL, NULL);
         double step = 1.0, dmax = 0.0, lnew = l;
         for (int k = 0; k < m; ++k) if (fabs(xi[p + k]) > dmax) dmax = fabs(xi[p + k]);
         int accepted = 0;
         for (int h = 0; h < 40; ++h, step *= 0.5) {
             for (int k = 0; k < m; ++k) trial[k] = freqs[k] + step * xi[p + k];
-            lnew = model_fit(t, y, sigma, N, trial, m, NULL, NULL, NULL);
+            lnew = model_fit(t, y, sigma, N, trial, m, NULL, NULL, NULL, NULL);
             if (lnew <= l) { accepted = 1; break; }
         }
         if (!accepted) break;
         for (int k = 0; k < m; ++k) freqs[k] = trial[k];
-        l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r);
+        l = model_fit(t, y, sigma, N, freqs, m, th, NULL, r, NULL);
         if (step * dmax * span < tol) { ++it; break; }
     }
     if (l_out) *l_out = l;

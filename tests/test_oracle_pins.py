@@ -145,6 +145,44 @@ def test_brute_force_lstsq_with_base():
         np.testing.assert_allclose(coef[j], x[-2:], rtol=1e-7, atol=1e-9 * np.abs(x).max())
 
 
+def test_high_precision_small_z():
+    """Small z under a large chi2 (big offset and noise): the oracle's z agrees
+    with a 40-digit normal-equation solve to 1e-12 relative, i.e. it does not
+    lose digits to the cancellation of chi2_base - chi2_new."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    rng = _rng(21)
+    N = 40
+    t = np.sort(rng.uniform(0, 50, N))
+    sigma = rng.lognormal(0, 0.3, N)
+    y = 1e3 + 30 * rng.standard_normal(N) + 0.05 * np.sin(2 * np.pi * 0.31 * t)
+    base = np.array([0.123])
+    f = np.array([0.31, 0.05, 0.77])
+    z, c2 = oracle.periodogram(t, y, sigma, base, f)
+
+    def chi2(freqs):
+        cols = [[mp.mpf(1)] * N]
+        for g in freqs:
+            cols.append([mp.cos(2 * mp.pi * mp.mpf(g) * mp.mpf(ti)) for ti in t])
+            cols.append([mp.sin(2 * mp.pi * mp.mpf(g) * mp.mpf(ti)) for ti in t])
+        w = [1 / mp.mpf(s) ** 2 for s in sigma]
+        k = len(cols)
+        G = mp.matrix(k, k)
+        r = mp.matrix(k, 1)
+        for a in range(k):
+            r[a] = mp.fsum(w[i] * cols[a][i] * mp.mpf(y[i]) for i in range(N))
+            for b in range(k):
+                G[a, b] = mp.fsum(w[i] * cols[a][i] * cols[b][i] for i in range(N))
+        th = mp.lu_solve(G, r)
+        return mp.fsum(w[i] * (mp.mpf(y[i]) - mp.fsum(th[a] * cols[a][i] for a in range(k))) ** 2 for i in range(N))
+
+    l0 = chi2(list(base))
+    for j, fj in enumerate(f):
+        zmp = (l0 - chi2(list(base) + [fj])) / 2
+        assert float(abs(z[j] - zmp) / abs(zmp)) < 1e-12, (j, z[j], float(zmp))
+    assert float(abs(c2 - l0) / l0) < 1e-13
+
+
 # ----------------------------------------------------------------------------
 # Invariants
 
