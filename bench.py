@@ -166,6 +166,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=30000)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="profiling runs: fixed launch shape, mixed steps only (no tuning, FP64, e2e or CPU legs)")
+    ap.add_argument("--fpt", type=int, default=4)
+    ap.add_argument("--warps", type=int, default=4)
     args = ap.parse_args()
     rank, ws = dist_setup()
     if args.impl == "reference":
@@ -187,15 +191,24 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     best = {}
-    for prec in ("mixed", "fp64"):
-        best[prec] = F.tune(prec, nb, N, nf)
+    if args.kernel_only:
+        best["mixed"] = (args.fpt, args.warps)
+    else:
+        for prec in ("mixed", "fp64"):
+            best[prec] = F.tune(prec, nb, N, nf)
 
     def timed_steps(prec, steps, warmup):
+        shape = best[prec]
         kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in kev:          # torch creates the CUDA events on first record; the library re-records them
+            a.record(stream)
+            b.record(stream)
+        torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             for _ in range(warmup):
-                F.periodogram_dev(t, y, sg, base, s.grid.f0, s.grid.df, nf, precision=prec, topk=5, out=z)
+                F.periodogram_dev(t, y, sg, base, s.grid.f0, s.grid.df, nf, precision=prec, topk=5, out=z,
+                                  fpt=shape[0], warps=shape[1])
             torch.cuda.synchronize()
             barrier(ws)
             torch.cuda.synchronize()
@@ -204,7 +217,8 @@ def main():
                 flush.fill_(float(k))                              # L2 flush between steps (untimed)
                 sev[k][0].record(stream)
                 F.profile_events(*kev[k])
-                F.periodogram_dev(t, y, sg, base, s.grid.f0, s.grid.df, nf, precision=prec, topk=5, out=z)
+                F.periodogram_dev(t, y, sg, base, s.grid.f0, s.grid.df, nf, precision=prec, topk=5, out=z,
+                                  fpt=shape[0], warps=shape[1])
                 F.profile_events(None, None)
                 sev[k][1].record(stream)
             torch.cuda.synchronize()
@@ -218,6 +232,10 @@ def main():
     with Clocks(torch.cuda.current_device()) as clk:
         step_ms, kern_ms, wall = timed_steps("mixed", args.steps, args.warmup)
     clocks = clk.summary()
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "step_ms": step_ms, "kernel_ms": kern_ms, "clocks": clocks}))
+        return
     T = reduce_max(sum(step_ms), ws)
     ms_per_step = T / args.steps
     value = ws * N * nf / (ms_per_step * 1e-3)

@@ -79,7 +79,7 @@ typedef struct fredec_opts {
     int32_t warps;      /* warps per CTA (point splits); 0 = tuned or default       */
     double  flag_tau;   /* MIXED: a bin is recomputed in FP64 when a pivot of its
                            2x2 system falls below flag_tau times its column norm.
-                           0 = default (0.05); negative = never recompute.          */
+                           0 = default (0.2); negative = never recompute.             */
 } fredec_opts;
 
 /* Fill *o with the defaults (FP64, no top-k, tuned launch shape). */

@@ -35,7 +35,10 @@ def _stale(src: str, obj: str, newest_header: float) -> bool:
     return t < os.path.getmtime(src) or t < newest_header
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None,
+          lib: str = LIB, obj: str = OBJ) -> str:
+    """Compile and link; ``extra`` nvcc flags, ``lib``/``obj`` output paths."""
+    LIB, OBJ = lib, obj
     os.makedirs(OBJ, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     newest = max([os.path.getmtime(h) for h in _headers()] + [0.0])

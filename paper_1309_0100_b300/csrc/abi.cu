@@ -69,8 +69,7 @@ size_t pgram_smem(int p, int prec, int F, int warps);
 namespace {
 
 __global__ void init_series_kernel(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int32_t *chunk_series,
-                                   int64_t nchunks, uint32_t *flag_words, int64_t nflag, int32_t *flag_count,
-                                   int32_t *err) {
+                                   int64_t nchunks, int32_t *flag_count, int32_t *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *desc = v;
@@ -80,8 +79,6 @@ __global__ void init_series_kernel(SeriesDesc *desc, SeriesDesc v, SeriesState *
         if (err) *err = FREDEC_OK;
     }
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
-    if (flag_words)
-        for (int64_t q = i; q < nflag; q += (int64_t)gridDim.x * blockDim.x) flag_words[q] = 0u;
 }
 
 __global__ void info_kernel(const SeriesState *state, double *info) {
@@ -113,11 +110,10 @@ struct SingleWork {
     double *psi;
     void *rec;       // records of the main precision
     void *rec64;     // FP64 records for re-evaluation (mixed) or == rec (FP64)
-    uint32_t *flag_words;
-    int32_t *flag_list;
+    int64_t *flag_list;
     int32_t *flag_count;
     int32_t *err;
-    int64_t nchunks, nflag;
+    int64_t nchunks;
 };
 
 int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
@@ -130,11 +126,10 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
                             SingleWork &w) {
     const int p = 2 * nb + 1;
     const int prec = o.precision;
-    const double tau = o.flag_tau == 0.0 ? 0.05 : o.flag_tau;
+    const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
     const bool fix = prec == FREDEC_MIXED && tau >= 0.0;
     const int64_t nchunks = (N + PREP_THREADS - 1) / PREP_THREADS;
-    const int fpt64 = fixup_fpt(p);
-    const int64_t nflag = fix ? (nf + 32LL * fpt64 - 1) / (32LL * fpt64) : 0;
+    const int64_t nflag = fix ? nf : 0;   // worst case: every bin flagged
     const size_t rb = (size_t)rec_bytes(p, prec);
     const size_t rb64 = (size_t)rec_bytes(p, FREDEC_FP64);
     // carve one allocation
@@ -144,7 +139,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
     const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * rb);
     const size_t o_rec64 = fix ? take(N * rb64) : 0;
-    const size_t o_fw = take(nflag * 4 + 4), o_fl = take(nflag * 4 + 4), o_fc = take(4), o_err = take(4);
+    const size_t o_fl = take(nflag * 8 + 8), o_fc = take(4), o_err = take(4);
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();
     w.desc = (SeriesDesc *)(b + o_desc);
@@ -154,12 +149,10 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     w.psi = (double *)(b + o_psi);
     w.rec = b + o_rec;
     w.rec64 = fix ? (void *)(b + o_rec64) : (prec == FREDEC_FP64 ? w.rec : nullptr);
-    w.flag_words = fix ? (uint32_t *)(b + o_fw) : nullptr;
-    w.flag_list = fix ? (int32_t *)(b + o_fl) : nullptr;
+    w.flag_list = fix ? (int64_t *)(b + o_fl) : nullptr;
     w.flag_count = (int32_t *)(b + o_fc);
     w.err = (int32_t *)(b + o_err);
     w.nchunks = nchunks;
-    w.nflag = nflag;
 
     SeriesDesc d{};
     d.f0 = f0;
@@ -169,8 +162,8 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     d.nb = nb;
     d.p = p;
     d.nchunks = (int32_t)nchunks;
-    init_series_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (std::max(nchunks, nflag) + 255) / 256)), 256, 0,
-                         st>>>(w.desc, d, w.state, w.chunk_series, nchunks, w.flag_words, nflag, w.flag_count, w.err);
+    init_series_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
+        w.desc, d, w.state, w.chunk_series, nchunks, w.flag_count, w.err);
     FREDEC_CUDA_TRY(cudaGetLastError());
 
     PrepPlan pp;
@@ -194,12 +187,12 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
         shape = default_shape(prec, p, N, nf);
     }
     if (nf > 0) {
-        if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_words,
-                                  w.flag_list, w.flag_count, w.err, st))
+        if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_list,
+                                  w.flag_count, w.err, st))
             return rc;
         if (fix) {
-            if (int rc = launch_fixup(w.desc, w.state, w.rec64, p, (int)N, nf, fpt64, w.flag_list, w.flag_count,
-                                      nflag, z, coef, w.err, st))
+            if (int rc = launch_fixup_bins(w.desc, w.state, 1, w.rec64, p, w.flag_list, w.flag_count, nf, z, coef,
+                                           st))
                 return rc;
         }
         nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);

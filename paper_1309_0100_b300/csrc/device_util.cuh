@@ -14,19 +14,19 @@ constexpr double TWO_POW_M64 = 5.421010862427522170037e-20;
 constexpr unsigned WAIT_LIMIT = 1u << 24;                       // bounded mbarrier polls
 
 // frac(f * t) as unsigned 64-bit fixed-point turns.  The product is split into
-// its rounded value x and exact error e (fma); floor(x) is removed exactly and
-// e is added as a small signed correction, so the result is accurate to about
-// 2^-64 turns for |f t| < 2^20.
+// its rounded value x and its exact rounding error e (fma).  r = x - rint(x)
+// is exact (Sterbenz: x and rint(x) are within a factor 2 unless rint(x) = 0,
+// where r = x), so r and e are converted to 2^-64 units separately and added
+// modulo 2^64; the result is within one unit (5.4e-20 turns) of frac(f t) for
+// |f t| < 2^20.
 __device__ __forceinline__ uint64_t frac_turns_u64(double f, double t) {
     const double x = f * t;
     const double e = fma(f, t, -x);
-    const double fr = x - floor(x);                 // exact, in [0, 1)
-    const double h = fr - 0.5;                      // [-0.5, 0.5)
-    double hs = h * TWO_POW_64;                     // |hs| <= 2^63
-    hs = fmin(fmax(hs, -9.223372036854775808e18), 9.2233720368547748e18);
-    const int64_t ih = __double2ll_rn(hs);
+    double r = x - rint(x);                         // exact, in [-0.5, 0.5]
+    if (r >= 0.5) r -= 1.0;                         // same phase, keeps r * 2^64 inside int64
+    const int64_t ir = __double2ll_rn(r * TWO_POW_64);
     const int64_t ie = __double2ll_rn(e * TWO_POW_64);
-    return (uint64_t)ih + 0x8000000000000000ull + (uint64_t)ie;
+    return (uint64_t)ir + (uint64_t)ie;
 }
 
 // Signed turns in [-0.5, 0.5) of a fixed-point phase, as double (53 bits).
@@ -58,6 +58,30 @@ __device__ __forceinline__ void seed_from_table(const SeedTable &tab, uint64_t p
     const double tc = tab.c[k], ts = tab.s[k];
     *c = fma(tc, pc, -ts * ps);
     *s = fma(ts, pc, tc * ps);
+}
+
+// FP32 variant for the mixed kernel: table of e^{2 pi i k/256} rounded to FP32
+// and a Taylor polynomial of degree 3 (sin) / 4 (cos) on the remaining
+// < 1/256 turn (truncation < 1e-10); the low 32 bits of the phase are dropped
+// (< 1.5e-9 rad).
+struct SeedTableF { float2 cs[256]; };
+
+__device__ __forceinline__ void seed_from_table_f(const SeedTableF &tab, uint32_t ph_hi, float *s, float *c) {
+    const float2 t = tab.cs[ph_hi >> 24];
+    const float th = (float)(int32_t)(ph_hi & 0x00FFFFFFu) * TWO_PI_OVER_2_32;
+    const float t2 = th * th;
+    const float ps = th * fmaf(t2, -1.0f / 6.0f, 1.0f);
+    const float pc = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
+    *c = fmaf(t.x, pc, -t.y * ps);
+    *s = fmaf(t.y, pc, t.x * ps);
+}
+
+__device__ __forceinline__ void fill_seed_table_f(SeedTableF &tab) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        double s, c;
+        sincospi((double)k / 128.0, &s, &c);
+        tab.cs[k] = make_float2((float)c, (float)s);
+    }
 }
 
 __device__ __forceinline__ void fill_seed_table(SeedTable &tab) {

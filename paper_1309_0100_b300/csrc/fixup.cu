@@ -1,0 +1,132 @@
+// FP64 re-evaluation of the bins that the mixed kernel flagged as
+// ill-conditioned (a pivot of the 2x2 Schur complement below flag_tau times
+// its column norm: near a base frequency, near f = 0, or where <c^2> or <s^2>
+// is tiny).  There the FP32 sums lose too many digits to cancellation, so each
+// flagged bin is recomputed from the FP64 records: one CTA per bin, its threads
+// split the observations, every term takes its own FP64 seed from the exact
+// fixed-point phase, and the partial sums are combined by a fixed-order block
+// reduction.  Deterministic; the list order does not matter.
+#include <algorithm>
+
+#include "pgram_impl.cuh"
+
+namespace fredec {
+
+namespace {
+
+constexpr int FX_THREADS = 256;
+
+struct FixupParams {
+    const SeriesDesc *desc;
+    const SeriesState *state;
+    int nseries;                 // > 1: find the series of a global z index by binary search on z_off
+    const unsigned char *rec64;  // FP64 records (series offsets: desc.rec64_off)
+    const int64_t *list;         // global z indices
+    const int32_t *count;
+    double *z, *coef;
+};
+
+template <int P>
+__global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
+    constexpr int Q = 2 * P + 4;
+    __shared__ SeedTable tab;
+    __shared__ double red[FX_THREADS / 32][Q];
+    fill_seed_table(tab);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t n = *prm.count;
+    for (int32_t it = blockIdx.x; it < n; it += gridDim.x) {
+        const int64_t g = prm.list[it];
+        int s = 0;
+        if (prm.nseries > 1) {
+            int lo = 0, hi = prm.nseries - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prm.desc[mid].z_off <= g) lo = mid; else hi = mid - 1;
+            }
+            s = lo;
+        }
+        const SeriesDesc &d = prm.desc[s];
+        const SeriesState &st = prm.state[s];
+        const int64_t j = g - d.z_off;
+        double acc[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+        const double2 *R0 = reinterpret_cast<const double2 *>(prm.rec64 + d.rec64_off);
+        constexpr int RW2 = rec64_words(P) / 2;
+        for (int i = threadIdx.x; i < d.N; i += FX_THREADS) {
+            const double2 *r2 = R0 + (int64_t)i * RW2;
+            const ulonglong2 h = *reinterpret_cast<const ulonglong2 *>(r2);
+            const double2 ww = r2[2];
+            double s_, c_;
+            seed_from_table(tab, h.x + (uint64_t)j * h.y, &s_, &c_);
+            const double wc = ww.x * c_;
+#pragma unroll
+            for (int q2 = 0; q2 < (P + 1) / 2; ++q2) {
+                const double2 u = r2[3 + q2];
+                acc[2 * q2] = fma(u.x, c_, acc[2 * q2]);
+                acc[P + 2 * q2] = fma(u.x, s_, acc[P + 2 * q2]);
+                if (2 * q2 + 1 < P) {
+                    acc[2 * q2 + 1] = fma(u.y, c_, acc[2 * q2 + 1]);
+                    acc[P + 2 * q2 + 1] = fma(u.y, s_, acc[P + 2 * q2 + 1]);
+                }
+            }
+            acc[2 * P] = fma(ww.y, c_, acc[2 * P]);
+            acc[2 * P + 1] = fma(ww.y, s_, acc[2 * P + 1]);
+            acc[2 * P + 2] = fma(wc, c_, acc[2 * P + 2]);
+            acc[2 * P + 3] = fma(wc, s_, acc[2 * P + 3]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const double v = warp_sum_d(acc[q]);
+            if (lane == 0) red[wid][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S[Q];
+            for (int q = 0; q < Q; ++q) {
+                double v = 0.0;
+                for (int w = 0; w < FX_THREADS / 32; ++w) v += red[w][q];
+                S[q] = v;
+            }
+            double vcc = 0.0, vcs = 0.0, vss = 0.0;
+            for (int q = 0; q < P; ++q) {
+                vcc = fma(S[q], S[q], vcc);
+                vcs = fma(S[q], S[P + q], vcs);
+                vss = fma(S[P + q], S[P + q], vss);
+            }
+            const double CC = S[2 * P + 2];
+            double a, b, ratio;
+            prm.z[g] = solve2(CC, S[2 * P + 3], st.W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &b, &ratio);
+            if (prm.coef) {
+                prm.coef[2 * g] = a;
+                prm.coef[2 * g + 1] = b;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int P>
+void launch_fx(const FixupParams &prm, int grid, cudaStream_t st) {
+    fixup_kernel<P><<<grid, FX_THREADS, 0, st>>>(prm);
+}
+
+}  // namespace
+
+int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
+                      const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
+                      cudaStream_t st) {
+    FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef};
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 4LL * sm_count());
+    switch (p) {
+#define C(P) case P: launch_fx<P>(prm, grid, st); break;
+        C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
+#undef C
+        default: return fail(FREDEC_EINVAL, "unsupported base size");
+    }
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
+}  // namespace fredec

@@ -14,7 +14,7 @@ namespace fredec {
 
 constexpr int PMAX = 2 * FREDEC_MAX_NBASE + 1;      // base columns (constant + cos/sin pairs)
 constexpr int NTRI = PMAX * (PMAX + 1) / 2;         // packed lower triangle
-constexpr int PREP_THREADS = 128;                    // one point per thread per prep chunk
+constexpr int PREP_THREADS = 32;                     // one point per thread, one warp per prep chunk
 constexpr int TILE_POINTS = 128;                     // observation records per smem tile
 constexpr double DROP2 = 1e-14;                      // squared column-drop ratio (1e-7)^2
 
@@ -38,7 +38,6 @@ struct SeriesDesc {
     int64_t psi_off;     // into the psi scratch, doubles (p*N per series)
     int64_t z_off;       // into z (and 2*z_off into coef)
     int64_t chunk_off;   // first prep chunk of this series
-    int64_t flag_off;    // first FP64 re-evaluation flag word of this series
     double f0, df;       // uniform grid f_j = f0 + j df
     int64_t nf;
     int32_t N, nb, nchunks, p;
@@ -107,16 +106,16 @@ int launch_prep(const PrepPlan &pp, const double *t, const double *y, const doub
 struct PgramShape { int fpt; int warps; };
 PgramShape default_shape(int precision, int p, int64_t N, int64_t nf);
 bool shape_supported(int precision, int p, int fpt);
-// Single-series launch: z (and optional coef) for all nf grid points.
+// Single-series launch: z (and optional coef) for all nf grid points; the
+// mixed path appends ill-conditioned bins (global z indices) to flag_list.
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev,
                  const void *rec, int p, int N, int64_t nf, PgramShape shape, double flag_tau,
-                 double *z, double *coef, uint32_t *flag_bytes, int32_t *flag_list,
-                 int32_t *flag_count, int32_t *err, cudaStream_t st);
-// FP64 re-evaluation of the listed FP64 blocks.
-int launch_fixup(const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec64, int p,
-                 int N, int64_t nf, int fpt64, const int32_t *flag_list, const int32_t *flag_count,
-                 int64_t max_items, double *z, double *coef, int32_t *err, cudaStream_t st);
-int fixup_fpt(int p);
+                 double *z, double *coef, int64_t *flag_list, int32_t *flag_count, int32_t *err,
+                 cudaStream_t st);
+// FP64 re-evaluation of the listed bins (fixup.cu).
+int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
+                      const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
+                      cudaStream_t st);
 
 // Top-k local maxima (topk.cu); segmented over series.
 int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S, int k,

@@ -2,6 +2,7 @@
 // frequencies per thread F).  The kernels themselves are in pgram_impl.cuh and
 // are instantiated per P in pgram_p*.cu.
 #include <algorithm>
+#include <cstdlib>
 
 #include "fpt_options.h"
 #include "pgram_impl.cuh"
@@ -9,21 +10,31 @@
 namespace fredec {
 
 static thread_local cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
+
+// Mixed-kernel sin/cos seed: 0 = table-driven FP32 (default), 1 = MUFU.
+// FREDEC_SEED_MODE=1 in the environment selects the MUFU seed (comparison runs).
+static int seed_mode() {
+    static int m = -1;
+    if (m < 0) {
+        const char *e = std::getenv("FREDEC_SEED_MODE");
+        m = (e && e[0] == '1') ? 1 : 0;
+    }
+    return m;
+}
 void set_profile_events(cudaEvent_t a, cudaEvent_t b) { g_ev0 = a; g_ev1 = b; }
 void profile_events(cudaEvent_t *a, cudaEvent_t *b) { *a = g_ev0; *b = g_ev1; }
 
 #define FREDEC_DECL_P(P)                                                                              \
-    int launch_pgram_p##P(int, int, const PgramParams &, int64_t, int, int, int, cudaStream_t);     \
+    int launch_pgram_p##P(int, int, const PgramParams &, int64_t, int, cudaStream_t);               \
     size_t smem_pgram_p##P(int, int, int);
 FREDEC_DECL_P(1) FREDEC_DECL_P(3) FREDEC_DECL_P(5) FREDEC_DECL_P(7) FREDEC_DECL_P(9) FREDEC_DECL_P(11)
 FREDEC_DECL_P(13) FREDEC_DECL_P(15) FREDEC_DECL_P(17) FREDEC_DECL_P(19) FREDEC_DECL_P(21)
 FREDEC_DECL_P(23) FREDEC_DECL_P(25)
 #undef FREDEC_DECL_P
 
-static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, int list_mode,
-                    int grid_override, cudaStream_t st) {
+static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
     switch (p) {
-#define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, list_mode, grid_override, st);
+#define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, st);
         C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
     }
@@ -82,14 +93,9 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
     return s;
 }
 
-int fixup_fpt(int p) {
-    const FptOptions *o = options_for(p);
-    return o ? o->fp64[0] : 1;
-}
-
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,
-                 int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef,
-                 uint32_t *flag_words, int32_t *flag_list, int32_t *flag_count, int32_t *err, cudaStream_t st) {
+                 int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef, int64_t *flag_list,
+                 int32_t *flag_count, int32_t *err, cudaStream_t st) {
     (void)N;
     if (!shape_supported(precision, p, shape.fpt))
         return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, frequencies per thread)");
@@ -100,41 +106,18 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
     prm.rec = (const unsigned char *)rec;
     prm.z = z;
     prm.coef = coef;
-    prm.flag_tau = (precision == FREDEC_MIXED && flag_words) ? flag_tau : -1.0;
-    prm.flag_words = flag_words;
+    prm.flag_tau = (precision == FREDEC_MIXED && flag_list) ? flag_tau : -1.0;
     prm.flag_list = flag_list;
     prm.flag_count = flag_count;
-    prm.fpt64 = fixup_fpt(p);
     prm.err = err;
+    prm.seed_mode = seed_mode();
     const int64_t nblocks = (nf + 32LL * shape.fpt - 1) / (32LL * shape.fpt);
     cudaEvent_t e0, e1;
     profile_events(&e0, &e1);
     if (e0) cudaEventRecord(e0, st);
-    const int rc = dispatch(p, precision, shape.fpt, prm, nblocks, shape.warps, 0, 0, st);
+    const int rc = dispatch(p, precision, shape.fpt, prm, nblocks, shape.warps, st);
     if (e1) cudaEventRecord(e1, st);
     return rc < 0 ? fail(FREDEC_EINVAL, "kernel dispatch failed") : rc;
-}
-
-int launch_fixup(const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec64, int p, int N,
-                 int64_t nf, int fpt64, const int32_t *flag_list, const int32_t *flag_count, int64_t max_items,
-                 double *z, double *coef, int32_t *err, cudaStream_t st) {
-    (void)N;
-    (void)nf;
-    PgramParams prm{};
-    prm.desc = desc_dev;
-    prm.state = state_dev;
-    prm.rec = (const unsigned char *)rec64;
-    prm.z = z;
-    prm.coef = coef;
-    prm.flag_tau = -1.0;
-    prm.fpt64 = fpt64;
-    prm.err = err;
-    prm.items = flag_list;
-    prm.item_count = flag_count;
-    prm.use_rec64_off = 1;
-    const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 2LL * sm_count());
-    const int rc = dispatch(p, FREDEC_FP64, fpt64, prm, 0, 4, 1, grid, st);
-    return rc < 0 ? fail(FREDEC_EINVAL, "fixup dispatch failed") : rc;
 }
 
 }  // namespace fredec

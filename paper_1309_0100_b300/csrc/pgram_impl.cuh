@@ -36,14 +36,10 @@ struct PgramParams {
     double *z;                  // output base (series offsets in desc)
     double *coef;               // optional (a_j, b_j) output, same offsets * 2
     double flag_tau;            // mixed: FP64 re-evaluation threshold (< 0: never)
-    uint32_t *flag_words;       // mixed: one word per FP64 block, set when requested
-    int32_t *flag_list;         // mixed: compacted FP64 block requests (series-local block ids)
+    int64_t *flag_list;         // mixed: global z indices of bins to re-evaluate in FP64
     int32_t *flag_count;
-    int fpt64;                  // frequencies per thread of the FP64 re-evaluation kernel
     int32_t *err;               // FREDEC_ETIMEOUT on a bounded-wait timeout
-    const int32_t *items;       // list mode: block ids to process
-    const int32_t *item_count;  // list mode: number of ids
-    int use_rec64_off;          // records are the extra FP64 records (read at desc.rec64_off)
+    int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
 };
 
 template <int PREC> struct AccT;
@@ -64,7 +60,7 @@ struct PgramLayout {
     }
     static __host__ __device__ size_t off_table(int nw) { return align_up(OFF_RED + red_bytes(nw), 16); }
     static __host__ __device__ size_t smem_bytes(int nw) {
-        return off_table(nw) + (PREC == FREDEC_FP64 ? sizeof(SeedTable) : 0);
+        return off_table(nw) + (PREC == FREDEC_FP64 ? sizeof(SeedTable) : sizeof(SeedTableF));
     }
 };
 
@@ -104,45 +100,91 @@ __device__ __forceinline__ double solve2(double CC, double CS, double SS, double
     return z;
 }
 
+// The same 2x2 solve with one reciprocal, for well-conditioned bins:
+// theta = S^{-1} rho by the adjugate, z = 1/2 rho^T theta.  Returns false
+// (and leaves the outputs alone) when a pivot ratio is below tau, i.e. when
+// the bin must be re-evaluated in FP64; no divisions are spent on the test.
+__device__ __forceinline__ bool solve2_fast(double CC, double CS, double SS, double vcc, double vcs, double vss,
+                                            double Rc, double Rs, double tau, double *pz, double *pa, double *pb) {
+    const double S11 = CC - vcc, S12 = CS - vcs, S22 = SS - vss;
+    const double det = fma(S11, S22, -S12 * S12);
+    // pivot ratios S11/CC and (det/S11)/SS, and the column-norm balance
+    const bool ok = S11 >= tau * CC && det >= tau * S11 * SS && CC >= tau * (CC + SS) && SS >= tau * (CC + SS) &&
+                    det > 0.0;
+    if (!ok) return false;
+    const double inv = 1.0 / det;
+    const double a = (S22 * Rc - S12 * Rs) * inv;
+    const double b = (S11 * Rs - S12 * Rc) * inv;
+    *pa = a;
+    *pb = b;
+    *pz = 0.5 * fma(a, Rc, b * Rs);
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Inner loops: one observation record against this thread's F frequencies.
 
-template <int P, int F>
-__device__ __forceinline__ void mixed_point(const uint4 *__restrict__ r4, uint32_t j0,
-                                            float (&acc)[F][2 * P + 4]) {
+// One observation record, ready for the F-step loop: the seed cos/sin at the
+// thread's first frequency, the rotation, and the weighted values.
+template <int P>
+struct MixedPoint {
+    float c, s, cr, sr, w, wr;
+    float u[4 * ((P + 3) / 4)];
+};
+
+template <int P>
+__device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, int seed_mode,
+                                           uint32_t j0, MixedPoint<P> &pt) {
     const uint4 h = r4[0];
     const float4 m = *reinterpret_cast<const float4 *>(r4 + 1);
-    float u[4 * ((P + 3) / 4)];
 #pragma unroll
     for (int q4 = 0; q4 < (P + 3) / 4; ++q4) {
         const float4 v = reinterpret_cast<const float4 *>(r4 + 2)[q4];
-        u[4 * q4] = v.x;
-        u[4 * q4 + 1] = v.y;
-        u[4 * q4 + 2] = v.z;
-        u[4 * q4 + 3] = v.w;
+        pt.u[4 * q4] = v.x;
+        pt.u[4 * q4 + 1] = v.y;
+        pt.u[4 * q4 + 2] = v.z;
+        pt.u[4 * q4 + 3] = v.w;
     }
     const uint64_t A = ((uint64_t)h.y << 32) | h.x;
     const uint64_t B = ((uint64_t)h.w << 32) | h.z;
     const uint64_t ph = A + (uint64_t)j0 * B;          // exact phase (turns * 2^64) at f_{j0}
-    const float ang = (float)(int32_t)(ph >> 32) * TWO_PI_OVER_2_32;
-    float s, c;
-    __sincosf(ang, &s, &c);
-    const float cr = m.x, sr = m.y, w = m.z, wr = m.w;
+    if (seed_mode == 0) {
+        seed_from_table_f(tab, (uint32_t)(ph >> 32), &pt.s, &pt.c);
+    } else {
+        const float ang = (float)(int32_t)(ph >> 32) * TWO_PI_OVER_2_32;
+        __sincosf(ang, &pt.s, &pt.c);
+    }
+    pt.cr = m.x;
+    pt.sr = m.y;
+    pt.w = m.z;
+    pt.wr = m.w;
+}
+
+template <int P>
+__device__ __forceinline__ void mixed_sums(float c, float s, const MixedPoint<P> &pt, float (&a)[2 * P + 4]) {
+    const float wc = pt.w * c;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        a[q] = fmaf(pt.u[q], c, a[q]);
+        a[P + q] = fmaf(pt.u[q], s, a[P + q]);
+    }
+    a[2 * P] = fmaf(pt.wr, c, a[2 * P]);
+    a[2 * P + 1] = fmaf(pt.wr, s, a[2 * P + 1]);
+    a[2 * P + 2] = fmaf(wc, c, a[2 * P + 2]);
+    a[2 * P + 3] = fmaf(wc, s, a[2 * P + 3]);
+}
+
+// F consecutive frequencies of one point: sums at (c, s), then one rotation
+// by e^{i 2 pi df t'} to the next frequency.
+template <int P, int F>
+__device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, float (&acc)[F][2 * P + 4]) {
+    float c = pt.c, s = pt.s;
 #pragma unroll
     for (int k = 0; k < F; ++k) {
-        const float wc = w * c;
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            acc[k][q] = fmaf(u[q], c, acc[k][q]);
-            acc[k][P + q] = fmaf(u[q], s, acc[k][P + q]);
-        }
-        acc[k][2 * P] = fmaf(wr, c, acc[k][2 * P]);
-        acc[k][2 * P + 1] = fmaf(wr, s, acc[k][2 * P + 1]);
-        acc[k][2 * P + 2] = fmaf(wc, c, acc[k][2 * P + 2]);
-        acc[k][2 * P + 3] = fmaf(wc, s, acc[k][2 * P + 3]);
+        mixed_sums<P>(c, s, pt, acc[k]);
         if (k + 1 < F) {
-            const float cn = fmaf(c, cr, -s * sr);
-            s = fmaf(s, cr, c * sr);
+            const float cn = fmaf(c, pt.cr, -s * pt.sr);
+            s = fmaf(s, pt.cr, c * pt.sr);
             c = cn;
         }
     }
@@ -187,11 +229,11 @@ __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const
 
 // ---------------------------------------------------------------------------
 // One CTA-block of 32*F frequencies of one series.
-// use[2]: per-buffer mbarrier phase counters, identical in all threads.
+// use0/use1: per-buffer mbarrier phase counters, identical in all threads.
 
 template <int PREC, int P, int F>
 __device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
-                                            int64_t blk, unsigned char *smem, uint32_t (&use)[2]) {
+                                            int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
     using L = PgramLayout<PREC, P, F>;
     using T = typename AccT<PREC>::T;
     constexpr int Q = L::Q;
@@ -200,11 +242,12 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     unsigned char *tiles = smem + L::OFF_TILES;
     T *red = reinterpret_cast<T *>(smem + L::OFF_RED);
     const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + L::off_table(nw));
+    const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + L::off_table(nw));
 
     const int N = d.N;
     const int64_t jblock = blk * 32 * F;
     const uint32_t j0 = (uint32_t)(jblock + lane * F);
-    const unsigned char *src = prm.rec + (prm.use_rec64_off ? d.rec64_off : d.rec_off);
+    const unsigned char *src = prm.rec + d.rec_off;
     const int ntiles = (N + TILE_POINTS - 1) / TILE_POINTS;
 
     __syncthreads();   // previous block's epilogue is done with red / tiles
@@ -223,6 +266,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
 #pragma unroll
         for (int q = 0; q < Q; ++q) acc[k][q] = T(0);
 
+    // Second summation level: block sums of FLUSH_POINTS terms are added into
+    // the warp's running sums in shared memory (mixed: FP32 blocked summation).
     auto flush = [&]() {
         T *mine = red + (size_t)warp * Q * F * 32;
 #pragma unroll
@@ -237,22 +282,40 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     int since = 0;
     for (int tile = 0; tile < ntiles; ++tile) {
         const int b = tile & 1;
-        if (!mbar_wait_bounded(&bars[b], use[b] & 1u)) {
+        const uint32_t par = b ? (use1++ & 1u) : (use0++ & 1u);
+        if (!mbar_wait_bounded(&bars[b], par)) {
             if (lane == 0) atomicExch(prm.err, FREDEC_ETIMEOUT);
         }
-        ++use[b];
         const int n = min(TILE_POINTS, N - tile * TILE_POINTS);
         const unsigned char *tb = tiles + b * L::TILE_BYTES;
-        for (int i = warp; i < n; i += nw) {
-            if constexpr (PREC == FREDEC_MIXED) {
-                mixed_point<P, F>(reinterpret_cast<const uint4 *>(tb + (size_t)i * L::RB), j0, acc);
+        if constexpr (PREC == FREDEC_MIXED) {
+            // software pipeline: the next point's record and seed are fetched
+            // while the current point's F-step loop runs
+            // (two alternating point buffers, so nothing is copied)
+            MixedPoint<P> pa, pb;
+            auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(tb + (size_t)i * L::RB); };
+            int i = warp;
+            if (i < n) mixed_load<P>(rec(i), tabf, prm.seed_mode, j0, pa);
+            while (i < n) {
+                if (i + nw < n) mixed_load<P>(rec(i + nw), tabf, prm.seed_mode, j0, pb);
+                mixed_accumulate<P, F>(pa, acc);
                 if (++since == FLUSH_POINTS) {
                     flush();
                     since = 0;
                 }
-            } else {
-                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, acc);
+                i += nw;
+                if (i >= n) break;
+                if (i + nw < n) mixed_load<P>(rec(i + nw), tabf, prm.seed_mode, j0, pa);
+                mixed_accumulate<P, F>(pb, acc);
+                if (++since == FLUSH_POINTS) {
+                    flush();
+                    since = 0;
+                }
+                i += nw;
             }
+        } else {
+            for (int i = warp; i < n; i += nw)
+                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, acc);
         }
         __syncthreads();   // all warps are done with buffer b
         if (tid == 0 && tile + 2 < ntiles) {
@@ -275,9 +338,11 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         double S[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            double sq = 0.0;
-            for (int w = 0; w < nw; ++w) sq += (double)red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
-            S[q] = sq;
+            // warps' partial sums combined in the accumulation precision (a
+            // handful of terms), then one conversion to FP64 per sum
+            T sq = T(0);
+            for (int w = 0; w < nw; ++w) sq += red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
+            S[q] = (double)sq;
         }
         double vcc = 0.0, vcs = 0.0, vss = 0.0;
 #pragma unroll
@@ -287,19 +352,23 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             vss = fma(S[P + q], S[P + q], vss);
         }
         const double CC = S[2 * P + 2], CS = S[2 * P + 3];
-        double a, bb, ratio;
-        const double zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
+        double a, bb, zz;
+        bool done = false;
+        if (mixed_flags) {
+            done = solve2_fast(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], prm.flag_tau, &zz, &a, &bb);
+            if (!done) {   // ill-conditioned: provisional value now, FP64 re-evaluation later
+                const int32_t at = atomicAdd(prm.flag_count, 1);
+                prm.flag_list[at] = d.z_off + j;
+            }
+        }
+        if (!done) {
+            double ratio;
+            zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
+        }
         prm.z[d.z_off + j] = zz;
         if (prm.coef) {
             prm.coef[2 * (d.z_off + j)] = a;
             prm.coef[2 * (d.z_off + j) + 1] = bb;
-        }
-        if (mixed_flags && ratio < prm.flag_tau) {
-            const int64_t fb = j / (32 * prm.fpt64);
-            if (atomicExch(&prm.flag_words[d.flag_off + fb], 1u) == 0u) {
-                const int32_t at = atomicAdd(prm.flag_count, 1);
-                prm.flag_list[at] = (int32_t)fb;
-            }
         }
     }
 }
@@ -315,39 +384,41 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
     }
     if constexpr (PREC == FREDEC_FP64)
         fill_seed_table(*reinterpret_cast<SeedTable *>(smem + L::off_table(blockDim.x >> 5)));
+    else
+        fill_seed_table_f(*reinterpret_cast<SeedTableF *>(smem + L::off_table(blockDim.x >> 5)));
     __syncthreads();
 }
 
-// Grid kernel: one CTA per block of the single series desc[0], or (list mode)
-// a persistent grid over prm.items.
+// Minimum resident CTAs of 256 threads asked from the compiler: 2 (at most 128
+// registers, 16 warps per SM) when the F x (2P+4) accumulators leave room for
+// it, else 1.
 template <int PREC, int P, int F>
-__global__ void __launch_bounds__(256, 1) pgram_kernel(PgramParams prm, int list_mode) {
+constexpr int pgram_minb() { return (PREC == FREDEC_MIXED && F * (2 * P + 4) <= 80) ? 2 : 1; }
+
+// Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
+template <int PREC, int P, int F>
+__global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC, P, F>(smem);
     const SeriesDesc d = prm.desc[0];
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
-    uint32_t use[2] = {0u, 0u};
-    if (!list_mode) {
-        pgram_block<PREC, P, F>(prm, d, st, blockIdx.x, smem, use);
-    } else {
-        const int32_t n = *prm.item_count;
-        for (int32_t it = blockIdx.x; it < n; it += gridDim.x)
-            pgram_block<PREC, P, F>(prm, d, st, prm.items[it], smem, use);
-    }
+    uint32_t use0 = 0u, use1 = 0u;
+    pgram_block<PREC, P, F>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
 template <int PREC, int P, int F>
-int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, int list_mode, int grid_override,
-                   cudaStream_t st) {
+int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
     using L = PgramLayout<PREC, P, F>;
     const size_t smem = L::smem_bytes(warps);
+    if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     auto kern = pgram_kernel<PREC, P, F>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
-    const int64_t grid = list_mode ? grid_override : nblocks;
-    if (grid <= 0) return FREDEC_OK;
-    kern<<<(unsigned)grid, warps * 32, smem, st>>>(prm, list_mode);
+    if (nblocks <= 0) return FREDEC_OK;
+    kern<<<(unsigned)nblocks, warps * 32, smem, st>>>(prm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram launch: ") + cudaGetErrorString(e));
     return FREDEC_OK;

@@ -3,17 +3,14 @@
 
 namespace fredec {
 
-int launch_pgram_p19(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, int list_mode,
-                     int grid_override, cudaStream_t st) {
-    if (prec == FREDEC_MIXED && F == 2) return launch_pgram_t<FREDEC_MIXED, 19, 2>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_MIXED && F == 3) return launch_pgram_t<FREDEC_MIXED, 19, 3>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 19, 1>(prm, nblocks, warps, list_mode, grid_override, st);
+int launch_pgram_p19(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    if (prec == FREDEC_MIXED && F == 2) return launch_pgram_t<FREDEC_MIXED, 19, 2>(prm, nblocks, warps, st);
+    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 19, 1>(prm, nblocks, warps, st);
     return -1;
 }
 
 size_t smem_pgram_p19(int prec, int F, int warps) {
     if (prec == FREDEC_MIXED && F == 2) return pgram_smem_t<FREDEC_MIXED, 19, 2>(warps);
-    if (prec == FREDEC_MIXED && F == 3) return pgram_smem_t<FREDEC_MIXED, 19, 3>(warps);
     if (prec == FREDEC_FP64 && F == 1) return pgram_smem_t<FREDEC_FP64, 19, 1>(warps);
     return 0;
 }

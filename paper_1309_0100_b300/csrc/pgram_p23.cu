@@ -3,10 +3,9 @@
 
 namespace fredec {
 
-int launch_pgram_p23(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, int list_mode,
-                     int grid_override, cudaStream_t st) {
-    if (prec == FREDEC_MIXED && F == 2) return launch_pgram_t<FREDEC_MIXED, 23, 2>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 23, 1>(prm, nblocks, warps, list_mode, grid_override, st);
+int launch_pgram_p23(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    if (prec == FREDEC_MIXED && F == 2) return launch_pgram_t<FREDEC_MIXED, 23, 2>(prm, nblocks, warps, st);
+    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 23, 1>(prm, nblocks, warps, st);
     return -1;
 }
 

@@ -3,18 +3,19 @@
 
 namespace fredec {
 
-int launch_pgram_p5(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, int list_mode,
-                     int grid_override, cudaStream_t st) {
-    if (prec == FREDEC_MIXED && F == 6) return launch_pgram_t<FREDEC_MIXED, 5, 6>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_MIXED && F == 10) return launch_pgram_t<FREDEC_MIXED, 5, 10>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 5, 2>(prm, nblocks, warps, list_mode, grid_override, st);
-    if (prec == FREDEC_FP64 && F == 4) return launch_pgram_t<FREDEC_FP64, 5, 4>(prm, nblocks, warps, list_mode, grid_override, st);
+int launch_pgram_p5(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    if (prec == FREDEC_MIXED && F == 4) return launch_pgram_t<FREDEC_MIXED, 5, 4>(prm, nblocks, warps, st);
+    if (prec == FREDEC_MIXED && F == 8) return launch_pgram_t<FREDEC_MIXED, 5, 8>(prm, nblocks, warps, st);
+    if (prec == FREDEC_MIXED && F == 14) return launch_pgram_t<FREDEC_MIXED, 5, 14>(prm, nblocks, warps, st);
+    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 5, 2>(prm, nblocks, warps, st);
+    if (prec == FREDEC_FP64 && F == 4) return launch_pgram_t<FREDEC_FP64, 5, 4>(prm, nblocks, warps, st);
     return -1;
 }
 
 size_t smem_pgram_p5(int prec, int F, int warps) {
-    if (prec == FREDEC_MIXED && F == 6) return pgram_smem_t<FREDEC_MIXED, 5, 6>(warps);
-    if (prec == FREDEC_MIXED && F == 10) return pgram_smem_t<FREDEC_MIXED, 5, 10>(warps);
+    if (prec == FREDEC_MIXED && F == 4) return pgram_smem_t<FREDEC_MIXED, 5, 4>(warps);
+    if (prec == FREDEC_MIXED && F == 8) return pgram_smem_t<FREDEC_MIXED, 5, 8>(warps);
+    if (prec == FREDEC_MIXED && F == 14) return pgram_smem_t<FREDEC_MIXED, 5, 14>(warps);
     if (prec == FREDEC_FP64 && F == 2) return pgram_smem_t<FREDEC_FP64, 5, 2>(warps);
     if (prec == FREDEC_FP64 && F == 4) return pgram_smem_t<FREDEC_FP64, 5, 4>(warps);
     return 0;

@@ -115,17 +115,23 @@ extern "C" int fredec_tune(int32_t precision, int32_t n_base, int64_t N, int64_t
                 o.warps = warps_opts[b];
                 o.flag_tau = -1.0;
                 float ms_min = 1e30f;
-                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                bool skip = false;
+                for (int rep = 0; rep < 3 && !rc && !skip; ++rep) {
                     cudaEventRecord(e0, st);
                     rc = fredec_periodogram_dev(t, y, s, N, base, n_base, 1e-4, 2e-6, nf, &o, out.as<double>(),
                                                 nullptr, nullptr, nullptr, st);
+                    if (rc == FREDEC_EINVAL) {   // shape does not fit (shared memory): not a candidate
+                        rc = FREDEC_OK;
+                        skip = true;
+                        break;
+                    }
                     cudaEventRecord(e1, st);
                     cudaEventSynchronize(e1);
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (rep > 0) ms_min = std::fmin(ms_min, ms);
                 }
-                if (!rc && ms_min < best_ms) {
+                if (!rc && !skip && ms_min < best_ms) {
                     best_ms = ms_min;
                     best = PgramShape{fpts[a], warps_opts[b]};
                 }
