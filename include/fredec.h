@@ -147,6 +147,33 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
                                const double *coef, const double *info, const double *v,
                                int32_t precision, double *dldy_out, void *stream);
 
+/*
+ * No-allocation variant of fredec_periodogram_dev (z and info only; the paper
+ * has no counterpart).  For callers that cannot allocate device memory when
+ * they call -- applications whose device memory is reserved up front by their
+ * own allocator, real-time loops that forbid allocation after start-up,
+ * plug-in hosts that keep extension code away from the CUDA allocator -- it
+ * calls no allocator: all of its scratch lives in one 16 MiB device array
+ * compiled into the library, held on every GPU that loads the library until
+ * the process exits.
+ *   - Same arguments and results as fredec_periodogram_dev without top-k
+ *     (opts->topk must be 0) and without coefficients.
+ *   - Scratch needed (p = 2*n_base + 1): about N*(16p + 50 + p*p/8) bytes for
+ *     FREDEC_FP64; FREDEC_MIXED adds N*(4p + 32) bytes of FP32 records and
+ *     8*nf bytes for its FP64 re-evaluation list.  A problem that does not
+ *     fit in 16 MiB is rejected with FREDEC_EINVAL and a message giving the
+ *     required and available byte counts.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call reuses the same array and clears what must start at zero;
+ *     calls whose work overlaps on the GPU (unordered streams or threads) race
+ *     on it and must be serialised by the caller.
+ */
+int fredec_periodogram_noalloc_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                                   const double *base_freqs, int32_t n_base,
+                                   double f0, double df, int64_t nf, const fredec_opts *opts,
+                                   double *z_out, double *info_out, void *stream);
+
 /* Host-pointer variant of the VJP on a uniform grid (recomputes the forward). */
 int fredec_periodogram_vjp(const double *t, const double *y, const double *sigma, int64_t N,
                            const double *base_freqs, int32_t n_base,

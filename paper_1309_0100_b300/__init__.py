@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
         "fredec_tune": (ctypes.c_int, [i32, i32, i64, i64, _c_i32p, _c_i32p]),
         "fredec_profile_events": (ctypes.c_int, [_vp, _vp]),
         "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
+        "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
+                                                          ctypes.POINTER(Opts), _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
