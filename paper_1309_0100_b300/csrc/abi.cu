@@ -365,6 +365,68 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
     return FREDEC_OK;
 }
 
+int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                               const double *base_freqs, int32_t n_base, double f0, double df, int64_t nf,
+                               const double *coef, const double *info, const double *v, int32_t precision,
+                               double *dldy_out, void *stream) {
+    (void)info;   // the time origin is recomputed identically from the same inputs
+    if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
+    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || !dldy_out || (nf > 0 && (!coef || !v)))
+        return fail(FREDEC_EINVAL, "null pointer argument");
+    if (!std::isfinite(f0) || !std::isfinite(df)) return fail(FREDEC_EINVAL, "f0 and df must be finite");
+    return launch_vjp_pipeline(t, y, sigma, N, base_freqs, n_base, f0, df, nf, coef, v, precision, dldy_out,
+                               (cudaStream_t)stream);
+}
+
+int fredec_periodogram_vjp(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
+                           int32_t n_base, double f0, double df, int64_t nf, const double *v, int32_t precision,
+                           double *dldy_out) {
+    if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
+    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (int rc = check_series_host(t, y, sigma, N, base_freqs, n_base)) return rc;
+    if (!dldy_out || (nf > 0 && !v)) return fail(FREDEC_EINVAL, "null pointer argument");
+    if (!std::isfinite(f0) || !std::isfinite(df) || (nf > 0 && !finite_all(v, nf)))
+        return fail(FREDEC_EINVAL, "f0, df and v must be finite");
+    HostStream hs;
+    if (int rc = hs.make()) return rc;
+    cudaStream_t st = hs.s;
+    int rc = FREDEC_OK;
+    {
+        DevBuf io;
+        if ((rc = io.alloc((3 * N + n_base + nf + 2 * nf + N + 8) * 8, st))) return rc;
+        double *d = io.as<double>();
+        double *dt = d, *dy = d + N, *ds = d + 2 * N, *db = d + 3 * N, *dv = db + n_base, *dcoef = dv + nf,
+               *dout = dcoef + 2 * nf, *dinfo = dout + N;
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(dt, t, N * 8, cudaMemcpyHostToDevice, st));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(dy, y, N * 8, cudaMemcpyHostToDevice, st));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(ds, sigma, N * 8, cudaMemcpyHostToDevice, st));
+        if (n_base) FREDEC_CUDA_TRY(cudaMemcpyAsync(db, base_freqs, n_base * 8, cudaMemcpyHostToDevice, st));
+        if (nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(dv, v, nf * 8, cudaMemcpyHostToDevice, st));
+        fredec_opts o;
+        fredec_opts_init(&o);
+        o.precision = precision;
+        const SeriesState *state = nullptr;
+        {
+            DevBuf ws;
+            SingleWork w;
+            DevBuf zbuf;
+            if ((rc = zbuf.alloc(std::max<int64_t>(nf, 1) * 8, st))) return rc;
+            if ((rc = periodogram_core(dt, dy, ds, N, db, n_base, f0, df, nf, o, zbuf.as<double>(), dinfo, nullptr,
+                                       dcoef, st, ws, w)))
+                return rc;
+            state = w.state;
+            if ((rc = finish_host(st, state, w.err))) return rc;
+        }
+        if ((rc = launch_vjp_pipeline(dt, dy, ds, N, db, n_base, f0, df, nf, dcoef, dv, precision, dout, st)))
+            return rc;
+        FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+        FREDEC_CUDA_TRY(cudaMemcpy(dldy_out, dout, N * 8, cudaMemcpyDeviceToHost));
+    }
+    FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+    return FREDEC_OK;
+}
+
 int fredec_periodogram(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
                        int32_t n_base, const double *f_grid, int64_t nf, double *z_out) {
     return fredec_periodogram_ex(t, y, sigma, N, base_freqs, n_base, f_grid, nf, nullptr, z_out, nullptr, nullptr,

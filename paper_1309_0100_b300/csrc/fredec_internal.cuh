@@ -122,10 +122,10 @@ int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S,
                 int64_t *idx_out, cudaStream_t st);
 int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st);
 
-// VJP (vjp.cu)
-int launch_vjp(const SeriesDesc *desc_dev, const SeriesState *state_dev, const double *t,
-               const double *sigma, const double *psi, int p, int N, double f0, double df, int64_t nf,
-               const double *coef, const double *v, int precision, double *dldy, cudaStream_t st);
+// VJP (vjp.cu): dL/dy for one series on a uniform grid, all pointers device.
+int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, int64_t N, const double *base, int nb,
+                        double f0, double df, int64_t nf, const double *coef, const double *v, int precision,
+                        double *dldy, cudaStream_t st);
 
 // Tuples (tuple.cu)
 int tuple_eval_dev(const double *t, const double *y, const double *sigma, int64_t N,

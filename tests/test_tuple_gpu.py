@@ -1,0 +1,91 @@
+"""GPU parity of the multifrequency tuple statistics (constant base) against
+the FP64 oracle: z for arbitrary tuples, the all-subtuple l table of a
+candidate pool, dz/df (adjoint sums) against the oracle and against central
+finite differences of z (step 1e-7/T), and Gauss-Newton refinement."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    ensure_built()
+    import paper_1309_0100_b300 as F
+    return F
+
+
+def _series(k, N=300, span=200.0):
+    rng = np.random.default_rng(900 + k)
+    t = np.sort(rng.uniform(0, span, N))
+    sigma = rng.lognormal(0, 0.4, N)
+    fr = np.array([0.0731, 0.151, 0.33, 0.0123])
+    y = 2.0 + sum(a * np.sin(2 * np.pi * f * t + p) for a, f, p in zip([4, 3, 2, 1.5], fr, [0.1, 1.2, 2.2, 0.7]))
+    return t, y + sigma * rng.standard_normal(N), sigma, fr
+
+
+def test_tuple_eval_vs_oracle(F):
+    t, y, s, fr = _series(1)
+    tuples = [[fr[0]], [fr[0], fr[1]], [fr[2], fr[1], 0.47], list(fr), [0.2, 0.21, 0.4, 0.41, 0.6]]
+    z, l0 = F.tuple_eval(t, y, s, tuples)
+    zr, l0r = oracle.tuple_eval(t, y, s, tuples)
+    assert l0 == pytest.approx(l0r, rel=1e-12)
+    np.testing.assert_allclose(z, zr, rtol=1e-10)
+
+
+@pytest.mark.parametrize("n,N", [(5, 120), (8, 257)])
+def test_pool_table_vs_oracle(F, n, N):
+    t, y, s, fr = _series(2 + n, N=N)
+    pool = np.concatenate([fr, np.linspace(0.05, 0.45, n - 4) + 0.003])[:n]
+    tab = F.pool_subtuples_eval(t, y, s, pool)
+    ref = oracle.pool_table(t, y, s, pool)
+    np.testing.assert_allclose(tab, ref, rtol=1e-10)
+
+
+def test_pool_table_config4_sampled(F):
+    s = synth.config4()
+    tab = F.pool_subtuples_eval(s.t, s.y, s.sigma, s.pool)
+    assert tab.size == 1 << 16
+    rng = np.random.default_rng(4)
+    for mask in np.concatenate([[0, 1, 0xFFFF, 0x003F], rng.integers(0, 1 << 16, 40)]):
+        fr = [s.pool[k] for k in range(16) if int(mask) >> k & 1]
+        lr = oracle.tuple_l(s.t, s.y, s.sigma, fr)
+        assert tab[mask] == pytest.approx(lr, rel=1e-9), mask
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 2e-4)])
+def test_tuple_grad_vs_oracle_and_fd(F, prec, tol):
+    t, y, s, fr = _series(3)
+    tuples = [[fr[0] + 0.0004], [fr[0] - 0.0003, fr[1] + 0.0002], [fr[2] + 0.0001, 0.47, fr[3]]]
+    z, g = F.tuple_grad(t, y, s, tuples, precision=prec)
+    zr, gr = oracle.tuple_grad(t, y, s, tuples)
+    assert np.max(np.abs(z - zr) / zr) < (1e-10 if prec == "fp64" else 1e-5)
+    assert np.max(np.abs(g - gr)) <= tol * np.max(np.abs(gr))
+    if prec == "fp64":
+        T = t.max() - t.min()
+        h = 1e-7 / T
+        k = 0
+        for tp in tuples:
+            for q in range(len(tp)):
+                a = list(tp); b = list(tp)
+                a[q] += h; b[q] -= h
+                fd = (F.tuple_eval(t, y, s, [a])[0][0] - F.tuple_eval(t, y, s, [b])[0][0]) / (2 * h)
+                assert abs(fd - g[k]) <= 1e-6 * max(abs(g[k]), 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
+                k += 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tuple_refine_vs_oracle(F, prec):
+    t, y, s, fr = _series(5)
+    T = t.max() - t.min()
+    starts = [[fr[0] + 0.2 / T], [fr[0] - 0.15 / T, fr[1] + 0.25 / T], [fr[0] + 0.1 / T, fr[1], fr[2] - 0.2 / T]]
+    got_f, got_l, its = F.tuple_refine(t, y, s, starts, max_iter=30, tol=1e-10, precision=prec)
+    for st, gf, gl in zip(starts, got_f, got_l):
+        rf, rl, _ = oracle.tuple_refine(t, y, s, st, max_iter=60, tol=1e-12)
+        ftol = (1e-7 if prec == "fp64" else 1e-4) / T
+        assert np.max(np.abs(gf - rf)) < ftol, (gf - rf) * T
+        assert gl == pytest.approx(rl, rel=1e-10 if prec == "fp64" else 1e-6)
