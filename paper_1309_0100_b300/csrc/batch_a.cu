@@ -1,0 +1,16 @@
+// Batch kernels for base sizes up to p = 5.
+#include "batch_impl.cuh"
+
+namespace fredec {
+
+int launch_batch_p5(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st) {
+    return prec == FREDEC_MIXED ? launch_batch_t<FREDEC_MIXED, 5>(bp, warps, grid, st)
+                                : launch_batch_t<FREDEC_FP64, 5>(bp, warps, grid, st);
+}
+
+int batch_occupancy_p5(int prec, int warps) {
+    return prec == FREDEC_MIXED ? batch_blocks_per_sm<FREDEC_MIXED, 5>(warps)
+                                : batch_blocks_per_sm<FREDEC_FP64, 5>(warps);
+}
+
+}  // namespace fredec

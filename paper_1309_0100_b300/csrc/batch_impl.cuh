@@ -1,0 +1,104 @@
+// Persistent periodogram kernel for a batch of series: CTAs take work items
+// (series, block of 32*F frequencies) from a device counter until the list is
+// exhausted; each item runs the same block routine as the single-series
+// kernel, with F fixed per base size P (a switch over the sizes of the class).
+#pragma once
+
+#include "pgram_impl.cuh"
+
+namespace fredec {
+
+// Frequencies per thread used by the batch kernels for each base size: the
+// largest that keeps a thread at about 128 registers (mixed) or the FP64
+// default.
+__host__ __device__ constexpr int batch_fpt(int prec, int p) {
+    return prec == FREDEC_MIXED ? (p == 1 ? 12 : p == 3 ? 8 : p <= 7 ? 4 : p <= 11 ? 3 : p <= 15 ? 2 : 1) : (p <= 5 ? 2 : 1);
+}
+
+struct BatchParams {
+    PgramParams prm;
+    const int2 *items;      // (series, block)
+    int64_t n_items;
+    unsigned long long *counter;
+};
+
+template <int PREC, int P>
+__device__ __forceinline__ void batch_item(const BatchParams &bp, const SeriesDesc &d, const SeriesState &st,
+                                           int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
+    constexpr int F = batch_fpt(PREC, P);
+    if (st.status != FREDEC_OK) {
+        for (int fs = threadIdx.x; fs < 32 * F; fs += blockDim.x) {
+            const int64_t j = blk * 32 * F + fs;
+            if (j < d.nf) bp.prm.z[d.z_off + j] = NAN;
+        }
+        return;
+    }
+    pgram_block<PREC, P, F>(bp.prm, d, st, blk, smem, use0, use1);
+}
+
+// Resident CTAs of 128 threads asked from the compiler: 3 for the small-base
+// class (about 170 registers), 2 when large base sizes are compiled in.
+template <int PMAXC>
+constexpr int batch_minb() { return PMAXC <= 5 ? 3 : 2; }
+
+template <int PREC, int PMAXC>
+__global__ void __launch_bounds__(128, batch_minb<PMAXC>()) pgram_batch_kernel(BatchParams bp) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ long long cur;
+    pgram_cta_init<PREC>(smem);
+    uint32_t use0 = 0u, use1 = 0u;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (long long)atomicAdd(bp.counter, 1ull);
+        __syncthreads();
+        const long long it = cur;
+        if (it >= bp.n_items) break;
+        const int2 w = bp.items[it];
+        const SeriesDesc d = bp.prm.desc[w.x];
+        const SeriesState &st = bp.prm.state[w.x];
+        switch (d.p) {
+            case 1: batch_item<PREC, 1>(bp, d, st, w.y, smem, use0, use1); break;
+            case 3: batch_item<PREC, 3>(bp, d, st, w.y, smem, use0, use1); break;
+            case 5: batch_item<PREC, 5>(bp, d, st, w.y, smem, use0, use1); break;
+#define C(P) case P: if constexpr (PMAXC >= P) batch_item<PREC, P>(bp, d, st, w.y, smem, use0, use1); break;
+            C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
+#undef C
+            default: break;
+        }
+        __syncthreads();   // all threads have read cur before it is replaced
+    }
+}
+
+template <int PREC, int PMAXC>
+size_t batch_smem(int warps) {
+    size_t m = 0;
+    auto upd = [&](size_t v) { m = v > m ? v : m; };
+    upd(PgramLayout<PREC, 1, batch_fpt(PREC, 1)>::smem_bytes(warps));
+    upd(PgramLayout<PREC, 3, batch_fpt(PREC, 3)>::smem_bytes(warps));
+    upd(PgramLayout<PREC, 5, batch_fpt(PREC, 5)>::smem_bytes(warps));
+#define C(P) if (PMAXC >= P) upd(PgramLayout<PREC, P, batch_fpt(PREC, P)>::smem_bytes(warps));
+    C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
+#undef C
+    return m;
+}
+
+template <int PREC, int PMAXC>
+int launch_batch_t(const BatchParams &bp, int warps, int grid, cudaStream_t st) {
+    const size_t smem = batch_smem<PREC, PMAXC>(warps);
+    auto kern = pgram_batch_kernel<PREC, PMAXC>;
+    FREDEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, warps * 32, smem, st>>>(bp);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
+template <int PREC, int PMAXC>
+int batch_blocks_per_sm(int warps) {
+    int n = 0;
+    const size_t smem = batch_smem<PREC, PMAXC>(warps);
+    auto kern = pgram_batch_kernel<PREC, PMAXC>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, warps * 32, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+}  // namespace fredec

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
         }
         const SeriesDesc &d = prm.desc[s];
         const SeriesState &st = prm.state[s];
+        if (d.p != P) continue;   // batches: another launch handles this base size
         const int64_t j = g - d.z_off;
         double acc[Q];
 #pragma unroll

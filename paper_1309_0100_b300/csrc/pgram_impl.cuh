@@ -27,7 +27,11 @@
 
 namespace fredec {
 
-constexpr int FLUSH_POINTS = 256;   // mixed: FP32 partials are flushed to shared sums every 256 points
+// Mixed path: FP32 block sums over 32 points are flushed into the warp's shared
+// running sums.  Short first-level blocks keep the FP32 rounding of
+// random-phase sums near a few ulps (measured: worst z error about 2x lower than
+// with 256-point blocks, for about 5% more instructions).
+constexpr int FLUSH_POINTS = 32;
 
 struct PgramParams {
     const SeriesDesc *desc;
@@ -48,20 +52,23 @@ template <> struct AccT<FREDEC_FP64> { using T = double; };
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Shared memory of a CTA: [mbarriers | seed table | 2 record tiles | warp
+// partial sums].  The seed table sits at a fixed offset (independent of P and
+// F) so that persistent kernels switching between (P, F) fill it once.
+constexpr size_t OFF_TABLE = 128;
+constexpr size_t OFF_TILES_BASE = OFF_TABLE + sizeof(SeedTable);
+
 template <int PREC, int P, int F>
 struct PgramLayout {
     static constexpr int Q = 2 * P + 4;
     static constexpr int RB = rec_bytes(P, PREC);
     static constexpr size_t TILE_BYTES = (size_t)TILE_POINTS * RB;
-    static constexpr size_t OFF_TILES = 128;
+    static constexpr size_t OFF_TILES = OFF_TILES_BASE;
     static constexpr size_t OFF_RED = OFF_TILES + 2 * TILE_BYTES;
     static __host__ __device__ size_t red_bytes(int nw) {
         return (size_t)nw * Q * F * 32 * sizeof(typename AccT<PREC>::T);
     }
-    static __host__ __device__ size_t off_table(int nw) { return align_up(OFF_RED + red_bytes(nw), 16); }
-    static __host__ __device__ size_t smem_bytes(int nw) {
-        return off_table(nw) + (PREC == FREDEC_FP64 ? sizeof(SeedTable) : sizeof(SeedTableF));
-    }
+    static __host__ __device__ size_t smem_bytes(int nw) { return OFF_RED + red_bytes(nw); }
 };
 
 // Per-frequency 2x2 solve in FP64.  Returns z; writes the joint-fit
@@ -241,8 +248,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     unsigned char *tiles = smem + L::OFF_TILES;
     T *red = reinterpret_cast<T *>(smem + L::OFF_RED);
-    const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + L::off_table(nw));
-    const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + L::off_table(nw));
+    const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + OFF_TABLE);
+    const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + OFF_TABLE);
 
     const int N = d.N;
     const int64_t jblock = blk * 32 * F;
@@ -373,9 +380,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     }
 }
 
-template <int PREC, int P, int F>
+template <int PREC>
 __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
-    using L = PgramLayout<PREC, P, F>;
     if (threadIdx.x == 0) {
         uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
         mbar_init(&bars[0], 1);
@@ -383,9 +389,9 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
         fence_mbar_init();
     }
     if constexpr (PREC == FREDEC_FP64)
-        fill_seed_table(*reinterpret_cast<SeedTable *>(smem + L::off_table(blockDim.x >> 5)));
+        fill_seed_table(*reinterpret_cast<SeedTable *>(smem + OFF_TABLE));
     else
-        fill_seed_table_f(*reinterpret_cast<SeedTableF *>(smem + L::off_table(blockDim.x >> 5)));
+        fill_seed_table_f(*reinterpret_cast<SeedTableF *>(smem + OFF_TABLE));
     __syncthreads();
 }
 
@@ -399,7 +405,7 @@ constexpr int pgram_minb() { return (PREC == FREDEC_MIXED && F * (2 * P + 4) <= 
 template <int PREC, int P, int F>
 __global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
-    pgram_cta_init<PREC, P, F>(smem);
+    pgram_cta_init<PREC>(smem);
     const SeriesDesc d = prm.desc[0];
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;

@@ -7,6 +7,7 @@
 // deterministic block argmax); stage 2: one CTA per series merges its chunks'
 // candidates the same way.  The result does not depend on scheduling.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "fredec_internal.cuh"
@@ -122,6 +123,60 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
 }
 
 }  // namespace
+
+// Plan-time part of the segmented top-k: chunk metadata, uploaded once.
+int topk_plan_bytes(const int64_t *nf_h, int S, int k, int64_t *nchunks_out) {
+    int64_t nch = 0;
+    for (int s = 0; s < S; ++s) nch += std::max<int64_t>(1, (nf_h[s] + TK_CHUNK - 1) / TK_CHUNK);
+    *nchunks_out = nch;
+    return (int)0;
+}
+
+size_t topk_plan_size(int S, int64_t nch, int k) { return nch * 4 + nch * 8 + (S + 1) * 8 + 2 * S * 8 + nch * k * 16 + 256; }
+
+// Upload the metadata into dev (topk_plan_size bytes, synchronous) and return
+// the argument block for topk_plan_launch.
+int topk_plan_make(const int64_t *z_off_h, const int64_t *nf_h, int S, int k, int64_t *idx_out, const double *z,
+                   unsigned char *dev, void *args_out) {
+    std::vector<int32_t> cs;
+    std::vector<int64_t> cb, coff(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        const int64_t nc = std::max<int64_t>(1, (nf_h[s] + TK_CHUNK - 1) / TK_CHUNK);
+        coff[s + 1] = coff[s] + nc;
+        for (int64_t c = 0; c < nc; ++c) {
+            cs.push_back(s);
+            cb.push_back(c * TK_CHUNK);
+        }
+    }
+    const int64_t nch = coff[S];
+    unsigned char *p = dev;
+    int64_t *d_cb = (int64_t *)p; p += nch * 8;
+    int64_t *d_coff = (int64_t *)p; p += (S + 1) * 8;
+    int64_t *d_zoff = (int64_t *)p; p += S * 8;
+    int64_t *d_nf = (int64_t *)p; p += S * 8;
+    double *d_cz = (double *)p; p += nch * k * 8;
+    int64_t *d_cj = (int64_t *)p; p += nch * k * 8;
+    int32_t *d_cs = (int32_t *)p;
+    FREDEC_CUDA_TRY(cudaMemcpy(d_cb, cb.data(), nch * 8, cudaMemcpyHostToDevice));
+    FREDEC_CUDA_TRY(cudaMemcpy(d_coff, coff.data(), (S + 1) * 8, cudaMemcpyHostToDevice));
+    FREDEC_CUDA_TRY(cudaMemcpy(d_zoff, z_off_h, S * 8, cudaMemcpyHostToDevice));
+    FREDEC_CUDA_TRY(cudaMemcpy(d_nf, nf_h, S * 8, cudaMemcpyHostToDevice));
+    FREDEC_CUDA_TRY(cudaMemcpy(d_cs, cs.data(), nch * 4, cudaMemcpyHostToDevice));
+    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0};
+    static_assert(sizeof(TopkArgs) <= 256, "args block");
+    std::memcpy(args_out, &a, sizeof(a));
+    return FREDEC_OK;
+}
+
+// Kernel launches only (capturable).
+int topk_plan_launch(const void *args, int64_t nch, int S, cudaStream_t st) {
+    TopkArgs a;
+    std::memcpy(&a, args, sizeof(a));
+    topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
+    topk_stage2<<<(unsigned)S, TK_THREADS, 0, st>>>(a);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
 
 int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, int S, int k, int64_t *idx_out,
                 cudaStream_t st) {

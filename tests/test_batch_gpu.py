@@ -1,0 +1,87 @@
+"""Batched periodograms (one plan, one persistent launch, CUDA graph replay)
+must reproduce the single-series results for every series, with uneven
+lengths, grid sizes and base sizes; replays are deterministic."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import ensure_built, local_max_topk, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def F():
+    ensure_built()
+    import paper_1309_0100_b300 as F
+    return F
+
+
+def _batch(n=24, seed=0, nbs=(0, 1, 2, 3, 5, 7)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nb = nbs[k % len(nbs)]
+        N = int(rng.integers(2 * nb + 10, 700))
+        nf = int(rng.integers(1, 3000))
+        out.append(synth.small_series(500 + 7 * k + seed, N=N, n_base=nb, nf=nf, span=float(rng.uniform(50, 500)),
+                                      fmax=float(rng.uniform(0.3, 2.0))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch_ref():
+    """The batch and, per series, the oracle's z and conditioning ratios."""
+    series = _batch()
+    ref = [oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), want_ratio=True) for s in series]
+    return series, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_vs_oracle_and_single_series(F, prec, batch_ref):
+    series, ref = batch_ref
+    z, zo, top = F.periodogram_batch(series, precision=prec, topk=3)
+    for k, s in enumerate(series):
+        zr, _, ratio = ref[k]
+        got = z[zo[k]:zo[k] + s.grid.nf]
+        assert rel_err(got, zr, ratio >= 1e-2) < TOL[prec], k
+        zs = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), precision=prec)
+        assert rel_err(got, zs, ratio >= 1e-2) < TOL[prec], k
+        if prec == "fp64":
+            assert list(top[k]) == local_max_topk(zr, 3)
+
+
+def test_plan_replay_deterministic(F):
+    import torch
+    series = _batch(12, seed=5, nbs=(0, 1, 2))
+    plan = F.BatchPlan(series, precision="mixed", topk=2)
+    plan.run()
+    torch.cuda.synchronize()
+    z1, t1 = plan.download()
+    plan.run()
+    plan.run()
+    torch.cuda.synchronize()
+    z2, t2 = plan.download()
+    assert np.array_equal(z1, z2) and np.array_equal(t1, t2)
+    zb, zo, tb = F.periodogram_batch(series, precision="mixed", topk=2)
+    assert rel_err(z1, zb) < 1e-5
+    plan.close()
+
+
+def test_batch_large_base_classes(F):
+    """Base sizes p = 13, 19 and 25 select the larger compiled classes."""
+    series = _batch(6, seed=9, nbs=(0,))
+    rng = np.random.default_rng(17)
+    for k, nb in enumerate((6, 9, 12, 6, 9, 12)):
+        s = series[k]
+        T = s.t.max() - s.t.min()
+        s.base_freqs = np.sort(rng.uniform(0.02, 0.9, nb)) + np.arange(nb) * 4.0 / T   # separated by > 4/T
+        s.t, s.y, s.sigma = s.t, s.y, s.sigma
+    for prec in ("fp64", "mixed"):
+        z, zo, _ = F.periodogram_batch(series, precision=prec)
+        for k, s in enumerate(series):
+            zr, _, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), want_ratio=True)
+            assert rel_err(z[zo[k]:zo[k] + s.grid.nf], zr, ratio >= 1e-2) < TOL[prec], (prec, k)
