@@ -225,6 +225,21 @@ int fredec_tuple_refine(const double *t, const double *y, const double *sigma, i
                         int32_t max_iter, double tol, int32_t precision,
                         double *l_out, int32_t *iters_out);
 
+/*
+ * Local refinement of subtuples of a candidate pool (Phase 2 of Section 4 with
+ * the local fits of Section 3): masks[k] selects the pool frequencies of tuple
+ * k (bit j = pool[j]); each tuple is refined as in fredec_tuple_refine,
+ * starting from its pool frequencies.  f_out[k * n_pool + j] receives the
+ * refined frequency of pool member j in tuple k (0 where bit j is clear);
+ * l_out[k] the final l; iters_out[k] (may be NULL) the iterations.  The exact
+ * cos/sin at the pool frequencies are computed once for all tuples.
+ * n_pool <= FREDEC_MAX_TUPLE.
+ */
+int fredec_pool_refine(const double *t, const double *y, const double *sigma, int64_t N,
+                       const double *pool, int32_t n_pool, const uint32_t *masks, int64_t n_masks,
+                       int32_t max_iter, double tol, int32_t precision,
+                       double *f_out, double *l_out, int32_t *iters_out);
+
 /* ------------------------------------------------------------------------ */
 /* Batched residual periodograms (many series, one persistent launch)        */
 

@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
     "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
-    "tuple_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
+    "tuple_refine", "pool_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
 ]
 
 FP64 = 0
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
         "fredec_batch_plan_destroy": (None, [_vp]),
         "fredec_tune": (ctypes.c_int, [i32, i32, i64, i64, _c_i32p, _c_i32p]),
         "fredec_profile_events": (ctypes.c_int, [_vp, _vp]),
+        "fredec_pool_refine": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, ctypes.POINTER(ctypes.c_uint32),
+                                              i64, i32, d, i32, _c_dp, _c_dp, _c_i32p]),
         "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
                                                           ctypes.POINTER(Opts), _vp, _vp, _vp]),
@@ -288,6 +290,23 @@ def tuple_refine(t, y, sigma, tuples, *, max_iter=20, tol=1e-9, precision=FP64):
     _check(lib().fredec_tuple_refine(_p(t), _p(y), _p(sigma), t.size, _p(flat), _p(off), n, int(max_iter),
                                      float(tol), _prec(precision), _p(l), _p(it)))
     return [flat[off[k]:off[k + 1]].copy() for k in range(n)], l[:n], it[:n]
+
+
+def pool_refine(t, y, sigma, pool, masks=None, *, max_iter=20, tol=1e-9, precision=FP64):
+    """Refine subtuples of a pool (all 2^n - 1 non-empty ones by default).
+    Returns (masks, f (n_masks, n_pool), l, iterations)."""
+    t, y, sigma, pool = map(_f64, (t, y, sigma, pool))
+    n = pool.size
+    if masks is None:
+        masks = np.arange(1, 1 << n, dtype=np.uint32)
+    masks = np.ascontiguousarray(np.asarray(masks, dtype=np.uint32))
+    f = np.empty((max(masks.size, 1), n))
+    l = np.empty(max(masks.size, 1))
+    it = np.empty(max(masks.size, 1), dtype=np.int32)
+    _check(lib().fredec_pool_refine(_p(t), _p(y), _p(sigma), t.size, _p(pool), n,
+                                    masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), masks.size, int(max_iter),
+                                    float(tol), _prec(precision), _p(f), _p(l), _p(it)))
+    return masks, f[:masks.size], l[:masks.size], it[:masks.size]
 
 
 # ---------------------------------------------------------------------------

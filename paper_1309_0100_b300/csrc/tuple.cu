@@ -101,12 +101,16 @@ __global__ void pool_seeds(const double *t, int64_t N, const double *pool, int n
     }
 }
 
-// Packed lower-triangular helpers for the FP64 solves.
-__device__ inline bool chol_inplace(double *A, int n) {
+// Packed lower-triangular helpers for the FP64 solves.  chol_inplace also
+// lowers *min_ratio to the smallest pivot / original diagonal seen (the
+// squared fraction of a column's norm left after projecting out the earlier
+// columns).
+__device__ inline bool chol_inplace(double *A, int n, double *min_ratio = nullptr) {
     for (int j = 0; j < n; ++j) {
         double d = A[tri(j, j)];
         const double d0 = d;
         for (int k = 0; k < j; ++k) d -= A[tri(j, k)] * A[tri(j, k)];
+        if (min_ratio && d0 > 0) *min_ratio = fmin(*min_ratio, d / d0);
         if (!(d > 1e-13 * d0) || !(d0 > 0)) return false;
         const double l = sqrt(d);
         A[tri(j, j)] = l;
@@ -163,8 +167,14 @@ struct TupleSmem {
     int pidx[MAXM];
     int m, M;
     double l, red;             // chi2 of the fit and its reduction sum_{r>=1} a_r^2 (= l_0 - l)
+    double min_ratio;          // smallest Cholesky pivot ratio met by this tuple
     int flag;
 };
+
+// FP32-accumulated Gram sums are trusted while every Cholesky pivot keeps at
+// least this fraction of its column's squared norm; below it the tuple is
+// recomputed with FP64 sums (same role as flag_tau for periodogram bins).
+constexpr double TUPLE_TAU = 1e-2;
 
 // Accumulate <x_r x_c> over all points for the packed entries of the first
 // ncol columns, where the per-point column vector is produced by make(i, x).
@@ -264,7 +274,7 @@ __device__ bool linear_fit(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
     if (threadIdx.x == 0) {
         for (int r = 0; r < M; ++r)
             for (int c = 0; c <= r; ++c) sm.Lq[tri(r, c)] = sm.G[tri(r, c)];
-        sm.flag = chol_inplace(sm.Lq, M) ? 1 : 0;
+        sm.flag = chol_inplace(sm.Lq, M, &sm.min_ratio) ? 1 : 0;
         if (sm.flag) {
             for (int r = 0; r < M; ++r) sm.a[r] = sm.G[tri(M, r)];
             fwd(sm.Lq, sm.a, M);
@@ -287,6 +297,7 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
     if (threadIdx.x == 0) {
         sm.m = (int)(a.off[k + 1] - o0);
         sm.M = 2 * sm.m + 1;
+        sm.min_ratio = 1.0;
         for (int q = 0; q < sm.m; ++q) {
             sm.pidx[q] = a.idx[o0 + q];
             sm.delta[q] = 0.0;
@@ -346,7 +357,7 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
             if (threadIdx.x < m) a.dzdf[a.off[k] + threadIdx.x] = sm.G[tri(M + m, M + threadIdx.x)];
             if (threadIdx.x == 0) {
                 a.z[k] = 0.5 * zred;
-                a.status[k] = 0;
+                a.status[k] = (sizeof(T) == 4 && sm.min_ratio < TUPLE_TAU) ? 2 : 0;
             }
             return;
         }
@@ -363,7 +374,7 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
                     sm.S[tri(q, p)] = v;
                 }
             for (int q = 0; q < m; ++q) sm.gd[q] = sm.G[tri(M + m, M + q)];
-            sm.flag = chol_inplace(sm.S, m) ? 1 : 0;
+            sm.flag = chol_inplace(sm.S, m, &sm.min_ratio) ? 1 : 0;
             if (sm.flag) {
                 fwd(sm.S, sm.gd, m);
                 bwd(sm.S, sm.gd, m);
@@ -373,7 +384,10 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
         if (!sm.flag || it >= a.max_iter) break;
         double dmax = 0.0;
         for (int q = 0; q < m; ++q) dmax = fmax(dmax, fabs(sm.gd[q]));
-        // step with halving until l does not increase
+        // step with halving until l does not increase; with FP32-accumulated
+        // Gram sums l is only known to a few 1e-6 of <y^2>, so a step is
+        // accepted when it does not raise l by more than that
+        const double margin = sizeof(T) == 4 ? 3e-6 * a.sp->D : 1e-15 * lcur;
         double fac = 1.0;
         bool accepted = false;
         for (int h = 0; h < 30; ++h, fac *= 0.5) {
@@ -384,7 +398,7 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
                 }
             __syncthreads();
             const bool ok = linear_fit<T>(sm, a, tab, tabf);
-            if (ok && sm.l <= lcur * (1.0 + 1e-15)) {
+            if (ok && sm.l <= lcur + margin) {
                 accepted = true;
                 break;
             }
@@ -404,7 +418,7 @@ __device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable
         for (int q = 0; q < m; ++q) a.f_out[a.off[k] + q] = a.pool[sm.pidx[q]] + sm.delta[q];
         a.l_out[k] = lcur;
         if (a.iters) a.iters[k] = it;
-        a.status[k] = 0;
+        a.status[k] = (sizeof(T) == 4 && sm.min_ratio < TUPLE_TAU) ? 2 : 0;
     }
 }
 
@@ -571,12 +585,45 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     std::vector<int32_t> status(std::max<int64_t>(nt, 1));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpy(status.data(), b + o_st, nt * 4, cudaMemcpyDeviceToHost));
     for (int64_t k = 0; k < nt; ++k)
-        if (status[k]) return fail(FREDEC_ESINGULAR, "a tuple's normal matrix is singular (repeated frequency?)");
+        if (status[k] == 1) return fail(FREDEC_ESINGULAR, "a tuple's normal matrix is singular (repeated frequency?)");
+    // tuples whose FP32-accumulated systems were ill-conditioned: redo in FP64
+    std::vector<int64_t> redo;
+    for (int64_t k = 0; k < nt; ++k)
+        if (status[k] == 2) redo.push_back(k);
+    std::vector<double> z2, g2, f2, l2;
+    std::vector<int32_t> it2;
+    std::vector<int64_t> off2(1, 0);
+    if (!redo.empty()) {
+        std::vector<int32_t> idx2;
+        for (int64_t k : redo) {
+            for (int64_t q = off_h[k]; q < off_h[k + 1]; ++q) idx2.push_back(idx_h[q]);
+            off2.push_back((int64_t)idx2.size());
+        }
+        const int64_t n2 = (int64_t)redo.size(), nf2 = off2.back();
+        z2.resize(n2 + 1);
+        l2.resize(n2 + 1);
+        it2.resize(n2 + 1);
+        g2.resize(nf2 + 1);
+        f2.resize(nf2 + 1);
+        if (int rc = tuple_run(t, y, sigma, N, pool_h, npool, idx2, off2, mode, FREDEC_FP64, max_iter, tol, z2.data(),
+                               g2.data(), f2.data(), l2.data(), it2.data(), nullptr, st))
+            return rc;
+    }
     if (z_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(z_h, b + o_z, nt * 8, cudaMemcpyDeviceToHost));
     if (dzdf_h && nflat) FREDEC_CUDA_TRY(cudaMemcpy(dzdf_h, b + o_g, nflat * 8, cudaMemcpyDeviceToHost));
     if (f_h && nflat) FREDEC_CUDA_TRY(cudaMemcpy(f_h, b + o_f, nflat * 8, cudaMemcpyDeviceToHost));
     if (l_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(l_h, b + o_l, nt * 8, cudaMemcpyDeviceToHost));
     if (iters_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(iters_h, b + o_it, nt * 4, cudaMemcpyDeviceToHost));
+    for (size_t r = 0; r < redo.size(); ++r) {
+        const int64_t k = redo[r];
+        if (z_h) z_h[k] = z2[r];
+        if (l_h) l_h[k] = l2[r];
+        if (iters_h) iters_h[k] = it2[r];
+        for (int64_t q = 0; q < off_h[k + 1] - off_h[k]; ++q) {
+            if (dzdf_h) dzdf_h[off_h[k] + q] = g2[off2[r] + q];
+            if (f_h) f_h[off_h[k] + q] = f2[off2[r] + q];
+        }
+    }
     if (l0_h) {
         SeriesPrep h;
         FREDEC_CUDA_TRY(cudaMemcpy(&h, sp, sizeof(h), cudaMemcpyDeviceToHost));
@@ -718,6 +765,36 @@ int fredec_tuple_grad(const double *t, const double *y, const double *sigma, int
     if (rc) return rc;
     // the kernel returns <d r> with d = dmu/df; dz/df = -1/2 dchi2/df = <r dmu/df>
     for (int64_t q = 0; q < nflat; ++q) dz_df_out[q] = g[q];
+    return FREDEC_OK;
+}
+
+int fredec_pool_refine(const double *t, const double *y, const double *sigma, int64_t N, const double *pool,
+                       int32_t n_pool, const uint32_t *masks, int64_t n_masks, int32_t max_iter, double tol,
+                       int32_t precision, double *f_out, double *l_out, int32_t *iters_out) {
+    if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
+    if (n_pool < 0 || n_pool > FREDEC_MAX_TUPLE || n_masks < 0 || (n_masks > 0 && (!masks || !f_out || !l_out)) ||
+        (n_pool > 0 && !pool) || max_iter < 0 || !(tol >= 0.0))
+        return fail(FREDEC_EINVAL, "bad pool refine arguments");
+    const int64_t pool_off[2] = {0, n_pool};
+    if (int rc = check_tuple_inputs(t, y, sigma, N, pool, pool_off, 1)) return rc;
+    std::vector<int32_t> idx;
+    std::vector<int64_t> off(1, 0);
+    for (int64_t k = 0; k < n_masks; ++k) {
+        if (n_pool < 32 && (masks[k] >> n_pool) != 0) return fail(FREDEC_EINVAL, "mask has bits beyond n_pool");
+        for (int j = 0; j < n_pool; ++j)
+            if (masks[k] >> j & 1) idx.push_back(j);
+        off.push_back((int64_t)idx.size());
+    }
+    std::vector<double> f(std::max<size_t>(idx.size(), 1));
+    TStream ts;
+    FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&ts.s, cudaStreamNonBlocking));
+    int rc = tuple_run(t, y, sigma, N, pool, n_pool, idx, off, 2, precision, max_iter, tol, nullptr, nullptr,
+                       f.data(), l_out, iters_out, nullptr, ts.s);
+    if (rc) return rc;
+    for (int64_t k = 0; k < n_masks; ++k) {
+        for (int j = 0; j < n_pool; ++j) f_out[k * n_pool + j] = 0.0;
+        for (int64_t q = off[k]; q < off[k + 1]; ++q) f_out[k * n_pool + idx[q]] = f[q];
+    }
     return FREDEC_OK;
 }
 

@@ -1,0 +1,89 @@
+"""Parity at the full benchmark sizes, on outputs the oracle can compute one by
+one: the 4096-series batch, the N=1e5 / 1e7-frequency survey series with its
+adjoint, and subtuple refinement on the 16-frequency pool."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import ensure_built, local_max_topk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    ensure_built()
+    import paper_1309_0100_b300 as F
+    return F
+
+
+def _check_sampled(z, s, idx, tol):
+    zr, _, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
+    floor = 1e-3 * np.max(z)
+    m = ratio >= 1e-2
+    err = np.abs(z[idx] - zr) / np.maximum(zr, floor)
+    assert np.max(err[m]) < tol, float(np.max(err[m]))
+
+
+def test_config3_batch_full(F):
+    w = synth.config3()
+    plan = F.BatchPlan(w.series, precision="mixed", topk=5)
+    plan.run()
+    z, top = plan.download()
+    plan.close()
+    rng = np.random.default_rng(3)
+    for k in rng.choice(len(w.series), 12, replace=False):
+        s = w.series[k]
+        zk = z[plan.z_offsets[k]:plan.z_offsets[k] + s.grid.nf]
+        idx = np.unique(np.concatenate([np.linspace(0, s.grid.nf - 1, 24).astype(int), top[k][top[k] >= 0]]))
+        _check_sampled(zk, s, idx, 1e-5)
+        z64, t64 = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), precision="fp64", topk=5)
+        zs = sorted(z64[t64], reverse=True)
+        if np.all(-np.diff(zs) > 1e-4 * zs[0]):
+            assert list(top[k]) == list(t64), k
+
+
+def test_config5_survey_full(F):
+    import torch
+    s = synth.config5()
+    dev = torch.device("cuda:0")
+    tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
+    t, y, sg, b = tt(s.t), tt(s.y), tt(s.sigma), tt(s.base_freqs)
+    r = F.periodogram_dev(t, y, sg, b, s.grid.f0, s.grid.df, s.grid.nf, precision="mixed", topk=5, want_coef=True)
+    z = r["z"].cpu().numpy()
+    top = r["topk"].cpu().numpy()
+    idx = np.unique(np.concatenate([np.linspace(0, s.grid.nf - 1, 25).astype(int)] +
+                                   [np.arange(j - 1, j + 2) for j in top]))
+    _check_sampled(z, s, idx, 1e-5)
+    for j in top:   # each reported peak is a local maximum of the oracle's z
+        zn, _ = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[j - 1:j + 2])
+        assert np.argmax(zn) == 1
+    # adjoint: v one-hot at the highest peak plus a few random frequencies
+    v = np.zeros(s.grid.nf)
+    picks = np.concatenate([[top[0]], np.random.default_rng(2).choice(s.grid.nf, 4, replace=False)])
+    v[picks] = np.random.default_rng(3).standard_normal(picks.size)
+    g = F.periodogram_vjp_dev(t, y, sg, b, s.grid.f0, s.grid.df, s.grid.nf, r["coef"], r["info"], tt(v),
+                              precision="mixed").cpu().numpy()
+    gr = oracle.periodogram_vjp(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[picks], v[picks])
+    assert np.max(np.abs(g - gr)) <= 1e-5 * np.max(np.abs(gr))
+
+
+@pytest.mark.parametrize("prec,ftol,ltol", [("fp64", 1e-5, 1e-10), ("mixed", 3e-3, 1e-6)])
+def test_config4_pool_refine_sampled(F, prec, ftol, ltol):
+    """Both refinements must reach the same local minimum of l: equal l, the
+    oracle's l at the GPU frequencies equal to the GPU's l, and frequencies
+    equal to a small fraction of the resolution 1/T (small-amplitude members
+    sit in flat minima, so their frequencies are only loosely determined)."""
+    s = synth.config4()
+    T = s.t.max() - s.t.min()
+    rng = np.random.default_rng(4)
+    masks = [m for m in rng.integers(1, 1 << 16, 400).astype(np.uint32) if bin(int(m)).count("1") <= 4][:10]
+    masks = np.asarray(masks + [1 << k for k in range(6)], dtype=np.uint32)
+    mk, f, l, it = F.pool_refine(s.t, s.y, s.sigma, s.pool, masks, max_iter=30, tol=1e-10, precision=prec)
+    for q, m in enumerate(mk):
+        sel = [k for k in range(16) if int(m) >> k & 1]
+        rf, rl, _ = oracle.tuple_refine(s.t, s.y, s.sigma, s.pool[sel], max_iter=60, tol=1e-12)
+        assert l[q] == pytest.approx(rl, rel=ltol), int(m)
+        assert oracle.tuple_l(s.t, s.y, s.sigma, f[q, sel]) == pytest.approx(l[q], rel=ltol), int(m)
+        assert np.max(np.abs(f[q, sel] - rf)) < ftol / T, (int(m), (f[q, sel] - rf) * T)
