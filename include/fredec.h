@@ -315,6 +315,16 @@ int fredec_profile_events(void *ev_start, void *ev_stop);
  */
 int fredec_pipe_peaks(double *out);
 
+/*
+ * Failure-detection self-test (no counterpart in the paper): runs one bounded
+ * device wait that nothing completes and stores the status the library's
+ * kernels report in that case (FREDEC_ETIMEOUT) in *status_out.  Synchronous;
+ * nothing faults or hangs.  Setting the environment variable
+ * FREDEC_FAIL_ALLOC=1 makes every scratch allocation of the library report
+ * FREDEC_ENOMEM (allocation-failure injection for tests).
+ */
+int fredec_selftest_wait_timeout(int32_t *status_out);
+
 /* ------------------------------------------------------------------------ */
 const char *fredec_last_error(void);
 const char *fredec_version(void);

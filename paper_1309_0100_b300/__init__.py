@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "fredec_pool_refine": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, ctypes.POINTER(ctypes.c_uint32),
                                               i64, i32, d, i32, _c_dp, _c_dp, _c_i32p]),
         "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
+        "fredec_selftest_wait_timeout": (ctypes.c_int, [_c_i32p]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
                                                           ctypes.POINTER(Opts), _vp, _vp, _vp]),
     }
@@ -153,7 +154,7 @@ def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0) -> Opts:
 # Residual periodogram
 
 def periodogram(t, y, sigma, base_freqs, f_grid, *, precision=FP64, topk=0, want_coef=False, want_info=False,
-                fpt=0, warps=0, flag_tau=0.0):
+                fpt=0, warps=0, flag_tau=0.0, out=None):
     """z(f) for every trial frequency (host arrays in, host arrays out).
 
     Returns z, or a tuple (z, [topk_idx], [info], [coef]) when extras are
@@ -163,7 +164,9 @@ def periodogram(t, y, sigma, base_freqs, f_grid, *, precision=FP64, topk=0, want
     t, y, sigma, f = map(_f64, (t, y, sigma, f_grid))
     base = _f64(base_freqs)
     nf = f.size
-    z = np.empty(nf)
+    z = out if out is not None else np.empty(nf)
+    if z.dtype != np.float64 or z.size != nf or not z.flags.c_contiguous:
+        raise TypeError("out must be a contiguous float64 array of size nf")
     top = np.empty(max(int(topk), 1), dtype=np.int64) if topk else None
     info = np.empty(3) if want_info else None
     coef = np.empty((nf, 2)) if want_coef else None

@@ -2,6 +2,7 @@
 // periodogram pipeline  prep -> periodogram -> FP64 re-evaluation -> top-k.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,6 +38,8 @@ int DevBuf::alloc(size_t n, cudaStream_t s) {
     stream = s;
     bytes = n;
     if (n == 0) return FREDEC_OK;
+    const char *inj = std::getenv("FREDEC_FAIL_ALLOC");
+    if (inj && inj[0] == '1') return fail(FREDEC_ENOMEM, "allocation failure injected (FREDEC_FAIL_ALLOC=1)");
     keep_pool_cached();
     cudaError_t e = cudaMallocAsync(&ptr, n, s);
     if (e != cudaSuccess) {
@@ -235,26 +238,40 @@ static int check_series_host(const double *t, const double *y, const double *sig
 }
 
 // Uniform-grid detection: f_j = f0 + j*df within 8 ulps of max |f|.
+// Uniform-grid detection: f_j = f0 + j*df within 8 ulps of max |f| (a uniform
+// grid is monotone, so max |f| is at an end point).  One pass, early exit.
 static bool grid_uniform(const double *f, int64_t nf, double *f0, double *df) {
     if (nf <= 0) { *f0 = 0.0; *df = 0.0; return true; }
     *f0 = f[0];
     *df = nf > 1 ? (f[nf - 1] - f[0]) / (double)(nf - 1) : 0.0;
-    double fmax = 0.0;
-    for (int64_t j = 0; j < nf; ++j) fmax = std::max(fmax, std::fabs(f[j]));
+    const double fmax = std::max(std::fabs(f[0]), std::fabs(f[nf - 1]));
     const double tol = 8.0 * std::ldexp(1.0, std::ilogb(fmax > 0 ? fmax : 1.0) - 52);
+    const double a = *f0, d = *df;
     for (int64_t j = 0; j < nf; ++j)
-        if (std::fabs(f[j] - (*f0 + (double)j * *df)) > tol) return false;
+        if (std::fabs(f[j] - (a + (double)j * d)) > tol) return false;
     return true;
 }
 
+// Host-pointer calls run on one non-blocking stream per host thread and
+// device, created on first use and kept.
 struct HostStream {
     cudaStream_t s = nullptr;
     int make() {
-        FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        static thread_local cudaStream_t cached[64] = {};
+        int dev = 0;
+        FREDEC_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) {
+            FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            owned = true;
+            return FREDEC_OK;
+        }
+        if (!cached[dev]) FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&cached[dev], cudaStreamNonBlocking));
+        s = cached[dev];
         return FREDEC_OK;
     }
+    bool owned = false;
     ~HostStream() {
-        if (s) cudaStreamDestroy(s);
+        if (owned && s) cudaStreamDestroy(s);
     }
 };
 
@@ -356,10 +373,11 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             return rc;
         }
         if ((rc = finish_host(st, state, err))) return rc;
-        if (nf) FREDEC_CUDA_TRY(cudaMemcpy(z_out, dz, nf * 8, cudaMemcpyDeviceToHost));
-        if (info_out) FREDEC_CUDA_TRY(cudaMemcpy(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost));
-        if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpy(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost));
-        if (coef_out && nf) FREDEC_CUDA_TRY(cudaMemcpy(coef_out, dcoef, 16 * nf, cudaMemcpyDeviceToHost));
+        if (nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(z_out, dz, nf * 8, cudaMemcpyDeviceToHost, st));
+        if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
+        if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost, st));
+        if (coef_out && nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(coef_out, dcoef, 16 * nf, cudaMemcpyDeviceToHost, st));
+        FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     }
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     return FREDEC_OK;

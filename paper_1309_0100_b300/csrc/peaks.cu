@@ -93,6 +93,40 @@ extern "C" int fredec_pipe_peaks(double *out) {
     return FREDEC_OK;
 }
 
+namespace {
+// A bounded wait that nothing completes: one mbarrier expecting one arrival,
+// polled a fixed number of times; reports FREDEC_ETIMEOUT, faults nothing.
+__global__ void wait_timeout_probe(int32_t *status, unsigned polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    }
+    __syncthreads();
+    unsigned ok = 0;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    for (unsigned it = 0; it < polls && !ok; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a)
+                     : "memory");
+    if (threadIdx.x == 0) *status = ok ? FREDEC_OK : FREDEC_ETIMEOUT;
+}
+}  // namespace
+
+extern "C" int fredec_selftest_wait_timeout(int32_t *status_out) {
+    if (!status_out) return fail(FREDEC_EINVAL, "null status");
+    int32_t *d = nullptr;
+    FREDEC_CUDA_TRY(cudaMalloc(&d, 4));
+    wait_timeout_probe<<<1, 32>>>(d, 1000u);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(status_out, d, 4, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(FREDEC_ECUDA, cudaGetErrorString(e));
+    return FREDEC_OK;
+}
+
 extern "C" int fredec_profile_events(void *ev_start, void *ev_stop) {
     set_profile_events((cudaEvent_t)ev_start, (cudaEvent_t)ev_stop);
     return FREDEC_OK;

@@ -1,0 +1,49 @@
+"""Failure detection without faulting the GPU: a bounded device wait that
+nothing completes reports FREDEC_ETIMEOUT and leaves the context usable;
+injected allocation failures report FREDEC_ENOMEM; invalid device inputs give
+non-finite outputs, not a fault."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    ensure_built()
+    import paper_1309_0100_b300 as F
+    return F
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(F):
+    st = ctypes.c_int32(-1)
+    assert F.lib().fredec_selftest_wait_timeout(ctypes.byref(st)) == 0
+    assert st.value == 5          # FREDEC_ETIMEOUT
+    s = synth.small_series(1, N=64, n_base=1, nf=100)
+    z = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array())
+    assert np.all(np.isfinite(z))
+
+
+def test_injected_allocation_failure(F, monkeypatch):
+    s = synth.small_series(2, N=64, n_base=1, nf=100)
+    monkeypatch.setenv("FREDEC_FAIL_ALLOC", "1")
+    with pytest.raises(F.FredecError) as ei:
+        F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array())
+    assert ei.value.code == 2
+    monkeypatch.delenv("FREDEC_FAIL_ALLOC")
+    z = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array())
+    assert np.all(np.isfinite(z))
+
+
+def test_device_path_singular_base_gives_nan(F):
+    import torch
+    s = synth.small_series(3, N=80, n_base=2, nf=50)
+    tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+    r = F.periodogram_dev(tt(s.t), tt(s.y), tt(s.sigma), tt([0.1, 0.1]), s.grid.f0, s.grid.df, s.grid.nf)
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(r["z"].cpu().numpy()))
