@@ -171,6 +171,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
 
     PrepPlan pp;
     pp.S = 1;
+    pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
     pp.desc = w.desc;

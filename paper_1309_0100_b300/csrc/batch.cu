@@ -38,7 +38,7 @@ struct fredec_batch_plan {
     int S = 0, precision = 0, topk = 0, pmax = 1, warps = 4;
     double tau = 0.2;
     bool fix = false;
-    int64_t ntot = 0, nbase = 0, z_total = 0, nchunks = 0, n_items = 0, terms = 0, tk_chunks = 0;
+    int64_t ntot = 0, nbase = 0, z_total = 0, nchunks = 0, n_items = 0, terms = 0, tk_chunks = 0, max_n = 0;
     std::vector<int> p_present;
     void *mem = nullptr;   // one device allocation holding everything
     double *t = nullptr, *y = nullptr, *sigma = nullptr, *base = nullptr, *z = nullptr, *partials = nullptr,
@@ -60,6 +60,7 @@ struct fredec_batch_plan {
         FREDEC_CUDA_TRY(cudaMemsetAsync(flag_count, 0, 4, st));
         PrepPlan pp;
         pp.S = S;
+        pp.max_n = max_n;
         pp.nchunks = nchunks;
         pp.pmax = pmax;
         pp.desc = desc;
@@ -209,6 +210,7 @@ int fredec_batch_plan_create(fredec_batch_plan **plan_out, const double *t, cons
         pl.pmax = std::max(pl.pmax, d.p);
         present[d.p] = 1;
         pl.terms += (int64_t)d.N * nf[s];
+        pl.max_n = std::max<int64_t>(pl.max_n, d.N);
     }
     for (int p = 1; p < (int)present.size(); ++p)
         if (present[p]) pl.p_present.push_back(p);

@@ -84,8 +84,11 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 // Prep (prep.cu)
 
+constexpr int64_t SERIES_PREP_MAX_N = 16384;   // one prep CTA per series up to this N
+
 struct PrepPlan {
     int S = 0;                 // series
+    int64_t max_n = 0;         // largest series (chooses the one-CTA-per-series prep)
     int64_t nchunks = 0;       // total prep chunks
     int pmax = 1;
     SeriesDesc *desc = nullptr;      // device [S]

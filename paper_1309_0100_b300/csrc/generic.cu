@@ -105,6 +105,7 @@ int generic_grid_periodogram(const double *t, const double *y, const double *sig
         dd, d, ss, (int32_t *)(b + o_cs), nchunks);
     PrepPlan pp;
     pp.S = 1;
+    pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
     pp.desc = dd;

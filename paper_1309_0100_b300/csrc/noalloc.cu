@@ -140,6 +140,7 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     FREDEC_CUDA_TRY(cudaGetLastError());
     PrepPlan pp;
     pp.S = 1;
+    pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
     pp.desc = desc;

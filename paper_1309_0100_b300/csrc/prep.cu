@@ -71,12 +71,28 @@ __device__ bool arrive_last(SeriesState &st, int which, int nchunks) {
     return last;
 }
 
-// Sum of partial q over the series' chunks, in chunk order.
-__device__ double sum_partial(const PrepArgs &a, const SeriesDesc &d, int q) {
-    double s = 0.0;
-    for (int c = 0; c < d.nchunks; ++c) s += __ldcg(&a.partials[(d.chunk_off + c) * a.npart + q]);
-    return s;
+// Sums of partials 0..nv-1 over the series' chunks into out[] (shared), by the
+// whole CTA: lanes take values, every value is summed over the chunks in chunk
+// order (deterministic); a chunk's values are contiguous, so the loads are
+// coalesced and independent across chunks.
+__device__ void sum_partials(const PrepArgs &a, const SeriesDesc &d, int nv, double *out) {
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        const double *col = a.partials + d.chunk_off * a.npart + q;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= d.nchunks; c += 4) {   // four chunks in flight, combined in a fixed order
+            s0 += __ldcg(col + (int64_t)c * a.npart);
+            s1 += __ldcg(col + (int64_t)(c + 1) * a.npart);
+            s2 += __ldcg(col + (int64_t)(c + 2) * a.npart);
+            s3 += __ldcg(col + (int64_t)(c + 3) * a.npart);
+        }
+        for (; c < d.nchunks; ++c) s0 += __ldcg(col + (int64_t)c * a.npart);
+        out[q] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
 }
+extern __shared__ double prep_sm[];
+__device__ double *fin_buf() { return prep_sm; }
 
 __device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &d, double tp, double *phi) {
     phi[0] = 1.0;
@@ -89,8 +105,6 @@ __device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &
         phi[2 + 2 * k] = s;
     }
 }
-
-extern __shared__ double prep_sm[];
 
 // K1: sum w, sum w t  ->  W, t_c.
 __global__ void __launch_bounds__(PREP_THREADS) prep_k1(PrepArgs a) {
@@ -108,8 +122,10 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k1(PrepArgs a) {
     }
     store_partials(a, chunk, v, 2, prep_sm);
     if (arrive_last(st, 0, d.nchunks)) {
+        double *f = fin_buf();
+        sum_partials(a, d, 2, f);
+        const double W = f[0], Swt = f[1];
         if (threadIdx.x == 0) {
-            const double W = sum_partial(a, d, 0), Swt = sum_partial(a, d, 1);
             st.W = W;
             st.Swt = Swt;
             st.tc = rint(Swt / W);
@@ -140,7 +156,9 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k2(PrepArgs a) {
     }
     store_partials(a, chunk, v, p * (p + 1) / 2, prep_sm);
     if (arrive_last(st, 1, d.nchunks)) {
-        for (int q = threadIdx.x; q < p * (p + 1) / 2; q += blockDim.x) st.L1[q] = sum_partial(a, d, q);
+        double *f = fin_buf();
+        sum_partials(a, d, p * (p + 1) / 2, f);
+        for (int q = threadIdx.x; q < p * (p + 1) / 2; q += blockDim.x) st.L1[q] = f[q];
         __syncthreads();
         if (threadIdx.x == 0) {
             if (!chol_packed(st.L1, p, 1e-12)) st.status = FREDEC_ESINGULAR;
@@ -172,9 +190,10 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k3(PrepArgs a) {
     }
     store_partials(a, chunk, v, nt + p, prep_sm);
     if (arrive_last(st, 2, d.nchunks)) {
+        double *f = fin_buf();
+        sum_partials(a, d, nt + p, f);
         for (int q = threadIdx.x; q < nt + p; q += blockDim.x) {
-            const double sq = sum_partial(a, d, q);
-            if (q < nt) st.L2[q] = sq; else st.a[q - nt] = sq;
+            if (q < nt) st.L2[q] = f[q]; else st.a[q - nt] = f[q];
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -212,9 +231,50 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
     }
     store_partials(a, chunk, v, p, prep_sm);
     if (arrive_last(st, 3, d.nchunks)) {
-        for (int q = threadIdx.x; q < p; q += blockDim.x) st.a2[q] = sum_partial(a, d, q);
+        double *f = fin_buf();
+        sum_partials(a, d, p, f);
+        for (int q = threadIdx.x; q < p; q += blockDim.x) st.a2[q] = f[q];
         __syncthreads();
         if (threadIdx.x == 0) st.counter[3] = 0;
+    }
+}
+
+// Writes the records of point i of series d (residual r, w, u = w psi).
+__device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, double tp, double w,
+                                              double r, const double *u) {
+    const int p = d.p;
+    const uint64_t A = frac_turns_u64(d.f0, tp);
+    const uint64_t B = frac_turns_u64(d.df, tp);
+    double sr, cr;
+    sincos_turns_d(B, &sr, &cr);
+    const float wf = (float)w;
+    if (a.precision == FREDEC_MIXED) {
+        uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + i * rec32_words(p);
+        R[0] = (uint32_t)A;
+        R[1] = (uint32_t)(A >> 32);
+        R[2] = (uint32_t)B;
+        R[3] = (uint32_t)(B >> 32);
+        float *Rf = (float *)R;
+        Rf[4] = (float)cr;
+        Rf[5] = (float)sr;
+        Rf[6] = wf;
+        Rf[7] = (float)(w * r);
+        for (int q = 0; q < p; ++q) Rf[8 + q] = (float)u[q];
+        for (int q = 8 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
+    }
+    unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : a.rec64;
+    if (r64) {
+        const int64_t off64 = a.precision == FREDEC_FP64 ? d.rec_off : d.rec64_off;
+        uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p);
+        R[0] = A;
+        R[1] = B;
+        double *Rd = (double *)R;
+        Rd[2] = cr;
+        Rd[3] = sr;
+        Rd[4] = w;
+        Rd[5] = w * r;
+        for (int q = 0; q < p; ++q) Rd[6 + q] = u[q];
+        for (int q = 6 + p; q < rec64_words(p); ++q) Rd[q] = 0.0;
     }
 }
 
@@ -239,49 +299,146 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
             r -= (st.a[q] + st.a2[q]) * ps;
             u[q] = w * ps;
         }
-        const uint64_t A = frac_turns_u64(d.f0, tp);
-        const uint64_t B = frac_turns_u64(d.df, tp);
-        double sr, cr;
-        sincos_turns_d(B, &sr, &cr);
-        const float wf = (float)w;
+        write_records(a, d, i, tp, w, r, u);
         v[0] = w * r * r;
-        v[1] = (double)wf;
-        if (a.precision == FREDEC_MIXED) {
-            uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + i * rec32_words(p);
-            R[0] = (uint32_t)A;
-            R[1] = (uint32_t)(A >> 32);
-            R[2] = (uint32_t)B;
-            R[3] = (uint32_t)(B >> 32);
-            float *Rf = (float *)R;
-            Rf[4] = (float)cr;
-            Rf[5] = (float)sr;
-            Rf[6] = wf;
-            Rf[7] = (float)(w * r);
-            for (int q = 0; q < p; ++q) Rf[8 + q] = (float)u[q];
-            for (int q = 8 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
-        }
-        unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : a.rec64;
-        if (r64) {
-            const int64_t off64 = a.precision == FREDEC_FP64 ? d.rec_off : d.rec64_off;
-            uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p);
-            R[0] = A;
-            R[1] = B;
-            double *Rd = (double *)R;
-            Rd[2] = cr;
-            Rd[3] = sr;
-            Rd[4] = w;
-            Rd[5] = w * r;
-            for (int q = 0; q < p; ++q) Rd[6 + q] = u[q];
-            for (int q = 6 + p; q < rec64_words(p); ++q) Rd[q] = 0.0;
-        }
+        v[1] = (double)(float)w;
     }
     store_partials(a, chunk, v, 2, prep_sm);
     if (arrive_last(st, 4, d.nchunks)) {
+        double *f = fin_buf();
+        sum_partials(a, d, 2, f);
+        const double c2 = f[0], wf = f[1];
         if (threadIdx.x == 0) {
-            st.chi2 = sum_partial(a, d, 0);
-            st.Wf = sum_partial(a, d, 1);
+            st.chi2 = c2;
+            st.Wf = wf;
             st.counter[4] = 0;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One CTA per series (series up to SERIES_PREP_MAX_N points): the same five
+// phases as prep_k1..k5, separated by block barriers instead of kernel
+// boundaries.  Per-thread partial sums over a strided set of points are
+// combined by a fixed-order block reduction (deterministic).
+
+constexpr int SP_THREADS = 256;
+constexpr int SP_NV = NTRI + PMAX + 4;
+
+// Block sum of vals[0..nv) (per-thread, may be local memory) into out[0..nv)
+// (shared); all threads see out after return.
+__device__ void block_reduce_vals(const double *vals, int nv, double *red, double *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < nv; ++q) {
+        const double v = warp_sum_d(vals[q]);
+        if (lane == 0) red[wid * SP_NV + q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        double sm = 0.0;
+        for (int w = 0; w < nw; ++w) sm += red[w * SP_NV + q];
+        out[q] = sm;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
+    extern __shared__ double sp_sm[];
+    double *red = sp_sm, *out = sp_sm + (SP_THREADS / 32) * SP_NV;
+    __shared__ int ok;
+    const int s = blockIdx.x;
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.p, nt = p * (p + 1) / 2;
+    const int64_t N = d.N;
+    double v[SP_NV];
+    // 1: W, <t>  ->  t_c
+    v[0] = v[1] = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        v[0] += w;
+        v[1] += w * a.t[d.obs_off + i];
+    }
+    block_reduce_vals(v, 2, red, out);
+    const double W = out[0], tc = rint(out[1] / W);
+    // 2: raw base columns, Gram Q1 -> L1
+    for (int q = 0; q < nt; ++q) v[q] = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        double phi[PMAX];
+        base_basis(a, d, a.t[d.obs_off + i] - tc, phi);
+        for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = phi[q];
+        for (int r = 0; r < p; ++r)
+            for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
+    }
+    block_reduce_vals(v, nt, red, out);
+    if (threadIdx.x == 0) {
+        st.W = W;
+        st.tc = tc;
+        for (int q = 0; q < nt; ++q) st.L1[q] = out[q];
+        ok = chol_packed(st.L1, p, 1e-12);
+        st.status = ok ? FREDEC_OK : FREDEC_ESINGULAR;
+    }
+    __syncthreads();
+    if (!ok) return;
+    // 3: psi1 = L1^{-1} phi, Gram Q2 and <psi1 y>  ->  L2, a
+    for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg), yi = a.y[d.obs_off + i];
+        double x[PMAX];
+        for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
+        forward_packed(st.L1, x, p);
+        for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
+        for (int r = 0; r < p; ++r)
+            for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
+        for (int q = 0; q < p; ++q) v[nt + q] += w * x[q] * yi;
+    }
+    block_reduce_vals(v, nt + p, red, out);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nt; ++q) st.L2[q] = out[q];
+        for (int q = 0; q < p; ++q) st.a[q] = out[nt + q];
+        ok = chol_packed(st.L2, p, 1e-12);
+        if (ok) forward_packed(st.L2, st.a, p);
+        else st.status = FREDEC_ESINGULAR;
+    }
+    __syncthreads();
+    if (!ok) return;
+    // 4: psi = L2^{-1} psi1, r = y - a^T psi, <psi r>  ->  a2
+    for (int q = 0; q < p; ++q) v[q] = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        double x[PMAX], r = a.y[d.obs_off + i];
+        for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
+        forward_packed(st.L2, x, p);
+        for (int q = 0; q < p; ++q) {
+            a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
+            r -= st.a[q] * x[q];
+        }
+        for (int q = 0; q < p; ++q) v[q] += w * x[q] * r;
+    }
+    block_reduce_vals(v, p, red, out);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < p; ++q) st.a2[q] = out[q];
+    __syncthreads();
+    // 5: final residual, records, chi2, sum of FP32 weights
+    v[0] = v[1] = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        const double tp = a.t[d.obs_off + i] - tc;
+        double r = a.y[d.obs_off + i], u[PMAX];
+        for (int q = 0; q < p; ++q) {
+            const double ps = a.psi[d.psi_off + (int64_t)q * N + i];
+            r -= (st.a[q] + st.a2[q]) * ps;
+            u[q] = w * ps;
+        }
+        write_records(a, d, i, tp, w, r, u);
+        v[0] += w * r * r;
+        v[1] += (double)(float)w;
+    }
+    block_reduce_vals(v, 2, red, out);
+    if (threadIdx.x == 0) {
+        st.chi2 = out[0];
+        st.Wf = out[1];
     }
 }
 
@@ -311,6 +468,14 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
     a.base = base;
     a.precision = precision;
     if (pp.nchunks <= 0) return FREDEC_OK;
+    // One CTA per series when there are many series (the FP64 work of a single
+    // series on one SM is slower than spreading it over many one-warp chunks).
+    if (pp.S >= 256 && pp.max_n > 0 && pp.max_n <= SERIES_PREP_MAX_N) {
+        const size_t smem = sizeof(double) * (SP_THREADS / 32 + 1) * SP_NV;
+        prep_series<<<(unsigned)pp.S, SP_THREADS, smem, st>>>(a);
+        FREDEC_CUDA_TRY(cudaGetLastError());
+        return FREDEC_OK;
+    }
     const size_t smem = sizeof(double) * (PREP_THREADS / 32) * (NTRI + PMAX + 4);
     const dim3 grid((unsigned)pp.nchunks);
     prep_k1<<<grid, PREP_THREADS, smem, st>>>(a);

@@ -227,6 +227,7 @@ int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, i
     FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_cnt, 0, 4, st));
     PrepPlan pp;
     pp.S = 1;
+    pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
     pp.desc = desc;
