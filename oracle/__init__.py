@@ -68,6 +68,14 @@ class Oracle:
         L.oracle_tuple_refine.argtypes = [_dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, _dp]
         L.oracle_tuple_refine.restype = ctypes.c_int
+        L.oracle_fap_bound.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.oracle_fap_bound.restype = ctypes.c_double
+        L.oracle_fap_threshold.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.oracle_fap_threshold.restype = ctypes.c_double
+        L.oracle_cascade.argtypes = [_dp, ctypes.c_int, ctypes.c_int64, _dp, ctypes.c_char_p, _dp, _i64p]
+        L.oracle_cascade_solutions.argtypes = [ctypes.c_char_p, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64]
+        L.oracle_cascade_solutions.restype = ctypes.c_int64
 
 
 _default: Optional[Oracle] = None
@@ -199,3 +207,76 @@ def tuple_refine(t, y, sigma, freqs, *, max_iter=50, tol=1e-10, lib=None):
     if it < 0:
         raise ValueError("oracle_tuple_refine rejected its arguments")
     return f, float(lout[0]), int(it)
+
+
+# ---------------------------------------------------------------------------
+# Phase 3 backward cascade, non-nested solutions, Phase 4 ordering (Sect. 4)
+
+def fap_bound(n, A, W, z, *, lib=None) -> float:
+    """M_n(z) = A W^n exp(-z) z^(3n/2-1) (Eq. zFAP; A supplied by the caller)."""
+    L = lib or _lib()
+    return float(L.oracle_fap_bound(int(n), float(A), float(W), float(z)))
+
+
+def fap_threshold(n, A, W, fap, *, lib=None) -> float:
+    """z with M_n(z) = fap on the decreasing branch of M_n."""
+    L = lib or _lib()
+    return float(L.oracle_fap_threshold(int(n), float(A), float(W), float(fap)))
+
+
+def effective_bandwidth(t, sigma, f_max) -> float:
+    """W = f_max T_eff with T_eff = sqrt(4 pi Var(t)), Var the weighted
+    variance of the times with weights 1/sigma^2 (Sect. 2)."""
+    t, sigma = map(_d, (t, sigma))
+    w = 1.0 / sigma ** 2
+    tm = np.sum(w * t) / np.sum(w)
+    var = np.sum(w * (t - tm) ** 2) / np.sum(w)
+    return float(f_max * np.sqrt(4.0 * np.pi * var))
+
+
+def cascade(l_table, N, zthr, *, lib=None):
+    """Phase 3 on a subtuple table.  Returns (pass (uint8, 2^n), slack (2^n),
+    number of tests formed)."""
+    L = lib or _lib()
+    l = _d(l_table)
+    n = int(l.size).bit_length() - 1
+    if l.size != 1 << n:
+        raise ValueError("l_table length must be a power of two")
+    zt = _d(zthr)
+    if zt.size < n:
+        raise ValueError("need one threshold per number of added frequencies")
+    ps = ctypes.create_string_buffer(l.size)
+    slack = np.empty(l.size)
+    nt = np.zeros(1, dtype=np.int64)
+    if L.oracle_cascade(_p(l), n, int(N), _p(zt), ps, _p(slack), nt.ctypes.data_as(_i64p)):
+        raise ValueError("oracle_cascade rejected its arguments")
+    return np.frombuffer(ps.raw, dtype=np.uint8).copy(), slack, int(nt[0])
+
+
+def cascade_solutions(passed, *, lib=None) -> np.ndarray:
+    """Passing masks contained in no other passing mask, in increasing order."""
+    L = lib or _lib()
+    passed = np.ascontiguousarray(np.asarray(passed, dtype=np.uint8))
+    n = int(passed.size).bit_length() - 1
+    buf = ctypes.create_string_buffer(passed.tobytes(), passed.size)
+    cnt = L.oracle_cascade_solutions(buf, n, None, 0)
+    out = np.zeros(max(cnt, 1), dtype=np.uint32)
+    L.oracle_cascade_solutions(buf, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cnt)
+    return out[:cnt]
+
+
+def phase4_order(masks, l_table, N):
+    """Phase 4 as far as the paper defines it: the solutions grouped by their
+    number of frequencies m and, within a group, in increasing chi2; with the
+    goodness of fit G = (l_S / l_0) (N - 1) / (N - 3m - 1) (ratio of reduced
+    chi2 of H_m and H_0).  Returns (masks, G) in that order."""
+    rows = []
+    for S in masks:
+        S = int(S)
+        m = bin(S).count("1")
+        rows.append((m, float(l_table[S]), S))
+    rows.sort()
+    l0v = float(l_table[0])
+    ms = np.array([r[2] for r in rows], dtype=np.uint32)
+    G = np.array([(r[1] / l0v) * (N - 1) / (N - 3 * r[0] - 1) for r in rows])
+    return ms, G

@@ -451,3 +451,135 @@ int oracle_tuple_refine(const double *t, const double *y, const double *sigma, i
     free(r); free(J); free(rb); free(trial);
     return it;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Phase 3 backward cascade and the non-nested solutions (Sect. 4).          */
+
+/*
+ * FAP bound of Eq. zFAP for n frequencies: M_n(z) = A W^n exp(-z) z^(3n/2 - 1).
+ * The coefficients A (the paper's A~_n) are not given in the paper; the caller
+ * supplies them.  W = f_max T_eff is the normalised bandwidth (Sect. 2).
+ */
+double oracle_fap_bound(int n, double A, double W, double z)
+{
+    if (n < 1 || !(z > 0.0)) return NAN;
+    return A * pow(W, n) * exp(-z) * pow(z, 1.5 * n - 1.0);
+}
+
+/*
+ * The z at which M_n(z) falls to fap, on the branch where M_n decreases
+ * (z above 3n/2 - 1, the maximum of the z-dependent factor).  Plain bisection
+ * on log M_n(z) - log fap.  Returns the bracket's lower end when M_n never
+ * exceeds fap there (every z passes).
+ */
+double oracle_fap_threshold(int n, double A, double W, double fap)
+{
+    if (n < 1 || !(A > 0.0) || !(W > 0.0) || !(fap > 0.0)) return NAN;
+    double a = 1.5 * n - 1.0;
+    double lo = a > 0.0 ? a : 1e-300;
+    double target = log(fap);
+#define LOGM(z) (log(A) + n * log(W) - (z) + a * log(z))
+    if (LOGM(lo) <= target) return lo;
+    double hi = lo + 1.0;
+    while (LOGM(hi) > target) hi = 2.0 * hi + 1.0;
+    for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (LOGM(mid) > target) lo = mid; else hi = mid;
+    }
+#undef LOGM
+    return 0.5 * (lo + hi);
+}
+
+static int popcount_u64(uint64_t x)
+{
+    int c = 0;
+    for (; x; x &= x - 1) ++c;
+    return c;
+}
+
+/*
+ * Phase 3 (backward cascade).  l[mask] (2^n entries) holds the minimised chi2
+ * of the subtuple {pool[j] : bit j of mask}; l[0] = l_0.  For a combination S
+ * with m members and a proper subset K of S with k members (0 <= k < m), the
+ * relative statistic of Eq. zpowrel in its log form, base K and alternative S,
+ * is
+ *     z(S\K | K) = (N - 3m - 1)/2 * ln( l[K] / l[S] ).
+ * The tests of S are grouped in layers of equal k; a layer passes when its
+ * smallest z reaches zthr[m-k-1], the threshold for m-k added frequencies
+ * (FAP thresholds depend only on the number of added frequencies, Eq. zFAP).
+ * S passes when all its layers pass.  A test with a negative or NaN l, or a
+ * NaN ratio, fails; S fails when N - 3m - 1 <= 0.
+ * Outputs: pass[S] (0/1), slack[S] = smallest (layer minimum - threshold)
+ * over the layers of S (-INFINITY when a test fails outright; pass[S] is
+ * slack[S] >= 0).  n_tests (may be NULL) receives the number of tests formed;
+ * every K of every S is formed, so it is 3^n - 2^n when N is large enough.
+ */
+int oracle_cascade(const double *l, int n, int64_t N, const double *zthr,
+                   unsigned char *pass, double *slack, int64_t *n_tests)
+{
+    if (n < 0 || n > 24 || N <= 0) return 1;
+    uint64_t full = (1ull << n);
+    int64_t tests = 0;
+    double zmin[32];
+    pass[0] = 0;
+    slack[0] = -INFINITY;
+    for (uint64_t S = 1; S < full; ++S) {
+        int m = popcount_u64(S);
+#if ORACLE_MUTANT == 4
+        double NH = (double)(N - 3 * (int64_t)(m - 1) - 1);   /* planted: base model's N_H */
+#else
+        double NH = (double)(N - 3 * (int64_t)m - 1);
+#endif
+        for (int k = 0; k < m; ++k) zmin[k] = INFINITY;
+        int bad = !(NH > 0.0) || !(l[S] >= 0.0);
+        /* every proper subset K of S, visited once */
+        for (uint64_t K = (S - 1) & S;; K = (K - 1) & S) {
+            int k = popcount_u64(K);
+            double z;
+            ++tests;
+            if (!(l[K] >= 0.0)) z = -INFINITY;
+            else {
+                z = 0.5 * NH * log(l[K] / l[S]);
+                if (isnan(z)) z = -INFINITY;
+            }
+            if (z < zmin[k]) zmin[k] = z;
+            if (K == 0) break;
+        }
+        double sl = INFINITY;
+        for (int k = 0; k < m; ++k) {
+            double d = zmin[k] - zthr[m - k - 1];
+            if (isnan(d)) d = -INFINITY;
+            if (d < sl) sl = d;
+        }
+        if (bad) sl = -INFINITY;
+        slack[S] = sl;
+        pass[S] = sl >= 0.0;
+    }
+    if (n_tests) *n_tests = tests;
+    return 0;
+}
+
+/*
+ * Non-nested solutions of Phase 3: the passing combinations that no other
+ * passing combination contains (the output never holds nested tuples,
+ * Sect. 4, Phase 4).  Writes up to cap masks in increasing mask order and
+ * returns how many there are.
+ */
+int64_t oracle_cascade_solutions(const unsigned char *pass, int n, uint32_t *out, int64_t cap)
+{
+    if (n < 0 || n > 24) return -1;
+    uint64_t full = (1ull << n) - 1;
+    int64_t count = 0;
+    for (uint64_t S = 1; S <= full; ++S) {
+        if (!pass[S]) continue;
+        uint64_t rest = full & ~S;
+        int maximal = 1;
+        for (uint64_t T = rest; T && maximal; T = (T - 1) & rest)
+            if (pass[S | T]) maximal = 0;
+        if (maximal) {
+            if (count < cap) out[count] = (uint32_t)S;
+            ++count;
+        }
+    }
+    return count;
+}
