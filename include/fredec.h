@@ -284,6 +284,60 @@ int fredec_batch_plan_download(fredec_batch_plan *plan, double *z_out, int64_t *
 void fredec_batch_plan_destroy(fredec_batch_plan *plan);
 
 /* ------------------------------------------------------------------------ */
+/* Phase 3 backward cascade, Phase 4 ordering, FAP levels (Section 4)        */
+
+/*
+ * FAP bound of Eq. zFAP for an n-frequency test statistic z:
+ *     M_n(z) = A W^n exp(-z) z^(3n/2 - 1).
+ * The paper does not give its coefficients A~_n: the caller supplies A.
+ * W = f_max T_eff is the normalised bandwidth (fredec_effective_bandwidth).
+ * Returns NaN for n < 1 or non-positive A, W or z.  Host computation.
+ */
+double fredec_fap_bound(int32_t n, double A, double W, double z);
+
+/*
+ * The z at which M_n(z) falls to fap, on the branch where M_n decreases
+ * (z > 3n/2 - 1); 3n/2 - 1 itself when M_n never exceeds fap there.  NaN for
+ * n < 1 or non-positive A, W or fap.  Host computation.
+ */
+double fredec_fap_threshold(int32_t n, double A, double W, double fap);
+
+/*
+ * W = f_max * sqrt(4 pi Var(t)), Var the variance of t weighted by 1/sigma^2
+ * (Section 2).  Host pointers, synchronous; one FP64 reduction kernel.
+ * FREDEC_EINVAL for N < 2, f_max <= 0, non-finite t or sigma <= 0.
+ */
+int fredec_effective_bandwidth(const double *t, const double *sigma, int64_t N, double f_max,
+                               double *W_out);
+
+/*
+ * Phase 3 (backward cascade) on a table of subtuple minima, and the order of
+ * Phase 4 (Section 4).
+ *   l_table[mask] (2^n_pool entries, host): the minimised chi2 of the subtuple
+ *     {pool[j] : bit j of mask}; l_table[0] = l_0.  Typically the l_out of
+ *     fredec_pool_refine over all masks, or fredec_pool_subtuples_eval.
+ *   N: number of observations (N_H = N - 3m - 1 for m frequencies).
+ *   z_thr[c-1], c = 1..n_pool: the threshold on the log-form statistic for c
+ *     added frequencies (e.g. fredec_fap_threshold(c, A_c, W, FAP_2)).
+ * For every combination S (m members) and proper subset K (k members) the
+ * relative test of Eq. zpowrel, z(S\K | K) = (N - 3m - 1)/2 ln(l_K / l_S),
+ * must reach z_thr[m-k-1]; S passes when all its 2^m - 1 tests do.  A test
+ * whose l_K is not positive, or whose l_S is negative, infinite or NaN, fails;
+ * S fails when N - 3m - 1 <= 0.
+ * Outputs:
+ *   pass_bits (may be NULL): max(1, 2^n_pool/32) words, bit (S mod 32) of
+ *     word S/32 set when S passes;
+ *   the solutions: passing combinations contained in no other passing
+ *     combination, ordered by m, then by l, then by mask; the first
+ *     min(count, capacity) go to solutions[] (masks) and G_out[] (goodness of
+ *     fit G = (l_S / l_0) (N - 1)/(N - 3m - 1)); *n_solutions = count.
+ * n_pool <= FREDEC_MAX_POOL.  Host pointers, synchronous.
+ */
+int fredec_cascade(const double *l_table, int32_t n_pool, int64_t N, const double *z_thr,
+                   uint32_t *pass_bits, uint32_t *solutions, double *G_out, int64_t capacity,
+                   int64_t *n_solutions);
+
+/* ------------------------------------------------------------------------ */
 /* Launch-shape autotuner                                                    */
 
 /*

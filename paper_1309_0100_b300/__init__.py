@@ -22,6 +22,7 @@ __all__ = [
     "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
     "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
     "tuple_refine", "pool_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
+    "fap_bound", "fap_threshold", "effective_bandwidth", "cascade",
 ]
 
 FP64 = 0
@@ -95,6 +96,11 @@ def lib() -> ctypes.CDLL:
         "fredec_selftest_wait_timeout": (ctypes.c_int, [_c_i32p]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
                                                           ctypes.POINTER(Opts), _vp, _vp, _vp]),
+        "fredec_fap_bound": (d, [i32, d, d, d]),
+        "fredec_fap_threshold": (d, [i32, d, d, d]),
+        "fredec_effective_bandwidth": (ctypes.c_int, [_c_dp, _c_dp, i64, d, _c_dp]),
+        "fredec_cascade": (ctypes.c_int, [_c_dp, i32, i64, _c_dp, ctypes.POINTER(ctypes.c_uint32),
+                                          ctypes.POINTER(ctypes.c_uint32), _c_dp, i64, _c_i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -310,6 +316,59 @@ def pool_refine(t, y, sigma, pool, masks=None, *, max_iter=20, tol=1e-9, precisi
                                     masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), masks.size, int(max_iter),
                                     float(tol), _prec(precision), _p(f), _p(l), _p(it)))
     return masks, f[:masks.size], l[:masks.size], it[:masks.size]
+
+
+# ---------------------------------------------------------------------------
+# Phase 3 backward cascade, Phase 4 ordering, FAP levels
+
+def fap_bound(n, A, W, z) -> float:
+    """M_n(z) = A W^n exp(-z) z^(3n/2 - 1) (Eq. zFAP, A supplied by the caller)."""
+    return float(lib().fredec_fap_bound(int(n), float(A), float(W), float(z)))
+
+
+def fap_threshold(n, A, W, fap) -> float:
+    """The z at which M_n(z) = fap on the decreasing branch."""
+    return float(lib().fredec_fap_threshold(int(n), float(A), float(W), float(fap)))
+
+
+def effective_bandwidth(t, sigma, f_max) -> float:
+    """W = f_max sqrt(4 pi Var_w(t)) (weights 1/sigma^2)."""
+    t, sigma = map(_f64, (t, sigma))
+    out = np.zeros(1)
+    _check(lib().fredec_effective_bandwidth(_p(t), _p(sigma), t.size, float(f_max), _p(out)))
+    return float(out[0])
+
+
+def cascade(l_table, N, z_thr, *, want_pass=False, capacity=None):
+    """Phase 3 on a subtuple table: the non-nested passing combinations in the
+    order of Phase 4.  Returns (masks, G) and, with want_pass, the pass flags
+    as a uint8 array over all masks."""
+    l = _f64(l_table)
+    n = int(l.size).bit_length() - 1
+    if l.size != 1 << n:
+        raise ValueError("l_table length must be a power of two")
+    zt = _f64(z_thr)
+    if zt.size < n:
+        raise ValueError("need one threshold per number of added frequencies")
+    words = np.zeros(max(1, l.size // 32), dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    cnt = np.zeros(1, dtype=np.int64)
+    cap = 1 << 16 if capacity is None else int(capacity)
+    while True:
+        masks = np.zeros(max(cap, 1), dtype=np.uint32)
+        G = np.empty(max(cap, 1))
+        _check(lib().fredec_cascade(_p(l), n, int(N), _p(zt) if zt.size else None,
+                                    words.ctypes.data_as(u32p) if want_pass else None,
+                                    masks.ctypes.data_as(u32p), _p(G), cap, _p(cnt)))
+        if capacity is not None or cnt[0] <= cap:
+            break
+        cap = int(cnt[0])
+    k = min(int(cnt[0]), cap)
+    out = (masks[:k], G[:k])
+    if want_pass:
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: l.size]
+        out = out + (bits.astype(np.uint8),)
+    return out
 
 
 # ---------------------------------------------------------------------------
