@@ -338,6 +338,75 @@ int fredec_cascade(const double *l_table, int32_t n_pool, int64_t N, const doubl
                    int64_t *n_solutions);
 
 /* ------------------------------------------------------------------------ */
+/* The decomposition: Phase 1 scan and Phases 1-4 (Section 4)                */
+
+typedef struct {
+    int32_t precision;    /* FREDEC_FP64 (default) or FREDEC_MIXED periodograms */
+    int32_t max_pool;     /* pool cap; 0: N/10; never above FREDEC_MAX_TUPLE */
+    int32_t max_base;     /* base frequencies (SLICK rounds); 0: FREDEC_MAX_NBASE;
+                             never above (N-3)/2 */
+    int32_t reserved;
+    double z_thr0;        /* the top peak joins the base while its z reaches this
+                             (FAP_0 for one frequency) */
+    double z_thr1;        /* other peaks join the pool from this z (FAP_1) */
+    double half;          /* ... and from this fraction of the top peak's z (0.5) */
+    double merge_dist;    /* candidates closer than this are one; 0: 0.5/(t_max-t_min) */
+} fredec_scan_opts;
+
+void fredec_scan_opts_init(fredec_scan_opts *o);   /* FP64, half = 0.5, rest 0 */
+
+/*
+ * Phase 1 (Section 4, SLICK and QUICK) on the uniform grid f0 + j df, j < nf.
+ * Each round computes the residual periodogram of the current base; its
+ * statistic is the log form of Eq. zpowrel for one added frequency,
+ *     z = (N - 3(m+1) - 1)/2 ln(l_base / (l_base - 2 z_diff)),
+ * m the base size.  Of the 64 highest local maxima (ranked as in top-k), the
+ * top one joins the base and the pool while its z reaches z_thr0, else the
+ * scan stops; the others join the pool when their z reaches z_thr1 and
+ * half * (top z).  A candidate within merge_dist of a pool member replaces it
+ * when its z is larger and is dropped otherwise.  The scan stops after
+ * max_base rounds.  The pool is returned in decreasing z (ties to the lower
+ * frequency), cut to max_pool (*truncated_out = 1 when candidates were cut).
+ * Outputs (host): pool_out / pool_z_out (FREDEC_MAX_TUPLE entries; pool_z_out
+ * may be NULL), base_out (FREDEC_MAX_NBASE entries, may be NULL), counts.
+ * Host pointers, synchronous.
+ */
+int fredec_scan(const double *t, const double *y, const double *sigma, int64_t N,
+                double f0, double df, int64_t nf, const fredec_scan_opts *opts,
+                double *pool_out, double *pool_z_out, int32_t *n_pool_out,
+                double *base_out, int32_t *n_base_out, int32_t *truncated_out);
+
+typedef struct {
+    fredec_scan_opts scan;      /* Phase 1 */
+    const double *z_thr;        /* Phase 3 thresholds, z_thr[c-1] for c = 1..FREDEC_MAX_TUPLE
+                                   added frequencies (FAP_2); required */
+    int32_t refine_precision;   /* Phase 2 sums: FREDEC_FP64 (default) or FREDEC_MIXED */
+    int32_t refine_iter;        /* Gauss-Newton steps per subtuple; 0: 20 */
+    double refine_tol;          /* stop when max |df| * span(t) < tol; 0: 1e-9 */
+} fredec_decompose_opts;
+
+void fredec_decompose_opts_init(fredec_decompose_opts *o);
+
+/*
+ * The whole decomposition (Section 4): Phase 1 (fredec_scan); Phase 2, the
+ * local fit of every non-empty subtuple of the pool starting from its pool
+ * frequencies (fredec_pool_refine); Phase 3 (fredec_cascade) on the table of
+ * fitted minima; Phase 4 ordering.  Outputs (host):
+ *   pool_out (FREDEC_MAX_TUPLE), *n_pool_out = n;
+ *   l_table_out (may be NULL; 2^n entries): the Phase 2 minima, entry 0 = l_0;
+ *   the first min(count, capacity) solutions in Phase 4 order: solutions[]
+ *     (masks over the pool), G_out[], freqs_out (may be NULL;
+ *     capacity x FREDEC_MAX_TUPLE, row i = the fitted frequencies of solution
+ *     i in increasing order, zero-padded); *n_solutions = count.
+ * Host pointers, synchronous.
+ */
+int fredec_decompose(const double *t, const double *y, const double *sigma, int64_t N,
+                     double f0, double df, int64_t nf, const fredec_decompose_opts *opts,
+                     double *pool_out, int32_t *n_pool_out, double *l_table_out,
+                     uint32_t *solutions, double *G_out, double *freqs_out,
+                     int64_t capacity, int64_t *n_solutions);
+
+/* ------------------------------------------------------------------------ */
 /* Launch-shape autotuner                                                    */
 
 /*

@@ -19,7 +19,8 @@ Readings taken where Sect. 4 is silent:
     pool member is the same candidate: the one with the larger z is kept;
   * at the end the pool is ordered by decreasing z (ties to the lower
     frequency) and cut to max_pool (default N/10, at most 20);
-  * the scan also stops after max_base base frequencies (default 12).
+  * the scan also stops after max_base base frequencies (default 12, and at
+    most (N-3)/2 so that the base model stays overdetermined).
 """
 from __future__ import annotations
 
@@ -66,6 +67,7 @@ def phase1_scan(t, y, sigma, f0, df, nf, z_thr0, z_thr1, *, max_pool=0, max_base
     md = merge_dist if merge_dist > 0 else 0.5 / T
     cap = max_pool if max_pool > 0 else N // 10
     cap = min(cap, 20)
+    max_base = min(max_base, max(0, (N - 3) // 2))
     grid = f0 + df * np.arange(nf)
     base, pool = [], []          # pool: list of [f, z]
 

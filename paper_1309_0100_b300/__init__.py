@@ -22,7 +22,7 @@ __all__ = [
     "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
     "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
     "tuple_refine", "pool_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
-    "fap_bound", "fap_threshold", "effective_bandwidth", "cascade",
+    "fap_bound", "fap_threshold", "effective_bandwidth", "cascade", "scan", "decompose",
 ]
 
 FP64 = 0
@@ -48,6 +48,21 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("topk", ctypes.c_int32), ("fpt", ctypes.c_int32),
                 ("warps", ctypes.c_int32), ("flag_tau", ctypes.c_double)]
 
+
+class ScanOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_pool", ctypes.c_int32), ("max_base", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("z_thr0", ctypes.c_double), ("z_thr1", ctypes.c_double),
+                ("half", ctypes.c_double), ("merge_dist", ctypes.c_double)]
+
+
+class DecomposeOpts(ctypes.Structure):
+    _fields_ = [("scan", ScanOpts), ("z_thr", ctypes.POINTER(ctypes.c_double)),
+                ("refine_precision", ctypes.c_int32), ("refine_iter", ctypes.c_int32),
+                ("refine_tol", ctypes.c_double)]
+
+
+MAX_TUPLE = 20
+MAX_NBASE = 12
 
 _lib_handle = None
 
@@ -101,6 +116,13 @@ def lib() -> ctypes.CDLL:
         "fredec_effective_bandwidth": (ctypes.c_int, [_c_dp, _c_dp, i64, d, _c_dp]),
         "fredec_cascade": (ctypes.c_int, [_c_dp, i32, i64, _c_dp, ctypes.POINTER(ctypes.c_uint32),
                                           ctypes.POINTER(ctypes.c_uint32), _c_dp, i64, _c_i64p]),
+        "fredec_scan_opts_init": (None, [ctypes.POINTER(ScanOpts)]),
+        "fredec_decompose_opts_init": (None, [ctypes.POINTER(DecomposeOpts)]),
+        "fredec_scan": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, d, d, i64, ctypes.POINTER(ScanOpts), _c_dp, _c_dp,
+                                       _c_i32p, _c_dp, _c_i32p, _c_i32p]),
+        "fredec_decompose": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, d, d, i64, ctypes.POINTER(DecomposeOpts),
+                                            _c_dp, _c_i32p, _c_dp, ctypes.POINTER(ctypes.c_uint32), _c_dp, _c_dp,
+                                            i64, _c_i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -369,6 +391,69 @@ def cascade(l_table, N, z_thr, *, want_pass=False, capacity=None):
         bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: l.size]
         out = out + (bits.astype(np.uint8),)
     return out
+
+
+def _scan_opts(z_thr0, z_thr1, precision, max_pool, max_base, half, merge_dist):
+    o = ScanOpts()
+    lib().fredec_scan_opts_init(ctypes.byref(o))
+    o.precision = _prec(precision)
+    o.max_pool = int(max_pool)
+    o.max_base = int(max_base)
+    o.z_thr0 = float(z_thr0)
+    o.z_thr1 = float(z_thr1)
+    o.half = float(half)
+    o.merge_dist = float(merge_dist)
+    return o
+
+
+def scan(t, y, sigma, f0, df, nf, z_thr0, z_thr1, *, precision=FP64, max_pool=0, max_base=0, half=0.5,
+         merge_dist=0.0):
+    """Phase 1 scan.  Returns (pool, pool_z, base, truncated)."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    o = _scan_opts(z_thr0, z_thr1, precision, max_pool, max_base, half, merge_dist)
+    pool = np.zeros(MAX_TUPLE)
+    pz = np.zeros(MAX_TUPLE)
+    base = np.zeros(MAX_NBASE)
+    npool = np.zeros(1, dtype=np.int32)
+    nbase = np.zeros(1, dtype=np.int32)
+    tr = np.zeros(1, dtype=np.int32)
+    _check(lib().fredec_scan(_p(t), _p(y), _p(sigma), t.size, float(f0), float(df), int(nf), ctypes.byref(o),
+                             _p(pool), _p(pz), _p(npool), _p(base), _p(nbase), _p(tr)))
+    k, b = int(npool[0]), int(nbase[0])
+    return pool[:k].copy(), pz[:k].copy(), base[:b].copy(), bool(tr[0])
+
+
+def decompose(t, y, sigma, f0, df, nf, z_thr0, z_thr1, z_thr, *, precision=FP64, refine_precision=FP64,
+              max_pool=0, max_base=0, half=0.5, merge_dist=0.0, refine_iter=20, refine_tol=1e-9,
+              capacity=4096):
+    """Phases 1-4.  Returns a dict: pool, l (Phase 2 table), masks, G, freqs
+    (list of increasing arrays), n_solutions."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    zt = np.zeros(MAX_TUPLE)
+    z_thr = _f64(z_thr)
+    zt[:min(MAX_TUPLE, z_thr.size)] = z_thr[:MAX_TUPLE]
+    o = DecomposeOpts()
+    lib().fredec_decompose_opts_init(ctypes.byref(o))
+    o.scan = _scan_opts(z_thr0, z_thr1, precision, max_pool, max_base, half, merge_dist)
+    o.z_thr = zt.ctypes.data_as(_c_dp)
+    o.refine_precision = _prec(refine_precision)
+    o.refine_iter = int(refine_iter)
+    o.refine_tol = float(refine_tol)
+    pool = np.zeros(MAX_TUPLE)
+    npool = np.zeros(1, dtype=np.int32)
+    cap_pool = min(MAX_TUPLE, t.size // 10 if max_pool == 0 else max_pool)
+    l = np.zeros(1 << max(cap_pool, 0))
+    masks = np.zeros(max(capacity, 1), dtype=np.uint32)
+    G = np.zeros(max(capacity, 1))
+    F = np.zeros((max(capacity, 1), MAX_TUPLE))
+    cnt = np.zeros(1, dtype=np.int64)
+    _check(lib().fredec_decompose(_p(t), _p(y), _p(sigma), t.size, float(f0), float(df), int(nf), ctypes.byref(o),
+                                  _p(pool), _p(npool), _p(l), masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                  _p(G), _p(F), int(capacity), _p(cnt)))
+    n = int(npool[0])
+    k = min(int(cnt[0]), capacity)
+    return dict(pool=pool[:n].copy(), l=l[:1 << n].copy(), masks=masks[:k].copy(), G=G[:k].copy(),
+                freqs=[F[i, :bin(int(masks[i])).count("1")].copy() for i in range(k)], n_solutions=int(cnt[0]))
 
 
 # ---------------------------------------------------------------------------
