@@ -5,20 +5,33 @@
 //   local refinement (Section 3, Eq. lsqf): Gauss-Newton on f with the linear
 //   parameters refitted at every step.
 //
-// Linear fit as in Section 3: Gram Q = <phi phi^T>, g = <phi y>, Q = L L^T,
-// a = L^{-1} g, theta = L^{-T} a; the chi2 reduction of the frequency columns
-// is sum_{k>=1} a_k^2 (y is centred by its weighted mean, so the constant
-// column carries a_0 = 0 and l_0 = <y^2>).  Refinement: with the derivative
-// columns d_k = d mu / d f_k the extended normal matrix is [[Q, C], [C^T, D]]
-// and its Cholesky factor extends L incrementally (Section 3):
-//   X = L^{-1} C,  S = D - X^T X = L2 L2^T,  df = S^{-1} <d r>
-// (the theta part of the gradient vanishes at the linear optimum).
+// One CTA per tuple (persistent CTAs, largest tuples first).  A pass over the
+// points builds the weighted columns of a chunk of points in shared memory
+// (one point per thread) and
+// accumulates their Gram matrix: every thread owns 4x4 blocks of the lower
+// triangle and runs over the chunk's points with float4 shared loads; when a
+// tuple has fewer blocks than threads the points are split among groups of
+// threads and the groups' sums are added in FP64 in a fixed order.  The mixed
+// path builds the columns and sums them in FP32 (chunk partials added into
+// running FP32 sums); the FP64 path does everything in FP64.
 //
-// Every tuple frequency is an index into a pool of base frequencies f0_k whose
-// FP64-exact cos/sin at every point are computed once; a tuple frequency
-// f = f0_k + delta (delta = 0 unless refined) is obtained with the small-angle
-// rotation e^{i 2 pi delta t'} (|delta t'| well below one turn).
+// The columns are [1, c_k, s_k, y] for a linear fit and, for gradients and
+// refinement, also [t'c_k, t's_k] (the t-weighted averages of Eq. avrg1/avrg2).
+// The CTA factors the leading [phi, y] block of the FP64 Gram in place
+// (right-looking Cholesky, threads over the trailing triangle): row y holds
+// a = L^{-1} <phi y>, so l = <y^2> - sum_{r>=1} a_r^2 (y is centred, so the
+// constant's a_0 ~ 0) and theta = L^{-T} a.  The derivative columns
+// d_k = 2 pi (b_k t'c_k - a_k t's_k) then enter by the incremental extension of
+// the factor (Section 3): X = L^{-1} <phi d>, S = <d d> - X^T X and the
+// gradient g = <d r> = <d y> - X^T a; the Gauss-Newton step is S^{-1} g.  A
+// refinement makes one pass per trial point, which gives the trial's l and,
+// when accepted, its exact Gauss-Newton step; a trial that raises l is halved.
+//
+// Every tuple frequency is an offset from a pool frequency whose exact
+// cos/sin at every point are computed once (FP64 phases); the offset's
+// rotation e^{i 2 pi delta t'} is small and is applied per pass.
 #include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include "device_util.cuh"
@@ -28,11 +41,21 @@ namespace fredec {
 
 namespace {
 
-constexpr int TU_THREADS = 128;
-constexpr int TU_TILE = 64;               // points per shared tile
-constexpr int MAXM = FREDEC_MAX_POOL;     // frequencies per tuple (and per pool Gram)
-constexpr int MAXC = 2 * MAXM + 1;        // linear columns
-constexpr int MAXE = MAXC + MAXM + 1;     // + derivative columns + residual/data column
+constexpr int WT_THREADS = 128;
+constexpr int QB = 2;                         // 4x4 Gram blocks per thread at most
+constexpr int MAXM = FREDEC_MAX_POOL;         // frequencies per tuple (FREDEC_MAX_TUPLE with derivatives)
+constexpr int MAXC = std::max(4 * FREDEC_MAX_TUPLE + 2, 2 * FREDEC_MAX_POOL + 2);   // Gram columns
+constexpr int MAX_HALVINGS = 30;              // FP64: halve a rejected step up to this often
+constexpr int MAX_HALVINGS_MIXED = 5;         // FP32 sums: a step still rejected after 5 halvings
+                                              // is below the noise of l
+constexpr double MIXED_L_NOISE = 3e-7;        // FP32-summed l is known to ~this fraction of <y^2>
+constexpr size_t CHUNK_BYTES = 16384;         // shared column tile
+
+// FP32-accumulated Gram sums are trusted while every pivot of the linear
+// block keeps at least this fraction of its column's squared norm; below it
+// the tuple is redone with FP64 sums (same role as flag_tau for periodogram
+// bins).
+constexpr double TUPLE_TAU = 1e-2;
 
 struct SeriesPrep {            // per-series constants (device)
     double W, ybar, tc, D;     // sum w, weighted mean of y, time origin, <(y - ybar)^2> = l_0
@@ -84,9 +107,25 @@ __global__ void series_prep(const double *t, const double *y, const double *sigm
     }
 }
 
-// Exact cos/sin of every pool frequency at every point: cs[k*N + i] (FP64).
-__global__ void pool_seeds(const double *t, int64_t N, const double *pool, int npool, const SeriesPrep *sp,
-                           double2 *cs) {
+template <class T> struct Pt { T sw, tp, yw, pad; };   // 1/sigma, t - t_c, (y - ybar)/sigma
+template <class T> struct V2T;
+template <> struct V2T<float> { using type = float2; };
+template <> struct V2T<double> { using type = double2; };
+
+template <class T>
+__global__ void point_prep(const double *t, const double *y, const double *sigma, int64_t N, const SeriesPrep *sp,
+                           Pt<T> *out) {
+    const double tc = sp->tc, ybar = sp->ybar;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double sw = 1.0 / sigma[i];
+        out[i] = Pt<T>{(T)sw, (T)(t[i] - tc), (T)((y[i] - ybar) * sw), T(0)};
+    }
+}
+
+// Exact cos/sin of every pool frequency at every point (FP64 phases), stored
+// in the pass precision: cs[k*N + i].
+template <class T2>
+__global__ void pool_seeds(const double *t, int64_t N, const double *pool, int npool, const SeriesPrep *sp, T2 *cs) {
     __shared__ SeedTable tab;
     fill_seed_table(tab);
     __syncthreads();
@@ -97,349 +136,527 @@ __global__ void pool_seeds(const double *t, int64_t N, const double *pool, int n
         const int64_t i = q - (int64_t)k * N;
         double s, c;
         seed_from_table(tab, frac_turns_u64(pool[k], t[i] - tc), &s, &c);
-        cs[q] = make_double2(c, s);
-    }
-}
-
-// Packed lower-triangular helpers for the FP64 solves.  chol_inplace also
-// lowers *min_ratio to the smallest pivot / original diagonal seen (the
-// squared fraction of a column's norm left after projecting out the earlier
-// columns).
-__device__ inline bool chol_inplace(double *A, int n, double *min_ratio = nullptr) {
-    for (int j = 0; j < n; ++j) {
-        double d = A[tri(j, j)];
-        const double d0 = d;
-        for (int k = 0; k < j; ++k) d -= A[tri(j, k)] * A[tri(j, k)];
-        if (min_ratio && d0 > 0) *min_ratio = fmin(*min_ratio, d / d0);
-        if (!(d > 1e-13 * d0) || !(d0 > 0)) return false;
-        const double l = sqrt(d);
-        A[tri(j, j)] = l;
-        for (int i = j + 1; i < n; ++i) {
-            double s = A[tri(i, j)];
-            for (int k = 0; k < j; ++k) s -= A[tri(i, k)] * A[tri(j, k)];
-            A[tri(i, j)] = s / l;
-        }
-    }
-    return true;
-}
-__device__ inline void fwd(const double *L, double *x, int n) {
-    for (int i = 0; i < n; ++i) {
-        double s = x[i];
-        for (int k = 0; k < i; ++k) s -= L[tri(i, k)] * x[k];
-        x[i] = s / L[tri(i, i)];
-    }
-}
-__device__ inline void bwd(const double *L, double *x, int n) {
-    for (int i = n - 1; i >= 0; --i) {
-        double s = x[i];
-        for (int k = i + 1; k < n; ++k) s -= L[tri(k, i)] * x[k];
-        x[i] = s / L[tri(i, i)];
+        cs[q].x = c;
+        cs[q].y = s;
     }
 }
 
 struct TupleArgs {
-    const double *t, *y, *sigma;
     int64_t N;
     const SeriesPrep *sp;
-    const double2 *seeds;      // [pool][N]
+    const void *pts;           // Pt<T>[N]
+    const void *seeds;         // V2T<T>[pool][N]
     const double *pool;        // pool frequencies
     const int32_t *idx;        // tuple -> pool indices (CSR)
     const int64_t *off;
+    const int32_t *order;      // processing order (largest tuples first)
     int64_t n_tuples;
-    int mode;                  // 0 eval, 1 grad, 2 refine
+    int mode;                  // 0 eval, 1 grad, 2 refine, 3 Gram of one tuple
     int max_iter;
     double tol;
     double *z, *dzdf, *f_out, *l_out;
     int32_t *iters;
-    int32_t *status;           // per-tuple: 0 ok, 1 singular
-    int32_t *next;             // work counter (persistent CTAs)
-    double *gram_out;          // mode 3: packed Gram of [1, c_k, s_k, y - ybar]
+    int32_t *status;           // per tuple: 0 ok, 1 singular, 2 redo in FP64
+    int32_t *next;             // work counter
+    double *gram_out;          // mode 3: packed Gram of [1, c_k, s_k, y]
+    int chunk;                 // points per shared tile
+    int cmax;                  // most columns of any tuple of the launch
 };
 
-// Shared state of one CTA working on one tuple.
-template <class T>
-struct TupleSmem {
-    T X[MAXE][TU_TILE + 1];    // weighted columns of the tile (padded stride)
-    double G[MAXE * (MAXE + 1) / 2];
-    double Lq[MAXC * (MAXC + 1) / 2];
-    double theta[MAXC], a[MAXC], delta[MAXM], step[MAXM], ftrial[MAXM], X2[MAXC * MAXM], S[MAXM * (MAXM + 1) / 2],
-        gd[MAXM];
+struct TState {
+    double theta[MAXC];        // coefficients at the accepted point
+    double x[MAXC];            // trial coefficients / scratch
+    double trial[MAXM];        // frequency offsets of the pass in progress
+    double delta[MAXM];        // accepted offsets
+    double step[MAXM];         // Gauss-Newton step at the accepted point
+    float trialf[MAXM];
+    double red, redx;          // sum_{r>=1} a_r^2 (accepted / trial)
+    double ratio;              // smallest linear pivot ratio of the last factorisation
     int pidx[MAXM];
-    int m, M;
-    double l, red;             // chi2 of the fit and its reduction sum_{r>=1} a_r^2 (= l_0 - l)
-    double min_ratio;          // smallest Cholesky pivot ratio met by this tuple
-    int flag;
+    int m, fail_at;
 };
 
-// FP32-accumulated Gram sums are trusted while every Cholesky pivot keeps at
-// least this fraction of its column's squared norm; below it the tuple is
-// recomputed with FP64 sums (same role as flag_tau for periodogram bins).
-constexpr double TUPLE_TAU = 1e-2;
-
-// Accumulate <x_r x_c> over all points for the packed entries of the first
-// ncol columns, where the per-point column vector is produced by make(i, x).
-// Entries are split over the threads; each sums a fixed subset in point order
-// (deterministic), in T, then the totals are stored in G as FP64.
-template <class T, class Make>
-__device__ void gram_pass(TupleSmem<T> &sm, const TupleArgs &a, int ncol, Make make) {
-    const int ne = ncol * (ncol + 1) / 2;
-    constexpr int NQ = (MAXE * (MAXE + 1) / 2 + TU_THREADS - 1) / TU_THREADS;
-    T acc[NQ];
-    unsigned char rr[NQ], cc[NQ];
-    const int per = (ne + TU_THREADS - 1) / TU_THREADS;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        acc[q] = T(0);
-        const int e = threadIdx.x + q * TU_THREADS;
-        int r = 0;
-        while (tri(r + 1, 0) <= e) ++r;
-        rr[q] = (unsigned char)r;
-        cc[q] = (unsigned char)(e - tri(r, 0));
-    }
-    for (int64_t i0 = 0; i0 < a.N; i0 += TU_TILE) {
-        const int n = (int)(a.N - i0 < TU_TILE ? a.N - i0 : TU_TILE);
-        __syncthreads();
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            T x[MAXE];
-            make(i0 + p, x);
-            for (int c = 0; c < ncol; ++c) sm.X[c][p] = x[c];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (q >= per) break;
-            const int e = threadIdx.x + q * TU_THREADS;
-            if (e >= ne) break;
-            const int r = rr[q], c = cc[q];
-            T s = T(0);
-            for (int p = 0; p < n; ++p) s = fma(sm.X[r][p], sm.X[c][p], s);
-            acc[q] += s;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int e = threadIdx.x + q * TU_THREADS;
-        if (q < per && e < ne) sm.G[e] = (double)acc[q];
-    }
-    __syncthreads();
-}
-
-// cos/sin of tuple frequency k at point i: pool seed rotated by delta_k.
-template <class T>
-__device__ __forceinline__ void tuple_cs(const TupleArgs &a, const TupleSmem<T> &sm, const SeedTable &tab,
-                                         const SeedTableF &tabf, int k, int64_t i, double tp, T *c, T *s) {
-    const double2 cs0 = a.seeds[(int64_t)sm.pidx[k] * a.N + i];
-    const double dl = sm.delta[k];
-    if (dl == 0.0) {
-        *c = (T)cs0.x;
-        *s = (T)cs0.y;
+// cos/sin of tuple frequency k at a point: the pool seed rotated by the
+// trial offset.
+__device__ __forceinline__ void tuple_cs(const TupleArgs &a, const TState &s, const void *tab, int k, int64_t i,
+                                         float tp, float *c, float *sn) {
+    const float2 c0 = static_cast<const float2 *>(a.seeds)[(int64_t)s.pidx[k] * a.N + i];
+    const float dl = s.trialf[k];
+    if (dl == 0.0f) {
+        *c = c0.x;
+        *sn = c0.y;
         return;
     }
-    if constexpr (sizeof(T) == 8) {
-        double ds, dc;
-        seed_from_table(tab, frac_turns_u64(dl, tp), &ds, &dc);
-        *c = cs0.x * dc - cs0.y * ds;
-        *s = cs0.y * dc + cs0.x * ds;
+    const float turns = dl * tp;                      // small: |delta t'| of a few turns at most
+    const float r = turns - rintf(turns);
+    const float sc = fminf(fmaxf(r * 4294967296.0f, -2147483648.0f), 2147483520.0f);
+    float ds, dc;
+    seed_from_table_f(*static_cast<const SeedTableF *>(tab), (uint32_t)__float2int_rn(sc), &ds, &dc);
+    *c = c0.x * dc - c0.y * ds;
+    *sn = c0.y * dc + c0.x * ds;
+}
+__device__ __forceinline__ void tuple_cs(const TupleArgs &a, const TState &s, const void *tab, int k, int64_t i,
+                                         double tp, double *c, double *sn) {
+    const double2 c0 = static_cast<const double2 *>(a.seeds)[(int64_t)s.pidx[k] * a.N + i];
+    const double dl = s.trial[k];
+    if (dl == 0.0) {
+        *c = c0.x;
+        *sn = c0.y;
+        return;
+    }
+    double ds, dc;
+    seed_from_table(*static_cast<const SeedTable *>(tab), frac_turns_u64(dl, tp), &ds, &dc);
+    *c = c0.x * dc - c0.y * ds;
+    *sn = c0.y * dc + c0.x * ds;
+}
+
+// Weighted columns of point i into row[0..CP): [1, c_k, s_k (k < m), y] and,
+// with uv, [t' c_k, t' s_k] after them (the t-weighted averages of Eq. avrg1
+// and avrg2 from which the derivative columns are formed).
+template <class T>
+__device__ __forceinline__ void make_row(const TupleArgs &a, const TState &s, const void *tab, int64_t i, int m,
+                                         bool with_uv, int C, int CP, T *row) {
+    const Pt<T> p = static_cast<const Pt<T> *>(a.pts)[i];
+    const int M = 2 * m + 1;
+    row[0] = p.sw;
+    row[M] = p.yw;
+    const T swt = p.sw * p.tp;
+    for (int k = 0; k < m; ++k) {
+        T c, sn;
+        tuple_cs(a, s, tab, k, i, p.tp, &c, &sn);
+        row[1 + 2 * k] = p.sw * c;
+        row[2 + 2 * k] = p.sw * sn;
+        if (with_uv) {
+            row[M + 1 + 2 * k] = swt * c;
+            row[M + 2 + 2 * k] = swt * sn;
+        }
+    }
+    for (int c = C; c < CP; ++c) row[c] = T(0);
+}
+
+__device__ __forceinline__ void load4(const float *p, float *v) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double *p, double *v) {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+}
+
+__device__ __forceinline__ void block_rc(int q, int *rb, int *cb) {
+    int r = 0;
+    while (tri(r + 1, 0) <= q) ++r;
+    *rb = r;
+    *cb = q - tri(r, 0);
+}
+
+// One pass over all points: the FP64 Gram (packed, C x C) of the columns at
+// the trial offsets.
+template <class T>
+__device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, double *Gs, unsigned char *R, int m,
+                          bool with_uv) {
+    const int M = 2 * m + 1, C = with_uv ? M + 1 + 2 * m : M + 1, CP = (C + 3) & ~3;
+    const int nb = CP / 4, nblk = nb * (nb + 1) / 2;
+    const int tid = threadIdx.x, L = blockDim.x;
+    int G = 1, g = 0, nq = 0, rb[QB], cb[QB], qid = 0;
+    if (nblk <= L) {
+        G = L / nblk;
+        g = tid / nblk;
+        qid = tid % nblk;
+        nq = tid < G * nblk ? 1 : 0;
+        block_rc(qid, &rb[0], &cb[0]);
+        rb[1] = cb[1] = 0;
     } else {
-        float ds, dc;
-        const float turns = (float)dl * (float)tp;            // small: |delta t'| well below one turn
-        const float r = turns - rintf(turns);
-        const float sc = fminf(fmaxf(r * 4294967296.0f, -2147483648.0f), 2147483520.0f);
-        seed_from_table_f(tabf, (uint32_t)__float2int_rn(sc), &ds, &dc);
-        const float c0 = (float)cs0.x, s0 = (float)cs0.y;
-        *c = c0 * dc - s0 * ds;
-        *s = s0 * dc + c0 * ds;
-    }
-}
-
-// Linear fit of the current tuple: Gram of [1, c_k, s_k, y], Cholesky, a,
-// theta, l.  Returns false if the normal matrix is singular.
-template <class T>
-__device__ bool linear_fit(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable &tab, const SeedTableF &tabf) {
-    const int m = sm.m, M = sm.M;
-    const double tc = a.sp->tc, ybar = a.sp->ybar;
-    gram_pass<T>(sm, a, M + 1, [&](int64_t i, T *x) {
-        const double sw = 1.0 / a.sigma[i];
-        const double tp = a.t[i] - tc;
-        x[0] = (T)sw;
-        for (int k = 0; k < m; ++k) {
-            T c, s;
-            tuple_cs<T>(a, sm, tab, tabf, k, i, tp, &c, &s);
-            x[1 + 2 * k] = (T)sw * c;
-            x[2 + 2 * k] = (T)sw * s;
+#pragma unroll
+        for (int b = 0; b < QB; ++b) {
+            const int q = tid + b * L;
+            rb[b] = cb[b] = 0;
+            if (q < nblk) {
+                block_rc(q, &rb[b], &cb[b]);
+                nq = b + 1;
+            }
         }
-        x[M] = (T)(sw * (a.y[i] - ybar));
-    });
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < M; ++r)
-            for (int c = 0; c <= r; ++c) sm.Lq[tri(r, c)] = sm.G[tri(r, c)];
-        sm.flag = chol_inplace(sm.Lq, M, &sm.min_ratio) ? 1 : 0;
-        if (sm.flag) {
-            for (int r = 0; r < M; ++r) sm.a[r] = sm.G[tri(M, r)];
-            fwd(sm.Lq, sm.a, M);
-            double red = 0.0;
-            for (int r = 1; r < M; ++r) red += sm.a[r] * sm.a[r];
-            sm.l = a.sp->D - red;
-            sm.red = red;          // z = red/2 without cancelling against D
-            for (int r = 0; r < M; ++r) sm.X2[r] = sm.a[r];
-            bwd(sm.Lq, sm.X2, M);
+    }
+    T acc[QB][16];
+#pragma unroll
+    for (int b = 0; b < QB; ++b)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[b][e] = T(0);
+    T *X = reinterpret_cast<T *>(R);
+    for (int64_t i0 = 0; i0 < a.N; i0 += a.chunk) {
+        const int n = (int)(a.N - i0 < a.chunk ? a.N - i0 : a.chunk);
+        __syncthreads();
+        for (int p = tid; p < n; p += L) make_row<T>(a, s, tab, i0 + p, m, with_uv, C, CP, X + (size_t)p * CP);
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < QB; ++b) {
+            if (b < nq) {
+                T part[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) part[e] = T(0);
+                const T *xr = X + 4 * rb[b], *xc = X + 4 * cb[b];
+                for (int p = g; p < n; p += G) {
+                    T r[4], c[4];
+                    load4(xr + (size_t)p * CP, r);
+                    load4(xc + (size_t)p * CP, c);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) part[4 * u + v] = fma(r[u], c[v], part[4 * u + v]);
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[b][e] += part[e];
+            }
         }
     }
     __syncthreads();
-    return sm.flag != 0;
+    if (G == 1) {
+#pragma unroll
+        for (int b = 0; b < QB; ++b)
+            if (b < nq)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int r = 4 * rb[b] + e / 4, c = 4 * cb[b] + e % 4;
+                    if (r < C && c <= r) Gs[tri(r, c)] = (double)acc[b][e];
+                }
+    } else {
+        double *red = reinterpret_cast<double *>(R);   // [G][nblk][16]
+        if (nq)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) red[((size_t)g * nblk + qid) * 16 + e] = (double)acc[0][e];
+        __syncthreads();
+        for (int qe = tid; qe < nblk * 16; qe += L) {
+            const int q = qe >> 4, e = qe & 15;
+            double v = 0.0;
+            for (int gg = 0; gg < G; ++gg) v += red[((size_t)gg * nblk + q) * 16 + e];
+            int r0, c0;
+            block_rc(q, &r0, &c0);
+            const int r = 4 * r0 + e / 4, c = 4 * c0 + e % 4;
+            if (r < C && c <= r) Gs[tri(r, c)] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// In-place right-looking Cholesky of the packed C x C matrix by the whole CTA.
+// Pivots 0..nchk-1 must keep more than 1e-13 of their original diagonal; the
+// index of the first that does not is left in s.fail_at (C when all do).
+// s.ratio = the smallest pivot ratio among the first nlin pivots.  Later
+// pivots (the data column) are factored without a check.
+__device__ void chol_cta(double *A, double *d0, int C, int nlin, int nchk, TState &s) {
+    const int tid = threadIdx.x, L = blockDim.x;
+    for (int j = tid; j < C; j += L) d0[j] = A[tri(j, j)];
+    __syncthreads();
+    double ratio = 1.0;
+    int fail_at = C;
+    for (int j = 0; j < C; ++j) {
+        const double d = A[tri(j, j)];
+        if (j < nchk) {
+            const double r = d0[j] > 0.0 ? d / d0[j] : -1.0;
+            if (j < nlin) ratio = fmin(ratio, r);
+            if (!(d > 1e-13 * d0[j]) || !(d0[j] > 0.0)) {
+                fail_at = j;
+                break;
+            }
+        }
+        const double ljj = d > 0.0 ? sqrt(d) : 0.0;
+        __syncthreads();
+        if (tid == 0) A[tri(j, j)] = ljj;
+        if (ljj > 0.0)
+            for (int i = j + 1 + tid; i < C; i += L) A[tri(i, j)] /= ljj;
+        __syncthreads();
+        const int nt = C - j - 1, ne = nt * (nt + 1) / 2;
+        for (int e = tid; e < ne; e += L) {
+            int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (tri(ii + 1, 0) <= e) ++ii;
+            while (tri(ii, 0) > e) --ii;
+            const int i = j + 1 + ii, k = j + 1 + (e - tri(ii, 0));
+            A[tri(i, k)] -= A[tri(i, j)] * A[tri(k, j)];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        s.fail_at = fail_at;
+        s.ratio = ratio;
+    }
+    __syncthreads();
+}
+
+// Warp 0: x[0..n) <- L^{-T} x for the diagonal block of the packed factor that
+// starts at row/column o.
+__device__ void bwd_warp(const double *A, int o, int n, double *x) {
+    const int lane = threadIdx.x & 31;
+    for (int i = n - 1; i >= 0; --i) {
+        if (lane == 0) x[i] /= A[tri(o + i, o + i)];
+        __syncwarp();
+        const double xi = x[i];
+        for (int r = lane; r < i; r += 32) x[r] -= A[tri(o + i, o + r)] * xi;
+        __syncwarp();
+    }
+}
+
+// Warp 0, after chol_cta of the leading [phi, y] block (data column at index
+// M): red = sum_{r=1}^{M-1} a_r^2 and the coefficients theta = L^{-T} a into
+// th[0..M).
+__device__ void linear_solution(const double *A, int M, double *th, double *red_out) {
+    const int lane = threadIdx.x & 31;
+    double r2 = 0.0;
+    for (int r = lane; r < M; r += 32) {
+        const double v = A[tri(M, r)];
+        th[r] = v;
+        if (r >= 1) r2 += v * v;
+    }
+    r2 = warp_sum_d(r2);
+    __syncwarp();
+    bwd_warp(A, 0, M, th);
+    if (lane == 0) *red_out = r2;
+    __syncwarp();
+}
+
+// Warp 0: x[0..n) <- L^{-1} x for the packed factor L (n x n).
+__device__ void fwd_warp(const double *A, int n, double *x) {
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < n; ++i) {
+        if (lane == 0) x[i] /= A[tri(i, i)];
+        __syncwarp();
+        const double xi = x[i];
+        for (int r = i + 1 + lane; r < n; r += 32) x[r] -= A[tri(r, i)] * xi;
+        __syncwarp();
+    }
+}
+
+// The incremental extension of Section 3 for the frequency columns.  H is the
+// pass's Gram of [phi (M), y, t'c_0, t's_0, ...] whose leading [phi, y] block
+// has been factored in place (L, and a in row M); theta = L^{-T} a.  The
+// derivative columns d_k = 2 pi (b_k t'c_k - a_k t's_k) (a_k = theta_{1+2k},
+// b_k = theta_{2+2k}) enter through their Gram entries:
+//     X = L^{-1} <phi d>,  g = <d y> - X^T a = <d r>,  S = <d d> - X^T X.
+// Writes g (the gradient <d r> = dz/df) and, with want_step, the Gauss-Newton
+// step S^{-1} g; returns false when S is not positive definite.
+// Scratch W: m*M + m(m+1)/2 + m doubles.
+__device__ bool extend_cta(const double *H, const double *theta, int M, int m, double *W, double *g, double *step,
+                           TState &s) {
+    const int tid = threadIdx.x, L = blockDim.x;
+    double *Xs = W, *Sp = W + (size_t)m * M, *d0s = Sp + m * (m + 1) / 2;
+    const double tp2 = TWO_PI_D;
+    auto Hs = [&](int r, int c) { return r >= c ? H[tri(r, c)] : H[tri(c, r)]; };
+    for (int e = tid; e < m * M; e += L) {
+        const int k = e / M, j = e - k * M, u = M + 1 + 2 * k;
+        Xs[e] = tp2 * (theta[2 + 2 * k] * H[tri(u, j)] - theta[1 + 2 * k] * H[tri(u + 1, j)]);
+    }
+    for (int k = tid; k < m; k += L) {
+        const int u = M + 1 + 2 * k;
+        g[k] = tp2 * (theta[2 + 2 * k] * H[tri(u, M)] - theta[1 + 2 * k] * H[tri(u + 1, M)]);
+    }
+    for (int e = tid; e < m * (m + 1) / 2; e += L) {
+        int k = 0;
+        while (tri(k + 1, 0) <= e) ++k;
+        const int l = e - tri(k, 0);
+        const double ak = theta[1 + 2 * k], bk = theta[2 + 2 * k], al = theta[1 + 2 * l], bl = theta[2 + 2 * l];
+        const int uk = M + 1 + 2 * k, ul = M + 1 + 2 * l;
+        Sp[e] = tp2 * tp2 *
+                (bk * bl * Hs(uk, ul) - bk * al * Hs(uk, ul + 1) - ak * bl * Hs(uk + 1, ul) + ak * al * Hs(uk + 1, ul + 1));
+    }
+    __syncthreads();
+    // X = L^{-1} <phi d>: column k of X is row k of Xs; rows eliminated in order
+    for (int r = 0; r < M; ++r) {
+        const double lrr = H[tri(r, r)];
+        for (int k = tid; k < m; k += L) Xs[k * M + r] /= lrr;
+        __syncthreads();
+        const int rest = M - r - 1;
+        for (int e = tid; e < m * rest; e += L) {
+            const int k = e / rest, rr = r + 1 + (e - k * rest);
+            Xs[k * M + rr] -= H[tri(rr, r)] * Xs[k * M + r];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < m * (m + 1) / 2; e += L) {
+        int k = 0;
+        while (tri(k + 1, 0) <= e) ++k;
+        const int l = e - tri(k, 0);
+        double v = Sp[e];
+        for (int r = 0; r < M; ++r) v -= Xs[k * M + r] * Xs[l * M + r];
+        Sp[e] = v;
+    }
+    for (int k = tid; k < m; k += L) {
+        double v = g[k];
+        for (int r = 0; r < M; ++r) v -= Xs[k * M + r] * H[tri(M, r)];
+        g[k] = v;
+    }
+    __syncthreads();
+    if (!step) return true;
+    chol_cta(Sp, d0s, m, 0, m, s);
+    if (s.fail_at < m) return false;
+    if (tid < 32) {
+        for (int k = tid; k < m; k += 32) step[k] = g[k];
+        __syncwarp();
+        fwd_warp(Sp, m, step);
+        bwd_warp(Sp, 0, m, step);
+    }
+    __syncthreads();
+    return true;
+}
+
+__device__ void set_trial(TState &s, int m, const double *src_delta, const double *src_step, double h) {
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double v = src_delta[q] + (src_step ? h * src_step[q] : 0.0);
+        s.trial[q] = v;
+        s.trialf[q] = (float)v;
+    }
 }
 
 template <class T>
-__device__ void tuple_work(TupleSmem<T> &sm, const TupleArgs &a, const SeedTable &tab, const SeedTableF &tabf,
+__device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, double *Gs, double *d0, unsigned char *R,
                            int64_t k) {
+    const int tid = threadIdx.x;
     const int64_t o0 = a.off[k];
-    if (threadIdx.x == 0) {
-        sm.m = (int)(a.off[k + 1] - o0);
-        sm.M = 2 * sm.m + 1;
-        sm.min_ratio = 1.0;
-        for (int q = 0; q < sm.m; ++q) {
-            sm.pidx[q] = a.idx[o0 + q];
-            sm.delta[q] = 0.0;
-        }
+    if (tid == 0) s.m = (int)(a.off[k + 1] - o0);
+    __syncthreads();
+    const int m = s.m, M = 2 * m + 1;
+    for (int q = tid; q < m; q += blockDim.x) {
+        s.pidx[q] = a.idx[o0 + q];
+        s.delta[q] = 0.0;
+        s.trial[q] = 0.0;
+        s.trialf[q] = 0.0f;
     }
     __syncthreads();
-    const int m = sm.m, M = sm.M;
-    const double tc = a.sp->tc, ybar = a.sp->ybar;
-    if (!linear_fit<T>(sm, a, tab, tabf)) {
-        if (threadIdx.x == 0) {
+    const double D = a.sp->D;
+    const bool mixed = sizeof(T) == 4;
+    const bool uv = a.mode == 1 || a.mode == 2;
+    double *W = reinterpret_cast<double *>(R);   // extension scratch (free after a pass)
+    gram_pass<T>(a, s, tab, Gs, R, m, uv);
+    if (a.mode == 3) {
+        for (int e = tid; e < (M + 1) * (M + 2) / 2; e += blockDim.x) a.gram_out[e] = Gs[e];
+        if (tid == 0) a.status[k] = 0;
+        return;
+    }
+    chol_cta(Gs, d0, M + 1, M, M, s);
+    if (s.fail_at < M) {
+        if (tid == 0) {
             a.status[k] = 1;
             if (a.z) a.z[k] = NAN;
             if (a.l_out) a.l_out[k] = NAN;
         }
         return;
     }
-    if (a.mode == 0) {
-        if (threadIdx.x == 0) {
-            a.z[k] = 0.5 * sm.red;
-            a.status[k] = 0;
+    if (tid < 32) linear_solution(Gs, M, s.theta, &s.red);
+    __syncthreads();
+    double ratio = s.ratio;
+    if (a.mode == 0 || a.mode == 1) {
+        if (a.mode == 1) extend_cta(Gs, s.theta, M, m, W, s.x, nullptr, s);
+        if (a.mode == 1)
+            for (int q = tid; q < m; q += blockDim.x) a.dzdf[o0 + q] = s.x[q];
+        if (tid == 0) {
+            a.z[k] = 0.5 * s.red;
+            a.status[k] = (mixed && ratio < TUPLE_TAU) ? 2 : 0;
         }
         return;
     }
-    if (a.mode == 3) {   // pool Gram for the subtuple table: [1, c_k, s_k, y]
-        for (int e = threadIdx.x; e < (M + 1) * (M + 2) / 2; e += blockDim.x) a.gram_out[e] = sm.G[e];
-        if (threadIdx.x == 0) a.status[k] = 0;
-        return;
-    }
-    double zred = sm.red;
-    // coefficients theta = L^{-T} a are in X2[0..M)
-    int it = 0;
-    double lcur = sm.l;
-    for (;;) {
+    // refinement: exact Gauss-Newton steps, each trial point one pass
+    bool have_step = extend_cta(Gs, s.theta, M, m, W, s.x, s.step, s);
+    double lacc = D - s.red;
+    const double margin = mixed ? MIXED_L_NOISE * D : 1e-15 * fabs(lacc);
+    const int max_halvings = mixed ? MAX_HALVINGS_MIXED : MAX_HALVINGS;
+    const double span = a.sp->span;
+    int it = 0, fails = 0, flat = 0;
+    double h = 1.0;
+    while (have_step && it < a.max_iter) {
+        set_trial(s, m, s.delta, s.step, h);
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int r = 0; r < M; ++r) sm.theta[r] = sm.X2[r];
+        gram_pass<T>(a, s, tab, Gs, R, m, true);
+        chol_cta(Gs, d0, M + 1, M, M, s);
+        const bool lin_ok = s.fail_at >= M;
+        if (lin_ok && tid < 32) linear_solution(Gs, M, s.x, &s.redx);
         __syncthreads();
-        // derivative columns and residual: [phi (M), d (m), r (1)]
-        const int ne = M + m + 1;
-        gram_pass<T>(sm, a, ne, [&](int64_t i, T *x) {
-            const double sw = 1.0 / a.sigma[i];
-            const double tp = a.t[i] - tc;
-            double mu = sm.theta[0];
-            x[0] = (T)sw;
-            for (int q = 0; q < m; ++q) {
-                T c, s;
-                tuple_cs<T>(a, sm, tab, tabf, q, i, tp, &c, &s);
-                const double ta = sm.theta[1 + 2 * q], tb = sm.theta[2 + 2 * q];
-                mu += ta * (double)c + tb * (double)s;
-                x[1 + 2 * q] = (T)sw * c;
-                x[2 + 2 * q] = (T)sw * s;
-                x[M + q] = (T)(sw * TWO_PI_D * tp * (-ta * (double)s + tb * (double)c));
-            }
-            x[M + m] = (T)(sw * (a.y[i] - ybar - mu));
-        });
-        if (a.mode == 1) {
-            if (threadIdx.x < m) a.dzdf[a.off[k] + threadIdx.x] = sm.G[tri(M + m, M + threadIdx.x)];
-            if (threadIdx.x == 0) {
-                a.z[k] = 0.5 * zred;
-                a.status[k] = (sizeof(T) == 4 && sm.min_ratio < TUPLE_TAU) ? 2 : 0;
-            }
-            return;
-        }
-        // Gauss-Newton step through the Schur complement
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < m; ++q) {
-                for (int r = 0; r < M; ++r) sm.X2[q * MAXC + r] = sm.G[tri(M + q, r)];
-                fwd(sm.Lq, &sm.X2[q * MAXC], M);
-            }
-            for (int q = 0; q < m; ++q)
-                for (int p = 0; p <= q; ++p) {
-                    double v = sm.G[tri(M + q, M + p)];
-                    for (int r = 0; r < M; ++r) v -= sm.X2[q * MAXC + r] * sm.X2[p * MAXC + r];
-                    sm.S[tri(q, p)] = v;
-                }
-            for (int q = 0; q < m; ++q) sm.gd[q] = sm.G[tri(M + m, M + q)];
-            sm.flag = chol_inplace(sm.S, m, &sm.min_ratio) ? 1 : 0;
-            if (sm.flag) {
-                fwd(sm.S, sm.gd, m);
-                bwd(sm.S, sm.gd, m);
-            }
-        }
-        __syncthreads();
-        if (!sm.flag || it >= a.max_iter) break;
-        double dmax = 0.0;
-        for (int q = 0; q < m; ++q) dmax = fmax(dmax, fabs(sm.gd[q]));
-        // step with halving until l does not increase; with FP32-accumulated
-        // Gram sums l is only known to a few 1e-6 of <y^2>, so a step is
-        // accepted when it does not raise l by more than that
-        const double margin = sizeof(T) == 4 ? 3e-6 * a.sp->D : 1e-15 * lcur;
-        double fac = 1.0;
-        bool accepted = false;
-        for (int h = 0; h < 30; ++h, fac *= 0.5) {
-            if (threadIdx.x == 0)
-                for (int q = 0; q < m; ++q) {
-                    sm.step[q] = sm.delta[q];
-                    sm.delta[q] = sm.step[q] + fac * sm.gd[q];
-                }
+        const double lt = D - s.redx;
+        if (lin_ok && lt <= lacc + margin) {
+            double smax = 0.0;
+            for (int q = 0; q < m; ++q) smax = fmax(smax, fabs(s.step[q]));
+            const double moved = h * smax * span;
+            const double gain = lacc - lt;
+            lacc = lt;
+            ratio = fmin(ratio, s.ratio);
+            ++it;
             __syncthreads();
-            const bool ok = linear_fit<T>(sm, a, tab, tabf);
-            if (ok && sm.l <= lcur + margin) {
-                accepted = true;
-                break;
-            }
-            if (threadIdx.x == 0)
-                for (int q = 0; q < m; ++q) sm.delta[q] = sm.step[q];
+            for (int q = tid; q < m; q += blockDim.x) s.delta[q] = s.trial[q];
+            for (int r = tid; r < M; r += blockDim.x) s.theta[r] = s.x[r];
+            if (tid == 0) s.red = s.redx;
             __syncthreads();
+            have_step = extend_cta(Gs, s.theta, M, m, W, s.x, s.step, s);
+            // two full Gauss-Newton steps in a row that change l by less than
+            // its FP32 noise: the mixed sums cannot resolve the minimum further
+            flat = (mixed && h == 1.0 && gain < 0.1 * margin) ? flat + 1 : 0;
+            h = 1.0;
+            fails = 0;
+            if (moved < a.tol || flat >= 2) break;
+        } else {
+            h *= 0.5;
+            if (++fails > max_halvings) break;
         }
-        ++it;
-        if (!accepted) {
-            linear_fit<T>(sm, a, tab, tabf);   // restore the fit at the last accepted frequencies
-            break;
-        }
-        lcur = sm.l;
-        if (fac * dmax * a.sp->span < a.tol) break;
     }
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < m; ++q) a.f_out[a.off[k] + q] = a.pool[sm.pidx[q]] + sm.delta[q];
-        a.l_out[k] = lcur;
+    if (tid == 0) {
+        for (int q = 0; q < m; ++q) a.f_out[o0 + q] = a.pool[s.pidx[q]] + s.delta[q];
+        a.l_out[k] = lacc;
         if (a.iters) a.iters[k] = it;
-        a.status[k] = (sizeof(T) == 4 && sm.min_ratio < TUPLE_TAU) ? 2 : 0;
+        a.status[k] = (mixed && ratio < TUPLE_TAU) ? 2 : 0;   // worst conditioning on the way
     }
 }
 
 template <class T>
-__global__ void __launch_bounds__(TU_THREADS) tuple_kernel(TupleArgs a) {
+__global__ void __launch_bounds__(WT_THREADS, 4) tuple_kernel(TupleArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    TupleSmem<T> &sm = *reinterpret_cast<TupleSmem<T> *>(smraw);
-    SeedTable &tab = *reinterpret_cast<SeedTable *>(smraw + sizeof(TupleSmem<T>));
-    SeedTableF &tabf = *reinterpret_cast<SeedTableF *>(smraw + sizeof(TupleSmem<T>) + sizeof(SeedTable));
-    fill_seed_table(tab);
-    fill_seed_table_f(tabf);
+    const int CP = (a.cmax + 3) & ~3;
+    size_t o = 0;
+    void *tab = smraw;
+    o += sizeof(T) == 4 ? sizeof(SeedTableF) : sizeof(SeedTable);
+    o = (o + 15) & ~(size_t)15;
+    TState &s = *reinterpret_cast<TState *>(smraw + o);
+    o += sizeof(TState);
+    o = (o + 15) & ~(size_t)15;
+    double *Gs = reinterpret_cast<double *>(smraw + o);
+    o += sizeof(double) * (size_t)a.cmax * (a.cmax + 1) / 2;
+    double *d0 = reinterpret_cast<double *>(smraw + o);
+    o += sizeof(double) * (size_t)a.cmax;
+    o = (o + 15) & ~(size_t)15;
+    unsigned char *R = smraw + o;
+    (void)CP;
+    if (sizeof(T) == 4) fill_seed_table_f(*static_cast<SeedTableF *>(tab));
+    else fill_seed_table(*static_cast<SeedTable *>(tab));
     __syncthreads();
     __shared__ int64_t cur;
     for (;;) {
         if (threadIdx.x == 0) cur = atomicAdd(a.next, 1);
         __syncthreads();
-        const int64_t k = cur;
-        if (k >= a.n_tuples) break;
-        tuple_work<T>(sm, a, tab, tabf, k);
+        const int64_t q = cur;
+        if (q >= a.n_tuples) break;
+        tuple_work<T>(a, s, tab, Gs, d0, R, a.order ? (int64_t)a.order[q] : q);
         __syncthreads();
     }
+}
+
+size_t tuple_smem(int prec, int cmax, int chunk) {
+    const size_t tsz = prec == FREDEC_MIXED ? 4 : 8;
+    const int CP = (cmax + 3) & ~3;
+    size_t o = prec == FREDEC_MIXED ? sizeof(SeedTableF) : sizeof(SeedTable);
+    o = (o + 15) & ~(size_t)15;
+    o += sizeof(TState);
+    o = (o + 15) & ~(size_t)15;
+    o += sizeof(double) * (size_t)cmax * (cmax + 1) / 2 + sizeof(double) * (size_t)cmax;
+    o = (o + 15) & ~(size_t)15;
+    o += std::max<size_t>((size_t)chunk * CP * tsz, (size_t)WT_THREADS * 16 * 8);
+    return o;
+}
+
+int tuple_chunk(int prec, int cmax) {
+    const size_t tsz = prec == FREDEC_MIXED ? 4 : 8;
+    const int CP = (cmax + 3) & ~3;
+    return (int)std::max<size_t>(1, std::min<size_t>(WT_THREADS, CHUNK_BYTES / (CP * tsz)));
 }
 
 // One warp per mask: gather the mask's columns [1, c_k, s_k (k in mask)] and
@@ -519,16 +736,43 @@ __global__ void __launch_bounds__(32 * PM_WARPS) pool_mask_kernel(const double *
 
 // Host side -------------------------------------------------------------------
 
+static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
+    const size_t smem = tuple_smem(precision, a.cmax, a.chunk);
+    auto kern = precision == FREDEC_MIXED ? tuple_kernel<float> : tuple_kernel<double>;
+    FREDEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FREDEC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WT_THREADS, smem));
+    const int64_t grid = std::min<int64_t>(std::max<int64_t>(a.n_tuples, 1), (int64_t)std::max(per_sm, 1) * sm_count());
+    kern<<<(unsigned)grid, WT_THREADS, smem, st>>>(a);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
+// Tuples given as indices into a pool of frequencies (CSR: tuple k holds
+// pool[idx[off[k] .. off[k+1])]).  mode 0 z, 1 z and dz/df, 2 refinement.
+// Host inputs and outputs; synchronous.  Mixed-precision tuples whose linear
+// system was ill-conditioned anywhere on their way are redone from scratch
+// with FP64 sums (an inaccurate early step can lead a refinement into another
+// basin, which a continuation would keep).
 static int tuple_run(const double *t, const double *y, const double *sigma, int64_t N, const double *pool_h,
                      int npool, const std::vector<int32_t> &idx_h, const std::vector<int64_t> &off_h, int mode,
                      int precision, int max_iter, double tol, double *z_h, double *dzdf_h, double *f_h, double *l_h,
                      int32_t *iters_h, double *l0_h, cudaStream_t st) {
     const int64_t nt = (int64_t)off_h.size() - 1;
     const int64_t nflat = off_h.back();
+    const size_t tsz = precision == FREDEC_MIXED ? 4 : 8;
+    int mmax = 0;
+    for (int64_t k = 0; k < nt; ++k) mmax = std::max<int>(mmax, (int)(off_h[k + 1] - off_h[k]));
+    std::vector<int32_t> order(std::max<int64_t>(nt, 1));
+    std::iota(order.begin(), order.begin() + nt, 0);
+    std::stable_sort(order.begin(), order.begin() + nt, [&](int32_t p, int32_t q) {
+        return off_h[p + 1] - off_h[p] > off_h[q + 1] - off_h[q];
+    });
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
     const size_t o_in = take(3 * N * 8), o_sp = take(sizeof(SeriesPrep)), o_pool = take(npool * 8 + 8),
-                 o_seed = take((size_t)npool * N * 16 + 16), o_idx = take(nflat * 4 + 4), o_off = take((nt + 1) * 8),
+                 o_pts = take(N * 4 * tsz), o_seed = take((size_t)npool * N * 2 * tsz + 16),
+                 o_idx = take(nflat * 4 + 4), o_off = take((nt + 1) * 8), o_ord = take(nt * 4 + 4),
                  o_z = take(nt * 8 + 8), o_g = take(nflat * 8 + 8), o_f = take(nflat * 8 + 8), o_l = take(nt * 8 + 8),
                  o_it = take(nt * 4 + 4), o_st = take(nt * 4 + 4), o_next = take(8);
     DevBuf ws;
@@ -541,22 +785,31 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     if (npool) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_pool, pool_h, npool * 8, cudaMemcpyHostToDevice, st));
     if (nflat) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_idx, idx_h.data(), nflat * 4, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_off, off_h.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (nt) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_ord, order.data(), nt * 4, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 8, st));
     SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
     series_prep<<<1, 256, 0, st>>>(dt, dy, ds, N, sp);
-    if (npool)
-        pool_seeds<<<(unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256), 256, 0, st>>>(
-            dt, N, (const double *)(b + o_pool), npool, sp, (double2 *)(b + o_seed));
+    const unsigned pb = (unsigned)std::min<int64_t>(1024, (N + 255) / 256);
+    const unsigned sb = (unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256);
+    if (precision == FREDEC_MIXED) {
+        point_prep<float><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<float> *)(b + o_pts));
+        if (npool) pool_seeds<float2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
+                                                          (float2 *)(b + o_seed));
+    } else {
+        point_prep<double><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<double> *)(b + o_pts));
+        if (npool) pool_seeds<double2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
+                                                           (double2 *)(b + o_seed));
+    }
+    FREDEC_CUDA_TRY(cudaGetLastError());
     TupleArgs a{};
-    a.t = dt;
-    a.y = dy;
-    a.sigma = ds;
     a.N = N;
     a.sp = sp;
-    a.seeds = (const double2 *)(b + o_seed);
+    a.pts = b + o_pts;
+    a.seeds = b + o_seed;
     a.pool = (const double *)(b + o_pool);
     a.idx = (const int32_t *)(b + o_idx);
     a.off = (const int64_t *)(b + o_off);
+    a.order = (const int32_t *)(b + o_ord);
     a.n_tuples = nt;
     a.mode = mode;
     a.max_iter = max_iter;
@@ -568,53 +821,45 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     a.iters = (int32_t *)(b + o_it);
     a.status = (int32_t *)(b + o_st);
     a.next = (int32_t *)(b + o_next);
-    const int grid = (int)std::min<int64_t>(std::max<int64_t>(nt, 1), 8LL * sm_count());
-    if (nt > 0) {
-        if (precision == FREDEC_MIXED) {
-            const size_t smem = sizeof(TupleSmem<float>) + sizeof(SeedTable) + sizeof(SeedTableF);
-            FREDEC_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            tuple_kernel<float><<<grid, TU_THREADS, smem, st>>>(a);
-        } else {
-            const size_t smem = sizeof(TupleSmem<double>) + sizeof(SeedTable) + sizeof(SeedTableF);
-            FREDEC_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            tuple_kernel<double><<<grid, TU_THREADS, smem, st>>>(a);
-        }
-    }
-    FREDEC_CUDA_TRY(cudaGetLastError());
+    a.cmax = std::max(2, mode == 0 ? 2 * mmax + 2 : 4 * mmax + 2);
+    a.chunk = tuple_chunk(precision, a.cmax);
+    if (nt > 0)
+        if (int rc = launch_tuples(a, precision, st)) return rc;
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int32_t> status(std::max<int64_t>(nt, 1));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpy(status.data(), b + o_st, nt * 4, cudaMemcpyDeviceToHost));
     for (int64_t k = 0; k < nt; ++k)
         if (status[k] == 1) return fail(FREDEC_ESINGULAR, "a tuple's normal matrix is singular (repeated frequency?)");
-    // tuples whose FP32-accumulated systems were ill-conditioned: redo in FP64
-    std::vector<int64_t> redo;
-    for (int64_t k = 0; k < nt; ++k)
-        if (status[k] == 2) redo.push_back(k);
-    std::vector<double> z2, g2, f2, l2;
-    std::vector<int32_t> it2;
-    std::vector<int64_t> off2(1, 0);
-    if (!redo.empty()) {
-        std::vector<int32_t> idx2;
-        for (int64_t k : redo) {
-            for (int64_t q = off_h[k]; q < off_h[k + 1]; ++q) idx2.push_back(idx_h[q]);
-            off2.push_back((int64_t)idx2.size());
-        }
-        const int64_t n2 = (int64_t)redo.size(), nf2 = off2.back();
-        z2.resize(n2 + 1);
-        l2.resize(n2 + 1);
-        it2.resize(n2 + 1);
-        g2.resize(nf2 + 1);
-        f2.resize(nf2 + 1);
-        if (int rc = tuple_run(t, y, sigma, N, pool_h, npool, idx2, off2, mode, FREDEC_FP64, max_iter, tol, z2.data(),
-                               g2.data(), f2.data(), l2.data(), it2.data(), nullptr, st))
-            return rc;
-    }
     if (z_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(z_h, b + o_z, nt * 8, cudaMemcpyDeviceToHost));
     if (dzdf_h && nflat) FREDEC_CUDA_TRY(cudaMemcpy(dzdf_h, b + o_g, nflat * 8, cudaMemcpyDeviceToHost));
     if (f_h && nflat) FREDEC_CUDA_TRY(cudaMemcpy(f_h, b + o_f, nflat * 8, cudaMemcpyDeviceToHost));
     if (l_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(l_h, b + o_l, nt * 8, cudaMemcpyDeviceToHost));
     if (iters_h && nt) FREDEC_CUDA_TRY(cudaMemcpy(iters_h, b + o_it, nt * 4, cudaMemcpyDeviceToHost));
-    for (size_t r = 0; r < redo.size(); ++r) {
+    if (l0_h) {
+        SeriesPrep h;
+        FREDEC_CUDA_TRY(cudaMemcpy(&h, sp, sizeof(h), cudaMemcpyDeviceToHost));
+        *l0_h = h.D;
+    }
+    // tuples whose FP32-accumulated systems were ill-conditioned: FP64 sums
+    std::vector<int64_t> redo;
+    for (int64_t k = 0; k < nt; ++k)
+        if (status[k] == 2) redo.push_back(k);
+    if (redo.empty()) return FREDEC_OK;
+    const int64_t n2 = (int64_t)redo.size();
+    std::vector<int64_t> off2(1, 0);
+    std::vector<int32_t> idx2;
+    for (int64_t k : redo) {
+        for (int64_t q = off_h[k]; q < off_h[k + 1]; ++q) idx2.push_back(idx_h[q]);
+        off2.push_back((int64_t)idx2.size());
+    }
+    const int64_t nf2 = off2.back();
+    std::vector<double> z2(n2 + 1), g2(nf2 + 1), f2(nf2 + 1), l2(n2 + 1);
+    std::vector<int32_t> it2(n2 + 1);
+    if (int rc = tuple_run(t, y, sigma, N, pool_h, npool, idx2, off2, mode, FREDEC_FP64,
+                           max_iter, tol, z2.data(), g2.data(),
+                           f2.data(), l2.data(), it2.data(), nullptr, st))
+        return rc;
+    for (int64_t r = 0; r < n2; ++r) {
         const int64_t k = redo[r];
         if (z_h) z_h[k] = z2[r];
         if (l_h) l_h[k] = l2[r];
@@ -623,11 +868,6 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
             if (dzdf_h) dzdf_h[off_h[k] + q] = g2[off2[r] + q];
             if (f_h) f_h[off_h[k] + q] = f2[off2[r] + q];
         }
-    }
-    if (l0_h) {
-        SeriesPrep h;
-        FREDEC_CUDA_TRY(cudaMemcpy(&h, sp, sizeof(h), cudaMemcpyDeviceToHost));
-        *l0_h = h.D;
     }
     return FREDEC_OK;
 }
@@ -639,8 +879,8 @@ static int pool_table_run(const double *t, const double *y, const double *sigma,
     const int Mx = 2 * npool + 2;
     const int64_t nmask = 1LL << npool;
     const size_t o_in = take(3 * N * 8), o_sp = take(sizeof(SeriesPrep)), o_pool = take(npool * 8 + 8),
-                 o_seed = take((size_t)npool * N * 16 + 16), o_idx = take(npool * 4 + 4), o_off = take(16),
-                 o_gram = take((size_t)Mx * (Mx + 1) / 2 * 8), o_st = take(8), o_next = take(8),
+                 o_pts = take(N * 32), o_seed = take((size_t)npool * N * 16 + 16), o_idx = take(npool * 4 + 4),
+                 o_off = take(16), o_gram = take((size_t)Mx * (Mx + 1) / 2 * 8), o_st = take(8), o_next = take(8),
                  o_tab = take(nmask * 8);
     DevBuf ws;
     if (int rc = ws.alloc(off, st)) return rc;
@@ -658,41 +898,39 @@ static int pool_table_run(const double *t, const double *y, const double *sigma,
     FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 8, st));
     SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
     series_prep<<<1, 256, 0, st>>>(dt, dy, ds, N, sp);
+    point_prep<double><<<(unsigned)std::min<int64_t>(1024, (N + 255) / 256), 256, 0, st>>>(dt, dy, ds, N, sp,
+                                                                                           (Pt<double> *)(b + o_pts));
     if (npool)
-        pool_seeds<<<(unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256), 256, 0, st>>>(
+        pool_seeds<double2><<<(unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256), 256, 0, st>>>(
             dt, N, (const double *)(b + o_pool), npool, sp, (double2 *)(b + o_seed));
     TupleArgs a{};
-    a.t = dt;
-    a.y = dy;
-    a.sigma = ds;
     a.N = N;
     a.sp = sp;
-    a.seeds = (const double2 *)(b + o_seed);
+    a.pts = b + o_pts;
+    a.seeds = b + o_seed;
     a.pool = (const double *)(b + o_pool);
     a.idx = (const int32_t *)(b + o_idx);
     a.off = (const int64_t *)(b + o_off);
+    a.order = nullptr;
     a.n_tuples = 1;
     a.mode = 3;
     a.status = (int32_t *)(b + o_st);
     a.next = (int32_t *)(b + o_next);
     a.gram_out = (double *)(b + o_gram);
-    const size_t smem = sizeof(TupleSmem<double>) + sizeof(SeedTable) + sizeof(SeedTableF);
-    FREDEC_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tuple_kernel<double><<<1, TU_THREADS, smem, st>>>(a);
+    a.cmax = Mx;
+    a.chunk = tuple_chunk(FREDEC_FP64, a.cmax);
+    if (int rc = launch_tuples(a, FREDEC_FP64, st)) return rc;
     const int64_t blocks = std::min<int64_t>((nmask + PM_WARPS - 1) / PM_WARPS, 64LL * sm_count());
     pool_mask_kernel<<<(unsigned)blocks, 32 * PM_WARPS, 0, st>>>((const double *)(b + o_gram), npool, sp, nmask,
                                                                   (double *)(b + o_tab));
     FREDEC_CUDA_TRY(cudaGetLastError());
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
-    int32_t status = 0;
-    FREDEC_CUDA_TRY(cudaMemcpy(&status, b + o_st, 4, cudaMemcpyDeviceToHost));
-    if (status) return fail(FREDEC_ESINGULAR, "the pool's normal matrix is singular (repeated pool frequency?)");
     FREDEC_CUDA_TRY(cudaMemcpy(l_table_h, b + o_tab, nmask * 8, cudaMemcpyDeviceToHost));
     return FREDEC_OK;
 }
 
 static int check_tuple_inputs(const double *t, const double *y, const double *sigma, int64_t N, const double *freqs,
-                              const int64_t *off, int64_t n) {
+                              const int64_t *off, int64_t n, int max_m = FREDEC_MAX_TUPLE) {
     if (!t || !y || !sigma || N < 1 || n < 0 || (n > 0 && !off)) return fail(FREDEC_EINVAL, "bad arguments");
     for (int64_t i = 0; i < N; ++i)
         if (!std::isfinite(t[i]) || !std::isfinite(y[i]) || !(sigma[i] > 0.0) || !std::isfinite(sigma[i]))
@@ -700,7 +938,9 @@ static int check_tuple_inputs(const double *t, const double *y, const double *si
     if (n > 0 && off[0] != 0) return fail(FREDEC_EINVAL, "tuple_offsets[0] must be 0");
     for (int64_t k = 0; k < n; ++k) {
         const int64_t m = off[k + 1] - off[k];
-        if (m < 0 || m > FREDEC_MAX_POOL) return fail(FREDEC_EINVAL, "tuple sizes must be in 0..FREDEC_MAX_TUPLE");
+        if (m < 0 || m > max_m)
+            return fail(FREDEC_EINVAL, max_m == FREDEC_MAX_TUPLE ? "tuple sizes must be in 0..FREDEC_MAX_TUPLE"
+                                                                  : "pool sizes must be in 0..FREDEC_MAX_POOL");
         if (N < 2 * m + 2) return fail(FREDEC_EINVAL, "N must exceed 2m+1 for every tuple");
     }
     if (n > 0 && !freqs && off[n] > 0) return fail(FREDEC_EINVAL, "null frequencies");
@@ -741,7 +981,7 @@ int fredec_pool_subtuples_eval(const double *t, const double *y, const double *s
     if (n_pool < 0 || n_pool > FREDEC_MAX_POOL || !l_table || (n_pool > 0 && !pool))
         return fail(FREDEC_EINVAL, "n_pool must be in 0..FREDEC_MAX_POOL");
     const int64_t off[2] = {0, n_pool};
-    if (int rc = check_tuple_inputs(t, y, sigma, N, pool, off, 1)) return rc;
+    if (int rc = check_tuple_inputs(t, y, sigma, N, pool, off, 1, FREDEC_MAX_POOL)) return rc;
     TStream ts;
     FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&ts.s, cudaStreamNonBlocking));
     return pool_table_run(t, y, sigma, N, pool, n_pool, l_table, ts.s);
