@@ -345,31 +345,36 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
 }
 
 // In-place right-looking Cholesky of the packed C x C matrix by the whole CTA.
+// Thread 0 takes each pivot (check, square root, reciprocal; the reciprocal
+// diagonal is kept in inv[] for the substitutions), the CTA scales the column
+// and updates the trailing triangle (threads over its entries).
 // Pivots 0..nchk-1 must keep more than 1e-13 of their original diagonal; the
 // index of the first that does not is left in s.fail_at (C when all do).
 // s.ratio = the smallest pivot ratio among the first nlin pivots.  Later
 // pivots (the data column) are factored without a check.
-__device__ void chol_cta(double *A, double *d0, int C, int nlin, int nchk, TState &s) {
+__device__ void chol_cta(double *A, double *d0, double *inv, int C, int nlin, int nchk, TState &s) {
     const int tid = threadIdx.x, L = blockDim.x;
     for (int j = tid; j < C; j += L) d0[j] = A[tri(j, j)];
+    if (tid == 0) {
+        s.fail_at = C;
+        s.ratio = 1.0;
+    }
     __syncthreads();
-    double ratio = 1.0;
-    int fail_at = C;
     for (int j = 0; j < C; ++j) {
-        const double d = A[tri(j, j)];
-        if (j < nchk) {
-            const double r = d0[j] > 0.0 ? d / d0[j] : -1.0;
-            if (j < nlin) ratio = fmin(ratio, r);
-            if (!(d > 1e-13 * d0[j]) || !(d0[j] > 0.0)) {
-                fail_at = j;
-                break;
+        if (tid == 0) {
+            const double d = A[tri(j, j)];
+            if (j < nchk) {
+                if (j < nlin) s.ratio = fmin(s.ratio, d0[j] > 0.0 ? d / d0[j] : -1.0);
+                if (!(d > 1e-13 * d0[j]) || !(d0[j] > 0.0)) s.fail_at = j;
             }
+            const double l = d > 0.0 ? sqrt(d) : 0.0;
+            A[tri(j, j)] = l;
+            inv[j] = l > 0.0 ? 1.0 / l : 0.0;
         }
-        const double ljj = d > 0.0 ? sqrt(d) : 0.0;
         __syncthreads();
-        if (tid == 0) A[tri(j, j)] = ljj;
-        if (ljj > 0.0)
-            for (int i = j + 1 + tid; i < C; i += L) A[tri(i, j)] /= ljj;
+        if (s.fail_at < C) break;
+        const double iv = inv[j];
+        for (int i = j + 1 + tid; i < C; i += L) A[tri(i, j)] *= iv;
         __syncthreads();
         const int nt = C - j - 1, ne = nt * (nt + 1) / 2;
         for (int e = tid; e < ne; e += L) {
@@ -381,19 +386,14 @@ __device__ void chol_cta(double *A, double *d0, int C, int nlin, int nchk, TStat
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        s.fail_at = fail_at;
-        s.ratio = ratio;
-    }
-    __syncthreads();
 }
 
 // Warp 0: x[0..n) <- L^{-T} x for the diagonal block of the packed factor that
-// starts at row/column o.
-__device__ void bwd_warp(const double *A, int o, int n, double *x) {
+// starts at row/column o (inv: its reciprocal diagonal).
+__device__ void bwd_warp(const double *A, const double *inv, int o, int n, double *x) {
     const int lane = threadIdx.x & 31;
     for (int i = n - 1; i >= 0; --i) {
-        if (lane == 0) x[i] /= A[tri(o + i, o + i)];
+        if (lane == 0) x[i] *= inv[o + i];
         __syncwarp();
         const double xi = x[i];
         for (int r = lane; r < i; r += 32) x[r] -= A[tri(o + i, o + r)] * xi;
@@ -404,7 +404,7 @@ __device__ void bwd_warp(const double *A, int o, int n, double *x) {
 // Warp 0, after chol_cta of the leading [phi, y] block (data column at index
 // M): red = sum_{r=1}^{M-1} a_r^2 and the coefficients theta = L^{-T} a into
 // th[0..M).
-__device__ void linear_solution(const double *A, int M, double *th, double *red_out) {
+__device__ void linear_solution(const double *A, const double *inv, int M, double *th, double *red_out) {
     const int lane = threadIdx.x & 31;
     double r2 = 0.0;
     for (int r = lane; r < M; r += 32) {
@@ -414,16 +414,17 @@ __device__ void linear_solution(const double *A, int M, double *th, double *red_
     }
     r2 = warp_sum_d(r2);
     __syncwarp();
-    bwd_warp(A, 0, M, th);
+    bwd_warp(A, inv, 0, M, th);
     if (lane == 0) *red_out = r2;
     __syncwarp();
 }
 
-// Warp 0: x[0..n) <- L^{-1} x for the packed factor L (n x n).
-__device__ void fwd_warp(const double *A, int n, double *x) {
+// Warp 0: x[0..n) <- L^{-1} x for the packed factor L (n x n, inv: its
+// reciprocal diagonal).
+__device__ void fwd_warp(const double *A, const double *inv, int n, double *x) {
     const int lane = threadIdx.x & 31;
     for (int i = 0; i < n; ++i) {
-        if (lane == 0) x[i] /= A[tri(i, i)];
+        if (lane == 0) x[i] *= inv[i];
         __syncwarp();
         const double xi = x[i];
         for (int r = i + 1 + lane; r < n; r += 32) x[r] -= A[tri(r, i)] * xi;
@@ -439,11 +440,11 @@ __device__ void fwd_warp(const double *A, int n, double *x) {
 //     X = L^{-1} <phi d>,  g = <d y> - X^T a = <d r>,  S = <d d> - X^T X.
 // Writes g (the gradient <d r> = dz/df) and, with want_step, the Gauss-Newton
 // step S^{-1} g; returns false when S is not positive definite.
-// Scratch W: m*M + m(m+1)/2 + m doubles.
-__device__ bool extend_cta(const double *H, const double *theta, int M, int m, double *W, double *g, double *step,
-                           TState &s) {
+// Scratch W: m*M + m(m+1)/2 + 2m doubles.
+__device__ bool extend_cta(const double *H, const double *invL, int M, int m, const double *theta, double *W, double *g,
+                           double *step, TState &s) {
     const int tid = threadIdx.x, L = blockDim.x;
-    double *Xs = W, *Sp = W + (size_t)m * M, *d0s = Sp + m * (m + 1) / 2;
+    double *Xs = W, *Sp = W + (size_t)m * M, *d0s = Sp + m * (m + 1) / 2, *invS = d0s + m;
     const double tp2 = TWO_PI_D;
     auto Hs = [&](int r, int c) { return r >= c ? H[tri(r, c)] : H[tri(c, r)]; };
     for (int e = tid; e < m * M; e += L) {
@@ -466,8 +467,8 @@ __device__ bool extend_cta(const double *H, const double *theta, int M, int m, d
     __syncthreads();
     // X = L^{-1} <phi d>: column k of X is row k of Xs; rows eliminated in order
     for (int r = 0; r < M; ++r) {
-        const double lrr = H[tri(r, r)];
-        for (int k = tid; k < m; k += L) Xs[k * M + r] /= lrr;
+        const double ir = invL[r];
+        for (int k = tid; k < m; k += L) Xs[k * M + r] *= ir;
         __syncthreads();
         const int rest = M - r - 1;
         for (int e = tid; e < m * rest; e += L) {
@@ -491,13 +492,13 @@ __device__ bool extend_cta(const double *H, const double *theta, int M, int m, d
     }
     __syncthreads();
     if (!step) return true;
-    chol_cta(Sp, d0s, m, 0, m, s);
+    chol_cta(Sp, d0s, invS, m, 0, m, s);
     if (s.fail_at < m) return false;
     if (tid < 32) {
         for (int k = tid; k < m; k += 32) step[k] = g[k];
         __syncwarp();
-        fwd_warp(Sp, m, step);
-        bwd_warp(Sp, 0, m, step);
+        fwd_warp(Sp, invS, m, step);
+        bwd_warp(Sp, invS, 0, m, step);
     }
     __syncthreads();
     return true;
@@ -512,8 +513,8 @@ __device__ void set_trial(TState &s, int m, const double *src_delta, const doubl
 }
 
 template <class T>
-__device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, double *Gs, double *d0, unsigned char *R,
-                           int64_t k) {
+__device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, double *Gs, double *d0, double *inv,
+                           unsigned char *R, int64_t k) {
     const int tid = threadIdx.x;
     const int64_t o0 = a.off[k];
     if (tid == 0) s.m = (int)(a.off[k + 1] - o0);
@@ -536,7 +537,7 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
         if (tid == 0) a.status[k] = 0;
         return;
     }
-    chol_cta(Gs, d0, M + 1, M, M, s);
+    chol_cta(Gs, d0, inv, M + 1, M, M, s);
     if (s.fail_at < M) {
         if (tid == 0) {
             a.status[k] = 1;
@@ -545,11 +546,11 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
         }
         return;
     }
-    if (tid < 32) linear_solution(Gs, M, s.theta, &s.red);
+    if (tid < 32) linear_solution(Gs, inv, M, s.theta, &s.red);
     __syncthreads();
     double ratio = s.ratio;
     if (a.mode == 0 || a.mode == 1) {
-        if (a.mode == 1) extend_cta(Gs, s.theta, M, m, W, s.x, nullptr, s);
+        if (a.mode == 1) extend_cta(Gs, inv, M, m, s.theta, W, s.x, nullptr, s);
         if (a.mode == 1)
             for (int q = tid; q < m; q += blockDim.x) a.dzdf[o0 + q] = s.x[q];
         if (tid == 0) {
@@ -559,7 +560,9 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
         return;
     }
     // refinement: exact Gauss-Newton steps, each trial point one pass
-    bool have_step = extend_cta(Gs, s.theta, M, m, W, s.x, s.step, s);
+    // a mixed tuple that meets an ill-conditioned system is redone from scratch
+    // in FP64, so its FP32 refinement stops there
+    bool have_step = !(mixed && ratio < TUPLE_TAU) && extend_cta(Gs, inv, M, m, s.theta, W, s.x, s.step, s);
     double lacc = D - s.red;
     const double margin = mixed ? MIXED_L_NOISE * D : 1e-15 * fabs(lacc);
     const int max_halvings = mixed ? MAX_HALVINGS_MIXED : MAX_HALVINGS;
@@ -570,9 +573,9 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
         set_trial(s, m, s.delta, s.step, h);
         __syncthreads();
         gram_pass<T>(a, s, tab, Gs, R, m, true);
-        chol_cta(Gs, d0, M + 1, M, M, s);
+        chol_cta(Gs, d0, inv, M + 1, M, M, s);
         const bool lin_ok = s.fail_at >= M;
-        if (lin_ok && tid < 32) linear_solution(Gs, M, s.x, &s.redx);
+        if (lin_ok && tid < 32) linear_solution(Gs, inv, M, s.x, &s.redx);
         __syncthreads();
         const double lt = D - s.redx;
         if (lin_ok && lt <= lacc + margin) {
@@ -588,7 +591,8 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
             for (int r = tid; r < M; r += blockDim.x) s.theta[r] = s.x[r];
             if (tid == 0) s.red = s.redx;
             __syncthreads();
-            have_step = extend_cta(Gs, s.theta, M, m, W, s.x, s.step, s);
+            if (mixed && ratio < TUPLE_TAU) break;
+            have_step = extend_cta(Gs, inv, M, m, s.theta, W, s.x, s.step, s);
             // two full Gauss-Newton steps in a row that change l by less than
             // its FP32 noise: the mixed sums cannot resolve the minimum further
             flat = (mixed && h == 1.0 && gain < 0.1 * margin) ? flat + 1 : 0;
@@ -623,6 +627,8 @@ __global__ void __launch_bounds__(WT_THREADS, 4) tuple_kernel(TupleArgs a) {
     o += sizeof(double) * (size_t)a.cmax * (a.cmax + 1) / 2;
     double *d0 = reinterpret_cast<double *>(smraw + o);
     o += sizeof(double) * (size_t)a.cmax;
+    double *inv = reinterpret_cast<double *>(smraw + o);
+    o += sizeof(double) * (size_t)a.cmax;
     o = (o + 15) & ~(size_t)15;
     unsigned char *R = smraw + o;
     (void)CP;
@@ -635,7 +641,7 @@ __global__ void __launch_bounds__(WT_THREADS, 4) tuple_kernel(TupleArgs a) {
         __syncthreads();
         const int64_t q = cur;
         if (q >= a.n_tuples) break;
-        tuple_work<T>(a, s, tab, Gs, d0, R, a.order ? (int64_t)a.order[q] : q);
+        tuple_work<T>(a, s, tab, Gs, d0, inv, R, a.order ? (int64_t)a.order[q] : q);
         __syncthreads();
     }
 }
@@ -647,7 +653,7 @@ size_t tuple_smem(int prec, int cmax, int chunk) {
     o = (o + 15) & ~(size_t)15;
     o += sizeof(TState);
     o = (o + 15) & ~(size_t)15;
-    o += sizeof(double) * (size_t)cmax * (cmax + 1) / 2 + sizeof(double) * (size_t)cmax;
+    o += sizeof(double) * (size_t)cmax * (cmax + 1) / 2 + 2 * sizeof(double) * (size_t)cmax;
     o = (o + 15) & ~(size_t)15;
     o += std::max<size_t>((size_t)chunk * CP * tsz, (size_t)WT_THREADS * 16 * 8);
     return o;
@@ -708,7 +714,8 @@ __global__ void __launch_bounds__(32 * PM_WARPS) pool_mask_kernel(const double *
             const double ljj = sqrt(d);
             __syncwarp();
             if (lane == 0) A[w][tri(j, j)] = ljj;
-            for (int i = j + 1 + lane; i < M; i += 32) A[w][tri(i, j)] /= ljj;
+            const double il = 1.0 / ljj;
+            for (int i = j + 1 + lane; i < M; i += 32) A[w][tri(i, j)] *= il;
             __syncwarp();
             for (int i = j + 1 + lane; i < M; i += 32) {
                 const double lij = A[w][tri(i, j)];
