@@ -68,6 +68,8 @@ class Oracle:
         L.oracle_tuple_refine.argtypes = [_dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, _dp]
         L.oracle_tuple_refine.restype = ctypes.c_int
+        L.oracle_periodogram_trend.argtypes = [_dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int, ctypes.c_int,
+                                               _dp, ctypes.c_int64, _dp, _dp]
         L.oracle_fap_bound.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_fap_bound.restype = ctypes.c_double
         L.oracle_fap_threshold.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -117,6 +119,29 @@ def periodogram(t, y, sigma, base_freqs, fgrid, *, lib=None, want_coef=False, wa
     if want_ratio:
         out.append(ratio)
     return tuple(out)
+
+
+def periodogram_trend(t, y, sigma, base_freqs, trend, fgrid, *, lib=None):
+    """Residual periodogram whose base model has a polynomial of degree
+    ``trend`` in time instead of the constant.  Returns z, chi2_base."""
+    L = lib or _lib()
+    t, y, sigma, base, f = map(_d, (t, y, sigma, base_freqs, fgrid))
+    z = np.empty(f.size)
+    c2 = np.zeros(1)
+    if L.oracle_periodogram_trend(_p(t), _p(y), _p(sigma), t.size, _p(base), base.size, int(trend), _p(f),
+                                  f.size, _p(z), _p(c2)):
+        raise ValueError("oracle_periodogram_trend rejected its arguments")
+    return z, float(c2[0])
+
+
+def log_form(z, chi2_base, N, n_alt, trend=0):
+    """Log form of Eq. zpowrel: (N_H/2) ln(l_base / (l_base - 2 z)) with
+    N_H = N - 3 n_alt - 1 - trend (n_alt frequencies in the alternative
+    model, a polynomial of degree trend in place of the constant)."""
+    NH = N - 3 * n_alt - 1 - trend
+    l_new = chi2_base - 2.0 * np.asarray(z, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(l_new > 0, 0.5 * NH * np.log(chi2_base / l_new), np.inf)
 
 
 def periodogram_grad(t, y, sigma, base_freqs, fgrid, *, lib=None):

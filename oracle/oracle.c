@@ -583,3 +583,71 @@ int64_t oracle_cascade_solutions(const unsigned char *pass, int n, uint32_t *out
     }
     return count;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Polynomial-trend base model (Sect. 2: the constant of Eq. H0 extended to  */
+/* a polynomial in time).                                                     */
+
+/*
+ * Residual periodogram with the base model
+ *     mu_b(t) = sum_{d=0..ntrend} c_d tau^d + sum_k (a_k cos 2pi g_k t + b_k sin 2pi g_k t),
+ * tau = (t - mean(t)) / half-span (any affine map of t spans the same
+ * columns; this one keeps the powers of order one).  For every f_j the base
+ * and the trial pair are fitted jointly by Householder QR and
+ *     z_j = (chi2_base - chi2_j)/2
+ * is the sum of the trial columns' comp[] terms, as in oracle_periodogram.
+ * chi2_base may be NULL.
+ */
+int oracle_periodogram_trend(const double *t, const double *y, const double *sigma, int64_t N,
+                             const double *base, int n_base, int ntrend, const double *fgrid, int64_t nf,
+                             double *z, double *chi2_base)
+{
+    if (N <= 0 || n_base < 0 || n_base > 40 || ntrend < 0 || ntrend > 8 || nf < 0) return 1;
+    int pb = 1 + ntrend + 2 * n_base, m = pb + 2;
+    double tmin = t[0], tmax = t[0], tmean = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (t[i] < tmin) tmin = t[i];
+        if (t[i] > tmax) tmax = t[i];
+        tmean += t[i];
+    }
+    tmean /= (double)N;
+    double half = 0.5 * (tmax - tmin) > 0 ? 0.5 * (tmax - tmin) : 1.0;
+    double *A = (double *)malloc(sizeof(double) * (size_t)N * m);
+    double *b = (double *)malloc(sizeof(double) * (size_t)N);
+    double th[160], comp[160];
+    /* base columns (fixed for all trial frequencies) */
+    for (int64_t i = 0; i < N; ++i) {
+        double sw = sqrt(weight(sigma[i])), tau = (t[i] - tmean) / half, pw = 1.0;
+        for (int d = 0; d <= ntrend; ++d) {
+            A[(size_t)d * N + i] = sw * pw;
+            pw *= tau;
+        }
+        for (int k = 0; k < n_base; ++k) {
+            double c, s;
+            trig(base[k], t[i], &c, &s);
+            A[(size_t)(1 + ntrend + 2 * k) * N + i] = sw * c;
+            A[(size_t)(2 + ntrend + 2 * k) * N + i] = sw * s;
+        }
+        b[i] = sw * y[i];
+    }
+    double *Ab = (double *)malloc(sizeof(double) * (size_t)N * m);
+    double *bb = (double *)malloc(sizeof(double) * (size_t)N);
+    memcpy(Ab, A, sizeof(double) * (size_t)N * pb);
+    memcpy(bb, b, sizeof(double) * (size_t)N);
+    double l0 = hh_lsq(Ab, bb, N, pb, th, NULL, NULL);
+    if (chi2_base) *chi2_base = l0;
+    for (int64_t j = 0; j < nf; ++j) {
+        memcpy(Ab, A, sizeof(double) * (size_t)N * pb);
+        memcpy(bb, b, sizeof(double) * (size_t)N);
+        for (int64_t i = 0; i < N; ++i) {
+            double sw = sqrt(weight(sigma[i])), c, s;
+            trig(fgrid[j], t[i], &c, &s);
+            Ab[(size_t)pb * N + i] = sw * c;
+            Ab[(size_t)(pb + 1) * N + i] = sw * s;
+        }
+        hh_lsq(Ab, bb, N, m, th, NULL, comp);
+        z[j] = 0.5 * (comp[pb] + comp[pb + 1]);
+    }
+    free(A); free(b); free(Ab); free(bb);
+    return 0;
+}
