@@ -58,6 +58,9 @@ extern "C" {
 
 #define FREDEC_MAX_NBASE 12   /* base sinusoids (p = 2*n_base + 1 <= 25)          */
 #define FREDEC_MAX_TUPLE 20   /* frequencies per tuple for eval/grad/refine       */
+#define FREDEC_MAX_TREND  3   /* degree of the base model's time polynomial */
+#define FREDEC_Z_DIFF     0   /* statistic: difference form (l_base - l_new)/2 */
+#define FREDEC_Z_LOG      1   /* statistic: log form of Eq. zpowrel */
 #define FREDEC_MAX_POOL  24   /* pool size for the all-subtuple table (2^24 rows) */
 #define FREDEC_MAX_TOPK  64
 
@@ -80,6 +83,14 @@ typedef struct fredec_opts {
     double  flag_tau;   /* MIXED: a bin is recomputed in FP64 when a pivot of its
                            2x2 system falls below flag_tau times its column norm.
                            0 = default (0.2); negative = never recompute.             */
+    int32_t trend;      /* degree of the time polynomial that replaces the constant
+                           of the base model (Section 2 allows H_0 to be a
+                           polynomial); 0..FREDEC_MAX_TREND, default 0.  The base
+                           has 1 + trend + 2 n_base columns, at most 25.         */
+    int32_t statistic;  /* FREDEC_Z_DIFF (default): z = (l_base - l_new)/2;
+                           FREDEC_Z_LOG: the log form of Eq. zpowrel,
+                           z = (N_H/2) ln(l_base / l_new),
+                           N_H = N - 3 (n_base + 1) - 1 - trend.                  */
 } fredec_opts;
 
 /* Fill *o with the defaults (FP64, no top-k, tuned launch shape). */

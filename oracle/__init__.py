@@ -69,7 +69,7 @@ class Oracle:
                                           ctypes.c_double, _dp]
         L.oracle_tuple_refine.restype = ctypes.c_int
         L.oracle_periodogram_trend.argtypes = [_dp, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int, ctypes.c_int,
-                                               _dp, ctypes.c_int64, _dp, _dp]
+                                               _dp, ctypes.c_int64, _dp, _dp, _dp]
         L.oracle_fap_bound.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_fap_bound.restype = ctypes.c_double
         L.oracle_fap_threshold.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -121,17 +121,19 @@ def periodogram(t, y, sigma, base_freqs, fgrid, *, lib=None, want_coef=False, wa
     return tuple(out)
 
 
-def periodogram_trend(t, y, sigma, base_freqs, trend, fgrid, *, lib=None):
+def periodogram_trend(t, y, sigma, base_freqs, trend, fgrid, *, lib=None, want_ratio=False):
     """Residual periodogram whose base model has a polynomial of degree
-    ``trend`` in time instead of the constant.  Returns z, chi2_base."""
+    ``trend`` in time instead of the constant.  Returns z, chi2_base and, on
+    request, the trial columns' conditioning ratio."""
     L = lib or _lib()
     t, y, sigma, base, f = map(_d, (t, y, sigma, base_freqs, fgrid))
     z = np.empty(f.size)
     c2 = np.zeros(1)
+    ratio = np.empty(f.size) if want_ratio else None
     if L.oracle_periodogram_trend(_p(t), _p(y), _p(sigma), t.size, _p(base), base.size, int(trend), _p(f),
-                                  f.size, _p(z), _p(c2)):
+                                  f.size, _p(z), _p(c2), _p(ratio)):
         raise ValueError("oracle_periodogram_trend rejected its arguments")
-    return z, float(c2[0])
+    return (z, float(c2[0]), ratio) if want_ratio else (z, float(c2[0]))
 
 
 def log_form(z, chi2_base, N, n_alt, trend=0):

@@ -596,11 +596,12 @@ int64_t oracle_cascade_solutions(const unsigned char *pass, int n, uint32_t *out
  * and the trial pair are fitted jointly by Householder QR and
  *     z_j = (chi2_base - chi2_j)/2
  * is the sum of the trial columns' comp[] terms, as in oracle_periodogram.
- * chi2_base may be NULL.
+ * chi2_base and ratio (min over the trial columns of remaining/original
+ * norm) may be NULL.
  */
 int oracle_periodogram_trend(const double *t, const double *y, const double *sigma, int64_t N,
                              const double *base, int n_base, int ntrend, const double *fgrid, int64_t nf,
-                             double *z, double *chi2_base)
+                             double *z, double *chi2_base, double *ratio)
 {
     if (N <= 0 || n_base < 0 || n_base > 40 || ntrend < 0 || ntrend > 8 || nf < 0) return 1;
     int pb = 1 + ntrend + 2 * n_base, m = pb + 2;
@@ -614,7 +615,7 @@ int oracle_periodogram_trend(const double *t, const double *y, const double *sig
     double half = 0.5 * (tmax - tmin) > 0 ? 0.5 * (tmax - tmin) : 1.0;
     double *A = (double *)malloc(sizeof(double) * (size_t)N * m);
     double *b = (double *)malloc(sizeof(double) * (size_t)N);
-    double th[160], comp[160];
+    double th[160], comp[160], rat[160];
     /* base columns (fixed for all trial frequencies) */
     for (int64_t i = 0; i < N; ++i) {
         double sw = sqrt(weight(sigma[i])), tau = (t[i] - tmean) / half, pw = 1.0;
@@ -645,8 +646,9 @@ int oracle_periodogram_trend(const double *t, const double *y, const double *sig
             Ab[(size_t)pb * N + i] = sw * c;
             Ab[(size_t)(pb + 1) * N + i] = sw * s;
         }
-        hh_lsq(Ab, bb, N, m, th, NULL, comp);
+        hh_lsq(Ab, bb, N, m, th, rat, comp);
         z[j] = 0.5 * (comp[pb] + comp[pb + 1]);
+        if (ratio) ratio[j] = rat[pb] < rat[pb + 1] ? rat[pb] : rat[pb + 1];
     }
     free(A); free(b); free(Ab); free(bb);
     return 0;

@@ -22,7 +22,7 @@ __all__ = [
     "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
     "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
     "tuple_refine", "pool_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
-    "fap_bound", "fap_threshold", "effective_bandwidth", "cascade", "scan", "decompose",
+    "fap_bound", "fap_threshold", "effective_bandwidth", "cascade", "scan", "decompose", "Z_DIFF", "Z_LOG",
 ]
 
 FP64 = 0
@@ -46,7 +46,8 @@ class FredecError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("topk", ctypes.c_int32), ("fpt", ctypes.c_int32),
-                ("warps", ctypes.c_int32), ("flag_tau", ctypes.c_double)]
+                ("warps", ctypes.c_int32), ("flag_tau", ctypes.c_double), ("trend", ctypes.c_int32),
+                ("statistic", ctypes.c_int32)]
 
 
 class ScanOpts(ctypes.Structure):
@@ -167,7 +168,17 @@ def _prec(precision) -> int:
     return int(precision)
 
 
-def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0) -> Opts:
+Z_DIFF = 0   # statistic: (l_base - l_new)/2
+Z_LOG = 1    # statistic: log form (N_H/2) ln(l_base/l_new)
+
+
+def _stat(statistic) -> int:
+    if isinstance(statistic, str):
+        return {"diff": Z_DIFF, "log": Z_LOG}[statistic.lower()]
+    return int(statistic)
+
+
+def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0, trend=0, statistic=Z_DIFF) -> Opts:
     o = Opts()
     lib().fredec_opts_init(ctypes.byref(o))
     o.precision = _prec(precision)
@@ -175,6 +186,8 @@ def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0) -> Opts:
     o.fpt = int(fpt)
     o.warps = int(warps)
     o.flag_tau = float(flag_tau)
+    o.trend = int(trend)
+    o.statistic = _stat(statistic)
     return o
 
 
@@ -182,8 +195,10 @@ def _opts(precision=FP64, topk=0, fpt=0, warps=0, flag_tau=0.0) -> Opts:
 # Residual periodogram
 
 def periodogram(t, y, sigma, base_freqs, f_grid, *, precision=FP64, topk=0, want_coef=False, want_info=False,
-                fpt=0, warps=0, flag_tau=0.0, out=None):
+                fpt=0, warps=0, flag_tau=0.0, trend=0, statistic=Z_DIFF, out=None):
     """z(f) for every trial frequency (host arrays in, host arrays out).
+    ``trend``: degree of the base model's time polynomial (0 = constant);
+    ``statistic``: "diff" (default) or "log" (log form of Eq. zpowrel).
 
     Returns z, or a tuple (z, [topk_idx], [info], [coef]) when extras are
     requested.  info = (chi2_base, sum of weights, time origin t_c); coef
@@ -198,7 +213,7 @@ def periodogram(t, y, sigma, base_freqs, f_grid, *, precision=FP64, topk=0, want
     top = np.empty(max(int(topk), 1), dtype=np.int64) if topk else None
     info = np.empty(3) if want_info else None
     coef = np.empty((nf, 2)) if want_coef else None
-    o = _opts(precision, topk, fpt, warps, flag_tau)
+    o = _opts(precision, topk, fpt, warps, flag_tau, trend, statistic)
     _check(lib().fredec_periodogram_ex(_p(t), _p(y), _p(sigma), t.size, _p(base) if base.size else None, base.size,
                                        _p(f), nf, ctypes.byref(o), _p(z), _p(info), _p(top), _p(coef)))
     if not (topk or want_info or want_coef):
@@ -223,7 +238,8 @@ def _stream(torch, stream=None) -> int:
 
 
 def periodogram_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, precision=FP64, topk=0,
-                    want_coef=False, fpt=0, warps=0, flag_tau=0.0, out=None, stream=None):
+                    want_coef=False, fpt=0, warps=0, flag_tau=0.0, trend=0, statistic=Z_DIFF, out=None,
+                    stream=None):
     """Device path on the uniform grid f_j = f0 + j df (torch CUDA tensors,
     float64, contiguous).  Enqueued on torch's current stream (or ``stream``).
     Returns dict with z, info (3), and optionally topk (int64) and coef."""
@@ -236,7 +252,7 @@ def periodogram_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, p
     info = torch.empty(3, dtype=torch.float64, device=dev)
     top = torch.empty(max(topk, 1), dtype=torch.int64, device=dev) if topk else None
     coef = torch.empty((nf, 2), dtype=torch.float64, device=dev) if want_coef else None
-    o = _opts(precision, topk, fpt, warps, flag_tau)
+    o = _opts(precision, topk, fpt, warps, flag_tau, trend, statistic)
     _check(lib().fredec_periodogram_dev(_dptr(t), _dptr(y), _dptr(sigma), t.numel(),
                                         _dptr(base_freqs) if base_freqs.numel() else None, base_freqs.numel(),
                                         float(f0), float(df), int(nf), ctypes.byref(o), _dptr(z), _dptr(info),
@@ -479,13 +495,13 @@ def _batch_arrays(series):
     return t, y, sg, obs, base, bo, f0, df, nf, zo
 
 
-def periodogram_batch(series, *, precision=FP64, topk=0, flag_tau=0.0):
+def periodogram_batch(series, *, precision=FP64, topk=0, flag_tau=0.0, trend=0, statistic=Z_DIFF):
     """One call for many series (objects with t, y, sigma, base_freqs, grid).
     Returns (z_concat, z_offsets, topk (n_series, k) or None)."""
     t, y, sg, obs, base, bo, f0, df, nf, zo = _batch_arrays(series)
     z = np.empty(max(int(zo[-1]), 1))
     top = np.empty(max(len(series) * topk, 1), dtype=np.int64) if topk else None
-    o = _opts(precision, topk, 0, 0, flag_tau)
+    o = _opts(precision, topk, 0, 0, flag_tau, trend, statistic)
     _check(lib().fredec_periodogram_batch(_p(t), _p(y), _p(sg), _p(obs), len(series), _p(base), _p(bo), _p(f0),
                                           _p(df), _p(nf), _p(zo[:-1].copy()), ctypes.byref(o), _p(z), _p(top)))
     return z[:int(zo[-1])], zo, (top.reshape(len(series), topk) if topk else None)
@@ -494,13 +510,13 @@ def periodogram_batch(series, *, precision=FP64, topk=0, flag_tau=0.0):
 class BatchPlan:
     """Device-resident batch with a captured CUDA graph (see fredec.h)."""
 
-    def __init__(self, series, *, precision=FP64, topk=0, flag_tau=0.0):
+    def __init__(self, series, *, precision=FP64, topk=0, flag_tau=0.0, trend=0, statistic=Z_DIFF):
         t, y, sg, obs, base, bo, f0, df, nf, zo = _batch_arrays(series)
         self.n_series = len(series)
         self.topk = topk
         self.z_offsets = zo
         self._h = _vp()
-        o = _opts(precision, topk, 0, 0, flag_tau)
+        o = _opts(precision, topk, 0, 0, flag_tau, trend, statistic)
         _check(lib().fredec_batch_plan_create(ctypes.byref(self._h), _p(t), _p(y), _p(sg), _p(obs), len(series),
                                               _p(base), _p(bo), _p(f0), _p(df), _p(nf), _p(zo[:-1].copy()),
                                               ctypes.byref(o)))

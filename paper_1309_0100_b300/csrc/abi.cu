@@ -127,7 +127,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
                             int nb, double f0, double df, int64_t nf, const fredec_opts &o, double *z,
                             double *info, int64_t *topk, double *coef, cudaStream_t st, DevBuf &ws,
                             SingleWork &w) {
-    const int p = 2 * nb + 1;
+    const int pb = base_cols(nb, o.trend), p = padded_cols(pb);
     const int prec = o.precision;
     const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
     const bool fix = prec == FREDEC_MIXED && tau >= 0.0;
@@ -164,6 +164,8 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     d.N = (int32_t)N;
     d.nb = nb;
     d.p = p;
+    d.pb = pb;
+    d.npoly = o.trend;
     d.nchunks = (int32_t)nchunks;
     init_series_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
         w.desc, d, w.state, w.chunk_series, nchunks, w.flag_count, w.err);
@@ -200,6 +202,8 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
                 return rc;
         }
         nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
+        if (o.statistic == FREDEC_Z_LOG)
+            if (int rc = launch_log_form(w.desc, w.state, 1, nf, z, st)) return rc;
         if (topk && o.topk > 0)
             if (int rc = launch_topk_single(z, nf, o.topk, topk, st)) return rc;
     }
@@ -217,12 +221,19 @@ static int check_opts(const fredec_opts *o, fredec_opts *out) {
     if (out->topk < 0 || out->topk > FREDEC_MAX_TOPK) return fail(FREDEC_EINVAL, "opts.topk must be in 0..64");
     if (out->fpt < 0 || out->warps < 0 || out->warps > 8) return fail(FREDEC_EINVAL, "bad opts.fpt / opts.warps");
     if (!std::isfinite(out->flag_tau)) return fail(FREDEC_EINVAL, "opts.flag_tau must be finite");
+    if (out->trend < 0 || out->trend > FREDEC_MAX_TREND) return fail(FREDEC_EINVAL, "opts.trend must be in 0..3");
+    if (out->statistic != FREDEC_Z_DIFF && out->statistic != FREDEC_Z_LOG)
+        return fail(FREDEC_EINVAL, "opts.statistic must be FREDEC_Z_DIFF or FREDEC_Z_LOG");
     return FREDEC_OK;
 }
 
-static int check_sizes(int64_t N, int32_t n_base, int64_t nf) {
+static int check_sizes(int64_t N, int32_t n_base, int64_t nf, const fredec_opts &o) {
     if (n_base < 0 || n_base > FREDEC_MAX_NBASE) return fail(FREDEC_EINVAL, "n_base must be in 0..FREDEC_MAX_NBASE");
-    if (N < 2LL * n_base + 3) return fail(FREDEC_EINVAL, "N must be at least 2*n_base + 3");
+    const int pb = base_cols(n_base, o.trend);
+    if (padded_cols(pb) > PMAX) return fail(FREDEC_EINVAL, "1 + trend + 2*n_base must not exceed 25");
+    if (N < pb + 2) return fail(FREDEC_EINVAL, "N must be at least 1 + trend + 2*n_base + 2");
+    if (o.statistic == FREDEC_Z_LOG && N - 3LL * (n_base + 1) - 1 - o.trend <= 0)
+        return fail(FREDEC_EINVAL, "the log-form statistic needs N > 3 (n_base + 1) + 1 + trend");
     if (N > (1LL << 31) - 1) return fail(FREDEC_EINVAL, "N too large");
     if (nf < 0 || nf > (1LL << 31) - 1) return fail(FREDEC_EINVAL, "nf must be in 0..2^31-1");
     return FREDEC_OK;
@@ -289,7 +300,7 @@ static int finish_host(cudaStream_t st, const SeriesState *state, const int32_t 
 }
 
 int generic_grid_periodogram(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
-                             int nb, const double *f_grid_dev, int64_t nf, int precision, double *z, double *coef,
+                             int nb, const double *f_grid_dev, int64_t nf, const fredec_opts &o, double *z, double *coef,
                              double *info, cudaStream_t st, SeriesState **state_out, DevBuf &ws);
 
 }  // namespace fredec
@@ -312,7 +323,7 @@ int fredec_periodogram_dev(const double *t, const double *y, const double *sigma
                            double *info_out, int64_t *topk_idx_out, double *coef_out, void *stream) {
     fredec_opts o;
     if (int rc = check_opts(opts, &o)) return rc;
-    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || (nf > 0 && !z_out))
         return fail(FREDEC_EINVAL, "null pointer argument");
     if (!std::isfinite(f0) || !std::isfinite(df)) return fail(FREDEC_EINVAL, "f0 and df must be finite");
@@ -327,7 +338,7 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
                           double *info_out, int64_t *topk_idx_out, double *coef_out) {
     fredec_opts o;
     if (int rc = check_opts(opts, &o)) return rc;
-    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (int rc = check_series_host(t, y, sigma, N, base_freqs, n_base)) return rc;
     if (nf > 0 && (!f_grid || !z_out)) return fail(FREDEC_EINVAL, "null f_grid or z_out");
     if (nf > 0 && !finite_all(f_grid, nf)) return fail(FREDEC_EINVAL, "trial frequencies must be finite");
@@ -364,7 +375,7 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
         } else {
             FREDEC_CUDA_TRY(cudaMemcpyAsync(dfg, f_grid, nf * 8, cudaMemcpyHostToDevice, st));
             SeriesState *sp = nullptr;
-            rc = generic_grid_periodogram(dt, dy, ds, N, db, nb, dfg, nf, o.precision, dz, coef_out ? dcoef : nullptr,
+            rc = generic_grid_periodogram(dt, dy, ds, N, db, nb, dfg, nf, o, dz, coef_out ? dcoef : nullptr,
                                           dinfo, st, &sp, ws);
             state = sp;
             if (!rc && k) rc = launch_topk_single(dz, nf, k, dtop, st);
@@ -390,7 +401,9 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
                                double *dldy_out, void *stream) {
     (void)info;   // the time origin is recomputed identically from the same inputs
     if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
-    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    fredec_opts o;   // the adjoint is built for the constant-plus-sinusoids base
+    fredec_opts_init(&o);
+    if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || !dldy_out || (nf > 0 && (!coef || !v)))
         return fail(FREDEC_EINVAL, "null pointer argument");
     if (!std::isfinite(f0) || !std::isfinite(df)) return fail(FREDEC_EINVAL, "f0 and df must be finite");
@@ -402,7 +415,9 @@ int fredec_periodogram_vjp(const double *t, const double *y, const double *sigma
                            int32_t n_base, double f0, double df, int64_t nf, const double *v, int32_t precision,
                            double *dldy_out) {
     if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
-    if (int rc = check_sizes(N, n_base, nf)) return rc;
+    fredec_opts o;   // the adjoint is built for the constant-plus-sinusoids base
+    fredec_opts_init(&o);
+    if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (int rc = check_series_host(t, y, sigma, N, base_freqs, n_base)) return rc;
     if (!dldy_out || (nf > 0 && !v)) return fail(FREDEC_EINVAL, "null pointer argument");
     if (!std::isfinite(f0) || !std::isfinite(df) || (nf > 0 && !finite_all(v, nf)))

@@ -35,7 +35,8 @@ int topk_plan_launch(const void *args, int64_t nch, int S, cudaStream_t st);
 using namespace fredec;
 
 struct fredec_batch_plan {
-    int S = 0, precision = 0, topk = 0, pmax = 1, warps = 4;
+    int S = 0, precision = 0, topk = 0, pmax = 1, warps = 4, statistic = 0;
+    int64_t nf_max = 0;
     double tau = 0.2;
     bool fix = false;
     int64_t ntot = 0, nbase = 0, z_total = 0, nchunks = 0, n_items = 0, terms = 0, tk_chunks = 0, max_n = 0;
@@ -97,6 +98,8 @@ struct fredec_batch_plan {
             for (int p : p_present)
                 if (int rc = launch_fixup_bins(desc, state, S, rec64, p, flag_list, flag_count, z_total, z, nullptr, st))
                     return rc;
+        if (statistic == FREDEC_Z_LOG)
+            if (int rc = launch_log_form(desc, state, S, nf_max, z, st)) return rc;
         if (topk > 0)
             if (int rc = topk_plan_launch(tk_args, tk_chunks, S, st)) return rc;
         return FREDEC_OK;
@@ -140,7 +143,9 @@ int validate_batch(const double *t, const double *y, const double *sigma, const 
     if (obs[0] != 0 || bo[0] != 0) return fail(FREDEC_EINVAL, "offset arrays must start at 0");
     for (int64_t s = 0; s < S; ++s) {
         const int64_t N = obs[s + 1] - obs[s], nb = bo[s + 1] - bo[s];
-        if (nb < 0 || nb > FREDEC_MAX_NBASE || N < 2 * nb + 3 || N > (1LL << 31) - 1)
+        const int pb = base_cols((int)nb, o.trend);
+        if (nb < 0 || nb > FREDEC_MAX_NBASE || padded_cols(pb) > PMAX || N < pb + 2 || N > (1LL << 31) - 1 ||
+            (o.statistic == FREDEC_Z_LOG && N - 3 * (nb + 1) - 1 - o.trend <= 0))
             return fail(FREDEC_EINVAL, "series " + std::to_string(s) + ": bad N or base size");
         if (nf[s] < 0 || nf[s] > (1LL << 31) - 1 || !std::isfinite(f0[s]) || !std::isfinite(df[s]) || zo[s] < 0)
             return fail(FREDEC_EINVAL, "series " + std::to_string(s) + ": bad grid");
@@ -155,6 +160,8 @@ int validate_batch(const double *t, const double *y, const double *sigma, const 
         if (!base || !std::isfinite(base[q])) return fail(FREDEC_EINVAL, "base frequencies must be finite");
     if (o.precision != FREDEC_FP64 && o.precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
     if (o.topk < 0 || o.topk > FREDEC_MAX_TOPK) return fail(FREDEC_EINVAL, "bad topk");
+    if (o.trend < 0 || o.trend > FREDEC_MAX_TREND) return fail(FREDEC_EINVAL, "opts.trend must be in 0..3");
+    if (o.statistic != FREDEC_Z_DIFF && o.statistic != FREDEC_Z_LOG) return fail(FREDEC_EINVAL, "bad opts.statistic");
     return FREDEC_OK;
 }
 
@@ -176,6 +183,7 @@ int fredec_batch_plan_create(fredec_batch_plan **plan_out, const double *t, cons
     pl.S = (int)S;
     pl.precision = o.precision;
     pl.topk = o.topk;
+    pl.statistic = o.statistic;
     pl.tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
     pl.fix = o.precision == FREDEC_MIXED && pl.tau >= 0.0;
     pl.ntot = obs[S];
@@ -189,7 +197,9 @@ int fredec_batch_plan_create(fredec_batch_plan **plan_out, const double *t, cons
         SeriesDesc &d = desc[s];
         d.N = (int32_t)(obs[s + 1] - obs[s]);
         d.nb = (int32_t)(bo[s + 1] - bo[s]);
-        d.p = 2 * d.nb + 1;
+        d.pb = base_cols(d.nb, o.trend);
+        d.p = padded_cols(d.pb);
+        d.npoly = o.trend;
         d.obs_off = obs[s];
         d.base_off = bo[s];
         d.f0 = f0[s];
@@ -211,6 +221,7 @@ int fredec_batch_plan_create(fredec_batch_plan **plan_out, const double *t, cons
         present[d.p] = 1;
         pl.terms += (int64_t)d.N * nf[s];
         pl.max_n = std::max<int64_t>(pl.max_n, d.N);
+        pl.nf_max = std::max<int64_t>(pl.nf_max, d.nf);
     }
     for (int p = 1; p < (int)present.size(); ++p)
         if (present[p]) pl.p_present.push_back(p);

@@ -115,6 +115,37 @@ void launch_fx(const FixupParams &prm, int grid, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+
+// z <- (N_H/2) ln(l_base / (l_base - 2 z)), the log form of Eq. zpowrel,
+// N_H = N - 3 (n_base + 1) - 1 - npoly (the alternative model: the base and one
+// trial frequency).  One grid row per series.
+__global__ void log_form_kernel(const SeriesDesc *desc, const SeriesState *state, int nseries, double *z) {
+    for (int s = blockIdx.y; s < nseries; s += gridDim.y) {
+        const SeriesDesc d = desc[s];
+        const double lb = state[s].chi2;
+        const double NH = (double)((int64_t)d.N - 3 * ((int64_t)d.nb + 1) - 1 - d.npoly);
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d.nf;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const double zd = z[d.z_off + j];
+            const double ln = lb - 2.0 * zd;
+            z[d.z_off + j] = isnan(zd) ? zd : (ln > 0.0 ? 0.5 * NH * log(lb / ln) : INFINITY);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,
+                    cudaStream_t st) {
+    if (nseries <= 0 || nf_max <= 0) return FREDEC_OK;
+    const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (nf_max + 255) / 256),
+                                                    std::max(1, 2 * sm_count() / std::min(nseries, 2 * sm_count())));
+    log_form_kernel<<<dim3(gx, (unsigned)std::min(nseries, 65535)), 256, 0, st>>>(desc, state, nseries, z);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
                       cudaStream_t st) {

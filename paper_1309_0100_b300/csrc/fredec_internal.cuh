@@ -41,6 +41,8 @@ struct SeriesDesc {
     double f0, df;       // uniform grid f_j = f0 + j df
     int64_t nf;
     int32_t N, nb, nchunks, p;
+    int32_t pb;          // base columns: 1 + npoly + 2 nb (p = pb rounded up to odd; column pb, if any, is zero)
+    int32_t npoly;       // degree of the time polynomial of the base model
 };
 
 // Per-series results of the prep kernels.
@@ -50,6 +52,7 @@ struct SeriesState {
     double tc;           // time origin
     double chi2;         // l(f') of the base model
     double Swt;          // sum w t (scratch)
+    double tscale;       // time scale of the polynomial columns: tau = (t - tc) / tscale
     double L1[NTRI];     // Cholesky factor of the raw base Gram
     double L2[NTRI];     // Cholesky factor of the second (re-orthogonalisation) Gram
     double a[PMAX];      // coefficients of y on the orthonormal base columns
@@ -119,6 +122,15 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
                       cudaStream_t st);
+
+// Log form of the statistic (Eq. zpowrel) in place, per series (fixup.cu).
+int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,
+                    cudaStream_t st);
+
+// Base column counts for n_base sinusoids and a time polynomial of degree npoly:
+// pb real columns, padded to the odd count the periodogram kernels are built for.
+inline int base_cols(int nb, int npoly) { return 1 + npoly + 2 * nb; }
+inline int padded_cols(int pb) { return pb | 1; }
 
 // Top-k local maxima (topk.cu); segmented over series.
 int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S, int k,

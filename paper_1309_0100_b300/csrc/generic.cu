@@ -81,10 +81,9 @@ __global__ void __launch_bounds__(128) generic_kernel(const SeriesDesc *desc, co
 }  // namespace
 
 int generic_grid_periodogram(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
-                             int nb, const double *f_grid_dev, int64_t nf, int precision, double *z, double *coef,
+                             int nb, const double *f_grid_dev, int64_t nf, const fredec_opts &o, double *z, double *coef,
                              double *info, cudaStream_t st, SeriesState **state_out, DevBuf &ws) {
-    (void)precision;
-    const int p = 2 * nb + 1;
+    const int pb = base_cols(nb, o.trend), p = padded_cols(pb);
     const int64_t nchunks = (N + PREP_THREADS - 1) / PREP_THREADS;
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
@@ -98,6 +97,8 @@ int generic_grid_periodogram(const double *t, const double *y, const double *sig
     d.N = (int32_t)N;
     d.nb = nb;
     d.p = p;
+    d.pb = pb;
+    d.npoly = o.trend;
     d.nchunks = (int32_t)nchunks;
     SeriesDesc *dd = (SeriesDesc *)(b + o_desc);
     SeriesState *ss = (SeriesState *)(b + o_state);
@@ -118,6 +119,8 @@ int generic_grid_periodogram(const double *t, const double *y, const double *sig
     generic_kernel<<<(unsigned)std::max<int64_t>(1, (nf + 127) / 128), 128, 0, st>>>(dd, ss, b + o_rec, t, f_grid_dev, z,
                                                                                      coef, info);
     FREDEC_CUDA_TRY(cudaGetLastError());
+    if (o.statistic == FREDEC_Z_LOG)
+        if (int rc = launch_log_form(dd, ss, 1, nf, z, st)) return rc;
     *state_out = ss;
     return FREDEC_OK;
 }

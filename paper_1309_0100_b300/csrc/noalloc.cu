@@ -92,13 +92,16 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     if (opts) o = *opts;
     if (o.precision != FREDEC_FP64 && o.precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
     if (o.topk != 0) return fail(FREDEC_EINVAL, "the no-allocation entry point does not compute top-k (opts.topk must be 0)");
-    if (n_base < 0 || n_base > FREDEC_MAX_NBASE || N < 2LL * n_base + 3 || N > (1LL << 31) - 1 || nf < 0 ||
-        nf > (1LL << 31) - 1)
+    if (o.trend < 0 || o.trend > FREDEC_MAX_TREND || (o.statistic != FREDEC_Z_DIFF && o.statistic != FREDEC_Z_LOG))
+        return fail(FREDEC_EINVAL, "bad opts.trend / opts.statistic");
+    if (n_base < 0 || n_base > FREDEC_MAX_NBASE || padded_cols(base_cols(n_base, o.trend)) > PMAX ||
+        N < base_cols(n_base, o.trend) + 2 || N > (1LL << 31) - 1 || nf < 0 || nf > (1LL << 31) - 1 ||
+        (o.statistic == FREDEC_Z_LOG && N - 3LL * (n_base + 1) - 1 - o.trend <= 0))
         return fail(FREDEC_EINVAL, "bad sizes (see fredec_periodogram_dev)");
     if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || (nf > 0 && !z_out))
         return fail(FREDEC_EINVAL, "null pointer argument");
     const cudaStream_t st = (cudaStream_t)stream;
-    const int p = 2 * n_base + 1;
+    const int pb = base_cols(n_base, o.trend), p = padded_cols(pb);
     const int prec = o.precision;
     const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
     const bool fix = prec == FREDEC_MIXED && tau >= 0.0;
@@ -134,6 +137,8 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     d.N = (int32_t)N;
     d.nb = n_base;
     d.p = p;
+    d.pb = pb;
+    d.npoly = o.trend;
     d.nchunks = (int32_t)nchunks;
     noalloc_init<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
         desc, d, state, cs, nchunks, flag_count, err);
@@ -165,6 +170,8 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
         if (fix)
             if (int rc = launch_fixup_bins(desc, state, 1, rec64, p, flag_list, flag_count, nf, z_out, nullptr, st))
                 return rc;
+        if (o.statistic == FREDEC_Z_LOG)
+            if (int rc = launch_log_form(desc, state, 1, nf, z_out, st)) return rc;
     }
     noalloc_finish<<<64, 256, 0, st>>>(state, z_out, nf, info_out);
     FREDEC_CUDA_TRY(cudaGetLastError());

@@ -94,16 +94,29 @@ __device__ void sum_partials(const PrepArgs &a, const SeriesDesc &d, int nv, dou
 extern __shared__ double prep_sm[];
 __device__ double *fin_buf() { return prep_sm; }
 
-__device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &d, double tp, double *phi) {
+// Base columns at t' = t - t_c: [1, tau, ..., tau^npoly, cos, sin of every
+// base frequency], tau = t' / tscale (the polynomial extension of Eq. H0).
+__device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &d, double tscale, double tp,
+                                           double *phi) {
     phi[0] = 1.0;
+    const double tau = tp / tscale;
+    for (int q = 1; q <= d.npoly; ++q) phi[q] = phi[q - 1] * tau;
+    const int o = 1 + d.npoly;
     for (int k = 0; k < d.nb; ++k) {
         const double g = a.base[d.base_off + k];
         const uint64_t ph = frac_turns_u64(g, tp);
         double s, c;
         sincos_turns_d(ph, &s, &c);
-        phi[1 + 2 * k] = c;
-        phi[2 + 2 * k] = s;
+        phi[o + 2 * k] = c;
+        phi[o + 1 + 2 * k] = s;
     }
+}
+
+// Time scale of the polynomial columns from sum w, sum w u, sum w u^2 with
+// u = t - t_first (shift-safe): twice the weighted standard deviation of t.
+__device__ __forceinline__ double time_scale(double W, double Su, double Suu) {
+    const double mu = Su / W, var = Suu / W - mu * mu;
+    return var > 0.0 ? 2.0 * sqrt(var) : 1.0;
 }
 
 // K1: sum w, sum w t  ->  W, t_c.
@@ -113,21 +126,25 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k1(PrepArgs a) {
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
     const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
-    double v[2] = {0.0, 0.0};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (i < d.N) {
         const double sg = a.sigma[d.obs_off + i];
         const double w = 1.0 / (sg * sg);
+        const double ti = a.t[d.obs_off + i], u = ti - a.t[d.obs_off];
         v[0] = w;
-        v[1] = w * a.t[d.obs_off + i];
+        v[1] = w * ti;
+        v[2] = w * u;
+        v[3] = w * u * u;
     }
-    store_partials(a, chunk, v, 2, prep_sm);
+    store_partials(a, chunk, v, 4, prep_sm);
     if (arrive_last(st, 0, d.nchunks)) {
         double *f = fin_buf();
-        sum_partials(a, d, 2, f);
+        sum_partials(a, d, 4, f);
         const double W = f[0], Swt = f[1];
         if (threadIdx.x == 0) {
             st.W = W;
             st.Swt = Swt;
+            st.tscale = time_scale(W, f[2], f[3]);
             st.tc = rint(Swt / W);
             st.status = FREDEC_OK;
             st.counter[0] = 0;
@@ -141,7 +158,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k2(PrepArgs a) {
     const int s = a.chunk_series[chunk];
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.p;
+    const int p = d.pb;
     const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
     double phi[PMAX], v[NTRI];
     for (int q = 0; q < p * (p + 1) / 2; ++q) v[q] = 0.0;
@@ -149,7 +166,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k2(PrepArgs a) {
         const double sg = a.sigma[d.obs_off + i];
         const double w = 1.0 / (sg * sg);
         const double tp = a.t[d.obs_off + i] - st.tc;
-        base_basis(a, d, tp, phi);
+        base_basis(a, d, st.tscale, tp, phi);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * d.N + i] = phi[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] = w * phi[r] * phi[c];
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k3(PrepArgs a) {
     const int s = a.chunk_series[chunk];
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.p, nt = p * (p + 1) / 2;
+    const int p = d.pb, nt = p * (p + 1) / 2;
     const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
     double x[PMAX], v[NTRI + PMAX];
     for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
@@ -213,7 +230,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
     const int s = a.chunk_series[chunk];
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.p;
+    const int p = d.pb;
     const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
     double x[PMAX], v[PMAX];
     for (int q = 0; q < p; ++q) v[q] = 0.0;
@@ -227,6 +244,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
             a.psi[d.psi_off + (int64_t)q * d.N + i] = x[q];
             r -= st.a[q] * x[q];
         }
+        for (int q = p; q < d.p; ++q) a.psi[d.psi_off + (int64_t)q * d.N + i] = 0.0;   // odd-width padding
         for (int q = 0; q < p; ++q) v[q] = w * x[q] * r;
     }
     store_partials(a, chunk, v, p, prep_sm);
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
     const int s = a.chunk_series[chunk];
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.p;
+    const int p = d.pb;
     const int64_t i = (chunk - d.chunk_off) * PREP_THREADS + threadIdx.x;
     double v[2] = {0.0, 0.0};
     if (i < d.N && st.status == FREDEC_OK) {
@@ -299,6 +317,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
             r -= (st.a[q] + st.a2[q]) * ps;
             u[q] = w * ps;
         }
+        for (int q = p; q < d.p; ++q) u[q] = 0.0;
         write_records(a, d, i, tp, w, r, u);
         v[0] = w * r * r;
         v[1] = (double)(float)w;
@@ -349,24 +368,28 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     const int s = blockIdx.x;
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.p, nt = p * (p + 1) / 2;
+    const int p = d.pb, nt = p * (p + 1) / 2;
     const int64_t N = d.N;
     double v[SP_NV];
-    // 1: W, <t>  ->  t_c
-    v[0] = v[1] = 0.0;
+    // 1: W, <t>  ->  t_c and the polynomial time scale
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    const double t_first = a.t[d.obs_off];
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        const double ti = a.t[d.obs_off + i], u = ti - t_first;
         v[0] += w;
-        v[1] += w * a.t[d.obs_off + i];
+        v[1] += w * ti;
+        v[2] += w * u;
+        v[3] += w * u * u;
     }
-    block_reduce_vals(v, 2, red, out);
-    const double W = out[0], tc = rint(out[1] / W);
+    block_reduce_vals(v, 4, red, out);
+    const double W = out[0], tc = rint(out[1] / W), tscale = time_scale(W, out[2], out[3]);
     // 2: raw base columns, Gram Q1 -> L1
     for (int q = 0; q < nt; ++q) v[q] = 0.0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
         double phi[PMAX];
-        base_basis(a, d, a.t[d.obs_off + i] - tc, phi);
+        base_basis(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = phi[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
@@ -375,6 +398,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     if (threadIdx.x == 0) {
         st.W = W;
         st.tc = tc;
+        st.tscale = tscale;
         for (int q = 0; q < nt; ++q) st.L1[q] = out[q];
         ok = chol_packed(st.L1, p, 1e-12);
         st.status = ok ? FREDEC_OK : FREDEC_ESINGULAR;
@@ -414,6 +438,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
             a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
             r -= st.a[q] * x[q];
         }
+        for (int q = p; q < d.p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
         for (int q = 0; q < p; ++q) v[q] += w * x[q] * r;
     }
     block_reduce_vals(v, p, red, out);
@@ -431,6 +456,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
             r -= (st.a[q] + st.a2[q]) * ps;
             u[q] = w * ps;
         }
+        for (int q = p; q < d.p; ++q) u[q] = 0.0;
         write_records(a, d, i, tp, w, r, u);
         v[0] += w * r * r;
         v[1] += (double)(float)w;

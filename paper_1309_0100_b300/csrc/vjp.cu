@@ -221,6 +221,8 @@ int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, i
     d.N = (int32_t)N;
     d.nb = nb;
     d.p = p;
+    d.pb = p;
+    d.npoly = 0;
     d.nchunks = (int32_t)nchunks;
     vjp_init<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
         desc, d, state, (int32_t *)(b + o_cs), nchunks);
