@@ -35,6 +35,11 @@ import synth  # noqa: E402
 WORKLOAD = "residual periodogram, N=2000, base = constant + 3 sinusoids (p=7), uniform grid nf=1e6 (0<f<=2 /d)"
 L2_FLUSH_BYTES = 256 << 20
 OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (rotation 4, sums 2p+4, w*c 1)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the mixed
+# periodogram kernel on this workload, keyed by (p, frequencies per thread,
+# warps per CTA); measured with ncu (summary and command in
+# profiles/pgram_mixed_p7_config2.md).  z (8 MB) stays in L2 during the launch.
+DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 199168 + 0, (7, 4, 4): 196096 + 0}
 
 
 def dist_setup():
@@ -276,6 +281,10 @@ def main():
     peak_ops = 148 * 128 * sm_max * 1e6
     k_ms = statistics.mean(kern_ms)
     achieved = OPS_PER_TERM(p) * N * nf / (k_ms * 1e-3)
+    # DRAM bytes (read + write) of one launch of this kernel at this launch
+    # shape, from an ncu capture of the same command (the profile summary for
+    # this workload under profiles/); None for shapes that were not captured
+    traffic = DRAM_BYTES_PER_LAUNCH.get((p, best["mixed"][0], best["mixed"][1]))
     # parity on a strided sample against the FP64 CPU oracle
     import oracle
     idx = np.unique(np.concatenate([np.arange(0, nf, nf // 200), np.asarray(top, dtype=np.int64)]))
@@ -299,7 +308,7 @@ def main():
         "max_rel_err_vs_oracle": {"mixed": err_mixed, "fp64": err_64, "sampled_bins": int(idx.size),
                                   "floor": "1e-3 of the highest sampled z"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "T FP32-FMA-pipe ops/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "T FP32-FMA-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "pgram_kernel<mixed, P=7>", "kernel_ms": k_ms,
                      "ops_per_term": OPS_PER_TERM(p),
                      "peak_source": f"148 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (unit counts x max clock)",
