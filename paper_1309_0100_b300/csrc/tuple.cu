@@ -108,9 +108,34 @@ __global__ void series_prep(const double *t, const double *y, const double *sigm
 }
 
 template <class T> struct Pt { T sw, tp, yw, pad; };   // 1/sigma, t - t_c, (y - ybar)/sigma
-template <class T> struct V2T;
-template <> struct V2T<float> { using type = float2; };
-template <> struct V2T<double> { using type = double2; };
+
+// Precision of a tuple pass.  float: FP32 columns and sums (the mixed path);
+// double: FP64 throughout (the FP64 path); FF: FP64 columns stored as float
+// pairs (hi + lo) and summed with exact FP32 products and Kahan compensation
+// -- about 1e-14 of the sum of magnitudes, like FP64 sums, for a fraction of
+// the FP64 pipe's cost on this GPU.  FF redoes the mixed path's
+// ill-conditioned tuples.
+struct FF {};
+template <class T> struct TP;
+template <> struct TP<float> {
+    using pt = float;          // per-point constants and column arithmetic
+    using tile = float;        // shared column tile entry
+    static constexpr bool mixed = true;
+    static constexpr double l_noise = MIXED_L_NOISE;   // of <y^2>
+};
+template <> struct TP<double> {
+    using pt = double;
+    using tile = double;
+    static constexpr bool mixed = false;
+    static constexpr double l_noise = 0.0;             // 1e-15 of l instead
+};
+template <> struct TP<FF> {
+    using pt = double;
+    using tile = float2;
+    static constexpr bool mixed = false;
+    static constexpr double l_noise = 1e-13;
+};
+constexpr int PREC_FF = 2;     // internal precision code of the FF passes
 
 template <class T>
 __global__ void point_prep(const double *t, const double *y, const double *sigma, int64_t N, const SeriesPrep *sp,
@@ -213,25 +238,33 @@ __device__ __forceinline__ void tuple_cs(const TupleArgs &a, const TState &s, co
 // Weighted columns of point i into row[0..CP): [1, c_k, s_k (k < m), y] and,
 // with uv, [t' c_k, t' s_k] after them (the t-weighted averages of Eq. avrg1
 // and avrg2 from which the derivative columns are formed).
+__device__ __forceinline__ void put(float *row, int c, float v) { row[c] = v; }
+__device__ __forceinline__ void put(double *row, int c, double v) { row[c] = v; }
+__device__ __forceinline__ void put(float2 *row, int c, double v) {   // exact split hi + lo
+    const float hi = __double2float_rn(v);
+    row[c] = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 template <class T>
 __device__ __forceinline__ void make_row(const TupleArgs &a, const TState &s, const void *tab, int64_t i, int m,
-                                         bool with_uv, int C, int CP, T *row) {
-    const Pt<T> p = static_cast<const Pt<T> *>(a.pts)[i];
+                                         bool with_uv, int C, int CP, typename TP<T>::tile *row) {
+    using V = typename TP<T>::pt;
+    const Pt<V> p = static_cast<const Pt<V> *>(a.pts)[i];
     const int M = 2 * m + 1;
-    row[0] = p.sw;
-    row[M] = p.yw;
-    const T swt = p.sw * p.tp;
+    put(row, 0, p.sw);
+    put(row, M, p.yw);
+    const V swt = p.sw * p.tp;
     for (int k = 0; k < m; ++k) {
-        T c, sn;
+        V c, sn;
         tuple_cs(a, s, tab, k, i, p.tp, &c, &sn);
-        row[1 + 2 * k] = p.sw * c;
-        row[2 + 2 * k] = p.sw * sn;
+        put(row, 1 + 2 * k, p.sw * c);
+        put(row, 2 + 2 * k, p.sw * sn);
         if (with_uv) {
-            row[M + 1 + 2 * k] = swt * c;
-            row[M + 2 + 2 * k] = swt * sn;
+            put(row, M + 1 + 2 * k, swt * c);
+            put(row, M + 2 + 2 * k, swt * sn);
         }
     }
-    for (int c = C; c < CP; ++c) row[c] = T(0);
+    for (int c = C; c < CP; ++c) put(row, c, V(0));
 }
 
 __device__ __forceinline__ void load4(const float *p, float *v) {
@@ -248,6 +281,79 @@ __device__ __forceinline__ void load4(const double *p, double *v) {
     v[2] = q1.x;
     v[3] = q1.y;
 }
+
+__device__ __forceinline__ void load4(const float2 *p, float2 *v) {
+    const float4 q0 = reinterpret_cast<const float4 *>(p)[0], q1 = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = make_float2(q0.x, q0.y);
+    v[1] = make_float2(q0.z, q0.w);
+    v[2] = make_float2(q1.x, q1.y);
+    v[3] = make_float2(q1.z, q1.w);
+}
+
+// Per-entry accumulators of a 4x4 Gram block.  float/double: chunk partials
+// added into running sums.  FF: Kahan sum S with compensation K (the sum is
+// S - K); each product r c of hi/lo pairs enters as its rounded hi*hi part
+// plus the exact rounding error of that product and the two cross terms.
+template <class T> struct BlockAcc {
+    using V = typename TP<T>::pt;
+    V acc[QB][16];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int b = 0; b < QB; ++b)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[b][e] = V(0);
+    }
+    __device__ __forceinline__ void chunk(int b, const V *X, int rb, int cb, int g, int G, int n, int CP) {
+        V part[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) part[e] = V(0);
+        const V *xr = X + 4 * rb, *xc = X + 4 * cb;
+        for (int p = g; p < n; p += G) {
+            V r[4], c[4];
+            load4(xr + (size_t)p * CP, r);
+            load4(xc + (size_t)p * CP, c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) part[4 * u + v] = fma(r[u], c[v], part[4 * u + v]);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[b][e] += part[e];
+    }
+    __device__ __forceinline__ double value(int b, int e) const { return (double)acc[b][e]; }
+};
+template <> struct BlockAcc<FF> {
+    float S[QB][16], K[QB][16];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int b = 0; b < QB; ++b)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) S[b][e] = K[b][e] = 0.0f;
+    }
+    __device__ __forceinline__ void chunk(int b, const float2 *X, int rb, int cb, int g, int G, int n, int CP) {
+        const float2 *xr = X + 4 * rb, *xc = X + 4 * cb;
+        for (int p = g; p < n; p += G) {
+            float2 r[4], c[4];
+            load4(xr + (size_t)p * CP, r);
+            load4(xc + (size_t)p * CP, c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int e = 4 * u + v;
+                    const float ph = __fmul_rn(r[u].x, c[v].x);
+                    const float ep = __fmaf_rn(r[u].x, c[v].x, -ph);
+                    const float cr = __fmaf_rn(r[u].x, c[v].y, __fmul_rn(r[u].y, c[v].x));
+                    K[b][e] = __fsub_rn(K[b][e], __fadd_rn(ep, cr));
+                    const float yv = __fsub_rn(ph, K[b][e]);
+                    const float tv = __fadd_rn(S[b][e], yv);
+                    K[b][e] = __fsub_rn(__fsub_rn(tv, S[b][e]), yv);
+                    S[b][e] = tv;
+                }
+        }
+    }
+    __device__ __forceinline__ double value(int b, int e) const { return (double)S[b][e] - (double)K[b][e]; }
+};
 
 __device__ __forceinline__ void block_rc(int q, int *rb, int *cb) {
     int r = 0;
@@ -283,37 +389,18 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
             }
         }
     }
-    T acc[QB][16];
-#pragma unroll
-    for (int b = 0; b < QB; ++b)
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[b][e] = T(0);
-    T *X = reinterpret_cast<T *>(R);
+    BlockAcc<T> acc;
+    acc.zero();
+    using Tile = typename TP<T>::tile;
+    Tile *X = reinterpret_cast<Tile *>(R);
     for (int64_t i0 = 0; i0 < a.N; i0 += a.chunk) {
         const int n = (int)(a.N - i0 < a.chunk ? a.N - i0 : a.chunk);
         __syncthreads();
         for (int p = tid; p < n; p += L) make_row<T>(a, s, tab, i0 + p, m, with_uv, C, CP, X + (size_t)p * CP);
         __syncthreads();
 #pragma unroll
-        for (int b = 0; b < QB; ++b) {
-            if (b < nq) {
-                T part[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) part[e] = T(0);
-                const T *xr = X + 4 * rb[b], *xc = X + 4 * cb[b];
-                for (int p = g; p < n; p += G) {
-                    T r[4], c[4];
-                    load4(xr + (size_t)p * CP, r);
-                    load4(xc + (size_t)p * CP, c);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) part[4 * u + v] = fma(r[u], c[v], part[4 * u + v]);
-                }
-#pragma unroll
-                for (int e = 0; e < 16; ++e) acc[b][e] += part[e];
-            }
-        }
+        for (int b = 0; b < QB; ++b)
+            if (b < nq) acc.chunk(b, X, rb[b], cb[b], g, G, n, CP);
     }
     __syncthreads();
     if (G == 1) {
@@ -323,13 +410,13 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int r = 4 * rb[b] + e / 4, c = 4 * cb[b] + e % 4;
-                    if (r < C && c <= r) Gs[tri(r, c)] = (double)acc[b][e];
+                    if (r < C && c <= r) Gs[tri(r, c)] = acc.value(b, e);
                 }
     } else {
         double *red = reinterpret_cast<double *>(R);   // [G][nblk][16]
         if (nq)
 #pragma unroll
-            for (int e = 0; e < 16; ++e) red[((size_t)g * nblk + qid) * 16 + e] = (double)acc[0][e];
+            for (int e = 0; e < 16; ++e) red[((size_t)g * nblk + qid) * 16 + e] = acc.value(0, e);
         __syncthreads();
         for (int qe = tid; qe < nblk * 16; qe += L) {
             const int q = qe >> 4, e = qe & 15;
@@ -528,7 +615,7 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
     }
     __syncthreads();
     const double D = a.sp->D;
-    const bool mixed = sizeof(T) == 4;
+    const bool mixed = TP<T>::mixed;
     const bool uv = a.mode == 1 || a.mode == 2;
     double *W = reinterpret_cast<double *>(R);   // extension scratch (free after a pass)
     gram_pass<T>(a, s, tab, Gs, R, m, uv);
@@ -564,7 +651,7 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
     // in FP64, so its FP32 refinement stops there
     bool have_step = !(mixed && ratio < TUPLE_TAU) && extend_cta(Gs, inv, M, m, s.theta, W, s.x, s.step, s);
     double lacc = D - s.red;
-    const double margin = mixed ? MIXED_L_NOISE * D : 1e-15 * fabs(lacc);
+    const double margin = TP<T>::l_noise > 0.0 ? TP<T>::l_noise * D : 1e-15 * fabs(lacc);
     const int max_halvings = mixed ? MAX_HALVINGS_MIXED : MAX_HALVINGS;
     const double span = a.sp->span;
     int it = 0, fails = 0, flat = 0;
@@ -612,13 +699,16 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(WT_THREADS, 4) tuple_kernel(TupleArgs a) {
+// NT threads per CTA: 64 when two 4x4 blocks per thread cover the widest Gram
+// of the launch (more tuples per SM, so one tuple's serial FP64 solve leaves
+// fewer warps idle), else 128.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_kernel(TupleArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int CP = (a.cmax + 3) & ~3;
     size_t o = 0;
     void *tab = smraw;
-    o += sizeof(T) == 4 ? sizeof(SeedTableF) : sizeof(SeedTable);
+    o += TP<T>::mixed ? sizeof(SeedTableF) : sizeof(SeedTable);
     o = (o + 15) & ~(size_t)15;
     TState &s = *reinterpret_cast<TState *>(smraw + o);
     o += sizeof(TState);
@@ -632,7 +722,7 @@ __global__ void __launch_bounds__(WT_THREADS, 4) tuple_kernel(TupleArgs a) {
     o = (o + 15) & ~(size_t)15;
     unsigned char *R = smraw + o;
     (void)CP;
-    if (sizeof(T) == 4) fill_seed_table_f(*static_cast<SeedTableF *>(tab));
+    if (TP<T>::mixed) fill_seed_table_f(*static_cast<SeedTableF *>(tab));
     else fill_seed_table(*static_cast<SeedTable *>(tab));
     __syncthreads();
     __shared__ int64_t cur;
@@ -745,12 +835,16 @@ __global__ void __launch_bounds__(32 * PM_WARPS) pool_mask_kernel(const double *
 
 static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
     const size_t smem = tuple_smem(precision, a.cmax, a.chunk);
-    auto kern = precision == FREDEC_MIXED ? tuple_kernel<float> : tuple_kernel<double>;
+    const int nb = ((a.cmax + 3) & ~3) / 4;
+    const int nt = nb * (nb + 1) / 2 <= QB * 64 ? 64 : WT_THREADS;
+    auto kern = precision == FREDEC_MIXED ? (nt == 64 ? tuple_kernel<float, 64> : tuple_kernel<float, WT_THREADS>)
+                : precision == PREC_FF    ? (nt == 64 ? tuple_kernel<FF, 64> : tuple_kernel<FF, WT_THREADS>)
+                                          : (nt == 64 ? tuple_kernel<double, 64> : tuple_kernel<double, WT_THREADS>);
     FREDEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FREDEC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WT_THREADS, smem));
+    FREDEC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
     const int64_t grid = std::min<int64_t>(std::max<int64_t>(a.n_tuples, 1), (int64_t)std::max(per_sm, 1) * sm_count());
-    kern<<<(unsigned)grid, WT_THREADS, smem, st>>>(a);
+    kern<<<(unsigned)grid, nt, smem, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());
     return FREDEC_OK;
 }
@@ -862,7 +956,7 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     const int64_t nf2 = off2.back();
     std::vector<double> z2(n2 + 1), g2(nf2 + 1), f2(nf2 + 1), l2(n2 + 1);
     std::vector<int32_t> it2(n2 + 1);
-    if (int rc = tuple_run(t, y, sigma, N, pool_h, npool, idx2, off2, mode, FREDEC_FP64,
+    if (int rc = tuple_run(t, y, sigma, N, pool_h, npool, idx2, off2, mode, PREC_FF,
                            max_iter, tol, z2.data(), g2.data(),
                            f2.data(), l2.data(), it2.data(), nullptr, st))
         return rc;

@@ -71,19 +71,36 @@ def test_config5_survey_full(F):
 
 @pytest.mark.parametrize("prec,ftol,ltol", [("fp64", 1e-5, 1e-10), ("mixed", 3e-3, 1e-6)])
 def test_config4_pool_refine_sampled(F, prec, ftol, ltol):
-    """Both refinements must reach the same local minimum of l: equal l, the
-    oracle's l at the GPU frequencies equal to the GPU's l, and frequencies
+    """The FP64 refinement must reach the oracle's local minimum of l: equal l,
+    the oracle's l at the GPU frequencies equal to the GPU's l, and frequencies
     equal to a small fraction of the resolution 1/T (small-amplitude members
-    sit in flat minima, so their frequencies are only loosely determined)."""
+    sit in flat minima, so their frequencies are only loosely determined).
+
+    The mixed refinement follows other steps (FP32 sums, FP64-grade redo of
+    ill-conditioned tuples); where the trajectory passes through a nearly
+    singular system it may end in another local minimum.  Several minima are
+    correct results: a different one is accepted only when it is a genuine
+    local minimum (the oracle's l there equals the GPU's, and the oracle's own
+    refinement started there stays there) and is at least as good as the
+    oracle's; such tuples must be rare."""
     s = synth.config4()
     T = s.t.max() - s.t.min()
     rng = np.random.default_rng(4)
     masks = [m for m in rng.integers(1, 1 << 16, 400).astype(np.uint32) if bin(int(m)).count("1") <= 4][:10]
     masks = np.asarray(masks + [1 << k for k in range(6)], dtype=np.uint32)
     mk, f, l, it = F.pool_refine(s.t, s.y, s.sigma, s.pool, masks, max_iter=30, tol=1e-10, precision=prec)
+    other_minimum = 0
     for q, m in enumerate(mk):
         sel = [k for k in range(16) if int(m) >> k & 1]
         rf, rl, _ = oracle.tuple_refine(s.t, s.y, s.sigma, s.pool[sel], max_iter=60, tol=1e-12)
-        assert l[q] == pytest.approx(rl, rel=ltol), int(m)
         assert oracle.tuple_l(s.t, s.y, s.sigma, f[q, sel]) == pytest.approx(l[q], rel=ltol), int(m)
+        if prec == "mixed" and not l[q] == pytest.approx(rl, rel=ltol):
+            gf, gl, _ = oracle.tuple_refine(s.t, s.y, s.sigma, f[q, sel], max_iter=60, tol=1e-12)
+            assert gl == pytest.approx(l[q], rel=ltol), int(m)                 # stationary for the oracle
+            assert np.max(np.abs(gf - f[q, sel])) < ftol / T, int(m)
+            assert l[q] <= rl * (1 + ltol), int(m)                            # at least as good
+            other_minimum += 1
+            continue
+        assert l[q] == pytest.approx(rl, rel=ltol), int(m)
         assert np.max(np.abs(f[q, sel] - rf)) < ftol / T, (int(m), (f[q, sel] - rf) * T)
+    assert other_minimum <= 2
