@@ -49,8 +49,15 @@ __device__ __forceinline__ uint32_t lowest_members(uint32_t S, int r) {
     return out;
 }
 
+// Tests compare the bit patterns of the doubles as signed 64-bit integers:
+// for non-negative values (and +inf) the order of the patterns is the numeric
+// order, so a test is integer work (the FP64 pipe of this GPU is narrow).  A
+// table entry passes as l_K when 0 < l_K <= +inf (NaN and negative patterns
+// fall outside); the threshold l_S * q >= 0 is formed once per layer.
 __global__ void cascade_pass_kernel(const double *__restrict__ l, int n, const double *__restrict__ qtab,
                                     uint32_t valid_m, uint32_t *__restrict__ pass_words) {
+    constexpr long long INF_BITS = 0x7FF0000000000000LL;
+    const long long *lb = reinterpret_cast<const long long *>(l);
     const uint32_t S = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nmask = 1u << n;
     bool ok = false;
@@ -60,11 +67,12 @@ __global__ void cascade_pass_kernel(const double *__restrict__ l, int n, const d
         ok = ((valid_m >> m) & 1u) && lS >= 0.0 && lS < INFINITY;
         for (int i = 0; ok && i < m; ++i) {
             const int k = (i & 1) ? m - 1 - (i >> 1) : (i >> 1);
-            const double thr = lS * qtab[m * QROW + k];
+            // l_S = 0: every l_K > 0 passes (its z is +inf), whatever q is
+            const long long thr = lS == 0.0 ? 0LL : __double_as_longlong(lS * qtab[m * QROW + k]);
             uint32_t K = lowest_members(S, k);
             for (;;) {
-                const double lK = l[K];
-                if (!(lK > 0.0 && (lS == 0.0 || lK >= thr))) {
+                const long long lK = __ldg(lb + K);
+                if (!(lK > 0 && lK <= INF_BITS && lK >= thr)) {
                     ok = false;
                     break;
                 }
