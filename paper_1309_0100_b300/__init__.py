@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
                                               i64, i32, d, i32, _c_dp, _c_dp, _c_i32p]),
         "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
         "fredec_selftest_wait_timeout": (ctypes.c_int, [_c_i32p]),
+        "fredec_selftest_ff_sincos": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), i64, _c_dp]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
                                                           ctypes.POINTER(Opts), _vp, _vp, _vp]),
         "fredec_fap_bound": (d, [i32, d, d, d]),

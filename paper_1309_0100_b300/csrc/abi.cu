@@ -112,7 +112,7 @@ struct SingleWork {
     double *partials;
     double *psi;
     void *rec;       // records of the main precision
-    void *rec64;     // FP64 records for re-evaluation (mixed) or == rec (FP64)
+    void *rec64;     // float-float records for the re-evaluation (mixed) or == rec (FP64)
     int64_t *flag_list;
     int32_t *flag_count;
     int32_t *err;
@@ -134,14 +134,14 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     const int64_t nchunks = (N + PREP_THREADS - 1) / PREP_THREADS;
     const int64_t nflag = fix ? nf : 0;   // worst case: every bin flagged
     const size_t rb = (size_t)rec_bytes(p, prec);
-    const size_t rb64 = (size_t)rec_bytes(p, FREDEC_FP64);
+    const size_t rbff = (size_t)recff_bytes(p);
     // carve one allocation
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
     const size_t o_desc = take(sizeof(SeriesDesc)), o_state = take(sizeof(SeriesState));
     const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
     const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * rb);
-    const size_t o_rec64 = fix ? take(N * rb64) : 0;
+    const size_t o_rec64 = fix ? take(N * rbff) : 0;
     const size_t o_fl = take(nflag * 8 + 8), o_fc = take(4), o_err = take(4);
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();

@@ -212,7 +212,7 @@ int fredec_batch_plan_create(fredec_batch_plan **plan_out, const double *t, cons
         d.chunk_off = chunk_off;
         d.nchunks = (d.N + PREP_THREADS - 1) / PREP_THREADS;
         rec_off += (int64_t)d.N * rec_bytes(d.p, o.precision);
-        rec64_off += pl.fix ? (int64_t)d.N * rec_bytes(d.p, FREDEC_FP64) : 0;
+        rec64_off += pl.fix ? (int64_t)d.N * recff_bytes(d.p) : 0;
         psi_off += (int64_t)d.p * d.N;
         chunk_off += d.nchunks;
         for (int c = 0; c < d.nchunks; ++c) chunk_series.push_back((int32_t)s);

@@ -94,6 +94,118 @@ __device__ __forceinline__ void fill_seed_table(SeedTable &tab) {
 }
 
 // ---------------------------------------------------------------------------
+// Float-float ("FF") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits, from the error-free transformations TwoSum
+// (Knuth), FastTwoSum (Dekker) and the FMA product error.  Every step is an
+// explicitly rounded intrinsic, so the compiler neither contracts nor
+// reassociates them.  On this GPU a float-float operation costs a few FP32
+// instructions, against one FP64 instruction at 1/64 of the FP32 rate.
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_from_double(double d) {
+    const float hi = __double2float_rn(d);
+    return {hi, __double2float_rn(d - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// a + b with both parts' errors carried (no loss when a ~ -b)
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    const ff t = ff_two_sum(a.lo, b.lo);
+    s = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+
+// Running float-float sum H + L: each addend's hi part enters by TwoSum, the
+// error and the lo parts go into L, and (H, L) is renormalised (FastTwoSum) --
+// the double-float sum, about 1e-16 of the summed magnitudes (a compensated
+// sum with a single-float compensation would keep an error of order 1e-7 of
+// them per term).
+struct ff_acc {
+    float H = 0.0f, L = 0.0f;
+    __device__ __forceinline__ void add(ff p) {
+        const ff s = ff_two_sum(H, p.hi);
+        const ff r = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(L, p.lo)));
+        H = r.hi;
+        L = r.lo;
+    }
+    __device__ __forceinline__ void add_prod(ff a, ff b) {   // add a * b (exact hi product, cross terms)
+        const float p = __fmul_rn(a.hi, b.hi);
+        float e = __fmaf_rn(a.hi, b.hi, -p);
+        e = __fmaf_rn(a.hi, b.lo, e);
+        e = __fmaf_rn(a.lo, b.hi, e);
+        add({p, e});
+    }
+    __device__ __forceinline__ double value() const { return (double)H + (double)L; }
+};
+
+// FF sin/cos of a 64-bit fixed-point phase (Tang's table method in float-float
+// arithmetic): the top 8 bits select e^{2 pi i k/256} from a table of FF pairs
+// (built from FP64 sincospi), the remaining < 1/256 turn x = 2 pi rem 2^-64
+// (|x| < 0.0246) is evaluated by its Taylor series -- the x^2 terms in FF, the
+// terms below 2e-8 in FP32 -- and the two rotations are multiplied in FF.
+// Error about 1e-15 absolute.
+struct SeedTableFF { float4 cs[256]; };   // (cos hi, cos lo, sin hi, sin lo)
+
+__device__ __forceinline__ void fill_seed_table_ff(SeedTableFF &tab) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        double s, c;
+        sincospi((double)k / 128.0, &s, &c);
+        const ff fc = ff_from_double(c), fs = ff_from_double(s);
+        tab.cs[k] = make_float4(fc.hi, fc.lo, fs.hi, fs.lo);
+    }
+}
+
+__device__ __forceinline__ void ff_sincos_turns(const SeedTableFF &tab, uint64_t ph, ff *s, ff *c) {
+    const unsigned k = (unsigned)(ph >> 56);
+    const uint64_t rem = ph & 0x00FFFFFFFFFFFFFFull;
+    // x = rem * (2 pi 2^-64): rem = rh + rl with rh exact in FP32, rl rounded
+    // (error < 2^-56 turn); 2 pi 2^-64 as an FF constant
+    const float rh = __fmul_rn((float)(uint32_t)(rem >> 32), 4294967296.0f);
+    const float rl = (float)(uint32_t)(rem & 0xFFFFFFFFull);
+    constexpr float CH = 3.4061216748705226e-19f, CL = -9.478396428567739e-27f;   // 2 pi 2^-64 = CH + CL
+    const float p = __fmul_rn(rh, CH);
+    float e = __fmaf_rn(rh, CH, -p);
+    e = __fmaf_rn(rh, CL, e);
+    e = __fmaf_rn(rl, CH, e);
+    const ff x = ff_fast_two_sum(p, e);
+    const ff x2 = ff_mul(x, x);
+    const float t4 = __fmul_rn(x2.hi, x2.hi);
+    // cos x = 1 - (x^2/2 - x^4/24 + x^6/720);  sin x = x - x (x^2/6 - x^4/120 + x^6/5040)
+    const float hc = __fmul_rn(t4, __fmaf_rn(-x2.hi, 1.0f / 720.0f, 1.0f / 24.0f));
+    const ff h = ff_add({__fmul_rn(x2.hi, 0.5f), __fmul_rn(x2.lo, 0.5f)}, {-hc, 0.0f});
+    const ff cx = ff_sub({1.0f, 0.0f}, h);
+    constexpr ff SIXTH = {0.1666666716337204f, -4.967053879312289e-09f};   // 1/6 = hi + lo
+    const float hs = __fmul_rn(t4, __fmaf_rn(-x2.hi, 1.0f / 5040.0f, 1.0f / 120.0f));
+    const ff g = ff_add(ff_mul(x2, SIXTH), {-hs, 0.0f});
+    const ff sx = ff_sub(x, ff_mul(x, g));
+    const float4 T = tab.cs[k];
+    const ff tc = {T.x, T.y}, ts = {T.z, T.w};
+    *c = ff_sub(ff_mul(tc, cx), ff_mul(ts, sx));
+    *s = ff_add(ff_mul(ts, cx), ff_mul(tc, sx));
+}
+
+// ---------------------------------------------------------------------------
 // Shared-memory addresses, mbarriers and TMA bulk copies (inline PTX).
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

@@ -1,11 +1,14 @@
-// FP64 re-evaluation of the bins that the mixed kernel flagged as
-// ill-conditioned (a pivot of the 2x2 Schur complement below flag_tau times
-// its column norm: near a base frequency, near f = 0, or where <c^2> or <s^2>
-// is tiny).  There the FP32 sums lose too many digits to cancellation, so each
-// flagged bin is recomputed from the FP64 records: one CTA per bin, its threads
-// split the observations, every term takes its own FP64 seed from the exact
-// fixed-point phase, and the partial sums are combined by a fixed-order block
-// reduction.  Deterministic; the list order does not matter.
+// Re-evaluation of the bins that the mixed kernel flagged as ill-conditioned
+// (a pivot of the 2x2 Schur complement below flag_tau times its column norm:
+// near a base frequency, near f = 0, or where <c^2> or <s^2> is tiny).  There
+// the FP32 sums lose too many digits to cancellation, so each flagged bin is
+// recomputed with FP64-grade sums: one CTA per bin, its threads split the
+// observations, every term takes its own float-float seed from the exact
+// fixed-point phase and enters double-float running sums (about 1e-16 of the
+// summed magnitudes, like FP64 sums, at a fraction of the FP64 pipe's cost on
+// this GPU); each thread's sums are then combined in FP64 by a
+// fixed-order block reduction, and the 2x2 solve is FP64.  Deterministic; the
+// list order does not matter.
 #include <algorithm>
 
 #include "pgram_impl.cuh"
@@ -20,7 +23,7 @@ struct FixupParams {
     const SeriesDesc *desc;
     const SeriesState *state;
     int nseries;                 // > 1: find the series of a global z index by binary search on z_off
-    const unsigned char *rec64;  // FP64 records (series offsets: desc.rec64_off)
+    const unsigned char *rec64;  // float-float records (series offsets: desc.rec64_off)
     const int64_t *list;         // global z indices
     const int32_t *count;
     double *z, *coef;
@@ -29,9 +32,9 @@ struct FixupParams {
 template <int P>
 __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
     constexpr int Q = 2 * P + 4;
-    __shared__ SeedTable tab;
+    __shared__ SeedTableFF tab;
     __shared__ double red[FX_THREADS / 32][Q];
-    fill_seed_table(tab);
+    fill_seed_table_ff(tab);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int32_t n = *prm.count;
@@ -50,33 +53,32 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
         const SeriesState &st = prm.state[s];
         if (d.p != P) continue;   // batches: another launch handles this base size
         const int64_t j = g - d.z_off;
+        ff_acc fa[Q];
+        const uint32_t *R0 = reinterpret_cast<const uint32_t *>(prm.rec64 + d.rec64_off);
+        constexpr int RW = recff_words(P);
+        for (int i = threadIdx.x; i < d.N; i += FX_THREADS) {
+            const uint32_t *R = R0 + (int64_t)i * RW;
+            const uint4 h = *reinterpret_cast<const uint4 *>(R);
+            const uint64_t A = ((uint64_t)h.y << 32) | h.x, B = ((uint64_t)h.w << 32) | h.z;
+            const float *Rf = reinterpret_cast<const float *>(R);
+            ff sn, cs;
+            ff_sincos_turns(tab, A + (uint64_t)j * B, &sn, &cs);
+            const ff w = {Rf[4], Rf[5]}, wr = {Rf[6], Rf[7]};
+            const ff wc = ff_mul(w, cs);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const ff u = {Rf[8 + 2 * q], Rf[9 + 2 * q]};
+                fa[q].add_prod(u, cs);
+                fa[P + q].add_prod(u, sn);
+            }
+            fa[2 * P].add_prod(wr, cs);
+            fa[2 * P + 1].add_prod(wr, sn);
+            fa[2 * P + 2].add_prod(wc, cs);
+            fa[2 * P + 3].add_prod(wc, sn);
+        }
         double acc[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) acc[q] = 0.0;
-        const double2 *R0 = reinterpret_cast<const double2 *>(prm.rec64 + d.rec64_off);
-        constexpr int RW2 = rec64_words(P) / 2;
-        for (int i = threadIdx.x; i < d.N; i += FX_THREADS) {
-            const double2 *r2 = R0 + (int64_t)i * RW2;
-            const ulonglong2 h = *reinterpret_cast<const ulonglong2 *>(r2);
-            const double2 ww = r2[2];
-            double s_, c_;
-            seed_from_table(tab, h.x + (uint64_t)j * h.y, &s_, &c_);
-            const double wc = ww.x * c_;
-#pragma unroll
-            for (int q2 = 0; q2 < (P + 1) / 2; ++q2) {
-                const double2 u = r2[3 + q2];
-                acc[2 * q2] = fma(u.x, c_, acc[2 * q2]);
-                acc[P + 2 * q2] = fma(u.x, s_, acc[P + 2 * q2]);
-                if (2 * q2 + 1 < P) {
-                    acc[2 * q2 + 1] = fma(u.y, c_, acc[2 * q2 + 1]);
-                    acc[P + 2 * q2 + 1] = fma(u.y, s_, acc[P + 2 * q2 + 1]);
-                }
-            }
-            acc[2 * P] = fma(ww.y, c_, acc[2 * P]);
-            acc[2 * P + 1] = fma(ww.y, s_, acc[2 * P + 1]);
-            acc[2 * P + 2] = fma(wc, c_, acc[2 * P + 2]);
-            acc[2 * P + 3] = fma(wc, s_, acc[2 * P + 3]);
-        }
+        for (int q = 0; q < Q; ++q) acc[q] = fa[q].value();
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const double v = warp_sum_d(acc[q]);

@@ -28,6 +28,11 @@ __host__ __device__ constexpr int rec64_words(int p) { return 6 + 2 * ((p + 1) /
 __host__ __device__ constexpr int rec_bytes(int p, int prec) {
     return prec == FREDEC_MIXED ? 4 * rec32_words(p) : 8 * rec64_words(p);
 }
+// Float-float records for the re-evaluation of flagged mixed bins (32-bit
+// words): [0..1] phase A, [2..3] phase B (u64), then hi/lo pairs of w, w r and
+// w psi_k; padded to 16 bytes.
+__host__ __device__ constexpr int recff_words(int p) { return 4 * ((8 + 2 * p + 3) / 4); }
+__host__ __device__ constexpr int recff_bytes(int p) { return 4 * recff_words(p); }
 
 // Per-series description (host-built, device-resident).
 struct SeriesDesc {

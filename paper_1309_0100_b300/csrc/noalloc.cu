@@ -111,7 +111,7 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     const size_t o_desc = take(sizeof(SeriesDesc)), o_state = take(sizeof(SeriesState));
     const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
     const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * (size_t)rec_bytes(p, prec));
-    const size_t o_rec64 = fix ? take(N * (size_t)rec_bytes(p, FREDEC_FP64)) : 0;
+    const size_t o_rec64 = fix ? take(N * (size_t)recff_bytes(p)) : 0;
     const size_t o_fl = fix ? take(nf * 8 + 8) : 0;
     const size_t o_fc = take(4), o_err = take(4);
     if (off > NOALLOC_SCRATCH_BYTES)

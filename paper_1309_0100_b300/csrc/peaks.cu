@@ -4,6 +4,7 @@
 // pipes, not latency, limit the rate.
 #include <algorithm>
 
+#include "device_util.cuh"
 #include "fredec_internal.cuh"
 
 namespace {
@@ -113,7 +114,48 @@ __global__ void wait_timeout_probe(int32_t *status, unsigned polls) {
                      : "memory");
     if (threadIdx.x == 0) *status = ok ? FREDEC_OK : FREDEC_ETIMEOUT;
 }
+// Largest |FF sin/cos - FP64 sin/cos| over the phases (FP64: the table seed
+// of the FP64 path, error < 1e-16).  Deterministic block maximum.
+__global__ void ff_sincos_check(const uint64_t *ph, int64_t n, double *out) {
+    __shared__ SeedTable tab;
+    __shared__ SeedTableFF tabff;
+    __shared__ double red[32];
+    fill_seed_table(tab);
+    fill_seed_table_ff(tabff);
+    __syncthreads();
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double s, c;
+        seed_from_table(tab, ph[i], &s, &c);
+        ff fs, fc;
+        ff_sincos_turns(tabff, ph[i], &fs, &fc);
+        m = fmax(m, fmax(fabs(ff_to_double(fs) - s), fabs(ff_to_double(fc) - c)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+        *out = r;
+    }
+}
 }  // namespace
+
+extern "C" int fredec_selftest_ff_sincos(const uint64_t *phases, int64_t n, double *max_err_out) {
+    if (!phases || n < 1 || !max_err_out) return fail(FREDEC_EINVAL, "bad self-test arguments");
+    void *d = nullptr;
+    FREDEC_CUDA_TRY(cudaMalloc(&d, (size_t)n * 8 + 8));
+    cudaError_t e = cudaMemcpy(d, phases, (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        ff_sincos_check<<<1, 256>>>((const uint64_t *)d, n, (double *)d + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(max_err_out, (double *)d + n, 8, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(FREDEC_ECUDA, cudaGetErrorString(e));
+    return FREDEC_OK;
+}
 
 extern "C" int fredec_selftest_wait_timeout(int32_t *status_out) {
     if (!status_out) return fail(FREDEC_EINVAL, "null status");

@@ -34,7 +34,7 @@ struct PrepArgs {
     int npart;
     double *psi;
     unsigned char *rec;
-    unsigned char *rec64;   // optional extra FP64 records (mixed runs with FP64 re-evaluation)
+    unsigned char *rec64;   // optional float-float records (mixed runs with re-evaluation of flagged bins)
     const double *t, *y, *sigma, *base;
     int precision;
 };
@@ -280,9 +280,26 @@ __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDes
         for (int q = 0; q < p; ++q) Rf[8 + q] = (float)u[q];
         for (int q = 8 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
     }
-    unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : a.rec64;
+    if (a.precision == FREDEC_MIXED && a.rec64) {   // float-float records for the re-evaluation
+        uint32_t *R = (uint32_t *)(a.rec64 + d.rec64_off) + i * recff_words(p);
+        R[0] = (uint32_t)A;
+        R[1] = (uint32_t)(A >> 32);
+        R[2] = (uint32_t)B;
+        R[3] = (uint32_t)(B >> 32);
+        float *Rf = (float *)R;
+        auto put = [&](int at, double v) {
+            const float hi = (float)v;
+            Rf[at] = hi;
+            Rf[at + 1] = (float)(v - (double)hi);
+        };
+        put(4, w);
+        put(6, w * r);
+        for (int q = 0; q < p; ++q) put(8 + 2 * q, u[q]);
+        for (int q = 8 + 2 * p; q < recff_words(p); ++q) Rf[q] = 0.f;
+    }
+    unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : nullptr;
     if (r64) {
-        const int64_t off64 = a.precision == FREDEC_FP64 ? d.rec_off : d.rec64_off;
+        const int64_t off64 = d.rec_off;
         uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p);
         R[0] = A;
         R[1] = B;
@@ -475,8 +492,8 @@ int launch_prep(const PrepPlan &pp, const double *t, const double *y, const doub
     return run_prep_records(pp, t, y, sigma, base, precision, nullptr, st);
 }
 
-// As launch_prep; rec64 (optional) also receives FP64 records at each series'
-// rec64_off.
+// As launch_prep; rec64 (optional, mixed runs) also receives float-float
+// records at each series' rec64_off.
 int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
                      const double *base, int precision, void *rec64, cudaStream_t st) {
     PrepArgs a;

@@ -111,10 +111,10 @@ template <class T> struct Pt { T sw, tp, yw, pad; };   // 1/sigma, t - t_c, (y -
 
 // Precision of a tuple pass.  float: FP32 columns and sums (the mixed path);
 // double: FP64 throughout (the FP64 path); FF: FP64 columns stored as float
-// pairs (hi + lo) and summed with exact FP32 products and Kahan compensation
-// -- about 1e-14 of the sum of magnitudes, like FP64 sums, for a fraction of
-// the FP64 pipe's cost on this GPU.  FF redoes the mixed path's
-// ill-conditioned tuples.
+// pairs (hi + lo) and summed as double-float values (exact FP32 products,
+// renormalised hi/lo running sums) -- about 1e-16 of the sum of magnitudes,
+// like FP64 sums, for a fraction of the FP64 pipe's cost on this GPU.  FF
+// redoes the mixed path's ill-conditioned tuples.
 struct FF {};
 template <class T> struct TP;
 template <> struct TP<float> {
@@ -291,9 +291,9 @@ __device__ __forceinline__ void load4(const float2 *p, float2 *v) {
 }
 
 // Per-entry accumulators of a 4x4 Gram block.  float/double: chunk partials
-// added into running sums.  FF: Kahan sum S with compensation K (the sum is
-// S - K); each product r c of hi/lo pairs enters as its rounded hi*hi part
-// plus the exact rounding error of that product and the two cross terms.
+// added into running sums.  FF: double-float running sums (ff_acc), each
+// product r c of hi/lo pairs entering as its rounded hi*hi part plus the exact
+// rounding error of that product and the two cross terms.
 template <class T> struct BlockAcc {
     using V = typename TP<T>::pt;
     V acc[QB][16];
@@ -323,12 +323,12 @@ template <class T> struct BlockAcc {
     __device__ __forceinline__ double value(int b, int e) const { return (double)acc[b][e]; }
 };
 template <> struct BlockAcc<FF> {
-    float S[QB][16], K[QB][16];
+    ff_acc a[QB][16];
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int b = 0; b < QB; ++b)
 #pragma unroll
-            for (int e = 0; e < 16; ++e) S[b][e] = K[b][e] = 0.0f;
+            for (int e = 0; e < 16; ++e) a[b][e] = ff_acc();
     }
     __device__ __forceinline__ void chunk(int b, const float2 *X, int rb, int cb, int g, int G, int n, int CP) {
         const float2 *xr = X + 4 * rb, *xc = X + 4 * cb;
@@ -339,20 +339,10 @@ template <> struct BlockAcc<FF> {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int e = 4 * u + v;
-                    const float ph = __fmul_rn(r[u].x, c[v].x);
-                    const float ep = __fmaf_rn(r[u].x, c[v].x, -ph);
-                    const float cr = __fmaf_rn(r[u].x, c[v].y, __fmul_rn(r[u].y, c[v].x));
-                    K[b][e] = __fsub_rn(K[b][e], __fadd_rn(ep, cr));
-                    const float yv = __fsub_rn(ph, K[b][e]);
-                    const float tv = __fadd_rn(S[b][e], yv);
-                    K[b][e] = __fsub_rn(__fsub_rn(tv, S[b][e]), yv);
-                    S[b][e] = tv;
-                }
+                for (int v = 0; v < 4; ++v) a[b][4 * u + v].add_prod({r[u].x, r[u].y}, {c[v].x, c[v].y});
         }
     }
-    __device__ __forceinline__ double value(int b, int e) const { return (double)S[b][e] - (double)K[b][e]; }
+    __device__ __forceinline__ double value(int b, int e) const { return a[b][e].value(); }
 };
 
 __device__ __forceinline__ void block_rc(int q, int *rb, int *cb) {
