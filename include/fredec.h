@@ -463,8 +463,9 @@ int fredec_selftest_wait_timeout(int32_t *status_out);
  * Self-test of the float-float sin/cos used where FP64-grade values are
  * computed with FP32 instructions (the re-evaluation of ill-conditioned bins
  * and tuples; no counterpart in the paper): for each 64-bit fixed-point phase
- * (turns * 2^64) it compares the float-float sin and cos with the FP64 path's
- * and stores the largest absolute difference in *max_err_out.  Host pointers,
+ * (turns * 2^64) it compares the float-float sin and cos -- from the fixed-point
+ * phase and from the phase given as a float-float number of turns -- with the
+ * FP64 path's and stores the largest absolute difference in *max_err_out.  Host pointers,
  * synchronous.
  */
 int fredec_selftest_ff_sincos(const uint64_t *phases, int64_t n, double *max_err_out);

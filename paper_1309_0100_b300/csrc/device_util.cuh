@@ -176,19 +176,9 @@ __device__ __forceinline__ void fill_seed_table_ff(SeedTableFF &tab) {
     }
 }
 
-__device__ __forceinline__ void ff_sincos_turns(const SeedTableFF &tab, uint64_t ph, ff *s, ff *c) {
-    const unsigned k = (unsigned)(ph >> 56);
-    const uint64_t rem = ph & 0x00FFFFFFFFFFFFFFull;
-    // x = rem * (2 pi 2^-64): rem = rh + rl with rh exact in FP32, rl rounded
-    // (error < 2^-56 turn); 2 pi 2^-64 as an FF constant
-    const float rh = __fmul_rn((float)(uint32_t)(rem >> 32), 4294967296.0f);
-    const float rl = (float)(uint32_t)(rem & 0xFFFFFFFFull);
-    constexpr float CH = 3.4061216748705226e-19f, CL = -9.478396428567739e-27f;   // 2 pi 2^-64 = CH + CL
-    const float p = __fmul_rn(rh, CH);
-    float e = __fmaf_rn(rh, CH, -p);
-    e = __fmaf_rn(rh, CL, e);
-    e = __fmaf_rn(rl, CH, e);
-    const ff x = ff_fast_two_sum(p, e);
+// sin/cos of 2 pi k/256 + x, |x| < 0.0246 (the shared part of the two entry
+// points below).
+__device__ __forceinline__ void ff_sincos_reduced(const SeedTableFF &tab, int k, ff x, ff *s, ff *c) {
     const ff x2 = ff_mul(x, x);
     const float t4 = __fmul_rn(x2.hi, x2.hi);
     // cos x = 1 - (x^2/2 - x^4/24 + x^6/720);  sin x = x - x (x^2/6 - x^4/120 + x^6/5040)
@@ -199,10 +189,36 @@ __device__ __forceinline__ void ff_sincos_turns(const SeedTableFF &tab, uint64_t
     const float hs = __fmul_rn(t4, __fmaf_rn(-x2.hi, 1.0f / 5040.0f, 1.0f / 120.0f));
     const ff g = ff_add(ff_mul(x2, SIXTH), {-hs, 0.0f});
     const ff sx = ff_sub(x, ff_mul(x, g));
-    const float4 T = tab.cs[k];
+    const float4 T = tab.cs[k & 255];
     const ff tc = {T.x, T.y}, ts = {T.z, T.w};
     *c = ff_sub(ff_mul(tc, cx), ff_mul(ts, sx));
     *s = ff_add(ff_mul(ts, cx), ff_mul(tc, sx));
+}
+
+__device__ __forceinline__ void ff_sincos_turns(const SeedTableFF &tab, uint64_t ph, ff *s, ff *c) {
+    const uint64_t rem = ph & 0x00FFFFFFFFFFFFFFull;
+    // x = rem * (2 pi 2^-64): rem = rh + rl with rh exact in FP32, rl rounded
+    // (error < 2^-56 turn); 2 pi 2^-64 as an FF constant
+    const float rh = __fmul_rn((float)(uint32_t)(rem >> 32), 4294967296.0f);
+    const float rl = (float)(uint32_t)(rem & 0xFFFFFFFFull);
+    constexpr float CH = 3.4061216748705226e-19f, CL = -9.478396428567739e-27f;   // 2 pi 2^-64 = CH + CL
+    const float p = __fmul_rn(rh, CH);
+    float e = __fmaf_rn(rh, CH, -p);
+    e = __fmaf_rn(rh, CL, e);
+    e = __fmaf_rn(rl, CH, e);
+    ff_sincos_reduced(tab, (int)(ph >> 56), ff_fast_two_sum(p, e), s, c);
+}
+
+// FF sin/cos of 2 pi r for a float-float number of turns r (any size; only its
+// fractional part matters): r is reduced to k/256 + rem with |rem| <= 1/512
+// turn, exactly, and rem is turned into radians in FF.
+__device__ __forceinline__ void ff_sincos_ff_turns(const SeedTableFF &tab, ff r, ff *s, ff *c) {
+    const float whole = rintf(r.hi);
+    r = ff_fast_two_sum(__fsub_rn(r.hi, whole), r.lo);          // exact: |r.hi - whole| <= 1/2
+    const float kf = rintf(__fmul_rn(r.hi, 256.0f));
+    const ff rem = ff_fast_two_sum(__fsub_rn(r.hi, __fmul_rn(kf, 1.0f / 256.0f)), r.lo);   // exact subtraction
+    constexpr ff TWO_PI = {6.2831854820251465f, -1.7484555314695172e-07f};   // 2 pi = hi + lo
+    ff_sincos_reduced(tab, (int)kf, ff_mul(rem, TWO_PI), s, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -130,6 +130,9 @@ __global__ void ff_sincos_check(const uint64_t *ph, int64_t n, double *out) {
         ff fs, fc;
         ff_sincos_turns(tabff, ph[i], &fs, &fc);
         m = fmax(m, fmax(fabs(ff_to_double(fs) - s), fabs(ff_to_double(fc) - c)));
+        // the same angle given as a float-float number of turns in [-1/2, 1/2)
+        ff_sincos_ff_turns(tabff, ff_from_double(turns_of(ph[i])), &fs, &fc);
+        m = fmax(m, fmax(fabs(ff_to_double(fs) - s), fabs(ff_to_double(fc) - c)));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;

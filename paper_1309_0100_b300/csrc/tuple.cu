@@ -32,6 +32,7 @@
 // rotation e^{i 2 pi delta t'} is small and is applied per pass.
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "device_util.cuh"
@@ -166,6 +167,37 @@ __global__ void pool_seeds(const double *t, int64_t N, const double *pool, int n
     }
 }
 
+// FF per-point constants: float4 pairs {sw, t'} and {(y - ybar) sw, sw t'} as
+// hi/lo floats; FF seeds: float4 {cos hi, cos lo, sin hi, sin lo}.
+__global__ void point_prep_ff(const double *t, const double *y, const double *sigma, int64_t N, const SeriesPrep *sp,
+                              float4 *out) {
+    const double tc = sp->tc, ybar = sp->ybar;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double sw = 1.0 / sigma[i], tp = t[i] - tc;
+        const ff a = ff_from_double(sw), b = ff_from_double(tp), c = ff_from_double((y[i] - ybar) * sw),
+                 d = ff_from_double(sw * tp);
+        out[2 * i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        out[2 * i + 1] = make_float4(c.hi, c.lo, d.hi, d.lo);
+    }
+}
+
+__global__ void pool_seeds_ff(const double *t, int64_t N, const double *pool, int npool, const SeriesPrep *sp,
+                              float4 *cs) {
+    __shared__ SeedTable tab;
+    fill_seed_table(tab);
+    __syncthreads();
+    const double tc = sp->tc;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)npool * N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(q / N);
+        const int64_t i = q - (int64_t)k * N;
+        double s, c;
+        seed_from_table(tab, frac_turns_u64(pool[k], t[i] - tc), &s, &c);
+        const ff fc = ff_from_double(c), fs = ff_from_double(s);
+        cs[q] = make_float4(fc.hi, fc.lo, fs.hi, fs.lo);
+    }
+}
+
 struct TupleArgs {
     int64_t N;
     const SeriesPrep *sp;
@@ -195,6 +227,7 @@ struct TState {
     double delta[MAXM];        // accepted offsets
     double step[MAXM];         // Gauss-Newton step at the accepted point
     float trialf[MAXM];
+    float2 trialff[MAXM];      // trial offsets as hi/lo floats (FF passes)
     double red, redx;          // sum_{r>=1} a_r^2 (accepted / trial)
     double ratio;              // smallest linear pivot ratio of the last factorisation
     int pidx[MAXM];
@@ -265,6 +298,41 @@ __device__ __forceinline__ void make_row(const TupleArgs &a, const TState &s, co
         }
     }
     for (int c = C; c < CP; ++c) put(row, c, V(0));
+}
+
+// FF columns: seed (FF) rotated by the FF sin/cos of the trial offset's
+// turns delta t' (formed in FF), then the weighted products in FF.
+template <>
+__device__ __forceinline__ void make_row<FF>(const TupleArgs &a, const TState &s, const void *tab, int64_t i, int m,
+                                             bool with_uv, int C, int CP, float2 *row) {
+    const float4 *P4 = static_cast<const float4 *>(a.pts) + 2 * i;
+    const float4 p0 = P4[0], p1 = P4[1];
+    const ff sw = {p0.x, p0.y}, tp = {p0.z, p0.w}, yw = {p1.x, p1.y}, swt = {p1.z, p1.w};
+    const SeedTableFF &T = *static_cast<const SeedTableFF *>(tab);
+    const int M = 2 * m + 1;
+    row[0] = make_float2(sw.hi, sw.lo);
+    row[M] = make_float2(yw.hi, yw.lo);
+    for (int k = 0; k < m; ++k) {
+        const float4 sd = static_cast<const float4 *>(a.seeds)[(int64_t)s.pidx[k] * a.N + i];
+        ff c = {sd.x, sd.y}, sn = {sd.z, sd.w};
+        const float2 dl = s.trialff[k];
+        if (dl.x != 0.0f) {
+            ff ds, dc;
+            ff_sincos_ff_turns(T, ff_mul({dl.x, dl.y}, tp), &ds, &dc);
+            const ff cn = ff_sub(ff_mul(c, dc), ff_mul(sn, ds));
+            sn = ff_add(ff_mul(sn, dc), ff_mul(c, ds));
+            c = cn;
+        }
+        const ff c1 = ff_mul(sw, c), s1 = ff_mul(sw, sn);
+        row[1 + 2 * k] = make_float2(c1.hi, c1.lo);
+        row[2 + 2 * k] = make_float2(s1.hi, s1.lo);
+        if (with_uv) {
+            const ff c2 = ff_mul(swt, c), s2 = ff_mul(swt, sn);
+            row[M + 1 + 2 * k] = make_float2(c2.hi, c2.lo);
+            row[M + 2 + 2 * k] = make_float2(s2.hi, s2.lo);
+        }
+    }
+    for (int c = C; c < CP; ++c) row[c] = make_float2(0.f, 0.f);
 }
 
 __device__ __forceinline__ void load4(const float *p, float *v) {
@@ -586,6 +654,8 @@ __device__ void set_trial(TState &s, int m, const double *src_delta, const doubl
         const double v = src_delta[q] + (src_step ? h * src_step[q] : 0.0);
         s.trial[q] = v;
         s.trialf[q] = (float)v;
+        const ff vf = ff_from_double(v);
+        s.trialff[q] = make_float2(vf.hi, vf.lo);
     }
 }
 
@@ -602,6 +672,7 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
         s.delta[q] = 0.0;
         s.trial[q] = 0.0;
         s.trialf[q] = 0.0f;
+        s.trialff[q] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
     const double D = a.sp->D;
@@ -698,7 +769,7 @@ __global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_ker
     const int CP = (a.cmax + 3) & ~3;
     size_t o = 0;
     void *tab = smraw;
-    o += TP<T>::mixed ? sizeof(SeedTableF) : sizeof(SeedTable);
+    o += std::is_same<T, FF>::value ? sizeof(SeedTableFF) : TP<T>::mixed ? sizeof(SeedTableF) : sizeof(SeedTable);
     o = (o + 15) & ~(size_t)15;
     TState &s = *reinterpret_cast<TState *>(smraw + o);
     o += sizeof(TState);
@@ -712,7 +783,8 @@ __global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_ker
     o = (o + 15) & ~(size_t)15;
     unsigned char *R = smraw + o;
     (void)CP;
-    if (TP<T>::mixed) fill_seed_table_f(*static_cast<SeedTableF *>(tab));
+    if constexpr (std::is_same<T, FF>::value) fill_seed_table_ff(*static_cast<SeedTableFF *>(tab));
+    else if constexpr (TP<T>::mixed) fill_seed_table_f(*static_cast<SeedTableF *>(tab));
     else fill_seed_table(*static_cast<SeedTable *>(tab));
     __syncthreads();
     __shared__ int64_t cur;
@@ -725,6 +797,8 @@ __global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_ker
         __syncthreads();
     }
 }
+
+static_assert(sizeof(SeedTable) == sizeof(SeedTableFF), "the FF passes reuse the FP64 table's space");
 
 size_t tuple_smem(int prec, int cmax, int chunk) {
     const size_t tsz = prec == FREDEC_MIXED ? 4 : 8;
@@ -886,6 +960,10 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
         point_prep<float><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<float> *)(b + o_pts));
         if (npool) pool_seeds<float2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
                                                           (float2 *)(b + o_seed));
+    } else if (precision == PREC_FF) {
+        point_prep_ff<<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (float4 *)(b + o_pts));
+        if (npool) pool_seeds_ff<<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
+                                                     (float4 *)(b + o_seed));
     } else {
         point_prep<double><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<double> *)(b + o_pts));
         if (npool) pool_seeds<double2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
