@@ -7,8 +7,7 @@ points; CUDA torch tensors through the stream-ordered ``*_dev`` entry points
 on torch's current stream.
 
 If the shared library has not been built, every call raises: there is no
-CPU fallback.  Build it with ``python -m paper_1309_0100_b300._build`` (or
-``__graft_entry__.build()``).
+CPU fallback.  Build it with ``python -m paper_1309_0100_b300._build``.
 """
 from __future__ import annotations
 
