@@ -34,6 +34,7 @@ import synth  # noqa: E402
 
 WORKLOAD = "residual periodogram, N=2000, base = constant + 3 sinusoids (p=7), uniform grid nf=1e6 (0<f<=2 /d)"
 L2_FLUSH_BYTES = 256 << 20
+METRIC = "freq*obs terms/s, mixed vs FP64 on 1 B300, at stated max rel err vs FP64 oracle"
 OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (rotation 4, sums 2p+4, w*c 1)
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the mixed
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
@@ -163,7 +164,7 @@ def run_reference(args, rank, ws):
             times.append(time.perf_counter() - t0)
     T = sum(times)
     value = s.N * nsample * args.steps / T
-    line = {"impl": "reference", "metric": "freq*obs terms/s", "value": value, "unit": "terms/s", "n_gpus": ws,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "N": s.N, "nf": s.grid.nf, "n_base": 3},
@@ -295,7 +296,7 @@ def main():
     err_64 = float(np.max(np.abs(z64[idx] - zr)[msk] / np.maximum(zr, floor)[msk]))
     cpu = None if args.no_cpu_baseline else cpu_baseline(s, args.cpu_sample)
     line = {
-        "metric": "freq*obs terms/s, mixed vs FP64 on 1 B300, at stated max rel err vs FP64 oracle",
+        "metric": METRIC,
         "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
