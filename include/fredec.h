@@ -408,13 +408,17 @@ void fredec_decompose_opts_init(fredec_decompose_opts *o);
  *   the first min(count, capacity) solutions in Phase 4 order: solutions[]
  *     (masks over the pool), G_out[], freqs_out (may be NULL;
  *     capacity x FREDEC_MAX_TUPLE, row i = the fitted frequencies of solution
- *     i in increasing order, zero-padded); *n_solutions = count.
+ *     i in increasing order, zero-padded), resid_z_out (may be NULL): the
+ *     log-form z of the highest peak left in the residual periodogram whose
+ *     base is the solution, on the scan's grid (its single-frequency FAP is
+ *     the last item Section 4 reports per solution; NaN for solutions of more
+ *     than FREDEC_MAX_NBASE frequencies); *n_solutions = count.
  * Host pointers, synchronous.
  */
 int fredec_decompose(const double *t, const double *y, const double *sigma, int64_t N,
                      double f0, double df, int64_t nf, const fredec_decompose_opts *opts,
                      double *pool_out, int32_t *n_pool_out, double *l_table_out,
-                     uint32_t *solutions, double *G_out, double *freqs_out,
+                     uint32_t *solutions, double *G_out, double *freqs_out, double *resid_z_out,
                      int64_t capacity, int64_t *n_solutions);
 
 /* ------------------------------------------------------------------------ */

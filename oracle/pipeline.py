@@ -20,7 +20,11 @@ Readings taken where Sect. 4 is silent:
   * at the end the pool is ordered by decreasing z (ties to the lower
     frequency) and cut to max_pool (default N/10, at most 20);
   * the scan also stops after max_base base frequencies (default 12, and at
-    most (N-3)/2 so that the base model stays overdetermined).
+    most (N-3)/2 so that the base model stays overdetermined);
+  * Phase 4's residual statistic of a solution is the log-form z of the
+    highest local maximum of the residual periodogram whose base is the
+    solution's fitted frequencies, on the scan's grid (N_H = N - 3(m+1) - 1);
+    NaN for solutions of more than 12 frequencies.
 """
 from __future__ import annotations
 
@@ -123,5 +127,14 @@ def decompose(t, y, sigma, f0, df, nf, z_thr0, z_thr1, z_thr, *, max_pool=0, max
     sols = cascade_solutions(passed)
     masks, G = phase4_order(sols, l, N)
     freqs = [np.sort(fref[int(S)][[j for j in range(n) if int(S) >> j & 1]]) for S in masks]
+    grid = f0 + df * np.arange(nf)
+    resid = []
+    for fs in freqs:
+        if fs.size > 12:
+            resid.append(np.nan)
+            continue
+        zd, lb = periodogram(t, y, sigma, fs, grid)
+        pk = local_maxima(zd)
+        resid.append(float(log_form(zd[pk[0]], lb, N, fs.size + 1)) if pk else np.nan)
     return dict(pool=pool, pool_z=pool_z, base=base, truncated=trunc, l=l, f=fref, passed=passed,
-                slack=slack, masks=masks, G=G, freqs=freqs)
+                slack=slack, masks=masks, G=G, freqs=freqs, resid_z=np.array(resid))

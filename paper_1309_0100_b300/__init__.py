@@ -123,7 +123,7 @@ def lib() -> ctypes.CDLL:
                                        _c_i32p, _c_dp, _c_i32p, _c_i32p]),
         "fredec_decompose": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, d, d, i64, ctypes.POINTER(DecomposeOpts),
                                             _c_dp, _c_i32p, _c_dp, ctypes.POINTER(ctypes.c_uint32), _c_dp, _c_dp,
-                                            i64, _c_i64p]),
+                                            _c_dp, i64, _c_i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -462,14 +462,16 @@ def decompose(t, y, sigma, f0, df, nf, z_thr0, z_thr1, z_thr, *, precision=FP64,
     masks = np.zeros(max(capacity, 1), dtype=np.uint32)
     G = np.zeros(max(capacity, 1))
     F = np.zeros((max(capacity, 1), MAX_TUPLE))
+    rz = np.zeros(max(capacity, 1))
     cnt = np.zeros(1, dtype=np.int64)
     _check(lib().fredec_decompose(_p(t), _p(y), _p(sigma), t.size, float(f0), float(df), int(nf), ctypes.byref(o),
                                   _p(pool), _p(npool), _p(l), masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-                                  _p(G), _p(F), int(capacity), _p(cnt)))
+                                  _p(G), _p(F), _p(rz), int(capacity), _p(cnt)))
     n = int(npool[0])
     k = min(int(cnt[0]), capacity)
     return dict(pool=pool[:n].copy(), l=l[:1 << n].copy(), masks=masks[:k].copy(), G=G[:k].copy(),
-                freqs=[F[i, :bin(int(masks[i])).count("1")].copy() for i in range(k)], n_solutions=int(cnt[0]))
+                freqs=[F[i, :bin(int(masks[i])).count("1")].copy() for i in range(k)], resid_z=rz[:k].copy(),
+                n_solutions=int(cnt[0]))
 
 
 # ---------------------------------------------------------------------------

@@ -218,7 +218,7 @@ extern "C" int fredec_scan(const double *t, const double *y, const double *sigma
 extern "C" int fredec_decompose(const double *t, const double *y, const double *sigma, int64_t N, double f0,
                                 double df, int64_t nf, const fredec_decompose_opts *opts, double *pool_out,
                                 int32_t *n_pool_out, double *l_table_out, uint32_t *solutions, double *G_out,
-                                double *freqs_out, int64_t capacity, int64_t *n_solutions) {
+                                double *freqs_out, double *resid_z_out, int64_t capacity, int64_t *n_solutions) {
     if (int rc = check_series(t, y, sigma, N)) return rc;
     if (!std::isfinite(f0) || !std::isfinite(df) || nf < 1 || nf > (1LL << 31) - 1)
         return fail(FREDEC_EINVAL, "bad frequency grid");
@@ -274,16 +274,42 @@ extern "C" int fredec_decompose(const double *t, const double *y, const double *
     if (int rc = cascade_run(lb.as<double>(), n, N, zt.data(), l0, nullptr, &sol, &G, s.s)) return rc;
     *n_solutions = (int64_t)sol.size();
     const int64_t nout = std::min<int64_t>(capacity, (int64_t)sol.size());
+    DevBuf rb;   // Phase 4 residual periodograms: z, base frequencies, top index
+    if (resid_z_out && nout > 0) {
+        if (int rc = rb.alloc((size_t)(nf + FREDEC_MAX_NBASE + 4) * 8, s.s)) return rc;
+    }
     for (int64_t i = 0; i < nout; ++i) {
         solutions[i] = sol[i];
         G_out[i] = G[i];
-        if (freqs_out) {
-            std::vector<double> f;
-            for (int j = 0; j < n; ++j)
-                if (sol[i] >> j & 1) f.push_back(fref[(size_t)(sol[i] - 1) * n + j]);
-            std::sort(f.begin(), f.end());
+        std::vector<double> f;
+        for (int j = 0; j < n; ++j)
+            if (sol[i] >> j & 1) f.push_back(fref[(size_t)(sol[i] - 1) * n + j]);
+        std::sort(f.begin(), f.end());
+        if (freqs_out)
             for (int j = 0; j < FREDEC_MAX_TUPLE; ++j)
                 freqs_out[i * FREDEC_MAX_TUPLE + j] = j < (int)f.size() ? f[j] : 0.0;
+        if (resid_z_out) {
+            // Phase 4: the highest peak left in the residual periodogram whose
+            // base is this solution (log form, N_H = N - 3(m+1) - 1)
+            resid_z_out[i] = NAN;
+            const int m = (int)f.size();
+            if (m > FREDEC_MAX_NBASE || N - 3LL * (m + 1) - 1 <= 0 || N < 2LL * m + 3) continue;
+            double *zr = rb.as<double>(), *bd = zr + nf;
+            int64_t *top = reinterpret_cast<int64_t *>(bd + FREDEC_MAX_NBASE);
+            if (m) FREDEC_CUDA_TRY(cudaMemcpyAsync(bd, f.data(), m * 8, cudaMemcpyHostToDevice, s.s));
+            fredec_opts po;
+            fredec_opts_init(&po);
+            po.precision = so.precision;
+            po.topk = 1;
+            po.statistic = FREDEC_Z_LOG;
+            if (int rc = fredec_periodogram_dev(t_d, y_d, s_d, N, bd, m, f0, df, nf, &po, zr, nullptr, top, nullptr,
+                                                s.s))
+                return rc;
+            gather_peaks<<<1, 32, 0, s.s>>>(zr, top, 1, bd + FREDEC_MAX_NBASE - 1);
+            FREDEC_CUDA_TRY(cudaGetLastError());
+            FREDEC_CUDA_TRY(cudaMemcpyAsync(&resid_z_out[i], bd + FREDEC_MAX_NBASE - 1, 8, cudaMemcpyDeviceToHost,
+                                            s.s));
+            FREDEC_CUDA_TRY(cudaStreamSynchronize(s.s));
         }
     }
     return FREDEC_OK;

@@ -99,6 +99,9 @@ def test_decompose_parity_fp64(case):
     T = t.max() - t.min()
     for a, b in zip(got["freqs"], ref["freqs"]):
         np.testing.assert_allclose(a, b, atol=1e-7 / T)
+    # Phase 4 residual statistic (the oracle's residual periodogram at its own
+    # fitted frequencies, equal to the GPU's to 1e-7/T)
+    np.testing.assert_allclose(got["resid_z"], ref["resid_z"], rtol=1e-6)
     if case == "sec61":
         best = got["freqs"][int(np.argmin(got["G"]))]
         np.testing.assert_allclose(best, [0.9, 1.1], atol=1e-3)
@@ -116,3 +119,7 @@ def test_decompose_mixed_refine_same_solutions():
     # FP32-accumulated sums: the error scales with the data's total power l_0
     np.testing.assert_allclose(got["l"], ref["l"], rtol=0, atol=1e-6 * ref["l"][0])
     assert np.array_equal(got["masks"], ref["masks"])
+    # the residual statistic from the mixed periodogram at mixed-refined
+    # frequencies: FP32 sums, the mixed path's 1e-5 bar with room for the
+    # frequencies' own FP32-level offsets
+    np.testing.assert_allclose(got["resid_z"], ref["resid_z"], rtol=1e-4)

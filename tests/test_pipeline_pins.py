@@ -113,6 +113,14 @@ def test_decompose_sec61_finds_the_true_pair():
     for f in r["freqs"]:
         _, g = oracle.tuple_grad(t, y, s, [f])
         assert np.max(np.abs(g)) * (t.max() - t.min()) < 1e-3 * oracle.l0(t, y, s)
+    # Phase 4 residual statistic: the true pair leaves only noise behind, so its
+    # residual periodogram's highest peak stays below the FAP_0 threshold;
+    # it equals the log form of the residual periodogram's maximum
+    best_i = int(np.argmin(r["G"]))
+    assert r["resid_z"][best_i] < z0
+    zres, lres = oracle.periodogram(t, y, s, r["freqs"][best_i], df * np.arange(1, nf + 1))
+    NH = t.size - 3 * 3 - 1
+    assert r["resid_z"][best_i] == pytest.approx(0.5 * NH * np.log(lres / (lres - 2 * zres.max())), rel=1e-12)
     # G = (l_S / l_0)(N-1)/(N-3m-1)
     for m, G in zip(masks, r["G"]):
         k = bin(m).count("1")
