@@ -76,11 +76,14 @@ __device__ __forceinline__ void seed_from_table_f(const SeedTableF &tab, uint32_
     *s = fmaf(t.y, pc, t.x * ps);
 }
 
+// FP32 entries from the FP32 sincospi (k/128 is exact in FP32; the entries are
+// within 1 ulp, below the FP32 seed's own rounding): a CTA fills its table on
+// the FP32 pipe instead of spending FP64 operations, which run at 1/64 rate.
 __device__ __forceinline__ void fill_seed_table_f(SeedTableF &tab) {
     for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        double s, c;
-        sincospi((double)k / 128.0, &s, &c);
-        tab.cs[k] = make_float2((float)c, (float)s);
+        float s, c;
+        sincospif((float)k * (1.0f / 128.0f), &s, &c);
+        tab.cs[k] = make_float2(c, s);
     }
 }
 

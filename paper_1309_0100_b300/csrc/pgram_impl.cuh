@@ -140,9 +140,9 @@ struct MixedPoint {
     float u[4 * ((P + 3) / 4)];
 };
 
-template <int P>
-__device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, int seed_mode,
-                                           uint32_t j0, MixedPoint<P> &pt) {
+template <int P, int SEED>
+__device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, uint32_t j0,
+                                           MixedPoint<P> &pt) {
     const uint4 h = r4[0];
     const float4 m = *reinterpret_cast<const float4 *>(r4 + 1);
 #pragma unroll
@@ -156,7 +156,7 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
     const uint64_t A = ((uint64_t)h.y << 32) | h.x;
     const uint64_t B = ((uint64_t)h.w << 32) | h.z;
     const uint64_t ph = A + (uint64_t)j0 * B;          // exact phase (turns * 2^64) at f_{j0}
-    if (seed_mode == 0) {
+    if constexpr (SEED == 0) {
         seed_from_table_f(tab, (uint32_t)(ph >> 32), &pt.s, &pt.c);
     } else {
         const float ang = (float)(int32_t)(ph >> 32) * TWO_PI_OVER_2_32;
@@ -196,6 +196,27 @@ __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, float 
             c = cn;
         }
     }
+}
+
+// m >= 1 consecutive points of this warp (records p, p + stride, ...),
+// software-pipelined: the next point's record and seed are fetched while the
+// current point's F-step loop runs (two alternating point buffers).  The loop
+// is over pairs with no per-point branch; an even run ends by re-fetching its
+// last point, which is not accumulated.
+template <int P, int F, int SEED>
+__device__ __forceinline__ void mixed_run(const unsigned char *p, size_t stride, int m, const SeedTableF &tab,
+                                          uint32_t j0, float (&acc)[F][2 * P + 4]) {
+    auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(p + (size_t)i * stride); };
+    MixedPoint<P> pa, pb;
+    mixed_load<P, SEED>(rec(0), tab, j0, pa);
+    int j = 0;
+    for (; j + 2 <= m; j += 2) {
+        mixed_load<P, SEED>(rec(j + 1), tab, j0, pb);
+        mixed_accumulate<P, F>(pa, acc);
+        mixed_load<P, SEED>(rec(min(j + 2, m - 1)), tab, j0, pa);
+        mixed_accumulate<P, F>(pb, acc);
+    }
+    if (j < m) mixed_accumulate<P, F>(pa, acc);
 }
 
 template <int P, int F>
@@ -275,8 +296,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         for (int q = 0; q < Q; ++q) acc[k][q] = T(0);
 
     int since = 0;   // points in the current first-level block of this warp
-    // Second summation level: block sums are added into the warp's running
-    // sums in shared memory.
+    // Second summation level: block sums of FLUSH_POINTS points are added into
+    // the warp's running sums in shared memory.
     auto flush = [&]() {
         T *mine = red + (size_t)warp * Q * F * 32;
 #pragma unroll
@@ -286,12 +307,6 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
                 mine[(q * F + k) * 32 + lane] += acc[k][q];
                 acc[k][q] = T(0);
             }
-    };
-    auto tick = [&]() {
-        if (++since == FLUSH_POINTS) {
-            flush();
-            since = 0;
-        }
     };
 
     for (int tile = 0; tile < ntiles; ++tile) {
@@ -303,23 +318,23 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         const int n = min(TILE_POINTS, N - tile * TILE_POINTS);
         const unsigned char *tb = tiles + b * L::TILE_BYTES;
         if constexpr (PREC == FREDEC_MIXED) {
-            // software pipeline: the next point's record and seed are fetched
-            // while the current point's F-step loop runs
-            // (two alternating point buffers, so nothing is copied)
-            MixedPoint<P> pa, pb;
-            auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(tb + (size_t)i * L::RB); };
-            int i = warp;
-            if (i < n) mixed_load<P>(rec(i), tabf, prm.seed_mode, j0, pa);
-            while (i < n) {
-                if (i + nw < n) mixed_load<P>(rec(i + nw), tabf, prm.seed_mode, j0, pb);
-                mixed_accumulate<P, F>(pa, acc);
-                tick();
-                i += nw;
-                if (i >= n) break;
-                if (i + nw < n) mixed_load<P>(rec(i + nw), tabf, prm.seed_mode, j0, pa);
-                mixed_accumulate<P, F>(pb, acc);
-                tick();
-                i += nw;
+            // this warp's points of the tile (warp, warp + nw, ...) in runs
+            // that end on the first-level block boundaries
+            const int cnt = n > warp ? (n - warp + nw - 1) / nw : 0;
+            const unsigned char *pw = tb + (size_t)warp * L::RB;
+            const size_t stride = (size_t)nw * L::RB;
+            for (int k = 0; k < cnt;) {
+                const int take = min(cnt - k, FLUSH_POINTS - since);
+                if (prm.seed_mode == 0)
+                    mixed_run<P, F, 0>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                else
+                    mixed_run<P, F, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                k += take;
+                since += take;
+                if (since == FLUSH_POINTS) {
+                    flush();
+                    since = 0;
+                }
             }
         } else {
             for (int i = warp; i < n; i += nw)
