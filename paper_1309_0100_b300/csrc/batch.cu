@@ -81,7 +81,7 @@ struct fredec_batch_plan {
         bp.prm.flag_list = fix ? flag_list : nullptr;
         bp.prm.flag_count = flag_count;
         bp.prm.err = err;
-        bp.prm.seed_mode = 0;
+        bp.prm.seed_mode = seed_mode();
         bp.items = items;
         bp.n_items = n_items;
         bp.counter = counter;

@@ -119,6 +119,8 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf);
 bool shape_supported(int precision, int p, int fpt);
 // Single-series launch: z (and optional coef) for all nf grid points; the
 // mixed path appends ill-conditioned bins (global z indices) to flag_list.
+// sin/cos seed of the mixed periodogram kernels (1 = MUFU, 0 = table)
+int seed_mode();
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev,
                  const void *rec, int p, int N, int64_t nf, PgramShape shape, double flag_tau,
                  double *z, double *coef, int64_t *flag_list, int32_t *flag_count, int32_t *err,
