@@ -249,18 +249,43 @@ static int check_series_host(const double *t, const double *y, const double *sig
     return FREDEC_OK;
 }
 
-// Uniform-grid detection: f_j = f0 + j*df within 8 ulps of max |f|.
 // Uniform-grid detection: f_j = f0 + j*df within 8 ulps of max |f| (a uniform
-// grid is monotone, so max |f| is at an end point).  One pass, early exit.
-static bool grid_uniform(const double *f, int64_t nf, double *f0, double *df) {
-    if (nf <= 0) { *f0 = 0.0; *df = 0.0; return true; }
+// grid is monotone, so max |f| is at an end point).  f0 and df come from the
+// end points; a NaN or infinite entry fails the test.  grid_uniform_sampled
+// tests 65 evenly spaced entries (the cheap check that decides whether to
+// start the uniform-grid pipeline before the full test); grid_uniform tests
+// every entry, in blocks of 4096 without early exit inside a block.
+static bool grid_params(const double *f, int64_t nf, double *f0, double *df, double *tol) {
     *f0 = f[0];
     *df = nf > 1 ? (f[nf - 1] - f[0]) / (double)(nf - 1) : 0.0;
     const double fmax = std::max(std::fabs(f[0]), std::fabs(f[nf - 1]));
-    const double tol = 8.0 * std::ldexp(1.0, std::ilogb(fmax > 0 ? fmax : 1.0) - 52);
+    if (!std::isfinite(fmax) || !std::isfinite(*df)) return false;
+    *tol = 8.0 * std::ldexp(1.0, std::ilogb(fmax > 0 ? fmax : 1.0) - 52);
+    return true;
+}
+
+static bool grid_uniform_sampled(const double *f, int64_t nf, double *f0, double *df) {
+    double tol;
+    if (nf <= 0) { *f0 = 0.0; *df = 0.0; return true; }
+    if (!grid_params(f, nf, f0, df, &tol)) return false;
+    for (int s = 0; s <= 64; ++s) {
+        const int64_t j = (int64_t)((double)(nf - 1) * s / 64.0);
+        if (!(std::fabs(f[j] - (*f0 + (double)j * *df)) <= tol)) return false;
+    }
+    return true;
+}
+
+static bool grid_uniform(const double *f, int64_t nf, double *f0, double *df) {
+    double tol;
+    if (nf <= 0) { *f0 = 0.0; *df = 0.0; return true; }
+    if (!grid_params(f, nf, f0, df, &tol)) return false;
     const double a = *f0, d = *df;
-    for (int64_t j = 0; j < nf; ++j)
-        if (std::fabs(f[j] - (a + (double)j * d)) > tol) return false;
+    for (int64_t j0 = 0; j0 < nf; j0 += 4096) {
+        const int64_t j1 = std::min<int64_t>(nf, j0 + 4096);
+        int bad = 0;
+        for (int64_t j = j0; j < j1; ++j) bad |= !(std::fabs(f[j] - (a + (double)j * d)) <= tol);
+        if (bad) return false;
+    }
     return true;
 }
 
@@ -341,9 +366,11 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
     if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (int rc = check_series_host(t, y, sigma, N, base_freqs, n_base)) return rc;
     if (nf > 0 && (!f_grid || !z_out)) return fail(FREDEC_EINVAL, "null f_grid or z_out");
-    if (nf > 0 && !finite_all(f_grid, nf)) return fail(FREDEC_EINVAL, "trial frequencies must be finite");
+    // A grid that looks uniform on a sample starts the uniform-grid pipeline
+    // at once; the full test of every entry runs on the host meanwhile, and a
+    // grid that fails it is redone by the generic-grid kernel.
     double f0, df;
-    const bool uniform = grid_uniform(f_grid, nf, &f0, &df);
+    const bool spec = grid_uniform_sampled(f_grid, nf, &f0, &df);
     HostStream hs;
     if (int rc = hs.make()) return rc;
     cudaStream_t st = hs.s;
@@ -352,32 +379,38 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
     int rc = FREDEC_OK;
     {
         DevBuf io;
-        const size_t nin = 3 * N + nb + (uniform ? 0 : nf);
+        const size_t nin = 3 * N + nb + nf;
         const size_t bytes = nin * 8 + (size_t)nf * 8 + 3 * 8 + (size_t)k * 8 + (coef_out ? 16 * nf : 0) + 64;
         if ((rc = io.alloc(bytes, st))) return rc;
         double *d = io.as<double>();
         double *dt = d, *dy = d + N, *ds = d + 2 * N, *db = d + 3 * N, *dfg = db + nb;
-        double *dz = dfg + (uniform ? 0 : nf), *dinfo = dz + nf, *dcoef = dinfo + 3;
+        double *dz = dfg + nf, *dinfo = dz + nf, *dcoef = dinfo + 3;
         int64_t *dtop = (int64_t *)(dcoef + (coef_out ? 2 * nf : 0));
         FREDEC_CUDA_TRY(cudaMemcpyAsync(dt, t, N * 8, cudaMemcpyHostToDevice, st));
         FREDEC_CUDA_TRY(cudaMemcpyAsync(dy, y, N * 8, cudaMemcpyHostToDevice, st));
         FREDEC_CUDA_TRY(cudaMemcpyAsync(ds, sigma, N * 8, cudaMemcpyHostToDevice, st));
         if (nb) FREDEC_CUDA_TRY(cudaMemcpyAsync(db, base_freqs, nb * 8, cudaMemcpyHostToDevice, st));
-        DevBuf ws;
+        DevBuf ws, ws_generic;
         const SeriesState *state = nullptr;
         const int32_t *err = nullptr;
-        if (uniform) {
+        bool uniform = false;
+        if (spec) {
             SingleWork w;
             rc = periodogram_core(dt, dy, ds, N, db, nb, f0, df, nf, o, dz, dinfo, k ? dtop : nullptr,
                                   coef_out ? dcoef : nullptr, st, ws, w);
             state = w.state;
             err = w.err;
-        } else {
+            uniform = grid_uniform(f_grid, nf, &f0, &df);   // overlaps the device work
+            if (!uniform && !rc) rc = cudaStreamSynchronize(st) == cudaSuccess ? FREDEC_OK : FREDEC_ECUDA;
+        }
+        if (!rc && !uniform) {
+            if (!finite_all(f_grid, nf)) return fail(FREDEC_EINVAL, "trial frequencies must be finite");
             FREDEC_CUDA_TRY(cudaMemcpyAsync(dfg, f_grid, nf * 8, cudaMemcpyHostToDevice, st));
             SeriesState *sp = nullptr;
             rc = generic_grid_periodogram(dt, dy, ds, N, db, nb, dfg, nf, o, dz, coef_out ? dcoef : nullptr,
-                                          dinfo, st, &sp, ws);
+                                          dinfo, st, &sp, ws_generic);
             state = sp;
+            err = nullptr;
             if (!rc && k) rc = launch_topk_single(dz, nf, k, dtop, st);
         }
         if (rc) {

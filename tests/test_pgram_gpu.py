@@ -102,6 +102,25 @@ def test_non_uniform_grid(F):
     assert rel_err(z, zr, ratio >= MIN_RATIO) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grid_nearly_uniform(F, prec):
+    # the host API starts the uniform-grid pipeline when 65 evenly spaced
+    # entries fit f0 + j df, and checks every entry meanwhile: one entry moved
+    # between the sampled ones must still give the periodogram at the
+    # frequencies given (the generic-grid kernel), a NaN there an error
+    s = synth.small_series(9, N=300, n_base=2, nf=6401, fmax=1.0)
+    f = s.grid.array().copy()
+    f[1234] += 0.3 * s.grid.df                     # 1234 is not a multiple of 6400/64
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
+    z, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=3)
+    assert rel_err(z, zr, ratio >= MIN_RATIO) < TOL[prec]
+    zu = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), precision=prec)
+    assert abs(z[1234] - zu[1234]) > 1e-6 * abs(zu[1234])   # not the uniform grid's value
+    f[2345] = np.nan
+    with pytest.raises(F.FredecError):
+        F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec)
+
+
 def test_singular_base_and_determinism(F):
     s = synth.small_series(9, N=80, n_base=2)
     with pytest.raises(F.FredecError) as ei:
