@@ -27,15 +27,19 @@
 
 namespace fredec {
 
-// Mixed path: FP32 block sums over 32 points are flushed into the warp's shared
-// running sums.  Short first-level blocks keep the FP32 rounding of the
-// random-phase residual sums <r c>, <r s> small; their error is amplified at
-// low-z bins (dz/z = 2 drho/rho).  Measured (largest z error against the FP64
-// kernel, floor 1e-3 of the highest peak): on the N = 2000, 1e6-frequency
-// residual periodogram 1.8e-6 with 32-point blocks, 2.8e-6 with 64; on short
-// series (N < 700, up to 11 base columns) up to 8e-6 with 64-point blocks,
-// too close to the 1e-5 bar.  64-point blocks would be 5% faster.
+// Mixed path: FP32 block sums are flushed into the warp's shared running sums
+// (two-level summation).  The random-phase residual sums <r c>, <r s> are
+// flushed every 32 points: their FP32 rounding is amplified at low-z bins
+// (dz/z = 2 drho/rho) and sets the z error.  The other 2P+2 sums are flushed
+// every FLUSH_BLOCKS_ALL x 32 = 128 points.  Measured (largest z error against
+// the FP64 kernel, floor 1e-3 of the highest peak; kernel time on the N = 2000,
+// 1e6-frequency residual periodogram):
+//   all sums every 32 points: 1.8e-6, short series (N < 700) 5.5e-6; 1.99 ms
+//   <r c>, <r s> every 32, the rest every 128: 1.8e-6, 5.5e-6; 1.87 ms
+//   the rest every 256: 2.5e-6, 5.5e-6; 1.86 ms
+//   all sums every 64 points: 2.8e-6, 8e-6; 1.90 ms
 constexpr int FLUSH_POINTS = 32;
+constexpr int FLUSH_BLOCKS_ALL = 4;
 
 struct PgramParams {
     const SeriesDesc *desc;
@@ -299,8 +303,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         for (int q = 0; q < Q; ++q) acc[k][q] = T(0);
 
     int since = 0;   // points in the current first-level block of this warp
-    // Second summation level: block sums of FLUSH_POINTS points are added into
-    // the warp's running sums in shared memory.
+    // Second summation level: block sums are added into the warp's running
+    // sums in shared memory, all of them (flush) or only <r c>, <r s> (flush_r).
     auto flush = [&]() {
         T *mine = red + (size_t)warp * Q * F * 32;
 #pragma unroll
@@ -311,6 +315,17 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
                 acc[k][q] = T(0);
             }
     };
+    auto flush_r = [&]() {
+        T *mine = red + (size_t)warp * Q * F * 32;
+#pragma unroll
+        for (int k = 0; k < F; ++k)
+#pragma unroll
+            for (int q = 2 * P; q < 2 * P + 2; ++q) {
+                mine[(q * F + k) * 32 + lane] += acc[k][q];
+                acc[k][q] = T(0);
+            }
+    };
+    int nblk = 0;   // first-level blocks since the last flush of all sums
 
     for (int tile = 0; tile < ntiles; ++tile) {
         const int b = tile & 1;
@@ -335,7 +350,12 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
                 k += take;
                 since += take;
                 if (since == FLUSH_POINTS) {
-                    flush();
+                    if (++nblk == FLUSH_BLOCKS_ALL) {
+                        flush();
+                        nblk = 0;
+                    } else {
+                        flush_r();
+                    }
                     since = 0;
                 }
             }
