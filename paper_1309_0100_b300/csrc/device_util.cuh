@@ -34,19 +34,41 @@ __device__ __forceinline__ double turns_of(uint64_t ph) {
     return (double)(int64_t)ph * TWO_POW_M64;
 }
 
-// FP64 sin/cos of a fixed-point phase with the CUDA sincospi (exact reduction
-// is already done by the fixed-point representation).
-__device__ __forceinline__ void sincos_turns_d(uint64_t ph, double *s, double *c) {
-    sincospi(2.0 * turns_of(ph), s, c);
+// cos and sin of 2 pi k / 256, k = 0..255, evaluated at compile time: the
+// quadrant and the complement symmetry reduce the angle to x = r pi/128 in
+// [0, pi/4], whose Taylor series (to x^24 / x^25, truncation below 1e-22) is
+// summed in nested form in double.  Within 1.3e-16 of the exact values (about
+// 1 ulp); the seed tables of every precision are filled from it, so no CTA
+// spends FP64 sin/cos work (FP64 runs at 1/64 of the FP32 rate on this GPU).
+struct SinCos256 { double c[256]; double s[256]; };
+constexpr SinCos256 make_sincos256() {
+    SinCos256 t{};
+    constexpr double PI_128 = 0.024543692606170259675489401431871;   // pi / 128
+    for (int k = 0; k < 256; ++k) {
+        const int q = k / 64, r = k % 64;
+        const bool comp = r > 32;                       // x = pi/2 - (64 - r) pi/128
+        const double x = (comp ? 64 - r : r) * PI_128, x2 = x * x;
+        double c = 1.0, s = 1.0;
+        for (int n = 12; n >= 1; --n) {
+            c = 1.0 - x2 / ((2.0 * n - 1.0) * (2.0 * n)) * c;
+            s = 1.0 - x2 / ((2.0 * n) * (2.0 * n + 1.0)) * s;
+        }
+        s *= x;
+        const double cr = comp ? s : c, sr = comp ? c : s;   // angle r pi/128
+        t.c[k] = q == 0 ? cr : q == 1 ? -sr : q == 2 ? -cr : sr;
+        t.s[k] = q == 0 ? sr : q == 1 ? cr : q == 2 ? -sr : -cr;
+    }
+    return t;
 }
+static __device__ const SinCos256 g_sincos256 = make_sincos256();
 
 // FP64 sin/cos of a fixed-point phase by table lookup and a short Taylor
 // polynomial (Tang's table-driven method): the top 8 bits select
-// e^{2 pi i k/256} from a table built with sincospi, the remaining fraction
-// (< 1/256 turn, |theta| < 0.0246 rad) is evaluated by Taylor series to
-// degree 7 (sin) and 8 (cos), then the two rotations are multiplied.
-// Truncation error < 1e-20.
-struct SeedTable { double c[256]; double s[256]; };
+// e^{2 pi i k/256} from the table above, the remaining fraction (< 1/256 turn,
+// |theta| < 0.0246 rad) is evaluated by Taylor series to degree 7 (sin) and
+// 8 (cos), then the two rotations are multiplied.  Truncation error < 1e-20,
+// about 2e-16 in all.  Kernels copy the table into shared memory.
+using SeedTable = SinCos256;
 
 __device__ __forceinline__ void seed_from_table(const SeedTable &tab, uint64_t ph, double *s, double *c) {
     const unsigned k = (unsigned)(ph >> 56);
@@ -58,6 +80,12 @@ __device__ __forceinline__ void seed_from_table(const SeedTable &tab, uint64_t p
     const double tc = tab.c[k], ts = tab.s[k];
     *c = fma(tc, pc, -ts * ps);
     *s = fma(ts, pc, tc * ps);
+}
+
+// The same from the table in global memory (L1/L2-resident), for code that
+// evaluates a few sin/cos per thread and keeps no table of its own.
+__device__ __forceinline__ void sincos_turns_d(uint64_t ph, double *s, double *c) {
+    seed_from_table(g_sincos256, ph, s, c);
 }
 
 // FP32 variant for the mixed kernel: table of e^{2 pi i k/256} rounded to FP32
@@ -76,23 +104,15 @@ __device__ __forceinline__ void seed_from_table_f(const SeedTableF &tab, uint32_
     *s = fmaf(t.y, pc, t.x * ps);
 }
 
-// FP32 entries from the FP32 sincospi (k/128 is exact in FP32; the entries are
-// within 1 ulp, below the FP32 seed's own rounding): a CTA fills its table on
-// the FP32 pipe instead of spending FP64 operations, which run at 1/64 rate.
 __device__ __forceinline__ void fill_seed_table_f(SeedTableF &tab) {
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        float s, c;
-        sincospif((float)k * (1.0f / 128.0f), &s, &c);
-        tab.cs[k] = make_float2(c, s);
-    }
+    for (int k = threadIdx.x; k < 256; k += blockDim.x)
+        tab.cs[k] = make_float2(__double2float_rn(g_sincos256.c[k]), __double2float_rn(g_sincos256.s[k]));
 }
 
 __device__ __forceinline__ void fill_seed_table(SeedTable &tab) {
     for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        double s, c;
-        sincospi((double)k / 128.0, &s, &c);
-        tab.c[k] = c;
-        tab.s[k] = s;
+        tab.c[k] = g_sincos256.c[k];
+        tab.s[k] = g_sincos256.s[k];
     }
 }
 
@@ -164,7 +184,7 @@ struct ff_acc {
 
 // FF sin/cos of a 64-bit fixed-point phase (Tang's table method in float-float
 // arithmetic): the top 8 bits select e^{2 pi i k/256} from a table of FF pairs
-// (built from FP64 sincospi), the remaining < 1/256 turn x = 2 pi rem 2^-64
+// (the compile-time table g_sincos256, split), the remaining < 1/256 turn x = 2 pi rem 2^-64
 // (|x| < 0.0246) is evaluated by its Taylor series -- the x^2 terms in FF, the
 // terms below 2e-8 in FP32 -- and the two rotations are multiplied in FF.
 // Error about 1e-15 absolute.
@@ -172,9 +192,7 @@ struct SeedTableFF { float4 cs[256]; };   // (cos hi, cos lo, sin hi, sin lo)
 
 __device__ __forceinline__ void fill_seed_table_ff(SeedTableFF &tab) {
     for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        double s, c;
-        sincospi((double)k / 128.0, &s, &c);
-        const ff fc = ff_from_double(c), fs = ff_from_double(s);
+        const ff fc = ff_from_double(g_sincos256.c[k]), fs = ff_from_double(g_sincos256.s[k]);
         tab.cs[k] = make_float4(fc.hi, fc.lo, fs.hi, fs.lo);
     }
 }
@@ -303,29 +321,32 @@ __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j
 
 // In-place Cholesky of a packed symmetric matrix.  Returns false when a pivot is
 // not positive or falls below rel * (its original diagonal).
-__device__ inline bool chol_packed(double *A, int n, double rel) {
+// rinv[j] receives 1 / L_jj: one FP64 division per column, the rest are
+// multiplications (an FP64 division is a long dependent sequence on this GPU).
+__device__ inline bool chol_packed(double *A, int n, double rel, double *rinv) {
     for (int j = 0; j < n; ++j) {
         const double d0 = A[tri(j, j)];
         double d = d0;
         for (int k = 0; k < j; ++k) d -= A[tri(j, k)] * A[tri(j, k)];
         if (!(d > rel * d0) || !(d0 > 0.0)) return false;
-        const double l = sqrt(d);
+        const double l = sqrt(d), il = 1.0 / l;
         A[tri(j, j)] = l;
+        rinv[j] = il;
         for (int i = j + 1; i < n; ++i) {
             double s = A[tri(i, j)];
             for (int k = 0; k < j; ++k) s -= A[tri(i, k)] * A[tri(j, k)];
-            A[tri(i, j)] = s / l;
+            A[tri(i, j)] = s * il;
         }
     }
     return true;
 }
 
-// x <- L^{-1} x (forward substitution), packed L.
-__device__ __forceinline__ void forward_packed(const double *L, double *x, int n) {
+// x <- L^{-1} x (forward substitution), packed L, rinv[i] = 1 / L_ii.
+__device__ __forceinline__ void forward_packed(const double *L, const double *rinv, double *x, int n) {
     for (int i = 0; i < n; ++i) {
         double s = x[i];
         for (int k = 0; k < i; ++k) s -= L[tri(i, k)] * x[k];
-        x[i] = s / L[tri(i, i)];
+        x[i] = s * rinv[i];
     }
 }
 

@@ -6,9 +6,9 @@
 // observations, every term takes its own float-float seed from the exact
 // fixed-point phase and enters double-float running sums (about 1e-16 of the
 // summed magnitudes, like FP64 sums, at a fraction of the FP64 pipe's cost on
-// this GPU); each thread's sums are then combined in FP64 by a
-// fixed-order block reduction, and the 2x2 solve is FP64.  Deterministic; the
-// list order does not matter.
+// this GPU); the threads' sums are combined in float-float by a fixed-order
+// block reduction, and the 2x2 solve is FP64.  Deterministic; the list order
+// does not matter.  CTAs beyond the number of flagged bins exit at once.
 #include <algorithm>
 
 #include "pgram_impl.cuh"
@@ -33,11 +33,13 @@ template <int P>
 __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
     constexpr int Q = 2 * P + 4;
     __shared__ SeedTableFF tab;
-    __shared__ double red[FX_THREADS / 32][Q];
+    __shared__ ff red[FX_THREADS / 32][Q];
+    __shared__ double S[Q];
+    const int32_t n = *prm.count;
+    if ((int32_t)blockIdx.x >= n) return;   // no flagged bin for this CTA
     fill_seed_table_ff(tab);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t n = *prm.count;
     for (int32_t it = blockIdx.x; it < n; it += gridDim.x) {
         const int64_t g = prm.list[it];
         int s = 0;
@@ -76,22 +78,25 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
             fa[2 * P + 2].add_prod(wc, cs);
             fa[2 * P + 3].add_prod(wc, sn);
         }
-        double acc[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) acc[q] = fa[q].value();
+        // the threads' double-float sums combined in float-float (warp
+        // butterflies, then over the warps in a fixed order), one conversion
+        // to FP64 per sum
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const double v = warp_sum_d(acc[q]);
+            ff v = {fa[q].H, fa[q].L};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v = ff_add(v, {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
             if (lane == 0) red[wid][q] = v;
         }
         __syncthreads();
+        if (threadIdx.x < Q) {
+            ff v = red[0][threadIdx.x];
+            for (int w = 1; w < FX_THREADS / 32; ++w) v = ff_add(v, red[w][threadIdx.x]);
+            S[threadIdx.x] = ff_to_double(v);
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double S[Q];
-            for (int q = 0; q < Q; ++q) {
-                double v = 0.0;
-                for (int w = 0; w < FX_THREADS / 32; ++w) v += red[w][q];
-                S[q] = v;
-            }
             double vcc = 0.0, vcs = 0.0, vss = 0.0;
             for (int q = 0; q < P; ++q) {
                 vcc = fma(S[q], S[q], vcc);

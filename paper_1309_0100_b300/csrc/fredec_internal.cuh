@@ -60,6 +60,8 @@ struct SeriesState {
     double tscale;       // time scale of the polynomial columns: tau = (t - tc) / tscale
     double L1[NTRI];     // Cholesky factor of the raw base Gram
     double L2[NTRI];     // Cholesky factor of the second (re-orthogonalisation) Gram
+    double R1[PMAX];     // 1 / diagonal of L1
+    double R2[PMAX];     // 1 / diagonal of L2
     double a[PMAX];      // coefficients of y on the orthonormal base columns
     double a2[PMAX];     // second-pass correction
     int32_t status;      // FREDEC_OK or FREDEC_ESINGULAR

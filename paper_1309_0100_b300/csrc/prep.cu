@@ -39,19 +39,37 @@ struct PrepArgs {
     int precision;
 };
 
+constexpr int PREP_NV = NTRI + PMAX + 4;    // values summed per point, at most
+constexpr int TR_WORDS = 32 * 33;           // a warp's transpose scratch (doubles)
+
+// Dynamic shared memory of the chunk kernels: per warp a transpose scratch and
+// its nv sums.
+constexpr size_t prep_chunk_smem() { return sizeof(double) * (PREP_THREADS / 32) * (TR_WORDS + PREP_NV); }
+
 // Reduce nv per-thread values over the CTA and store them as this chunk's
-// partials.  vals may live in local memory.
+// partials.  vals may live in local memory.  Within a warp the values go
+// through shared memory transposed, 32 at a time, and lane q adds the 32
+// lanes' value q in lane order: nv FP64 additions per warp instead of the
+// 5 nv of a butterfly (FP64 runs at 1/64 of the FP32 rate on this GPU).
 __device__ void store_partials(const PrepArgs &a, int64_t chunk, const double *vals, int nv, double *sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    for (int q = 0; q < nv; ++q) {
-        const double v = warp_sum_d(vals[q]);
-        if (lane == 0) sm[wid * (NTRI + PMAX + 4) + q] = v;
+    double *tr = sm + wid * TR_WORDS, *ws = sm + nw * TR_WORDS;
+    for (int q0 = 0; q0 < nv; q0 += 32) {
+        const int m = min(32, nv - q0);
+        for (int q = 0; q < m; ++q) tr[lane * 33 + q] = vals[q0 + q];
+        __syncwarp();
+        if (lane < m) {
+            double s = 0.0;
+            for (int l = 0; l < 32; ++l) s += tr[l * 33 + lane];
+            ws[wid * PREP_NV + q0 + lane] = s;
+        }
+        __syncwarp();
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nv; q += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sm[w * (NTRI + PMAX + 4) + q];
+        for (int w = 0; w < nw; ++w) s += ws[w * PREP_NV + q];
         a.partials[chunk * a.npart + q] = s;
     }
 }
@@ -74,7 +92,8 @@ __device__ bool arrive_last(SeriesState &st, int which, int nchunks) {
 // Sums of partials 0..nv-1 over the series' chunks into out[] (shared), by the
 // whole CTA: lanes take values, every value is summed over the chunks in chunk
 // order (deterministic); a chunk's values are contiguous, so the loads are
-// coalesced and independent across chunks.
+// coalesced and independent across chunks.  (Measured: four chunks in flight
+// are faster here than sixteen.)
 __device__ void sum_partials(const PrepArgs &a, const SeriesDesc &d, int nv, double *out) {
     for (int q = threadIdx.x; q < nv; q += blockDim.x) {
         const double *col = a.partials + d.chunk_off * a.npart + q;
@@ -178,7 +197,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k2(PrepArgs a) {
         for (int q = threadIdx.x; q < p * (p + 1) / 2; q += blockDim.x) st.L1[q] = f[q];
         __syncthreads();
         if (threadIdx.x == 0) {
-            if (!chol_packed(st.L1, p, 1e-12)) st.status = FREDEC_ESINGULAR;
+            if (!chol_packed(st.L1, p, 1e-12, st.R1)) st.status = FREDEC_ESINGULAR;
             st.counter[1] = 0;
         }
     }
@@ -199,7 +218,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k3(PrepArgs a) {
         const double w = 1.0 / (sg * sg);
         const double yi = a.y[d.obs_off + i];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * d.N + i];
-        forward_packed(st.L1, x, p);
+        forward_packed(st.L1, st.R1, x, p);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * d.N + i] = x[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] = w * x[r] * x[c];
@@ -215,8 +234,8 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k3(PrepArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) {
             if (st.status == FREDEC_OK) {
-                if (!chol_packed(st.L2, p, 1e-12)) st.status = FREDEC_ESINGULAR;
-                else forward_packed(st.L2, st.a, p);
+                if (!chol_packed(st.L2, p, 1e-12, st.R2)) st.status = FREDEC_ESINGULAR;
+                else forward_packed(st.L2, st.R2, st.a, p);
             }
             st.counter[2] = 0;
         }
@@ -239,7 +258,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
         const double w = 1.0 / (sg * sg);
         double r = a.y[d.obs_off + i];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * d.N + i];
-        forward_packed(st.L2, x, p);
+        forward_packed(st.L2, st.R2, x, p);
         for (int q = 0; q < p; ++q) {
             a.psi[d.psi_off + (int64_t)q * d.N + i] = x[q];
             r -= st.a[q] * x[q];
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
 // combined by a fixed-order block reduction (deterministic).
 
 constexpr int SP_THREADS = 256;
-constexpr int SP_NV = NTRI + PMAX + 4;
+constexpr int SP_NV = PREP_NV;
 
 // Block sum of vals[0..nv) (per-thread, may be local memory) into out[0..nv)
 // (shared); all threads see out after return.
@@ -417,7 +436,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
         st.tc = tc;
         st.tscale = tscale;
         for (int q = 0; q < nt; ++q) st.L1[q] = out[q];
-        ok = chol_packed(st.L1, p, 1e-12);
+        ok = chol_packed(st.L1, p, 1e-12, st.R1);
         st.status = ok ? FREDEC_OK : FREDEC_ESINGULAR;
     }
     __syncthreads();
@@ -428,7 +447,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg), yi = a.y[d.obs_off + i];
         double x[PMAX];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
-        forward_packed(st.L1, x, p);
+        forward_packed(st.L1, st.R1, x, p);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
@@ -438,8 +457,8 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     if (threadIdx.x == 0) {
         for (int q = 0; q < nt; ++q) st.L2[q] = out[q];
         for (int q = 0; q < p; ++q) st.a[q] = out[nt + q];
-        ok = chol_packed(st.L2, p, 1e-12);
-        if (ok) forward_packed(st.L2, st.a, p);
+        ok = chol_packed(st.L2, p, 1e-12, st.R2);
+        if (ok) forward_packed(st.L2, st.R2, st.a, p);
         else st.status = FREDEC_ESINGULAR;
     }
     __syncthreads();
@@ -450,7 +469,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
         double x[PMAX], r = a.y[d.obs_off + i];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
-        forward_packed(st.L2, x, p);
+        forward_packed(st.L2, st.R2, x, p);
         for (int q = 0; q < p; ++q) {
             a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
             r -= st.a[q] * x[q];
@@ -519,7 +538,7 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
         FREDEC_CUDA_TRY(cudaGetLastError());
         return FREDEC_OK;
     }
-    const size_t smem = sizeof(double) * (PREP_THREADS / 32) * (NTRI + PMAX + 4);
+    const size_t smem = prep_chunk_smem();
     const dim3 grid((unsigned)pp.nchunks);
     prep_k1<<<grid, PREP_THREADS, smem, st>>>(a);
     prep_k2<<<grid, PREP_THREADS, smem, st>>>(a);

@@ -3,9 +3,13 @@
 // A local maximum is z_j > z_{j-1} and z_j >= z_{j+1}; an end point counts when
 // it exceeds its one neighbour (a single-point grid counts).  Maxima are ranked
 // by decreasing z, ties to the lower index; missing ranks are -1.  Stage 1:
-// every CTA selects the k best maxima of a 4096-point chunk (k rounds of a
-// deterministic block argmax); stage 2: one CTA per series merges its chunks'
-// candidates the same way.  The result does not depend on scheduling.
+// every CTA takes a 4096-point chunk (thread t holds points t, t + 256, ...,
+// so the loads are coalesced); each warp finds its k best maxima by k rounds of
+// a shuffle-only warp argmax, and one warp merges the CTA's 8k candidates the
+// same way.  Stage 2: one CTA per series merges its chunks' candidates: each
+// warp selects the k best of a fixed slice, one warp merges them.  Every step
+// is a fixed-order selection over a strict total order, so the result does not
+// depend on scheduling.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -17,32 +21,55 @@ namespace fredec {
 namespace {
 
 constexpr int TK_THREADS = 256;
-constexpr int TK_PER = 16;
+constexpr int TK_WARPS = TK_THREADS / 32;
+constexpr int TK_PER = 16;                       // points per thread (<= 32: a bit mask of live maxima)
 constexpr int TK_CHUNK = TK_THREADS * TK_PER;
 
+// (z1, j1) ranks before (z2, j2); j < 0 is an empty slot, after everything.
 __device__ __forceinline__ bool better(double z1, int64_t j1, double z2, int64_t j2) {
     if (j2 < 0) return j1 >= 0;
     if (j1 < 0) return false;
     return z1 > z2 || (z1 == z2 && j1 < j2);
 }
 
-// Block-wide best (z, j); every thread receives it.
-__device__ void block_best(double &z, int64_t &j) {
-    __shared__ double sz[32];
-    __shared__ int64_t sj[32];
+// Warp argmax of (z, j); every lane receives it.
+__device__ __forceinline__ void warp_best(double &z, int64_t &j) {
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double oz = __shfl_xor_sync(0xffffffffu, z, o);
         const int64_t oj = __shfl_xor_sync(0xffffffffu, j, o);
-        if (better(oz, oj, z, j)) { z = oz; j = oj; }
+        if (better(oz, oj, z, j)) {
+            z = oz;
+            j = oj;
+        }
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0) { sz[wid] = z; sj[wid] = j; }
-    __syncthreads();
-    z = sz[0];
-    j = sj[0];
-    for (int w = 1; w < nw; ++w)
-        if (better(sz[w], sj[w], z, j)) { z = sz[w]; j = sj[w]; }
+}
+
+// One warp: the k best of the n candidates (cz, cj) (shared or global memory;
+// the taken ones are marked j = -1), written to oj[0..k) and, unless it is
+// null, oz[0..k).
+__device__ void warp_select(const double *cz, int64_t *cj, int64_t n, int k, double *oz, int64_t *oj) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < k; ++r) {
+        double bz = -INFINITY;
+        int64_t bj = -1, bq = -1;
+        for (int64_t q = lane; q < n; q += 32) {
+            const int64_t j = cj[q];
+            if (better(cz[q], j, bz, bj)) {
+                bz = cz[q];
+                bj = j;
+                bq = q;
+            }
+        }
+        const int64_t mine = bj;
+        warp_best(bz, bj);
+        if (bj >= 0 && mine == bj) cj[bq] = -1;   // the owning lane drops it
+        __syncwarp();
+        if (lane == 0) {
+            if (oz) oz[r] = bz;
+            oj[r] = bj;
+        }
+    }
 }
 
 struct TopkArgs {
@@ -61,19 +88,21 @@ struct TopkArgs {
 };
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
+    __shared__ double wz[TK_WARPS * FREDEC_MAX_TOPK];
+    __shared__ int64_t wj[TK_WARPS * FREDEC_MAX_TOPK];
     const int64_t c = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool single = a.chunk_series == nullptr;
     const int s = single ? 0 : a.chunk_series[c];
     const double *z = a.z + (single ? 0 : a.z_off[s]);
     const int64_t n = single ? a.nf_single : a.nf[s];
-    const int64_t j0 = (single ? c * TK_CHUNK : a.chunk_begin[c]) + (int64_t)threadIdx.x * TK_PER;
+    const int64_t cb = single ? c * TK_CHUNK : a.chunk_begin[c];
     double vz[TK_PER];
-    int64_t vj[TK_PER];
+    uint32_t live = 0;   // bit e: point cb + e*TK_THREADS + tid is a local maximum not yet taken
 #pragma unroll
     for (int e = 0; e < TK_PER; ++e) {
-        const int64_t j = j0 + e;
-        vz[e] = -INFINITY;
-        vj[e] = -1;
+        const int64_t j = cb + (int64_t)e * TK_THREADS + tid;
+        vz[e] = 0.0;
         if (j < n) {
             const double zj = z[j];
             bool m;
@@ -81,45 +110,51 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
             else if (j == 0) m = zj > z[1];
             else if (j == n - 1) m = zj > z[n - 2];
             else m = zj > z[j - 1] && zj >= z[j + 1];
-            if (m && zj == zj) { vz[e] = zj; vj[e] = j; }
+            if (m && zj == zj) {
+                vz[e] = zj;
+                live |= 1u << e;
+            }
         }
     }
     for (int r = 0; r < a.k; ++r) {
         double bz = -INFINITY;
         int64_t bj = -1;
+        int be = -1;
 #pragma unroll
-        for (int e = 0; e < TK_PER; ++e)
-            if (better(vz[e], vj[e], bz, bj)) { bz = vz[e]; bj = vj[e]; }
-        block_best(bz, bj);
-#pragma unroll
-        for (int e = 0; e < TK_PER; ++e)
-            if (vj[e] == bj && bj >= 0) vj[e] = -1;
-        if (threadIdx.x == 0) {
-            a.cand_z[c * a.k + r] = bz;
-            a.cand_j[c * a.k + r] = bj;
+        for (int e = 0; e < TK_PER; ++e) {
+            const int64_t j = cb + (int64_t)e * TK_THREADS + tid;
+            if ((live >> e & 1u) && better(vz[e], j, bz, bj)) {
+                bz = vz[e];
+                bj = j;
+                be = e;
+            }
+        }
+        const int64_t mine = bj;
+        warp_best(bz, bj);
+        if (bj >= 0 && mine == bj) live &= ~(1u << be);
+        if (lane == 0) {
+            wz[warp * a.k + r] = bz;
+            wj[warp * a.k + r] = bj;
         }
     }
+    __syncthreads();
+    if (warp == 0) warp_select(wz, wj, (int64_t)TK_WARPS * a.k, a.k, a.cand_z + c * a.k, a.cand_j + c * a.k);
 }
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
+    __shared__ double wz[TK_WARPS * FREDEC_MAX_TOPK];
+    __shared__ int64_t wj[TK_WARPS * FREDEC_MAX_TOPK];
     const int s = blockIdx.x;
+    const int warp = threadIdx.x >> 5;
     const bool single = a.chunk_series == nullptr;
     const int64_t c0 = single ? 0 : a.chunk_off[s], c1 = single ? a.nchunks_single : a.chunk_off[s + 1];
     const int64_t ncand = (c1 - c0) * a.k;
-    for (int r = 0; r < a.k; ++r) {
-        double bz = -INFINITY;
-        int64_t bj = -1;
-        for (int64_t q = threadIdx.x; q < ncand; q += blockDim.x) {
-            const double cz = a.cand_z[c0 * a.k + q];
-            const int64_t cj = a.cand_j[c0 * a.k + q];
-            if (better(cz, cj, bz, bj)) { bz = cz; bj = cj; }
-        }
-        block_best(bz, bj);
-        for (int64_t q = threadIdx.x; q < ncand; q += blockDim.x)
-            if (a.cand_j[c0 * a.k + q] == bj && bj >= 0) a.cand_j[c0 * a.k + q] = -1;
-        if (threadIdx.x == 0) a.out[(int64_t)s * a.k + r] = bj;
-        __syncthreads();
-    }
+    // warp w: candidates [w ncand / 8, (w + 1) ncand / 8)
+    const int64_t q0 = ncand * warp / TK_WARPS, q1 = ncand * (warp + 1) / TK_WARPS;
+    warp_select(a.cand_z + c0 * a.k + q0, a.cand_j + c0 * a.k + q0, q1 - q0, a.k, wz + warp * a.k,
+                wj + warp * a.k);
+    __syncthreads();
+    if (warp == 0) warp_select(wz, wj, (int64_t)TK_WARPS * a.k, a.k, nullptr, a.out + (int64_t)s * a.k);
 }
 
 }  // namespace
