@@ -95,6 +95,7 @@ struct DevBuf {
 // Prep (prep.cu)
 
 constexpr int64_t SERIES_PREP_MAX_N = 16384;   // one prep CTA per series up to this N
+constexpr int64_t CLUSTER_PREP_MAX_N = 65536;  // one prep cluster per series up to this N (fewer than 256 series)
 
 struct PrepPlan {
     int S = 0;                 // series

@@ -15,6 +15,8 @@
 // per thread).  Each chunk writes partial sums; the last chunk of a series to
 // finish (atomic counter) reduces them in chunk order, so results do not
 // depend on scheduling.
+#include <cooperative_groups.h>
+
 #include "device_util.cuh"
 #include "fredec_internal.cuh"
 
@@ -504,11 +506,234 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// One thread-block cluster per series (up to CL_MAX CTAs of CL_THREADS
+// threads; series up to CLUSTER_PREP_MAX_N points): the five phases of
+// prep_k1..k5 in one launch.  The phases are separated by cluster barriers
+// instead of kernel boundaries, and the per-phase sums are exchanged through
+// distributed shared memory: each CTA reduces its points (transposed warp
+// sums, then its warps in order), publishes the CTA sums, and after the
+// barrier every CTA adds the published sums of all CTAs in rank order, so all
+// CTAs hold bitwise the same totals.  Each CTA then factors the Gram matrix
+// itself: the factors, and every branch taken on them, are identical in all
+// CTAs of the cluster, so every CTA reaches every barrier.
+
+constexpr int CL_THREADS = 128;
+constexpr int CL_MAX = 16;
+constexpr int CL_WARPS = CL_THREADS / 32;
+
+struct ClusterSmem {
+    double tr[CL_WARPS][TR_WORDS];   // per-warp transpose scratch
+    double ws[CL_WARPS][PREP_NV];    // per-warp sums
+    double x[2][PREP_NV];            // published CTA sums (alternating)
+    double out[PREP_NV];             // cluster totals
+    double L1[NTRI], L2[NTRI], R1[PMAX], R2[PMAX], av[PMAX], a2[PMAX];
+    int ok;
+};
+
+// Cluster totals of nv per-thread values into sm.out (all threads of all CTAs).
+// Buffer x[ph] is written before the barrier and read remotely after it; the
+// next use of the same buffer comes after the next reduction's barrier, by
+// which time every CTA has finished reading it.
+__device__ void cluster_reduce(const double *vals, int nv, ClusterSmem &sm, int &ph) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q0 = 0; q0 < nv; q0 += 32) {
+        const int m = min(32, nv - q0);
+        for (int q = 0; q < m; ++q) sm.tr[wid][lane * 33 + q] = vals[q0 + q];
+        __syncwarp();
+        if (lane < m) {
+            double v = 0.0;
+            for (int l = 0; l < 32; ++l) v += sm.tr[wid][l * 33 + lane];
+            sm.ws[wid][q0 + lane] = v;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv; q += CL_THREADS) {
+        double v = 0.0;
+        for (int w = 0; w < CL_WARPS; ++w) v += sm.ws[w][q];
+        sm.x[ph][q] = v;
+    }
+    cl.sync();
+    const int nr = (int)cl.num_blocks();
+    for (int q = threadIdx.x; q < nv; q += CL_THREADS) {
+        double v = 0.0;
+        for (int r = 0; r < nr; ++r) v += cl.map_shared_rank(&sm.x[ph][0], r)[q];
+        sm.out[q] = v;
+    }
+    __syncthreads();
+    ph ^= 1;
+}
+
+__global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    ClusterSmem &sm = *reinterpret_cast<ClusterSmem *>(cl_raw);
+    const int nr = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int s = blockIdx.x / nr;
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    const int p = d.pb, nt = p * (p + 1) / 2;
+    const int64_t N = d.N, i0 = (int64_t)rank * CL_THREADS + threadIdx.x, di = (int64_t)nr * CL_THREADS;
+    const bool lead = rank == 0 && threadIdx.x == 0;
+    double v[PREP_NV];
+    int ph = 0;
+    // 1: W, <t>  ->  t_c and the polynomial time scale
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    const double t_first = a.t[d.obs_off];
+    for (int64_t i = i0; i < N; i += di) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        const double ti = a.t[d.obs_off + i], u = ti - t_first;
+        v[0] += w;
+        v[1] += w * ti;
+        v[2] += w * u;
+        v[3] += w * u * u;
+    }
+    cluster_reduce(v, 4, sm, ph);
+    const double W = sm.out[0], tc = rint(sm.out[1] / W), tscale = time_scale(W, sm.out[2], sm.out[3]);
+    // 2: raw base columns, Gram Q1 -> L1
+    for (int q = 0; q < nt; ++q) v[q] = 0.0;
+    for (int64_t i = i0; i < N; i += di) {
+        const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+        double phi[PMAX];
+        base_basis(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
+        for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = phi[q];
+        for (int r = 0; r < p; ++r)
+            for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
+    }
+    cluster_reduce(v, nt, sm, ph);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nt; ++q) sm.L1[q] = sm.out[q];
+        sm.ok = chol_packed(sm.L1, p, 1e-12, sm.R1);
+    }
+    __syncthreads();
+    if (lead) {
+        st.W = W;
+        st.tc = tc;
+        st.tscale = tscale;
+        st.status = sm.ok ? FREDEC_OK : FREDEC_ESINGULAR;
+    }
+    if (sm.ok) {
+        // 3: psi1 = L1^{-1} phi, Gram Q2 and <psi1 y>  ->  L2, a
+        for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
+        for (int64_t i = i0; i < N; i += di) {
+            const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg), yi = a.y[d.obs_off + i];
+            double x[PMAX];
+            for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
+            forward_packed(sm.L1, sm.R1, x, p);
+            for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
+            for (int r = 0; r < p; ++r)
+                for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
+            for (int q = 0; q < p; ++q) v[nt + q] += w * x[q] * yi;
+        }
+        cluster_reduce(v, nt + p, sm, ph);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < nt; ++q) sm.L2[q] = sm.out[q];
+            for (int q = 0; q < p; ++q) sm.av[q] = sm.out[nt + q];
+            sm.ok = chol_packed(sm.L2, p, 1e-12, sm.R2);
+            if (sm.ok) forward_packed(sm.L2, sm.R2, sm.av, p);
+        }
+        __syncthreads();
+        if (lead && !sm.ok) st.status = FREDEC_ESINGULAR;
+    }
+    if (sm.ok) {
+        // 4: psi = L2^{-1} psi1, r = y - a^T psi, <psi r>  ->  a2
+        for (int q = 0; q < p; ++q) v[q] = 0.0;
+        for (int64_t i = i0; i < N; i += di) {
+            const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+            double x[PMAX], r = a.y[d.obs_off + i];
+            for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
+            forward_packed(sm.L2, sm.R2, x, p);
+            for (int q = 0; q < p; ++q) {
+                a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
+                r -= sm.av[q] * x[q];
+            }
+            for (int q = p; q < d.p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
+            for (int q = 0; q < p; ++q) v[q] += w * x[q] * r;
+        }
+        cluster_reduce(v, p, sm, ph);
+        if (threadIdx.x < p) sm.a2[threadIdx.x] = sm.out[threadIdx.x];
+        __syncthreads();
+        // 5: final residual, records, chi2, sum of FP32 weights
+        v[0] = v[1] = 0.0;
+        for (int64_t i = i0; i < N; i += di) {
+            const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
+            const double tp = a.t[d.obs_off + i] - tc;
+            double r = a.y[d.obs_off + i], u[PMAX];
+            for (int q = 0; q < p; ++q) {
+                const double ps = a.psi[d.psi_off + (int64_t)q * N + i];
+                r -= (sm.av[q] + sm.a2[q]) * ps;
+                u[q] = w * ps;
+            }
+            for (int q = p; q < d.p; ++q) u[q] = 0.0;
+            write_records(a, d, i, tp, w, r, u);
+            v[0] += w * r * r;
+            v[1] += (double)(float)w;
+        }
+        cluster_reduce(v, 2, sm, ph);
+        if (lead) {
+            for (int q = 0; q < nt; ++q) {
+                st.L1[q] = sm.L1[q];
+                st.L2[q] = sm.L2[q];
+            }
+            for (int q = 0; q < p; ++q) {
+                st.R1[q] = sm.R1[q];
+                st.R2[q] = sm.R2[q];
+                st.a[q] = sm.av[q];
+                st.a2[q] = sm.a2[q];
+            }
+            st.chi2 = sm.out[0];
+            st.Wf = sm.out[1];
+        }
+    }
+    cl.sync();   // no CTA leaves while another may still read its published sums
+}
+
 }  // namespace
 
 int launch_prep(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
                 const double *base, int precision, cudaStream_t st) {
     return run_prep_records(pp, t, y, sigma, base, precision, nullptr, st);
+}
+
+// CTAs per cluster for series of up to max_n points: enough for about one
+// point per thread, at most 16 (8 where the device refuses 16); 0 when cluster
+// launches cannot be used.  The attributes are set once.
+static int cluster_size_for(int64_t max_n) {
+    static int cap = -1;
+    if (cap < 0) {
+        cap = 0;
+        if (cudaFuncSetAttribute(prep_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ClusterSmem)) == cudaSuccess) {
+            cap = 8;
+            if (cudaFuncSetAttribute(prep_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(CL_MAX);
+                cfg.blockDim = dim3(CL_THREADS);
+                cfg.dynamicSmemBytes = sizeof(ClusterSmem);
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = CL_MAX;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, prep_cluster, &cfg) == cudaSuccess && nclusters > 0)
+                    cap = CL_MAX;
+            }
+        }
+        cudaGetLastError();   // clear a refused attribute
+    }
+    if (cap == 0) return 0;
+    const int64_t want = (max_n + CL_THREADS - 1) / CL_THREADS;
+    int cs = 1;
+    while (cs < cap && cs < want) cs *= 2;
+    return cs;
 }
 
 // As launch_prep; rec64 (optional, mixed runs) also receives float-float
@@ -537,6 +762,26 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
         prep_series<<<(unsigned)pp.S, SP_THREADS, smem, st>>>(a);
         FREDEC_CUDA_TRY(cudaGetLastError());
         return FREDEC_OK;
+    }
+    // A few series of moderate length: one cluster of up to 16 CTAs per series.
+    if (pp.max_n > 0 && pp.max_n <= CLUSTER_PREP_MAX_N) {
+        const int cs = cluster_size_for(pp.max_n);
+        if (cs > 0) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(pp.S * cs));
+            cfg.blockDim = dim3(CL_THREADS);
+            cfg.dynamicSmemBytes = sizeof(ClusterSmem);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)cs;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            FREDEC_CUDA_TRY(cudaLaunchKernelEx(&cfg, prep_cluster, a));
+            return FREDEC_OK;
+        }
     }
     const size_t smem = prep_chunk_smem();
     const dim3 grid((unsigned)pp.nchunks);
