@@ -3,13 +3,21 @@
 // A local maximum is z_j > z_{j-1} and z_j >= z_{j+1}; an end point counts when
 // it exceeds its one neighbour (a single-point grid counts).  Maxima are ranked
 // by decreasing z, ties to the lower index; missing ranks are -1.  Stage 1:
-// every CTA takes a 4096-point chunk (thread t holds points t, t + 256, ...,
-// so the loads are coalesced); each warp finds its k best maxima by k rounds of
-// a shuffle-only warp argmax, and one warp merges the CTA's 8k candidates the
-// same way.  Stage 2: one CTA per series merges its chunks' candidates: each
-// warp selects the k best of a fixed slice, one warp merges them.  Every step
-// is a fixed-order selection over a strict total order, so the result does not
-// depend on scheduling.
+// every CTA takes a 4096-point chunk (thread t holds points t, t + 1024, ...,
+// so the loads are coalesced), gathers its local maxima in shared memory (at
+// most 2048: two maxima are never adjacent) and sorts them with a bitonic
+// network; its first k, in rank order, are the chunk's candidates.  Stage 2:
+// one CTA per series.  Few candidates (<= 512, or <= 2048 with k >= 16) are
+// sorted the same way; otherwise the chunks' sorted lists are merged by a
+// k-round tournament (thread t holds the head of chunk t; each round an argmax
+// takes the best head and that chunk advances), by one warp with shuffles only
+// for up to 32 chunks, by the block for up to 1024.  Series of more chunks use
+// k rounds of warp selection over fixed slices, then a merge of the slices.
+// 1024 threads per CTA: one compare-exchange per thread per sorting step.
+// The order is strict and total, so the result does not depend on scheduling
+// or on the order in which the maxima were gathered.  Every comparison is on
+// integers: z is mapped once to an order-preserving 64-bit key (double
+// comparisons run on the FP64 pipe, at 1/64 of the FP32 rate on this GPU).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -20,23 +28,63 @@ namespace fredec {
 
 namespace {
 
-constexpr int TK_THREADS = 256;
+constexpr int TK_THREADS = 1024;
 constexpr int TK_WARPS = TK_THREADS / 32;
-constexpr int TK_PER = 16;                       // points per thread (<= 32: a bit mask of live maxima)
+constexpr int TK_PER = 4;                        // points per thread
 constexpr int TK_CHUNK = TK_THREADS * TK_PER;
+constexpr int TK_SORT = TK_CHUNK / 2;            // sort capacity (maxima of a chunk)
 
-// (z1, j1) ranks before (z2, j2); j < 0 is an empty slot, after everything.
-__device__ __forceinline__ bool better(double z1, int64_t j1, double z2, int64_t j2) {
+// Order-preserving key of a non-NaN double: z1 < z2 exactly when
+// key(z1) < key(z2) as unsigned integers (-0 is taken as +0).
+__device__ __forceinline__ uint64_t order_key(double z) {
+    uint64_t b = (uint64_t)__double_as_longlong(z);
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ bool is_nan_bits(double z) {
+    return ((uint64_t)__double_as_longlong(z) & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+}
+
+// (k1, j1) ranks before (k2, j2); j < 0 is an empty slot, after everything.
+__device__ __forceinline__ bool better(uint64_t k1, int64_t j1, uint64_t k2, int64_t j2) {
     if (j2 < 0) return j1 >= 0;
     if (j1 < 0) return false;
-    return z1 > z2 || (z1 == z2 && j1 < j2);
+    return k1 > k2 || (k1 == k2 && j1 < j2);
+}
+
+// Sorts (kz, kj)[0..n) in shared memory into rank order; n a power of two.
+__device__ void block_sort(uint64_t *kz, int64_t *kj, int n) {
+    for (int size = 2; size <= n; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool first = (lo & size) == 0;   // this half-block in rank order
+                const bool sw = first ? better(kz[hi], kj[hi], kz[lo], kj[lo]) : better(kz[lo], kj[lo], kz[hi], kj[hi]);
+                if (sw) {
+                    const uint64_t tz = kz[lo];
+                    const int64_t tj = kj[lo];
+                    kz[lo] = kz[hi];
+                    kj[lo] = kj[hi];
+                    kz[hi] = tz;
+                    kj[hi] = tj;
+                }
+            }
+        }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int pow2_at_least(int n) {
+    int m = 2;
+    while (m < n) m <<= 1;
+    return m;
 }
 
 // Warp argmax of (z, j); every lane receives it.
-__device__ __forceinline__ void warp_best(double &z, int64_t &j) {
+__device__ __forceinline__ void warp_best(uint64_t &z, int64_t &j) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double oz = __shfl_xor_sync(0xffffffffu, z, o);
+        const uint64_t oz = __shfl_xor_sync(0xffffffffu, z, o);
         const int64_t oj = __shfl_xor_sync(0xffffffffu, j, o);
         if (better(oz, oj, z, j)) {
             z = oz;
@@ -46,12 +94,11 @@ __device__ __forceinline__ void warp_best(double &z, int64_t &j) {
 }
 
 // One warp: the k best of the n candidates (cz, cj) (shared or global memory;
-// the taken ones are marked j = -1), written to oj[0..k) and, unless it is
-// null, oz[0..k).
-__device__ void warp_select(const double *cz, int64_t *cj, int64_t n, int k, double *oz, int64_t *oj) {
+// the taken ones are marked j = -1), written to oz[0..k), oj[0..k).
+__device__ void warp_select(const uint64_t *cz, int64_t *cj, int64_t n, int k, uint64_t *oz, int64_t *oj) {
     const int lane = threadIdx.x & 31;
     for (int r = 0; r < k; ++r) {
-        double bz = -INFINITY;
+        uint64_t bz = 0;
         int64_t bj = -1, bq = -1;
         for (int64_t q = lane; q < n; q += 32) {
             const int64_t j = cj[q];
@@ -66,7 +113,7 @@ __device__ void warp_select(const double *cz, int64_t *cj, int64_t n, int k, dou
         if (bj >= 0 && mine == bj) cj[bq] = -1;   // the owning lane drops it
         __syncwarp();
         if (lane == 0) {
-            if (oz) oz[r] = bz;
+            oz[r] = bz;
             oj[r] = bj;
         }
     }
@@ -80,7 +127,7 @@ struct TopkArgs {
     const int64_t *chunk_begin; // first grid index of each chunk (series-local)
     const int64_t *chunk_off;  // [S+1] first chunk of each series
     int k;
-    double *cand_z;            // [nchunks * k]
+    uint64_t *cand_z;          // [nchunks * k] order keys
     int64_t *cand_j;
     int64_t *out;              // [S * k]
     int64_t nf_single;         // single-series mode (chunk_series == nullptr)
@@ -88,73 +135,156 @@ struct TopkArgs {
 };
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
-    __shared__ double wz[TK_WARPS * FREDEC_MAX_TOPK];
-    __shared__ int64_t wj[TK_WARPS * FREDEC_MAX_TOPK];
+    __shared__ uint64_t kz[TK_SORT];
+    __shared__ int64_t kj[TK_SORT];
+    __shared__ int count;
     const int64_t c = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const bool single = a.chunk_series == nullptr;
     const int s = single ? 0 : a.chunk_series[c];
     const double *z = a.z + (single ? 0 : a.z_off[s]);
     const int64_t n = single ? a.nf_single : a.nf[s];
     const int64_t cb = single ? c * TK_CHUNK : a.chunk_begin[c];
-    double vz[TK_PER];
-    uint32_t live = 0;   // bit e: point cb + e*TK_THREADS + tid is a local maximum not yet taken
+    if (tid == 0) count = 0;
+    __syncthreads();
 #pragma unroll
     for (int e = 0; e < TK_PER; ++e) {
         const int64_t j = cb + (int64_t)e * TK_THREADS + tid;
-        vz[e] = 0.0;
         if (j < n) {
+            // the rule in double semantics: any comparison with a NaN is false
             const double zj = z[j];
+            const double zl = j > 0 ? z[j - 1] : 0.0, zr = j + 1 < n ? z[j + 1] : 0.0;
+            const uint64_t kc = order_key(zj);
+            const bool lok = j > 0 && !is_nan_bits(zl), rok = j + 1 < n && !is_nan_bits(zr);
             bool m;
             if (n == 1) m = true;
-            else if (j == 0) m = zj > z[1];
-            else if (j == n - 1) m = zj > z[n - 2];
-            else m = zj > z[j - 1] && zj >= z[j + 1];
-            if (m && zj == zj) {
-                vz[e] = zj;
-                live |= 1u << e;
+            else if (j == 0) m = rok && kc > order_key(zr);
+            else if (j == n - 1) m = lok && kc > order_key(zl);
+            else m = lok && rok && kc > order_key(zl) && kc >= order_key(zr);
+            if (m && !is_nan_bits(zj)) {
+                const int at = atomicAdd(&count, 1);   // < TK_SORT: maxima are never adjacent
+                kz[at] = kc;
+                kj[at] = j;
             }
-        }
-    }
-    for (int r = 0; r < a.k; ++r) {
-        double bz = -INFINITY;
-        int64_t bj = -1;
-        int be = -1;
-#pragma unroll
-        for (int e = 0; e < TK_PER; ++e) {
-            const int64_t j = cb + (int64_t)e * TK_THREADS + tid;
-            if ((live >> e & 1u) && better(vz[e], j, bz, bj)) {
-                bz = vz[e];
-                bj = j;
-                be = e;
-            }
-        }
-        const int64_t mine = bj;
-        warp_best(bz, bj);
-        if (bj >= 0 && mine == bj) live &= ~(1u << be);
-        if (lane == 0) {
-            wz[warp * a.k + r] = bz;
-            wj[warp * a.k + r] = bj;
         }
     }
     __syncthreads();
-    if (warp == 0) warp_select(wz, wj, (int64_t)TK_WARPS * a.k, a.k, a.cand_z + c * a.k, a.cand_j + c * a.k);
+    const int cnt = count, m = pow2_at_least(max(cnt, a.k));
+    for (int q = cnt + tid; q < m; q += TK_THREADS) {
+        kz[q] = 0;
+        kj[q] = -1;
+    }
+    block_sort(kz, kj, m);
+    for (int r = tid; r < a.k; r += TK_THREADS) {
+        a.cand_z[c * a.k + r] = kz[r];
+        a.cand_j[c * a.k + r] = kj[r];
+    }
 }
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
-    __shared__ double wz[TK_WARPS * FREDEC_MAX_TOPK];
-    __shared__ int64_t wj[TK_WARPS * FREDEC_MAX_TOPK];
+    __shared__ uint64_t kz[TK_SORT];
+    __shared__ int64_t kj[TK_SORT];
+    __shared__ uint64_t oz[FREDEC_MAX_TOPK];
+    __shared__ int64_t oj[FREDEC_MAX_TOPK];
     const int s = blockIdx.x;
-    const int warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool single = a.chunk_series == nullptr;
     const int64_t c0 = single ? 0 : a.chunk_off[s], c1 = single ? a.nchunks_single : a.chunk_off[s + 1];
-    const int64_t ncand = (c1 - c0) * a.k;
-    // warp w: candidates [w ncand / 8, (w + 1) ncand / 8)
+    const int64_t nch = c1 - c0, ncand = nch * a.k;
+    const uint64_t *cz = a.cand_z + c0 * a.k;
+    int64_t *cj = a.cand_j + c0 * a.k;
+    if (ncand <= 512 || (a.k >= 16 && ncand <= TK_SORT)) {
+        const int m = pow2_at_least((int)ncand);
+        for (int q = tid; q < m; q += TK_THREADS) {
+            kz[q] = q < ncand ? cz[q] : 0;
+            kj[q] = q < ncand ? cj[q] : -1;
+        }
+        block_sort(kz, kj, m);
+        for (int r = tid; r < a.k; r += TK_THREADS) a.out[(int64_t)s * a.k + r] = kj[r];
+        return;
+    }
+    if (nch <= 32) {   // all candidates (<= 32 k <= TK_SORT) into shared memory, then one warp
+        for (int64_t q = tid; q < ncand; q += TK_THREADS) {
+            kz[q] = cz[q];
+            kj[q] = cj[q];
+        }
+        __syncthreads();
+        if (warp != 0) return;
+        const bool own = lane < nch;
+        uint64_t hz = own ? kz[lane * a.k] : 0;
+        int64_t hj = own ? kj[lane * a.k] : -1;
+        int ptr = 0;
+        for (int r = 0; r < a.k; ++r) {
+            uint64_t bz = hz;
+            int64_t bj = hj;
+            warp_best(bz, bj);
+            if (lane == 0) a.out[(int64_t)s * a.k + r] = bj;
+            if (hj >= 0 && hj == bj) {   // the winning chunk advances
+                ++ptr;
+                hz = ptr < a.k ? kz[lane * a.k + ptr] : 0;
+                hj = ptr < a.k ? kj[lane * a.k + ptr] : -1;
+            }
+        }
+        return;
+    }
+    if (nch <= TK_THREADS) {
+        // head (hz, hj) of chunk tid and the entry after it (nz, nj), loaded
+        // one round ahead so that the winner's advance waits for no load
+        const bool own = tid < nch;
+        const uint64_t *mz = cz + (int64_t)tid * a.k;
+        const int64_t *mj = cj + (int64_t)tid * a.k;
+        uint64_t hz = 0, nz = 0;
+        int64_t hj = -1, nj = -1;
+        if (own) {
+            hz = mz[0];
+            hj = mj[0];
+            if (a.k > 1) {
+                nz = mz[1];
+                nj = mj[1];
+            }
+        }
+        int ptr = 1;   // rank of (nz, nj) in chunk tid
+        for (int r = 0; r < a.k; ++r) {
+            uint64_t bz = hz;
+            int64_t bj = hj;
+            warp_best(bz, bj);
+            if (lane == 0) {
+                kz[warp] = bz;
+                kj[warp] = bj;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                bz = kz[lane];
+                bj = kj[lane];
+                warp_best(bz, bj);
+                if (lane == 0) oj[r] = bj;
+            }
+            __syncthreads();
+            if (hj >= 0 && hj == oj[r]) {   // the winning chunk advances
+                hz = nz;
+                hj = nj;
+                ++ptr;
+                nz = 0;
+                nj = -1;
+                if (ptr < a.k) {
+                    nz = mz[ptr];
+                    nj = mj[ptr];
+                }
+            }
+        }
+        for (int r = tid; r < a.k; r += TK_THREADS) a.out[(int64_t)s * a.k + r] = oj[r];
+        return;
+    }
+    // many chunks: warp w selects the k best of [w ncand / 32, (w + 1) ncand / 32),
+    // then one warp merges the 32k (<= TK_SORT)
     const int64_t q0 = ncand * warp / TK_WARPS, q1 = ncand * (warp + 1) / TK_WARPS;
-    warp_select(a.cand_z + c0 * a.k + q0, a.cand_j + c0 * a.k + q0, q1 - q0, a.k, wz + warp * a.k,
-                wj + warp * a.k);
+    warp_select(cz + q0, cj + q0, q1 - q0, a.k, kz + warp * a.k, kj + warp * a.k);
     __syncthreads();
-    if (warp == 0) warp_select(wz, wj, (int64_t)TK_WARPS * a.k, a.k, nullptr, a.out + (int64_t)s * a.k);
+    if (warp == 0) {
+        warp_select(kz, kj, (int64_t)TK_WARPS * a.k, a.k, oz, oj);
+        __syncwarp();
+        for (int r = lane; r < a.k; r += 32) a.out[(int64_t)s * a.k + r] = oj[r];
+    }
 }
 
 }  // namespace
@@ -189,7 +319,7 @@ int topk_plan_make(const int64_t *z_off_h, const int64_t *nf_h, int S, int k, in
     int64_t *d_coff = (int64_t *)p; p += (S + 1) * 8;
     int64_t *d_zoff = (int64_t *)p; p += S * 8;
     int64_t *d_nf = (int64_t *)p; p += S * 8;
-    double *d_cz = (double *)p; p += nch * k * 8;
+    uint64_t *d_cz = (uint64_t *)p; p += nch * k * 8;
     int64_t *d_cj = (int64_t *)p; p += nch * k * 8;
     int32_t *d_cs = (int32_t *)p;
     FREDEC_CUDA_TRY(cudaMemcpy(d_cb, cb.data(), nch * 8, cudaMemcpyHostToDevice));
@@ -235,7 +365,7 @@ int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, in
     int64_t *d_coff = (int64_t *)p; p += (S + 1) * 8;
     int64_t *d_zoff = (int64_t *)p; p += S * 8;
     int64_t *d_nf = (int64_t *)p; p += S * 8;
-    double *d_cz = (double *)p; p += nch * k * 8;
+    uint64_t *d_cz = (uint64_t *)p; p += nch * k * 8;
     int64_t *d_cj = (int64_t *)p; p += nch * k * 8;
     int32_t *d_cs = (int32_t *)p;
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_cb, cb.data(), nch * 8, cudaMemcpyHostToDevice, st));
@@ -259,8 +389,8 @@ int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cud
     const int64_t nch = std::max<int64_t>(1, (nf + TK_CHUNK - 1) / TK_CHUNK);
     DevBuf cand;
     if (int rc = cand.alloc(nch * k * 16, st)) return rc;
-    TopkArgs a{z, nullptr, nullptr, nullptr, nullptr, nullptr, k, cand.as<double>(),
-               reinterpret_cast<int64_t *>(cand.as<double>() + nch * k), idx_out, nf, nch};
+    TopkArgs a{z, nullptr, nullptr, nullptr, nullptr, nullptr, k, cand.as<uint64_t>(),
+               reinterpret_cast<int64_t *>(cand.as<uint64_t>() + nch * k), idx_out, nf, nch};
     topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
     topk_stage2<<<1, TK_THREADS, 0, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());
