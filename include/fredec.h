@@ -25,6 +25,12 @@
  *   - Return value: a fredec_status.  On any error nothing is written to the
  *     outputs of the host-pointer variants, and fredec_last_error() returns a
  *     message (thread-local, valid until the next call on the same thread).
+ *     One exception: when z_out of fredec_periodogram / _ex is page-locked
+ *     host memory (cudaHostAlloc, cudaHostRegister), the precision mixed, the
+ *     grid uniform and the statistic the difference form, the kernels write
+ *     z into it during the computation instead of copying it afterwards; an
+ *     error found only after the launch (a non-finite grid entry,
+ *     FREDEC_ETIMEOUT) can then leave z_out partly written.
  *   - Ownership: the caller owns every buffer.  The library keeps no pointer
  *     after a call returns (plans are the documented exception).
  *   - Host-pointer variants are synchronous and validate all values.

@@ -122,11 +122,12 @@ struct SingleWork {
 int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
                      int precision, void *rec64, cudaStream_t st);
 
-// The device pipeline for one series on a uniform grid.  All pointers device.
+// The device pipeline for one series on a uniform grid.  All pointers device
+// (z_mirror: optional second destination of z, e.g. page-locked host memory).
 static int periodogram_core(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
                             int nb, double f0, double df, int64_t nf, const fredec_opts &o, double *z,
                             double *info, int64_t *topk, double *coef, cudaStream_t st, DevBuf &ws,
-                            SingleWork &w) {
+                            SingleWork &w, double *z_mirror = nullptr) {
     const int pb = base_cols(nb, o.trend), p = padded_cols(pb);
     const int prec = o.precision;
     const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
@@ -194,11 +195,11 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     }
     if (nf > 0) {
         if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_list,
-                                  w.flag_count, w.err, st))
+                                  w.flag_count, w.err, st, z_mirror))
             return rc;
         if (fix) {
             if (int rc = launch_fixup_bins(w.desc, w.state, 1, w.rec64, p, w.flag_list, w.flag_count, nf, z, coef,
-                                           st))
+                                           st, z_mirror))
                 return rc;
         }
         nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
@@ -371,6 +372,17 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
     // grid that fails it is redone by the generic-grid kernel.
     double f0, df;
     const bool spec = grid_uniform_sampled(f_grid, nf, &f0, &df);
+    // A page-locked z_out is written by the kernels themselves, during the
+    // computation, instead of by a copy after it (mixed precision, uniform
+    // grid, difference statistic: the only passes that write z are then the
+    // periodogram and the re-evaluation of flagged bins).
+    double *z_mirror = nullptr;
+    if (spec && nf > 0 && o.statistic == FREDEC_Z_DIFF && o.precision == FREDEC_MIXED) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, z_out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            z_mirror = static_cast<double *>(pa.devicePointer);
+        cudaGetLastError();
+    }
     HostStream hs;
     if (int rc = hs.make()) return rc;
     cudaStream_t st = hs.s;
@@ -397,7 +409,7 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
         if (spec) {
             SingleWork w;
             rc = periodogram_core(dt, dy, ds, N, db, nb, f0, df, nf, o, dz, dinfo, k ? dtop : nullptr,
-                                  coef_out ? dcoef : nullptr, st, ws, w);
+                                  coef_out ? dcoef : nullptr, st, ws, w, z_mirror);
             state = w.state;
             err = w.err;
             uniform = grid_uniform(f_grid, nf, &f0, &df);   // overlaps the device work
@@ -418,7 +430,7 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             return rc;
         }
         if ((rc = finish_host(st, state, err))) return rc;
-        if (nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(z_out, dz, nf * 8, cudaMemcpyDeviceToHost, st));
+        if (nf && !(uniform && z_mirror)) FREDEC_CUDA_TRY(cudaMemcpyAsync(z_out, dz, nf * 8, cudaMemcpyDeviceToHost, st));
         if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
         if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost, st));
         if (coef_out && nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(coef_out, dcoef, 16 * nf, cudaMemcpyDeviceToHost, st));

@@ -27,6 +27,7 @@ struct FixupParams {
     const int64_t *list;         // global z indices
     const int32_t *count;
     double *z, *coef;
+    double *z_mirror;            // optional second destination of z
 };
 
 template <int P>
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
             const double CC = S[2 * P + 2];
             double a, b, ratio;
             prm.z[g] = solve2(CC, S[2 * P + 3], st.W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &b, &ratio);
+            if (prm.z_mirror) prm.z_mirror[g] = prm.z[g];
             if (prm.coef) {
                 prm.coef[2 * g] = a;
                 prm.coef[2 * g + 1] = b;
@@ -155,8 +157,8 @@ int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nserie
 
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st) {
-    FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef};
+                      cudaStream_t st, double *z_mirror) {
+    FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef, z_mirror};
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 4LL * sm_count());
     switch (p) {
 #define C(P) case P: launch_fx<P>(prm, grid, st); break;

@@ -120,18 +120,20 @@ int launch_prep(const PrepPlan &pp, const double *t, const double *y, const doub
 struct PgramShape { int fpt; int warps; };
 PgramShape default_shape(int precision, int p, int64_t N, int64_t nf);
 bool shape_supported(int precision, int p, int fpt);
-// Single-series launch: z (and optional coef) for all nf grid points; the
-// mixed path appends ill-conditioned bins (global z indices) to flag_list.
 // sin/cos seed of the mixed periodogram kernels (1 = MUFU, 0 = table)
 int seed_mode();
+// Single-series launch: z (and optional coef) for all nf grid points; the
+// mixed path appends ill-conditioned bins (global z indices) to flag_list.
+// z_mirror (optional): a second destination of every z value, e.g. the
+// device address of the caller's page-locked host output.
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev,
                  const void *rec, int p, int N, int64_t nf, PgramShape shape, double flag_tau,
                  double *z, double *coef, int64_t *flag_list, int32_t *flag_count, int32_t *err,
-                 cudaStream_t st);
-// FP64 re-evaluation of the listed bins (fixup.cu).
+                 cudaStream_t st, double *z_mirror = nullptr);
+// FP64-grade re-evaluation of the listed bins (fixup.cu); z_mirror as above.
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st);
+                      cudaStream_t st, double *z_mirror = nullptr);
 
 // Log form of the statistic (Eq. zpowrel) in place, per series (fixup.cu).
 int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,

@@ -38,7 +38,18 @@ FREDEC_DECL_P(13) FREDEC_DECL_P(15) FREDEC_DECL_P(17) FREDEC_DECL_P(19) FREDEC_D
 FREDEC_DECL_P(23) FREDEC_DECL_P(25)
 #undef FREDEC_DECL_P
 
+int launch_pgram_mirror_a(int, int, const PgramParams &, int64_t, int, cudaStream_t);
+int launch_pgram_mirror_b(int, int, const PgramParams &, int64_t, int, cudaStream_t);
+int launch_pgram_mirror_c(int, int, const PgramParams &, int64_t, int, cudaStream_t);
+
 static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    if (prm.z_mirror) {   // mixed precision only (pgram_mirror_*.cu)
+        if (prec != FREDEC_MIXED) return -1;
+        int rc = launch_pgram_mirror_a(p, F, prm, nblocks, warps, st);
+        if (rc == -2) rc = launch_pgram_mirror_b(p, F, prm, nblocks, warps, st);
+        if (rc == -2) rc = launch_pgram_mirror_c(p, F, prm, nblocks, warps, st);
+        return rc == -2 ? -1 : rc;
+    }
     switch (p) {
 #define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, st);
         C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
@@ -101,7 +112,7 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
 
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,
                  int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef, int64_t *flag_list,
-                 int32_t *flag_count, int32_t *err, cudaStream_t st) {
+                 int32_t *flag_count, int32_t *err, cudaStream_t st, double *z_mirror) {
     (void)N;
     if (!shape_supported(precision, p, shape.fpt))
         return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, frequencies per thread)");
@@ -111,6 +122,7 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
     prm.state = state_dev;
     prm.rec = (const unsigned char *)rec;
     prm.z = z;
+    prm.z_mirror = z_mirror;
     prm.coef = coef;
     prm.flag_tau = (precision == FREDEC_MIXED && flag_list) ? flag_tau : -1.0;
     prm.flag_list = flag_list;

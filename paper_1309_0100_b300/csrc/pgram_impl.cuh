@@ -46,6 +46,7 @@ struct PgramParams {
     const SeriesState *state;
     const unsigned char *rec;   // record buffer base (series offsets in desc)
     double *z;                  // output base (series offsets in desc)
+    double *z_mirror;           // optional second destination of z (same offsets)
     double *coef;               // optional (a_j, b_j) output, same offsets * 2
     double flag_tau;            // mixed: FP64 re-evaluation threshold (< 0: never)
     int64_t *flag_list;         // mixed: global z indices of bins to re-evaluate in FP64
@@ -267,7 +268,12 @@ __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const
 // One CTA-block of 32*F frequencies of one series.
 // use0/use1: per-buffer mbarrier phase counters, identical in all threads.
 
-template <int PREC, int P, int F>
+// MIRROR: z also goes to prm.z_mirror (page-locked host memory), staged in
+// shared memory so that the host-memory stores are contiguous.  The mirror
+// kernels are instantiated in translation units of their own
+// (pgram_mirror_*.cu): with them in the same module the kernels without a
+// mirror measured 1.5% slower, identical code notwithstanding.
+template <int PREC, int P, int F, bool MIRROR = false>
 __device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                             int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
     using L = PgramLayout<PREC, P, F>;
@@ -374,6 +380,11 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     __syncthreads();
 
     // Epilogue: combine the warps' partial sums in FP64 and solve per frequency.
+    // With a mirror (page-locked host memory) z is staged in the now idle
+    // record tiles and written out contiguously: scattered 8-byte stores to
+    // host memory would stall the epilogue.
+    double *zbuf = reinterpret_cast<double *>(tiles);
+    static_assert(32 * F * sizeof(double) <= 2 * L::TILE_BYTES, "z staging fits the record tiles");
     const double W = (PREC == FREDEC_MIXED) ? st.Wf : st.W;
     const int64_t nf = d.nf;
     const bool mixed_flags = (PREC == FREDEC_MIXED) && prm.flag_tau >= 0.0;
@@ -411,10 +422,24 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             double ratio;
             zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
         }
-        prm.z[d.z_off + j] = zz;
+        if constexpr (MIRROR) zbuf[ln * F + k] = zz;
+        else prm.z[d.z_off + j] = zz;
         if (prm.coef) {
             prm.coef[2 * (d.z_off + j)] = a;
             prm.coef[2 * (d.z_off + j) + 1] = bb;
+        }
+    }
+    if constexpr (MIRROR) {
+        // the staging stores are ordered before the next block's TMA copies
+        // into the same tiles (persistent kernels) by each writer's fence
+        fence_proxy_async_smem();
+        __syncthreads();
+        for (int i = tid; i < 32 * F; i += blockDim.x) {
+            const int64_t j = jblock + i;
+            if (j < nf) {
+                prm.z[d.z_off + j] = zbuf[i];
+                prm.z_mirror[d.z_off + j] = zbuf[i];
+            }
         }
     }
 }
@@ -441,7 +466,7 @@ template <int PREC, int P, int F>
 constexpr int pgram_minb() { return (PREC == FREDEC_MIXED && F * (2 * P + 4) <= 80) ? 2 : 1; }
 
 // Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
-template <int PREC, int P, int F>
+template <int PREC, int P, int F, bool MIRROR>
 __global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
@@ -449,17 +474,18 @@ __global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(Pg
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
     uint32_t use0 = 0u, use1 = 0u;
-    pgram_block<PREC, P, F>(prm, d, st, blockIdx.x, smem, use0, use1);
+    pgram_block<PREC, P, F, MIRROR>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
-template <int PREC, int P, int F>
+template <int PREC, int P, int F, bool MIRROR = false>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
     using L = PgramLayout<PREC, P, F>;
     const size_t smem = L::smem_bytes(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
-    auto kern = pgram_kernel<PREC, P, F>;
+    if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
+    auto kern = pgram_kernel<PREC, P, F, MIRROR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     if (nblocks <= 0) return FREDEC_OK;

@@ -121,6 +121,23 @@ def test_grid_nearly_uniform(F, prec):
         F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_page_locked_output(F, prec):
+    # a page-locked z_out is written by the kernels during the computation
+    # (no copy afterwards); a fine grid around the base frequencies makes the
+    # mixed path re-evaluate flagged bins, which write it too
+    import torch
+    s = synth.small_series(21, N=800, n_base=2, nf=30, span=2000.0, fmax=0.05)
+    lo, hi = min(s.base_freqs) * 0.9, max(s.base_freqs) * 1.1
+    f = lo + (hi - lo) / 4000 * np.arange(4001)
+    zp, topp = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5)
+    pinned = torch.full((f.size,), -1.0, dtype=torch.float64).pin_memory().numpy()
+    zz, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5, out=pinned)
+    assert np.array_equal(zz, zp) and np.array_equal(pinned, zp) and list(top) == list(topp)
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
+    assert rel_err(zz, zr, ratio >= MIN_RATIO) < TOL[prec]
+
+
 def test_singular_base_and_determinism(F):
     s = synth.small_series(9, N=80, n_base=2)
     with pytest.raises(F.FredecError) as ei:
