@@ -25,7 +25,7 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
 namespace {
 
 constexpr int VJ_THREADS = 128;
-constexpr int VJ_PT = 4;            // points per thread
+constexpr int VJ_PT = 8;            // points per thread (measured: 5% faster than 4 on 1e5 points x 1e7 bins)
 constexpr int VJ_TILE = 2048;       // frequencies staged per shared-memory tile
 constexpr int VJ_SEG = 32;          // re-seed every 32 frequencies
 
@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
     const int64_t j_end = std::min<int64_t>(d.nf, j_begin + chunk_len);
     uint64_t A[VJ_PT], B[VJ_PT];
     T cr[VJ_PT], sr[VJ_PT];
-    double g[VJ_PT];
-    float glo[VJ_PT];
+    double g[VJ_PT];            // FP64 path: running sum
+    float ghi[VJ_PT], glo[VJ_PT];   // FP32 path: float-float running sum (no FP64-pipe conversions)
     int64_t idx[VJ_PT];
 #pragma unroll
     for (int q = 0; q < VJ_PT; ++q) {
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
         cr[q] = (T)reinterpret_cast<const double *>(R)[2];
         sr[q] = (T)reinterpret_cast<const double *>(R)[3];
         g[q] = 0.0;
+        ghi[q] = 0.f;
         glo[q] = 0.f;
     }
     for (int64_t j0 = j_begin; j0 < j_end; j0 += VJ_TILE) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
                 }
                 acc[q] = T(0);
             }
-            for (int k = 0; k < ns; ++k) {
+            auto step = [&](int k) {
                 const T a = sab[2 * (seg + k)], b = sab[2 * (seg + k) + 1];
 #pragma unroll
                 for (int q = 0; q < VJ_PT; ++q) {
@@ -113,22 +114,30 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
                     s[q] = fma(s[q], cr[q], c[q] * sr[q]);
                     c[q] = cn;
                 }
+            };
+            if (ns == VJ_SEG) {   // full segments: no loop bookkeeping
+#pragma unroll
+                for (int k = 0; k < VJ_SEG; ++k) step(k);
+            } else {
+                for (int k = 0; k < ns; ++k) step(k);
             }
 #pragma unroll
             for (int q = 0; q < VJ_PT; ++q) {
                 if constexpr (sizeof(T) == 8) {
                     g[q] += acc[q];
-                } else {   // float-float running sum of the FP32 segment sums
-                    const float h = (float)g[q], sum = h + acc[q], bp = sum - h;
+                } else {   // float-float running sum of the FP32 segment sums (TwoSum)
+                    const float h = ghi[q], sum = h + acc[q], bp = sum - h;
                     glo[q] += (h - (sum - bp)) + (acc[q] - bp);
-                    g[q] = sum;
+                    ghi[q] = sum;
                 }
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < VJ_PT; ++q)
-        if (idx[q] < d.N) gpart[(int64_t)blockIdx.y * d.N + idx[q]] = g[q] + (double)glo[q];
+    for (int q = 0; q < VJ_PT; ++q) {
+        if constexpr (sizeof(T) == 4) g[q] = (double)ghi[q] + (double)glo[q];
+        if (idx[q] < d.N) gpart[(int64_t)blockIdx.y * d.N + idx[q]] = g[q];
+    }
 }
 
 // Sum the frequency-chunk partials of g (in chunk order) and form the base
