@@ -383,8 +383,13 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             z_mirror = static_cast<double *>(pa.devicePointer);
         cudaGetLastError();
     }
+    // a CUDA failure before the full grid check: a non-finite grid entry is
+    // still reported as the validation error it is
+    auto early = [&](int code) {
+        return nf > 0 && !finite_all(f_grid, nf) ? fail(FREDEC_EINVAL, "trial frequencies must be finite") : code;
+    };
     HostStream hs;
-    if (int rc = hs.make()) return rc;
+    if (int rc = hs.make()) return early(rc);
     cudaStream_t st = hs.s;
     const int nb = n_base;
     const int k = o.topk;
@@ -393,7 +398,7 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
         DevBuf io;
         const size_t nin = 3 * N + nb + nf;
         const size_t bytes = nin * 8 + (size_t)nf * 8 + 3 * 8 + (size_t)k * 8 + (coef_out ? 16 * nf : 0) + 64;
-        if ((rc = io.alloc(bytes, st))) return rc;
+        if ((rc = io.alloc(bytes, st))) return early(rc);
         double *d = io.as<double>();
         double *dt = d, *dy = d + N, *ds = d + 2 * N, *db = d + 3 * N, *dfg = db + nb;
         double *dz = dfg + nf, *dinfo = dz + nf, *dcoef = dinfo + 3;
