@@ -347,6 +347,44 @@ __device__ inline bool chol_packed(double *A, int n, double rel, double *rinv) {
     return true;
 }
 
+// The same factorisation by the 32 lanes of one warp (n <= 32), right-looking:
+// for each column j one FP64 reciprocal square root gives 1 / L_jj (and
+// L_jj = d / sqrt(d)), the lanes scale column j, then update the trailing
+// lower triangle one entry per lane.  Every entry is updated by one lane in a
+// fixed order, so the result is deterministic.  The pivot test is the serial
+// version's: the updated diagonal against rel times the original one.  All
+// lanes return the same value.
+__device__ inline bool chol_packed_warp(double *A, int n, double rel, double *rinv) {
+    const int lane = threadIdx.x & 31;
+    const double d0_own = lane < n ? A[tri(lane, lane)] : 0.0;
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {
+        const double d = A[tri(j, j)];
+        const double d0 = __shfl_sync(0xffffffffu, d0_own, j);
+        if (!(d > rel * d0) || !(d0 > 0.0)) return false;   // the same in every lane
+        const double il = rsqrt(d);
+        __syncwarp();
+        if (lane == 0) {
+            A[tri(j, j)] = d * il;
+            rinv[j] = il;
+        }
+        for (int i = j + 1 + lane; i < n; i += 32) A[tri(i, j)] *= il;
+        __syncwarp();
+        const int m = n - j - 1, cnt = m * (m + 1) / 2;
+        for (int e = lane; e < cnt; e += 32) {
+            // e = r (r + 1) / 2 + c, c <= r: entry (j+1+r, j+1+c) of the trailing triangle
+            int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            if ((r + 1) * (r + 2) / 2 <= e) ++r;
+            if (r * (r + 1) / 2 > e) --r;
+            const int c = e - r * (r + 1) / 2;
+            const int i = j + 1 + r, k = j + 1 + c;
+            A[tri(i, k)] -= A[tri(i, j)] * A[tri(k, j)];
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
 // x <- L^{-1} x (forward substitution), packed L, rinv[i] = 1 / L_ii.
 __device__ __forceinline__ void forward_packed(const double *L, const double *rinv, double *x, int n) {
     for (int i = 0; i < n; ++i) {

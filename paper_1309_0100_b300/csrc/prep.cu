@@ -543,10 +543,16 @@ __device__ void cluster_reduce(const double *vals, int nv, ClusterSmem &sm, int 
         const int m = min(32, nv - q0);
         for (int q = 0; q < m; ++q) sm.tr[wid][lane * 33 + q] = vals[q0 + q];
         __syncwarp();
-        if (lane < m) {
-            double v = 0.0;
-            for (int l = 0; l < 32; ++l) v += sm.tr[wid][l * 33 + lane];
-            sm.ws[wid][q0 + lane] = v;
+        if (lane < m) {   // the 32 lanes' values in four interleaved chains, combined in a fixed order
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+#pragma unroll
+            for (int l = 0; l < 32; l += 4) {
+                v0 += sm.tr[wid][l * 33 + lane];
+                v1 += sm.tr[wid][(l + 1) * 33 + lane];
+                v2 += sm.tr[wid][(l + 2) * 33 + lane];
+                v3 += sm.tr[wid][(l + 3) * 33 + lane];
+            }
+            sm.ws[wid][q0 + lane] = (v0 + v1) + (v2 + v3);
         }
         __syncwarp();
     }
@@ -559,8 +565,12 @@ __device__ void cluster_reduce(const double *vals, int nv, ClusterSmem &sm, int 
     cl.sync();
     const int nr = (int)cl.num_blocks();
     for (int q = threadIdx.x; q < nv; q += CL_THREADS) {
+        double x[CL_MAX];   // all remote loads in flight, then added in rank order
+#pragma unroll
+        for (int r = 0; r < CL_MAX; ++r) x[r] = r < nr ? cl.map_shared_rank(&sm.x[ph][0], r)[q] : 0.0;
         double v = 0.0;
-        for (int r = 0; r < nr; ++r) v += cl.map_shared_rank(&sm.x[ph][0], r)[q];
+#pragma unroll
+        for (int r = 0; r < CL_MAX; ++r) v += x[r];
         sm.out[q] = v;
     }
     __syncthreads();
@@ -605,9 +615,11 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
     }
     cluster_reduce(v, nt, sm, ph);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < nt; ++q) sm.L1[q] = sm.out[q];
-        sm.ok = chol_packed(sm.L1, p, 1e-12, sm.R1);
+    if (threadIdx.x < 32) {   // warp 0 factors
+        for (int q = threadIdx.x; q < nt; q += 32) sm.L1[q] = sm.out[q];
+        __syncwarp();
+        const bool ok = chol_packed_warp(sm.L1, p, 1e-12, sm.R1);
+        if (threadIdx.x == 0) sm.ok = ok;
     }
     __syncthreads();
     if (lead) {
@@ -630,11 +642,15 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
             for (int q = 0; q < p; ++q) v[nt + q] += w * x[q] * yi;
         }
         cluster_reduce(v, nt + p, sm, ph);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < nt; ++q) sm.L2[q] = sm.out[q];
-            for (int q = 0; q < p; ++q) sm.av[q] = sm.out[nt + q];
-            sm.ok = chol_packed(sm.L2, p, 1e-12, sm.R2);
-            if (sm.ok) forward_packed(sm.L2, sm.R2, sm.av, p);
+        if (threadIdx.x < 32) {   // warp 0 factors
+            for (int q = threadIdx.x; q < nt; q += 32) sm.L2[q] = sm.out[q];
+            for (int q = threadIdx.x; q < p; q += 32) sm.av[q] = sm.out[nt + q];
+            __syncwarp();
+            const bool ok = chol_packed_warp(sm.L2, p, 1e-12, sm.R2);
+            if (threadIdx.x == 0) {
+                sm.ok = ok;
+                if (ok) forward_packed(sm.L2, sm.R2, sm.av, p);
+            }
         }
         __syncthreads();
         if (lead && !sm.ok) st.status = FREDEC_ESINGULAR;
