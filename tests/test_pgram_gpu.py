@@ -54,6 +54,16 @@ def test_parity_small(F, prec, nb, N, nf):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [5000, 40000, 70000])
+def test_prep_paths_long_series(F, prec, N):
+    # the base fit of one series: a thread-block cluster of up to 16 CTAs for
+    # N <= 65536 (5000: about 2.5 points per thread; 40000: about 20), the
+    # one-warp chunk kernels above; parity of z and chi2_base either way
+    s = synth.small_series(900 + N % 97, N=N, n_base=3, nf=48, span=3000.0, fmax=0.5)
+    _compare(F, s, s.grid.array(), prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_full_grid(F, prec):
     s = synth.config1()
     f = s.grid.array()
