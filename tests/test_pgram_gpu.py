@@ -73,11 +73,14 @@ def test_config1_full_grid(F, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config2_full_size_sampled(F, prec):
-    """Full 1e6-point grid on the GPU in the benchmark launch shape; the oracle
-    evaluates a strided sample plus the neighbourhoods of the top-5 peaks."""
+    """Full 1e6-point grid on the GPU in the benchmark launch shape (the shapes
+    its tuner picks: 6 frequencies per thread in mixed precision, 4 in FP64,
+    4 warps); the oracle evaluates a strided sample plus the neighbourhoods of
+    the top-5 peaks."""
     s = synth.config2()
     f = s.grid.array()
-    z, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5)
+    z, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5,
+                           fpt=6 if prec == "mixed" else 4, warps=4)
     idx = np.unique(np.concatenate([np.arange(0, f.size, 997), np.arange(f.size - 3, f.size)]))
     zr, _, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f[idx], want_ratio=True)
     mask = ratio >= MIN_RATIO
