@@ -44,6 +44,23 @@ struct Cand {
     double f, z;
 };
 
+// Page-locked host memory for the small per-round transfers (asynchronous
+// copies, one synchronisation per round), allocated once per host thread
+// (page-locking is an operating-system call, far slower than a round) and
+// kept for the life of the process.
+static void *pinned_scratch(size_t bytes) {
+    static thread_local void *p = nullptr;
+    static thread_local size_t have = 0;
+    if (have < bytes) {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        have = 0;
+        if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+        have = bytes;
+    }
+    return p;
+}
+
 int check_scan_opts(const fredec_scan_opts *in, int64_t N, fredec_scan_opts *o) {
     fredec_scan_opts_init(o);
     if (in) *o = *in;
@@ -80,9 +97,15 @@ int scan_run(const double *t_d, const double *y_d, const double *s_d, int64_t N,
     size_t off = 0;
     auto take = [&](size_t b) { size_t at = off; off = (off + b + 255) / 256 * 256; return at; };
     const size_t o_z = take((size_t)std::max<int64_t>(nf, 1) * 8), o_b = take(FREDEC_MAX_NBASE * 8);
+    // top indices, their z and info are contiguous: one copy back per round
     const size_t o_k = take(SCAN_PEAKS * 8), o_zk = take(SCAN_PEAKS * 8), o_i = take(4 * 8);
+    const size_t back = o_i + 4 * 8 - o_k;
     DevBuf buf;
     if (int rc = buf.alloc(off, st)) return rc;
+    void *pin = pinned_scratch(FREDEC_MAX_NBASE * 8 + back);   // [base frequencies | the copied-back block]
+    if (!pin) return fail(FREDEC_ECUDA, "cudaMallocHost of the scan's transfer buffer failed");
+    double *base_h = static_cast<double *>(pin);
+    char *back_h = static_cast<char *>(pin) + FREDEC_MAX_NBASE * 8;
     char *b = buf.as<char>();
     double *z_d = (double *)(b + o_z), *base_d = (double *)(b + o_b), *zk_d = (double *)(b + o_zk);
     double *info_d = (double *)(b + o_i);
@@ -104,19 +127,20 @@ int scan_run(const double *t_d, const double *y_d, const double *s_d, int64_t N,
     po.topk = SCAN_PEAKS;
     while ((int)base.size() < o.max_base || (base.empty() && !std::isfinite(*l0_out))) {
         const int m = (int)base.size();
-        if (m)
-            FREDEC_CUDA_TRY(cudaMemcpyAsync(base_d, base.data(), m * 8, cudaMemcpyHostToDevice, st));
+        if (m) {
+            std::copy(base.begin(), base.end(), base_h);
+            FREDEC_CUDA_TRY(cudaMemcpyAsync(base_d, base_h, m * 8, cudaMemcpyHostToDevice, st));
+        }
         if (int rc = fredec_periodogram_dev(t_d, y_d, s_d, N, base_d, m, f0, df, nf, &po, z_d, info_d, top_d,
                                             nullptr, st))
             return rc;
         gather_peaks<<<1, SCAN_PEAKS, 0, st>>>(z_d, top_d, SCAN_PEAKS, zk_d);
         FREDEC_CUDA_TRY(cudaGetLastError());
-        int64_t top[SCAN_PEAKS];
-        double zk[SCAN_PEAKS], info[3];
-        FREDEC_CUDA_TRY(cudaMemcpyAsync(top, top_d, sizeof(top), cudaMemcpyDeviceToHost, st));
-        FREDEC_CUDA_TRY(cudaMemcpyAsync(zk, zk_d, sizeof(zk), cudaMemcpyDeviceToHost, st));
-        FREDEC_CUDA_TRY(cudaMemcpyAsync(info, info_d, sizeof(info), cudaMemcpyDeviceToHost, st));
+        FREDEC_CUDA_TRY(cudaMemcpyAsync(back_h, b + o_k, back, cudaMemcpyDeviceToHost, st));
         FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+        const int64_t *top = reinterpret_cast<const int64_t *>(back_h);
+        const double *zk = reinterpret_cast<const double *>(back_h + (o_zk - o_k));
+        const double *info = reinterpret_cast<const double *>(back_h + (o_i - o_k));
         if (m == 0) *l0_out = info[0];
         if (o.max_base == 0 || top[0] < 0) break;
         const double lb = info[0], NH = (double)(N - 3 * (int64_t)(m + 1) - 1);

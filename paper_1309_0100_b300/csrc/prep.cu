@@ -286,8 +286,9 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k4(PrepArgs a) {
 // (measured: z error 1.05e-5 at N = 70000 in time order).  Points spread over
 // the whole span make them random walks.  The FP64 records stay in time order
 // (the adjoint reads them per point).
-__device__ inline int64_t record_slot(int64_t i, int64_t N) {
-    if (N <= 2) return i;
+// record_multiplier: K, computed once per thread; record_slot: i K mod N.
+__device__ inline int64_t record_multiplier(int64_t N) {
+    if (N <= 2) return 1;
     int64_t K = (int64_t)(0.6180339887498949 * (double)N);
     for (;; ++K) {   // ends at K = N - 1 at the latest (gcd(N - 1, N) = 1); in practice within a few steps
         int64_t x = K, y = N;
@@ -296,16 +297,19 @@ __device__ inline int64_t record_slot(int64_t i, int64_t N) {
             x = y;
             y = r;
         }
-        if (x == 1) break;
+        if (x == 1) return K;
     }
+}
+__device__ __forceinline__ int64_t record_slot(int64_t i, int64_t K, int64_t N) {
     return (int64_t)(((unsigned long long)i * (unsigned long long)K) % (unsigned long long)N);
 }
 
-// Writes the records of point i of series d (residual r, w, u = w psi).
-__device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, double tp, double w,
-                                              double r, const double *u) {
+// Writes the records of point i of series d (residual r, w, u = w psi);
+// K = record_multiplier(d.N).
+__device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, int64_t K, double tp,
+                                              double w, double r, const double *u) {
     const int p = d.p;
-    const int64_t slot = a.precision == FREDEC_MIXED ? record_slot(i, d.N) : i;
+    const int64_t slot = a.precision == FREDEC_MIXED ? record_slot(i, K, d.N) : i;
     const uint64_t A = frac_turns_u64(d.f0, tp);
     const uint64_t B = frac_turns_u64(d.df, tp);
     double sr, cr;
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
             u[q] = w * ps;
         }
         for (int q = p; q < d.p; ++q) u[q] = 0.0;
-        write_records(a, d, i, tp, w, r, u);
+        write_records(a, d, i, record_multiplier(d.N), tp, w, r, u);
         v[0] = w * r * r;
         v[1] = (double)(float)w;
     }
@@ -509,6 +513,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     __syncthreads();
     // 5: final residual, records, chi2, sum of FP32 weights
     v[0] = v[1] = 0.0;
+    const int64_t K = record_multiplier(N);
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
         const double tp = a.t[d.obs_off + i] - tc;
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
             u[q] = w * ps;
         }
         for (int q = p; q < d.p; ++q) u[q] = 0.0;
-        write_records(a, d, i, tp, w, r, u);
+        write_records(a, d, i, K, tp, w, r, u);
         v[0] += w * r * r;
         v[1] += (double)(float)w;
     }
@@ -699,6 +704,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
         __syncthreads();
         // 5: final residual, records, chi2, sum of FP32 weights
         v[0] = v[1] = 0.0;
+        const int64_t K = record_multiplier(N);
         for (int64_t i = i0; i < N; i += di) {
             const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
             const double tp = a.t[d.obs_off + i] - tc;
@@ -709,7 +715,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
                 u[q] = w * ps;
             }
             for (int q = p; q < d.p; ++q) u[q] = 0.0;
-            write_records(a, d, i, tp, w, r, u);
+            write_records(a, d, i, K, tp, w, r, u);
             v[0] += w * r * r;
             v[1] += (double)(float)w;
         }
