@@ -8,11 +8,11 @@
 // most 2048: two maxima are never adjacent) and sorts them with a bitonic
 // network; its first k, in rank order, are the chunk's candidates.  Stage 2:
 // one CTA per series.  Few candidates (<= 512, or <= 2048 with k >= 16) are
-// sorted the same way; otherwise the chunks' sorted lists are merged by a
-// k-round tournament (thread t holds the head of chunk t; each round an argmax
-// takes the best head and that chunk advances), by one warp with shuffles only
-// for up to 32 chunks, by the block for up to 1024.  Series of more chunks use
-// k rounds of warp selection over fixed slices, then a merge of the slices.
+// sorted the same way; otherwise (up to 1024 chunks) the chunks' sorted lists
+// are merged by a k-round tournament (thread t holds the head of chunk t; each
+// round a block argmax takes the best head and that chunk advances).  Series
+// of more chunks use k rounds of warp selection over fixed slices, then a
+// merge of the slices.
 // 1024 threads per CTA: one compare-exchange per thread per sorting step.
 // The order is strict and total, so the result does not depend on scheduling
 // or on the order in which the maxima were gathered.  Every comparison is on
@@ -201,30 +201,6 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
         }
         block_sort(kz, kj, m);
         for (int r = tid; r < a.k; r += TK_THREADS) a.out[(int64_t)s * a.k + r] = kj[r];
-        return;
-    }
-    if (nch <= 32) {   // all candidates (<= 32 k <= TK_SORT) into shared memory, then one warp
-        for (int64_t q = tid; q < ncand; q += TK_THREADS) {
-            kz[q] = cz[q];
-            kj[q] = cj[q];
-        }
-        __syncthreads();
-        if (warp != 0) return;
-        const bool own = lane < nch;
-        uint64_t hz = own ? kz[lane * a.k] : 0;
-        int64_t hj = own ? kj[lane * a.k] : -1;
-        int ptr = 0;
-        for (int r = 0; r < a.k; ++r) {
-            uint64_t bz = hz;
-            int64_t bj = hj;
-            warp_best(bz, bj);
-            if (lane == 0) a.out[(int64_t)s * a.k + r] = bj;
-            if (hj >= 0 && hj == bj) {   // the winning chunk advances
-                ++ptr;
-                hz = ptr < a.k ? kz[lane * a.k + ptr] : 0;
-                hj = ptr < a.k ? kj[lane * a.k + ptr] : -1;
-            }
-        }
         return;
     }
     if (nch <= TK_THREADS) {
