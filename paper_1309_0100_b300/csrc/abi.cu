@@ -313,6 +313,23 @@ struct HostStream {
     }
 };
 
+void *pinned_scratch(int slot, size_t bytes) {
+    static thread_local void *p[PIN_SLOTS] = {};
+    static thread_local size_t have[PIN_SLOTS] = {};
+    if (slot < 0 || slot >= PIN_SLOTS) return nullptr;
+    if (have[slot] < bytes) {
+        if (p[slot]) cudaFreeHost(p[slot]);
+        p[slot] = nullptr;
+        have[slot] = 0;
+        if (cudaMallocHost(&p[slot], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        have[slot] = bytes;
+    }
+    return p[slot];
+}
+
 // Read back status words after a synchronous host call.
 static int finish_host(cudaStream_t st, const SeriesState *state, const int32_t *err) {
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -434,14 +451,37 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             cudaStreamSynchronize(st);
             return rc;
         }
-        if ((rc = finish_host(st, state, err))) return rc;
+        // the status words and the small outputs in one page-locked block,
+        // copied behind the device work: one synchronisation
+        char *pin = static_cast<char *>(pinned_scratch(PIN_HOST_CALL, 32 + (size_t)FREDEC_MAX_TOPK * 8));
+        if (!pin) {
+            if ((rc = finish_host(st, state, err))) return rc;
+        } else {
+            int32_t *words = reinterpret_cast<int32_t *>(pin);
+            words[0] = FREDEC_OK;
+            words[1] = FREDEC_OK;
+            if (state) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[0], &state->status, 4, cudaMemcpyDeviceToHost, st));
+            if (err) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[1], err, 4, cudaMemcpyDeviceToHost, st));
+            if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 8, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
+            if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 32, dtop, k * 8, cudaMemcpyDeviceToHost, st));
+            FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+            if (words[0] == FREDEC_ESINGULAR)
+                return fail(FREDEC_ESINGULAR, "the base model's normal matrix is singular (duplicate base frequencies?)");
+            if (words[1] == FREDEC_ETIMEOUT) return fail(FREDEC_ETIMEOUT, "a bounded device wait gave up");
+        }
+        const bool copies = (nf && !(uniform && z_mirror)) || (coef_out && nf);
         if (nf && !(uniform && z_mirror)) FREDEC_CUDA_TRY(cudaMemcpyAsync(z_out, dz, nf * 8, cudaMemcpyDeviceToHost, st));
-        if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
-        if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost, st));
         if (coef_out && nf) FREDEC_CUDA_TRY(cudaMemcpyAsync(coef_out, dcoef, 16 * nf, cudaMemcpyDeviceToHost, st));
-        FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (pin) {
+            if (info_out) std::memcpy(info_out, pin + 8, 3 * 8);
+            if (k && topk_idx_out) std::memcpy(topk_idx_out, pin + 32, (size_t)k * 8);
+        } else {
+            if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(info_out, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
+            if (k && topk_idx_out)
+                FREDEC_CUDA_TRY(cudaMemcpyAsync(topk_idx_out, dtop, k * 8, cudaMemcpyDeviceToHost, st));
+        }
+        if (copies || !pin) FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     return FREDEC_OK;
 }
 

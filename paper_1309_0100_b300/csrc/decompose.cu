@@ -44,22 +44,7 @@ struct Cand {
     double f, z;
 };
 
-// Page-locked host memory for the small per-round transfers (asynchronous
-// copies, one synchronisation per round), allocated once per host thread
-// (page-locking is an operating-system call, far slower than a round) and
-// kept for the life of the process.
-static void *pinned_scratch(size_t bytes) {
-    static thread_local void *p = nullptr;
-    static thread_local size_t have = 0;
-    if (have < bytes) {
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        have = 0;
-        if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
-        have = bytes;
-    }
-    return p;
-}
+
 
 int check_scan_opts(const fredec_scan_opts *in, int64_t N, fredec_scan_opts *o) {
     fredec_scan_opts_init(o);
@@ -102,7 +87,7 @@ int scan_run(const double *t_d, const double *y_d, const double *s_d, int64_t N,
     const size_t back = o_i + 4 * 8 - o_k;
     DevBuf buf;
     if (int rc = buf.alloc(off, st)) return rc;
-    void *pin = pinned_scratch(FREDEC_MAX_NBASE * 8 + back);   // [base frequencies | the copied-back block]
+    void *pin = pinned_scratch(PIN_SCAN, FREDEC_MAX_NBASE * 8 + back);   // [base frequencies | the copied-back block]
     if (!pin) return fail(FREDEC_ECUDA, "cudaMallocHost of the scan's transfer buffer failed");
     double *base_h = static_cast<double *>(pin);
     char *back_h = static_cast<char *>(pin) + FREDEC_MAX_NBASE * 8;

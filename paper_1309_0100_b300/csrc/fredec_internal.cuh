@@ -122,6 +122,12 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf);
 bool shape_supported(int precision, int p, int fpt);
 // sin/cos seed of the mixed periodogram kernels (1 = MUFU, 0 = table)
 int seed_mode();
+// Page-locked host scratch for small asynchronous transfers, per host thread
+// and slot (one slot per user, so that one user's pointer stays valid while
+// another runs), allocated once (page-locking is an operating-system call)
+// and kept for the life of the process; nullptr if cudaMallocHost fails.
+enum PinnedSlot { PIN_HOST_CALL = 0, PIN_SCAN = 1, PIN_SLOTS = 2 };
+void *pinned_scratch(int slot, size_t bytes);
 // Single-series launch: z (and optional coef) for all nf grid points; the
 // mixed path appends ill-conditioned bins (global z indices) to flag_list.
 // z_mirror (optional): a second destination of every z value, e.g. the
