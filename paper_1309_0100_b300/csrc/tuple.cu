@@ -512,9 +512,11 @@ __device__ void chol_cta(double *A, double *d0, double *inv, int C, int nlin, in
                 if (j < nlin) s.ratio = fmin(s.ratio, d0[j] > 0.0 ? d / d0[j] : -1.0);
                 if (!(d > 1e-13 * d0[j]) || !(d0[j] > 0.0)) s.fail_at = j;
             }
-            const double l = d > 0.0 ? sqrt(d) : 0.0;
-            A[tri(j, j)] = l;
-            inv[j] = l > 0.0 ? 1.0 / l : 0.0;
+            // one FP64 reciprocal square root per pivot (no division): 1/L_jj,
+            // and L_jj = d / sqrt(d)
+            const double il = d > 0.0 ? rsqrt(d) : 0.0;
+            A[tri(j, j)] = d * il;
+            inv[j] = il;
         }
         __syncthreads();
         if (s.fail_at < C) break;
