@@ -327,16 +327,17 @@ __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j
 
 // In-place Cholesky of a packed symmetric matrix.  Returns false when a pivot is
 // not positive or falls below rel * (its original diagonal).
-// rinv[j] receives 1 / L_jj: one FP64 division per column, the rest are
-// multiplications (an FP64 division is a long dependent sequence on this GPU).
+// rinv[j] receives 1 / L_jj: one FP64 reciprocal square root per column
+// (L_jj = d / sqrt(d)), the rest are multiplications (an FP64 square root or
+// division is a long dependent sequence on this GPU).
 __device__ inline bool chol_packed(double *A, int n, double rel, double *rinv) {
     for (int j = 0; j < n; ++j) {
         const double d0 = A[tri(j, j)];
         double d = d0;
         for (int k = 0; k < j; ++k) d -= A[tri(j, k)] * A[tri(j, k)];
         if (!(d > rel * d0) || !(d0 > 0.0)) return false;
-        const double l = sqrt(d), il = 1.0 / l;
-        A[tri(j, j)] = l;
+        const double il = rsqrt(d);
+        A[tri(j, j)] = d * il;
         rinv[j] = il;
         for (int i = j + 1; i < n; ++i) {
             double s = A[tri(i, j)];
