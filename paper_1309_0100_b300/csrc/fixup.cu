@@ -159,7 +159,10 @@ int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nser
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
                       cudaStream_t st, double *z_mirror) {
     FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef, z_mirror};
-    const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 4LL * sm_count());
+    // one wave for up to 8 bins per SM (8 CTAs of 256 threads are resident per
+    // SM): the flagged count is known only on the device, and CTAs beyond it
+    // exit at once
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 8LL * sm_count());
     switch (p) {
 #define C(P) case P: launch_fx<P>(prm, grid, st); break;
         C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
