@@ -177,6 +177,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
+    pp.base_p = o.trend == 0 ? pb : 0;
     pp.desc = w.desc;
     pp.state = w.state;
     pp.chunk_series = w.chunk_series;

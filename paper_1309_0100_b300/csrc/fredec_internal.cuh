@@ -102,6 +102,7 @@ struct PrepPlan {
     int64_t max_n = 0;         // largest series (chooses the one-CTA-per-series prep)
     int64_t nchunks = 0;       // total prep chunks
     int pmax = 1;
+    int base_p = 0;            // base columns of every series when none has polynomial terms, else 0
     SeriesDesc *desc = nullptr;      // device [S]
     SeriesState *state = nullptr;    // device [S]
     int32_t *chunk_series = nullptr; // device [nchunks]

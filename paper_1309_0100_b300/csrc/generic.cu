@@ -109,6 +109,7 @@ int generic_grid_periodogram(const double *t, const double *y, const double *sig
     pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
+    pp.base_p = o.trend == 0 ? pb : 0;
     pp.desc = dd;
     pp.state = ss;
     pp.chunk_series = (int32_t *)(b + o_cs);

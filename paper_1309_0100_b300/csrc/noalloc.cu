@@ -148,6 +148,7 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
+    pp.base_p = o.trend == 0 ? pb : 0;
     pp.desc = desc;
     pp.state = state;
     pp.chunk_series = cs;

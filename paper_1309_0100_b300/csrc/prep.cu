@@ -15,6 +15,8 @@
 // per thread).  Each chunk writes partial sums; the last chunk of a series to
 // finish (atomic counter) reduces them in chunk order, so results do not
 // depend on scheduling.
+#include <atomic>
+
 #include <cooperative_groups.h>
 
 #include "device_util.cuh"
@@ -117,13 +119,17 @@ __device__ double *fin_buf() { return prep_sm; }
 
 // Base columns at t' = t - t_c: [1, tau, ..., tau^npoly, cos, sin of every
 // base frequency], tau = t' / tscale (the polynomial extension of Eq. H0).
+// PT > 0: a base of PT = 1 + 2 nb columns without polynomial terms, known at
+// compile time; PT = 0: the widths of the series descriptor.
+template <int PT = 0>
 __device__ __forceinline__ void base_basis(const PrepArgs &a, const SeriesDesc &d, double tscale, double tp,
                                            double *phi) {
+    const int npoly = PT > 0 ? 0 : d.npoly, nb = PT > 0 ? (PT - 1) / 2 : d.nb;
     phi[0] = 1.0;
     const double tau = tp / tscale;
-    for (int q = 1; q <= d.npoly; ++q) phi[q] = phi[q - 1] * tau;
-    const int o = 1 + d.npoly;
-    for (int k = 0; k < d.nb; ++k) {
+    for (int q = 1; q <= npoly; ++q) phi[q] = phi[q - 1] * tau;
+    const int o = 1 + npoly;
+    for (int k = 0; k < nb; ++k) {
         const double g = a.base[d.base_off + k];
         const uint64_t ph = frac_turns_u64(g, tp);
         double s, c;
@@ -305,10 +311,11 @@ __device__ __forceinline__ int64_t record_slot(int64_t i, int64_t K, int64_t N) 
 }
 
 // Writes the records of point i of series d (residual r, w, u = w psi);
-// K = record_multiplier(d.N).
+// K = record_multiplier(d.N); PT as for base_basis (d.p = PT when PT > 0).
+template <int PT = 0>
 __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, int64_t K, double tp,
                                               double w, double r, const double *u) {
-    const int p = d.p;
+    const int p = PT > 0 ? PT : d.p;
     const int64_t slot = a.precision == FREDEC_MIXED ? record_slot(i, K, d.N) : i;
     const uint64_t A = frac_turns_u64(d.f0, tp);
     const uint64_t B = frac_turns_u64(d.df, tp);
@@ -557,39 +564,43 @@ struct ClusterSmem {
     double x[2][PREP_NV];            // published CTA sums (alternating)
     double out[PREP_NV];             // cluster totals
     double L1[NTRI], L2[NTRI], R1[PMAX], R2[PMAX], av[PMAX], a2[PMAX];
+    int64_t K;                       // record multiplier (one-point-per-thread kernel)
     int ok;
 };
 
 // Cluster totals of nv per-thread values into sm.out (all threads of all CTAs).
 // Buffer x[ph] is written before the barrier and read remotely after it; the
 // next use of the same buffer comes after the next reduction's barrier, by
-// which time every CTA has finished reading it.
-__device__ void cluster_reduce(const double *vals, int nv, ClusterSmem &sm, int &ph) {
+// which time every CTA has finished reading it.  NV > 0: nv = NV, known at
+// compile time (the loops unroll and vals stays in registers).
+template <int NV>
+__device__ __forceinline__ void cluster_reduce(const double *vals, int nv_rt, ClusterSmem &sm, int &ph) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nv = NV > 0 ? NV : nv_rt;
+#pragma unroll
     for (int q0 = 0; q0 < nv; q0 += 32) {
         const int m = min(32, nv - q0);
+#pragma unroll
         for (int q = 0; q < m; ++q) sm.tr[wid][lane * 33 + q] = vals[q0 + q];
         __syncwarp();
-        if (lane < m) {   // the 32 lanes' values in four interleaved chains, combined in a fixed order
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        if (lane < m) {   // the 32 lanes' values in eight interleaved chains, combined as a fixed tree
+            double c[8];
 #pragma unroll
-            for (int l = 0; l < 32; l += 4) {
-                v0 += sm.tr[wid][l * 33 + lane];
-                v1 += sm.tr[wid][(l + 1) * 33 + lane];
-                v2 += sm.tr[wid][(l + 2) * 33 + lane];
-                v3 += sm.tr[wid][(l + 3) * 33 + lane];
-            }
-            sm.ws[wid][q0 + lane] = (v0 + v1) + (v2 + v3);
+            for (int k = 0; k < 8; ++k) c[k] = sm.tr[wid][k * 33 + lane];
+#pragma unroll
+            for (int l = 8; l < 32; l += 8)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c[k] += sm.tr[wid][(l + k) * 33 + lane];
+            sm.ws[wid][q0 + lane] = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
         }
         __syncwarp();
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nv; q += CL_THREADS) {
-        double v = 0.0;
-        for (int w = 0; w < CL_WARPS; ++w) v += sm.ws[w][q];
-        sm.x[ph][q] = v;
+        static_assert(CL_WARPS == 4, "CTA sum tree");
+        sm.x[ph][q] = (sm.ws[0][q] + sm.ws[1][q]) + (sm.ws[2][q] + sm.ws[3][q]);
     }
     cl.sync();
     const int nr = (int)cl.num_blocks();
@@ -597,15 +608,20 @@ __device__ void cluster_reduce(const double *vals, int nv, ClusterSmem &sm, int 
         double x[CL_MAX];   // all remote loads in flight, then added in rank order
 #pragma unroll
         for (int r = 0; r < CL_MAX; ++r) x[r] = r < nr ? cl.map_shared_rank(&sm.x[ph][0], r)[q] : 0.0;
-        double v = 0.0;
 #pragma unroll
-        for (int r = 0; r < CL_MAX; ++r) v += x[r];
-        sm.out[q] = v;
+        for (int h = CL_MAX / 2; h >= 1; h /= 2)   // pairwise tree in rank order (absent ranks add 0)
+#pragma unroll
+            for (int r = 0; r < h; ++r) x[r] = x[2 * r] + x[2 * r + 1];
+        sm.out[q] = x[0];
     }
     __syncthreads();
     ph ^= 1;
 }
 
+// PT > 0: every series has the PT = 1 + 2 nb columns of a sinusoidal base
+// (no polynomial terms), so that the per-point sums and columns are
+// compile-time sized and stay in registers; PT = 0: any base.
+template <int PT>
 __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -615,10 +631,12 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
     const int s = blockIdx.x / nr;
     const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.pb, nt = p * (p + 1) / 2;
+    const int p = PT > 0 ? PT : d.pb, nt = p * (p + 1) / 2, pw = PT > 0 ? PT : d.p;
+    constexpr int NT = PT * (PT + 1) / 2;                 // compile-time counts (0 when PT = 0)
+    constexpr int PA = PT > 0 ? PT : PMAX;                // extent of the per-point column arrays
     const int64_t N = d.N, i0 = (int64_t)rank * CL_THREADS + threadIdx.x, di = (int64_t)nr * CL_THREADS;
     const bool lead = rank == 0 && threadIdx.x == 0;
-    double v[PREP_NV];
+    double v[PT > 0 ? NT + PT + 4 : PREP_NV];
     int ph = 0;
     // 1: W, <t>  ->  t_c and the polynomial time scale
     v[0] = v[1] = v[2] = v[3] = 0.0;
@@ -631,19 +649,19 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
         v[2] += w * u;
         v[3] += w * u * u;
     }
-    cluster_reduce(v, 4, sm, ph);
+    cluster_reduce<4>(v, 4, sm, ph);
     const double W = sm.out[0], tc = rint(sm.out[1] / W), tscale = time_scale(W, sm.out[2], sm.out[3]);
     // 2: raw base columns, Gram Q1 -> L1
     for (int q = 0; q < nt; ++q) v[q] = 0.0;
     for (int64_t i = i0; i < N; i += di) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
-        double phi[PMAX];
-        base_basis(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
+        double phi[PA];
+        base_basis<PT>(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = phi[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
     }
-    cluster_reduce(v, nt, sm, ph);
+    cluster_reduce<NT>(v, nt, sm, ph);
     if (threadIdx.x < 32) {   // warp 0 factors
         for (int q = threadIdx.x; q < nt; q += 32) sm.L1[q] = sm.out[q];
         __syncwarp();
@@ -662,7 +680,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
         for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
         for (int64_t i = i0; i < N; i += di) {
             const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg), yi = a.y[d.obs_off + i];
-            double x[PMAX];
+            double x[PA];
             for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
             forward_packed(sm.L1, sm.R1, x, p);
             for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
@@ -670,7 +688,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
                 for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
             for (int q = 0; q < p; ++q) v[nt + q] += w * x[q] * yi;
         }
-        cluster_reduce(v, nt + p, sm, ph);
+        cluster_reduce<NT + PT>(v, nt + p, sm, ph);
         if (threadIdx.x < 32) {   // warp 0 factors
             for (int q = threadIdx.x; q < nt; q += 32) sm.L2[q] = sm.out[q];
             for (int q = threadIdx.x; q < p; q += 32) sm.av[q] = sm.out[nt + q];
@@ -689,17 +707,17 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
         for (int q = 0; q < p; ++q) v[q] = 0.0;
         for (int64_t i = i0; i < N; i += di) {
             const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
-            double x[PMAX], r = a.y[d.obs_off + i];
+            double x[PA], r = a.y[d.obs_off + i];
             for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
             forward_packed(sm.L2, sm.R2, x, p);
             for (int q = 0; q < p; ++q) {
                 a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
                 r -= sm.av[q] * x[q];
             }
-            for (int q = p; q < d.p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
+            for (int q = p; q < pw; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
             for (int q = 0; q < p; ++q) v[q] += w * x[q] * r;
         }
-        cluster_reduce(v, p, sm, ph);
+        cluster_reduce<PT>(v, p, sm, ph);
         if (threadIdx.x < p) sm.a2[threadIdx.x] = sm.out[threadIdx.x];
         __syncthreads();
         // 5: final residual, records, chi2, sum of FP32 weights
@@ -708,24 +726,167 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
         for (int64_t i = i0; i < N; i += di) {
             const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
             const double tp = a.t[d.obs_off + i] - tc;
-            double r = a.y[d.obs_off + i], u[PMAX];
+            double r = a.y[d.obs_off + i], u[PA];
             for (int q = 0; q < p; ++q) {
                 const double ps = a.psi[d.psi_off + (int64_t)q * N + i];
                 r -= (sm.av[q] + sm.a2[q]) * ps;
                 u[q] = w * ps;
             }
-            for (int q = p; q < d.p; ++q) u[q] = 0.0;
-            write_records(a, d, i, K, tp, w, r, u);
+            for (int q = p; q < pw; ++q) u[q] = 0.0;
+            write_records<PT>(a, d, i, K, tp, w, r, u);
             v[0] += w * r * r;
             v[1] += (double)(float)w;
         }
-        cluster_reduce(v, 2, sm, ph);
+        cluster_reduce<2>(v, 2, sm, ph);
         if (lead) {
             for (int q = 0; q < nt; ++q) {
                 st.L1[q] = sm.L1[q];
                 st.L2[q] = sm.L2[q];
             }
             for (int q = 0; q < p; ++q) {
+                st.R1[q] = sm.R1[q];
+                st.R2[q] = sm.R2[q];
+                st.a[q] = sm.av[q];
+                st.a2[q] = sm.a2[q];
+            }
+            st.chi2 = sm.out[0];
+            st.Wf = sm.out[1];
+        }
+    }
+    cl.sync();   // no CTA leaves while another may still read its published sums
+}
+
+// The same for series of at most one point per thread (N <= CTAs x
+// CL_THREADS) with a sinusoidal base of PT columns, kept in registers: each
+// thread loads its point once, its weight is computed once, and its base
+// columns stay in registers from phase to phase (only the final orthonormal
+// columns are stored, for the adjoint).  The time origin's sums are added
+// with the first Gram matrix, so the raw base columns take the series' first
+// time as their origin (an origin shift rotates each cos/sin pair, so the
+// columns' span, its orthonormal basis up to that rotation, and every result
+// are unchanged); the records use t_c as before.  Warp 1 computes the record
+// multiplier while warp 0 factors the first Gram matrix.
+template <int PT>
+__global__ void __launch_bounds__(CL_THREADS) prep_cluster_one(PrepArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    ClusterSmem &sm = *reinterpret_cast<ClusterSmem *>(cl_raw);
+    const int nr = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int s = blockIdx.x / nr;
+    const SeriesDesc d = a.desc[s];
+    SeriesState &st = a.state[s];
+    constexpr int NT = PT * (PT + 1) / 2;
+    constexpr int NV = NT + PT > NT + 4 ? NT + PT : NT + 4;
+    const int64_t N = d.N, i = (int64_t)rank * CL_THREADS + threadIdx.x;
+    const bool has = i < N, lead = rank == 0 && threadIdx.x == 0;
+    int ph = 0;
+    const double t_first = a.t[d.obs_off];
+    double w = 0.0, ti = t_first, yi = 0.0;
+    if (has) {
+        const double sg = a.sigma[d.obs_off + i];
+        w = 1.0 / (sg * sg);
+        ti = a.t[d.obs_off + i];
+        yi = a.y[d.obs_off + i];
+    }
+    double x[PT], v[NV];
+    // 1-2: W, <t>, the time scale's sums and the Gram Q1 of the raw columns -> t_c, L1
+    const double u = ti - t_first;
+    base_basis<PT>(a, d, 1.0, u, x);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    if (has) {
+        v[0] = w;
+        v[1] = w * ti;
+        v[2] = w * u;
+        v[3] = w * u * u;
+#pragma unroll
+        for (int r = 0; r < PT; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c) v[4 + tri(r, c)] += w * x[r] * x[c];
+    }
+    cluster_reduce<NT + 4>(v, NT + 4, sm, ph);
+    const double W = sm.out[0], tc = rint(sm.out[1] / W), tscale = time_scale(W, sm.out[2], sm.out[3]);
+    if (threadIdx.x < 32) {   // warp 0 factors
+        for (int q = threadIdx.x; q < NT; q += 32) sm.L1[q] = sm.out[4 + q];
+        __syncwarp();
+        const bool ok = chol_packed_warp(sm.L1, PT, 1e-12, sm.R1);
+        if (threadIdx.x == 0) sm.ok = ok;
+    } else if (threadIdx.x == 32) {
+        sm.K = record_multiplier(N);
+    }
+    __syncthreads();
+    if (lead) {
+        st.W = W;
+        st.tc = tc;
+        st.tscale = tscale;
+        st.status = sm.ok ? FREDEC_OK : FREDEC_ESINGULAR;
+    }
+    if (sm.ok) {
+        // 3: psi1 = L1^{-1} phi, Gram Q2 and <psi1 y>  ->  L2, a
+        forward_packed(sm.L1, sm.R1, x, PT);
+#pragma unroll
+        for (int q = 0; q < NT + PT; ++q) v[q] = 0.0;
+        if (has) {
+#pragma unroll
+            for (int r = 0; r < PT; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
+#pragma unroll
+            for (int q = 0; q < PT; ++q) v[NT + q] += w * x[q] * yi;
+        }
+        cluster_reduce<NT + PT>(v, NT + PT, sm, ph);
+        if (threadIdx.x < 32) {   // warp 0 factors
+            for (int q = threadIdx.x; q < NT; q += 32) sm.L2[q] = sm.out[q];
+            for (int q = threadIdx.x; q < PT; q += 32) sm.av[q] = sm.out[NT + q];
+            __syncwarp();
+            const bool ok = chol_packed_warp(sm.L2, PT, 1e-12, sm.R2);
+            if (threadIdx.x == 0) {
+                sm.ok = ok;
+                if (ok) forward_packed(sm.L2, sm.R2, sm.av, PT);
+            }
+        }
+        __syncthreads();
+        if (lead && !sm.ok) st.status = FREDEC_ESINGULAR;
+    }
+    if (sm.ok) {
+        // 4: psi = L2^{-1} psi1, r = y - a^T psi, <psi r>  ->  a2
+        forward_packed(sm.L2, sm.R2, x, PT);
+        double r = yi;
+#pragma unroll
+        for (int q = 0; q < PT; ++q) r -= sm.av[q] * x[q];
+#pragma unroll
+        for (int q = 0; q < PT; ++q) v[q] = 0.0;
+        if (has) {
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
+                v[q] += w * x[q] * r;
+            }
+        }
+        cluster_reduce<PT>(v, PT, sm, ph);
+        if (threadIdx.x < PT) sm.a2[threadIdx.x] = sm.out[threadIdx.x];
+        __syncthreads();
+        // 5: final residual, records, chi2, sum of FP32 weights
+        v[0] = v[1] = 0.0;
+        if (has) {
+            double r2 = yi, uu[PT];
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                r2 -= (sm.av[q] + sm.a2[q]) * x[q];
+                uu[q] = w * x[q];
+            }
+            write_records<PT>(a, d, i, sm.K, ti - tc, w, r2, uu);
+            v[0] += w * r2 * r2;
+            v[1] += (double)(float)w;
+        }
+        cluster_reduce<2>(v, 2, sm, ph);
+        if (lead) {
+            for (int q = 0; q < NT; ++q) {
+                st.L1[q] = sm.L1[q];
+                st.L2[q] = sm.L2[q];
+            }
+            for (int q = 0; q < PT; ++q) {
                 st.R1[q] = sm.R1[q];
                 st.R2[q] = sm.R2[q];
                 st.a[q] = sm.av[q];
@@ -745,18 +906,45 @@ int launch_prep(const PrepPlan &pp, const double *t, const double *y, const doub
     return run_prep_records(pp, t, y, sigma, base, precision, nullptr, st);
 }
 
+using PrepKernel = void (*)(PrepArgs);
+
+// The cluster prep for a base width: specialised for the sinusoidal bases of
+// up to five base frequencies, generic otherwise.
+// Slots 1-6: prep_cluster for base widths 1, 3, ..., 11; 7-12: prep_cluster_one
+// for the same widths; 0: the generic prep_cluster.
+constexpr int CLUSTER_SLOTS = 13;
+static int cluster_slot(int base_p) { return base_p >= 1 && base_p <= 11 && (base_p & 1) ? (base_p + 1) / 2 : 0; }
+static PrepKernel cluster_kernel(int slot) {
+    switch (slot) {
+    case 1: return prep_cluster<1>;
+    case 2: return prep_cluster<3>;
+    case 3: return prep_cluster<5>;
+    case 4: return prep_cluster<7>;
+    case 5: return prep_cluster<9>;
+    case 6: return prep_cluster<11>;
+    case 7: return prep_cluster_one<1>;
+    case 8: return prep_cluster_one<3>;
+    case 9: return prep_cluster_one<5>;
+    case 10: return prep_cluster_one<7>;
+    case 11: return prep_cluster_one<9>;
+    case 12: return prep_cluster_one<11>;
+    default: return prep_cluster<0>;
+    }
+}
+
 // CTAs per cluster for series of up to max_n points: enough for about one
 // point per thread, at most 16 (8 where the device refuses 16); 0 when cluster
-// launches cannot be used.  The attributes are set once.
-static int cluster_size_for(int64_t max_n) {
-    static int cap = -1;
+// launches cannot be used.  The attributes are set once per kernel.
+static int cluster_size_for(int64_t max_n, int slot) {
+    static std::atomic<int> caps[CLUSTER_SLOTS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int cap = caps[slot].load();
     if (cap < 0) {
+        const PrepKernel k = cluster_kernel(slot);
         cap = 0;
-        if (cudaFuncSetAttribute(prep_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(ClusterSmem)) == cudaSuccess) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ClusterSmem)) ==
+            cudaSuccess) {
             cap = 8;
-            if (cudaFuncSetAttribute(prep_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(CL_MAX);
                 cfg.blockDim = dim3(CL_THREADS);
@@ -769,11 +957,12 @@ static int cluster_size_for(int64_t max_n) {
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
                 int nclusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&nclusters, prep_cluster, &cfg) == cudaSuccess && nclusters > 0)
+                if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0)
                     cap = CL_MAX;
             }
         }
         cudaGetLastError();   // clear a refused attribute
+        caps[slot].store(cap);
     }
     if (cap == 0) return 0;
     const int64_t want = (max_n + CL_THREADS - 1) / CL_THREADS;
@@ -811,7 +1000,12 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
     }
     // A few series of moderate length: one cluster of up to 16 CTAs per series.
     if (pp.max_n > 0 && pp.max_n <= CLUSTER_PREP_MAX_N) {
-        const int cs = cluster_size_for(pp.max_n);
+        int slot = cluster_slot(pp.base_p);
+        int cs = cluster_size_for(pp.max_n, slot);
+        if (slot > 0 && cs > 0 && pp.max_n <= (int64_t)cs * CL_THREADS) {   // at most one point per thread
+            const int one = cluster_size_for(pp.max_n, slot + 6);
+            if (one == cs) slot += 6;
+        }
         if (cs > 0) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)(pp.S * cs));
@@ -825,7 +1019,7 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            FREDEC_CUDA_TRY(cudaLaunchKernelEx(&cfg, prep_cluster, a));
+            FREDEC_CUDA_TRY(cudaLaunchKernelEx(&cfg, cluster_kernel(slot), a));
             return FREDEC_OK;
         }
     }

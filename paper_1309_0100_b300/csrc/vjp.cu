@@ -241,6 +241,7 @@ int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, i
     pp.max_n = N;
     pp.nchunks = nchunks;
     pp.pmax = p;
+    pp.base_p = p;
     pp.desc = desc;
     pp.state = state;
     pp.chunk_series = (int32_t *)(b + o_cs);
