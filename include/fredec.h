@@ -150,6 +150,23 @@ int fredec_periodogram_dev(const double *t, const double *y, const double *sigma
                            double *coef_out, void *stream);
 
 /*
+ * Top-k local maxima of a device array z[0..nf): the peak step of the
+ * periodogram calls on its own (the candidate frequencies of Sect. 4, Phase 1,
+ * are the highest peaks of the residual periodogram), e.g. for a statistic
+ * computed elsewhere.  A local maximum is z_j > z_{j-1} and z_j >= z_{j+1}; an
+ * end point counts when it exceeds its one neighbour, a single point counts;
+ * a NaN is never a maximum and disqualifies its neighbours.  idx_out[0..k)
+ * receives the indices by decreasing z, ties to the lower index, -1 where
+ * fewer maxima exist (all -1 for nf = 0).  z and idx_out are device pointers;
+ * stream-ordered on stream (cudaStream_t as void*; NULL: the legacy default
+ * stream); nothing is retained after return.  Errors (nothing written):
+ * FREDEC_EINVAL for k outside 1..FREDEC_MAX_TOPK, nf < 0 or a NULL pointer
+ * (z may be NULL when nf = 0); FREDEC_ENOMEM / FREDEC_ECUDA from the
+ * stream-ordered scratch allocation or the launch.
+ */
+int fredec_topk_dev(const double *z, int64_t nf, int32_t k, int64_t *idx_out, void *stream);
+
+/*
  * Vector-Jacobian product of the periodogram with respect to the data y
  * (the adjoint of the map y -> z on a fixed uniform grid):
  *   dldy_out[i] = sum_j v_j dz_j/dy_i = w_i sum_j v_j ( mu_j(t_i) - mu_base(t_i) ),

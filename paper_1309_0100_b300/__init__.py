@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "fredec_pool_refine": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, ctypes.POINTER(ctypes.c_uint32),
                                               i64, i32, d, i32, _c_dp, _c_dp, _c_i32p]),
         "fredec_pipe_peaks": (ctypes.c_int, [_c_dp]),
+        "fredec_topk_dev": (ctypes.c_int, [_vp, i64, i32, _vp, _vp]),
         "fredec_selftest_wait_timeout": (ctypes.c_int, [_c_i32p]),
         "fredec_selftest_ff_sincos": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), i64, _c_dp]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
@@ -263,6 +264,18 @@ def periodogram_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, p
     if want_coef:
         res["coef"] = coef
     return res
+
+
+def topk_dev(z, k: int, *, stream=None):
+    """Top-k local maxima of a contiguous float64 CUDA tensor z (device kernels;
+    ranks by decreasing z, ties to the lower index, -1 where fewer exist)."""
+    import torch
+    if z.dtype != torch.float64 or not z.is_cuda or not z.is_contiguous():
+        raise TypeError("topk_dev wants a contiguous float64 CUDA tensor")
+    out = torch.empty(max(int(k), 1), dtype=torch.int64, device=z.device)
+    _check(lib().fredec_topk_dev(_dptr(z) if z.numel() else None, z.numel(), int(k), _dptr(out),
+                                 _stream(torch, stream)))
+    return out
 
 
 def periodogram_vjp_dev(t, y, sigma, base_freqs, f0, df, nf, coef, info, v, *, precision=FP64, out=None,

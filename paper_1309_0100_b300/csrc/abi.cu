@@ -377,6 +377,13 @@ int fredec_periodogram_dev(const double *t, const double *y, const double *sigma
                             coef_out, (cudaStream_t)stream, ws, w);
 }
 
+int fredec_topk_dev(const double *z, int64_t nf, int32_t k, int64_t *idx_out, void *stream) {
+    if (k < 1 || k > FREDEC_MAX_TOPK) return fail(FREDEC_EINVAL, "k must be in 1..64");
+    if (nf < 0) return fail(FREDEC_EINVAL, "nf must be >= 0");
+    if (!idx_out || (nf > 0 && !z)) return fail(FREDEC_EINVAL, "null pointer argument");
+    return launch_topk_single(z, nf, k, idx_out, (cudaStream_t)stream);
+}
+
 int fredec_periodogram_ex(const double *t, const double *y, const double *sigma, int64_t N, const double *base_freqs,
                           int32_t n_base, const double *f_grid, int64_t nf, const fredec_opts *opts, double *z_out,
                           double *info_out, int64_t *topk_idx_out, double *coef_out) {
