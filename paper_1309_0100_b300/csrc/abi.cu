@@ -198,16 +198,20 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
         if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_list,
                                   w.flag_count, w.err, st, z_mirror))
             return rc;
+        // the NaN fill of a failed prep rides on the re-evaluation launch when there is one
         if (fix) {
             if (int rc = launch_fixup_bins(w.desc, w.state, 1, w.rec64, p, w.flag_list, w.flag_count, nf, z, coef,
-                                           st, z_mirror))
+                                           st, z_mirror, nf))
                 return rc;
+        } else {
+            nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
         }
-        nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
         if (o.statistic == FREDEC_Z_LOG)
             if (int rc = launch_log_form(w.desc, w.state, 1, nf, z, st)) return rc;
-        if (topk && o.topk > 0)
-            if (int rc = launch_topk_single(z, nf, o.topk, topk, st)) return rc;
+        if (topk && o.topk > 0) {   // its last kernel also copies info
+            if (int rc = launch_topk_single(z, nf, o.topk, topk, st, w.state, info)) return rc;
+            info = nullptr;
+        }
     }
     if (info) info_kernel<<<1, 1, 0, st>>>(w.state, info);
     FREDEC_CUDA_TRY(cudaGetLastError());

@@ -28,6 +28,7 @@ struct FixupParams {
     const int32_t *count;
     double *z, *coef;
     double *z_mirror;            // optional second destination of z
+    int64_t nan_nf;              // > 0 (single series): if its prep failed, z[0..nan_nf) <- NaN instead
 };
 
 template <int P>
@@ -36,6 +37,12 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
     __shared__ SeedTableFF tab;
     __shared__ ff red[FX_THREADS / 32][Q];
     __shared__ double S[Q];
+    if (prm.nan_nf > 0 && prm.state[0].status != FREDEC_OK) {   // nothing was computed: z is NaN
+        for (int64_t j = (int64_t)blockIdx.x * FX_THREADS + threadIdx.x; j < prm.nan_nf;
+             j += (int64_t)gridDim.x * FX_THREADS)
+            prm.z[j] = NAN;
+        return;
+    }
     const int32_t n = *prm.count;
     if ((int32_t)blockIdx.x >= n) return;   // no flagged bin for this CTA
     fill_seed_table_ff(tab);
@@ -157,8 +164,9 @@ int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nserie
 
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st, double *z_mirror) {
-    FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef, z_mirror};
+                      cudaStream_t st, double *z_mirror, int64_t nan_nf) {
+    FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef, z_mirror,
+                    nseries == 1 ? nan_nf : 0};
     // one wave for up to 8 bins per SM (8 CTAs of 256 threads are resident per
     // SM): the flagged count is known only on the device, and CTAs beyond it
     // exit at once

@@ -138,9 +138,11 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
                  double *z, double *coef, int64_t *flag_list, int32_t *flag_count, int32_t *err,
                  cudaStream_t st, double *z_mirror = nullptr);
 // FP64-grade re-evaluation of the listed bins (fixup.cu); z_mirror as above.
+// nan_nf > 0 (one series): if the series' prep failed, the launch sets
+// z[0..nan_nf) to NaN instead (the NaN fill of a failed call).
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st, double *z_mirror = nullptr);
+                      cudaStream_t st, double *z_mirror = nullptr, int64_t nan_nf = 0);
 
 // Log form of the statistic (Eq. zpowrel) in place, per series (fixup.cu).
 int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,
@@ -154,7 +156,9 @@ inline int padded_cols(int pb) { return pb | 1; }
 // Top-k local maxima (topk.cu); segmented over series.
 int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S, int k,
                 int64_t *idx_out, cudaStream_t st);
-int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st);
+// info (optional): (chi2, W, t_c) of *state, written by the last top-k kernel.
+int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st,
+                       const SeriesState *state = nullptr, double *info = nullptr);
 
 // VJP (vjp.cu): dL/dy for one series on a uniform grid, all pointers device.
 int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, int64_t N, const double *base, int nb,

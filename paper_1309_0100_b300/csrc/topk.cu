@@ -132,6 +132,8 @@ struct TopkArgs {
     int64_t *out;              // [S * k]
     int64_t nf_single;         // single-series mode (chunk_series == nullptr)
     int64_t nchunks_single;
+    const SeriesState *state;  // single-series mode, optional: stage 2 copies (chi2, W, t_c) to info
+    double *info;
 };
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
@@ -193,6 +195,11 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
     const int64_t nch = c1 - c0, ncand = nch * a.k;
     const uint64_t *cz = a.cand_z + c0 * a.k;
     int64_t *cj = a.cand_j + c0 * a.k;
+    if (a.info && tid == 0) {
+        a.info[0] = a.state->chi2;
+        a.info[1] = a.state->W;
+        a.info[2] = a.state->tc;
+    }
     if (ncand <= 512 || (a.k >= 16 && ncand <= TK_SORT)) {
         const int m = pow2_at_least((int)ncand);
         for (int q = tid; q < m; q += TK_THREADS) {
@@ -303,7 +310,7 @@ int topk_plan_make(const int64_t *z_off_h, const int64_t *nf_h, int S, int k, in
     FREDEC_CUDA_TRY(cudaMemcpy(d_zoff, z_off_h, S * 8, cudaMemcpyHostToDevice));
     FREDEC_CUDA_TRY(cudaMemcpy(d_nf, nf_h, S * 8, cudaMemcpyHostToDevice));
     FREDEC_CUDA_TRY(cudaMemcpy(d_cs, cs.data(), nch * 4, cudaMemcpyHostToDevice));
-    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0};
+    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr};
     static_assert(sizeof(TopkArgs) <= 256, "args block");
     std::memcpy(args_out, &a, sizeof(a));
     return FREDEC_OK;
@@ -349,7 +356,7 @@ int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, in
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_zoff, z_off_h, S * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_nf, nf_h, S * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), nch * 4, cudaMemcpyHostToDevice, st));
-    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0};
+    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr};
     topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
     topk_stage2<<<(unsigned)S, TK_THREADS, 0, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());
@@ -360,13 +367,15 @@ int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, in
 
 // Single series: chunk metadata is implicit, so nothing is uploaded from the
 // host and the launch stays asynchronous (and capturable).
-int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st) {
+int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st,
+                       const SeriesState *state, double *info) {
     if (k <= 0) return FREDEC_OK;
     const int64_t nch = std::max<int64_t>(1, (nf + TK_CHUNK - 1) / TK_CHUNK);
     DevBuf cand;
     if (int rc = cand.alloc(nch * k * 16, st)) return rc;
     TopkArgs a{z, nullptr, nullptr, nullptr, nullptr, nullptr, k, cand.as<uint64_t>(),
-               reinterpret_cast<int64_t *>(cand.as<uint64_t>() + nch * k), idx_out, nf, nch};
+               reinterpret_cast<int64_t *>(cand.as<uint64_t>() + nch * k), idx_out, nf, nch,
+               info ? state : nullptr, state ? info : nullptr};
     topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
     topk_stage2<<<1, TK_THREADS, 0, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());

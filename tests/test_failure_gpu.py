@@ -40,10 +40,29 @@ def test_injected_allocation_failure(F, monkeypatch):
     assert np.all(np.isfinite(z))
 
 
-def test_device_path_singular_base_gives_nan(F):
+@pytest.mark.parametrize("prec,topk", [("fp64", 0), ("fp64", 3), ("mixed", 0), ("mixed", 3)])
+def test_device_path_singular_base_gives_nan(F, prec, topk):
+    # the NaN fill runs in its own kernel (FP64) or in the re-evaluation launch (mixed)
     import torch
     s = synth.small_series(3, N=80, n_base=2, nf=50)
     tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
-    r = F.periodogram_dev(tt(s.t), tt(s.y), tt(s.sigma), tt([0.1, 0.1]), s.grid.f0, s.grid.df, s.grid.nf)
+    r = F.periodogram_dev(tt(s.t), tt(s.y), tt(s.sigma), tt([0.1, 0.1]), s.grid.f0, s.grid.df, s.grid.nf,
+                          precision=prec, topk=topk)
     torch.cuda.synchronize()
     assert np.all(np.isnan(r["z"].cpu().numpy()))
+    if topk:
+        assert r["topk"].cpu().tolist() == [-1] * topk
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_device_path_info_with_and_without_topk(F, prec):
+    # info comes from the top-k launch when there is one, else from its own kernel
+    import torch
+    s = synth.small_series(4, N=300, n_base=1, nf=3000)
+    tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+    args = (tt(s.t), tt(s.y), tt(s.sigma), tt(s.base_freqs), s.grid.f0, s.grid.df, s.grid.nf)
+    a = F.periodogram_dev(*args, precision=prec, topk=5)
+    b = F.periodogram_dev(*args, precision=prec, topk=0)
+    torch.cuda.synchronize()
+    ia, ib = a["info"].cpu().numpy(), b["info"].cpu().numpy()
+    assert np.array_equal(ia, ib) and np.all(np.isfinite(ia)) and ia[0] > 0 and ia[1] > 0
