@@ -13,6 +13,16 @@ constexpr double TWO_POW_64 = 18446744073709551616.0;
 constexpr double TWO_POW_M64 = 5.421010862427522170037e-20;
 constexpr unsigned WAIT_LIMIT = 1u << 24;                       // bounded mbarrier polls
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialization attribute (launch_pdl) may start while its predecessor
+// in the stream is still running; grid_dependency_wait() returns once every
+// prerequisite grid has completed and its memory writes are visible (at once
+// when there is none), so it comes before the first read of their results.
+// allow_dependents() lets the next such kernel start launching before this
+// grid ends (otherwise it does when this grid's CTAs exit).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // frac(f * t) as unsigned 64-bit fixed-point turns.  The product is split into
 // its rounded value x and its exact rounding error e (fma).  r = x - rint(x)
 // is exact (Sterbenz: x and rint(x) are within a factor 2 unless rint(x) = 0,

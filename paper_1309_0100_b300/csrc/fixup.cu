@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
     __shared__ SeedTableFF tab;
     __shared__ ff red[FX_THREADS / 32][Q];
     __shared__ double S[Q];
+    grid_dependency_wait();   // the periodogram kernel's flag list and z
     if (prm.nan_nf > 0 && prm.state[0].status != FREDEC_OK) {   // nothing was computed: z is NaN
         for (int64_t j = (int64_t)blockIdx.x * FX_THREADS + threadIdx.x; j < prm.nan_nf;
              j += (int64_t)gridDim.x * FX_THREADS)
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
 
 template <int P>
 void launch_fx(const FixupParams &prm, int grid, cudaStream_t st) {
-    fixup_kernel<P><<<grid, FX_THREADS, 0, st>>>(prm);
+    launch_pdl(fixup_kernel<P>, dim3(grid), dim3(FX_THREADS), 0, st, prm);
 }
 
 }  // namespace

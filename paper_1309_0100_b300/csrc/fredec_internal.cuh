@@ -183,6 +183,23 @@ int tuple_refine_dev(const double *t, const double *y, const double *sigma, int6
 bool tuned_shape(int precision, int p, int64_t N, int64_t nf, PgramShape *out);
 
 int sm_count();
+
+// Launch with the programmatic stream serialization attribute (the kernel
+// calls grid_dependency_wait() before reading its predecessor's results).
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 // Events recorded around the main periodogram kernel (fredec_profile_events).
 void set_profile_events(cudaEvent_t a, cudaEvent_t b);
 void profile_events(cudaEvent_t *a, cudaEvent_t *b);

@@ -470,6 +470,7 @@ template <int PREC, int P, int F, bool MIRROR>
 __global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
+    grid_dependency_wait();   // prep's records and state
     const SeriesDesc d = prm.desc[0];
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
@@ -489,8 +490,8 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     if (nblocks <= 0) return FREDEC_OK;
-    kern<<<(unsigned)nblocks, warps * 32, smem, st>>>(prm);
-    e = cudaGetLastError();
+    e = launch_pdl(kern, dim3((unsigned)nblocks), dim3(warps * 32), smem, st, prm);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram launch: ") + cudaGetErrorString(e));
     return FREDEC_OK;
 }

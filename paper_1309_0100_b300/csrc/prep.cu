@@ -623,6 +623,7 @@ __device__ __forceinline__ void cluster_reduce(const double *vals, int nv_rt, Cl
 // compile-time sized and stay in registers; PT = 0: any base.
 template <int PT>
 __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
+    allow_dependents();   // the periodogram kernel's CTAs may launch on the other SMs and wait there
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
@@ -768,6 +769,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
 // multiplier while warp 0 factors the first Gram matrix.
 template <int PT>
 __global__ void __launch_bounds__(CL_THREADS) prep_cluster_one(PrepArgs a) {
+    allow_dependents();   // the periodogram kernel's CTAs may launch on the other SMs and wait there
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];

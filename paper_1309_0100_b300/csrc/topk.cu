@@ -22,6 +22,7 @@
 #include <cstring>
 #include <vector>
 
+#include "device_util.cuh"
 #include "fredec_internal.cuh"
 
 namespace fredec {
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
     __shared__ uint64_t kz[TK_SORT];
     __shared__ int64_t kj[TK_SORT];
     __shared__ int count;
+    grid_dependency_wait();   // z
     const int64_t c = blockIdx.x;
     const int tid = threadIdx.x;
     const bool single = a.chunk_series == nullptr;
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
     __shared__ int64_t kj[TK_SORT];
     __shared__ uint64_t oz[FREDEC_MAX_TOPK];
     __shared__ int64_t oj[FREDEC_MAX_TOPK];
+    grid_dependency_wait();   // stage 1's candidates
     const int s = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool single = a.chunk_series == nullptr;
@@ -376,8 +379,8 @@ int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cud
     TopkArgs a{z, nullptr, nullptr, nullptr, nullptr, nullptr, k, cand.as<uint64_t>(),
                reinterpret_cast<int64_t *>(cand.as<uint64_t>() + nch * k), idx_out, nf, nch,
                info ? state : nullptr, state ? info : nullptr};
-    topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
-    topk_stage2<<<1, TK_THREADS, 0, st>>>(a);
+    FREDEC_CUDA_TRY(launch_pdl(topk_stage1, dim3((unsigned)nch), dim3(TK_THREADS), 0, st, a));
+    FREDEC_CUDA_TRY(launch_pdl(topk_stage2, dim3(1), dim3(TK_THREADS), 0, st, a));
     FREDEC_CUDA_TRY(cudaGetLastError());
     return FREDEC_OK;
 }
