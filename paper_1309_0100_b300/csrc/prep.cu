@@ -624,6 +624,7 @@ __device__ __forceinline__ void cluster_reduce(const double *vals, int nv_rt, Cl
 template <int PT>
 __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
     allow_dependents();   // the periodogram kernel's CTAs may launch on the other SMs and wait there
+    grid_dependency_wait();   // the series descriptor and state initialised by the previous kernel
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
@@ -770,6 +771,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
 template <int PT>
 __global__ void __launch_bounds__(CL_THREADS) prep_cluster_one(PrepArgs a) {
     allow_dependents();   // the periodogram kernel's CTAs may launch on the other SMs and wait there
+    grid_dependency_wait();   // the series descriptor and state initialised by the previous kernel
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
@@ -1014,13 +1016,15 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
             cfg.blockDim = dim3(CL_THREADS);
             cfg.dynamicSmemBytes = sizeof(ClusterSmem);
             cfg.stream = st;
-            cudaLaunchAttribute at[1];
+            cudaLaunchAttribute at[2];
             at[0].id = cudaLaunchAttributeClusterDimension;
             at[0].val.clusterDim.x = (unsigned)cs;
             at[0].val.clusterDim.y = 1;
             at[0].val.clusterDim.z = 1;
+            at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see grid_dependency_wait
+            at[1].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = at;
-            cfg.numAttrs = 1;
+            cfg.numAttrs = 2;
             FREDEC_CUDA_TRY(cudaLaunchKernelEx(&cfg, cluster_kernel(slot), a));
             return FREDEC_OK;
         }
