@@ -40,6 +40,9 @@ OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
 # warps per CTA); measured with ncu (summary and command in
 # profiles/pgram_mixed_p7_config2.md).  z (8 MB) stays in L2 during the launch.
+# Library kernels per mixed step (ncu launch list of this workload): initialisation, prep,
+# periodogram, re-evaluation of flagged bins, top-k stages 1 and 2.
+KERNELS_PER_STEP = 6
 DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 206080 + 0}
 
 
@@ -317,7 +320,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": int(8 * (3 * N + nb)),
                 "d2h_bytes_per_step": int(8 * nf + 8 * 5)},
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
