@@ -92,14 +92,24 @@ int compiled_fpts(int precision, int p, int *out) {
     return n;
 }
 
-// Built-in default: the largest compiled F (fewest re-seeds) and 4 warps,
+// Widest mixed shape worth taking for series of at most SHORT_N points, by p
+// = 1, 3, ..., 13 (measured with the autotuner at N = 2000, nf = 1e6: the
+// per-CTA epilogue weighs more against a short point loop, and the widest
+// shapes run fewer CTAs per SM); longer series take the widest compiled shape.
+constexpr int64_t SHORT_N = 4096;
+constexpr int SHORT_MIXED_FPT[7] = {12, 8, 14, 6, 8, 6, 4};
+
+// Built-in default (without a tuned entry): the largest compiled F (fewest
+// re-seeds; for short mixed series at most SHORT_MIXED_FPT) and 4 warps,
 // reduced when the grid would not fill the GPU once.
 PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
     PgramShape s{1, 4};
     const FptOptions *o = options_for(p);
     if (!o) return s;
     const int *v = precision == FREDEC_MIXED ? o->mixed : o->fp64;
-    const int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
+    int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
+    if (precision == FREDEC_MIXED && N <= SHORT_N && p <= 13)
+        while (n > 1 && v[n - 1] > SHORT_MIXED_FPT[(p - 1) / 2]) --n;
     s.fpt = v[n - 1];
     const int64_t want = 2LL * sm_count();
     for (int i = n - 1; i > 0; --i) {
