@@ -16,6 +16,7 @@
 // finish (atomic counter) reduces them in chunk order, so results do not
 // depend on scheduling.
 #include <atomic>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -938,10 +939,22 @@ static PrepKernel cluster_kernel(int slot) {
 
 // CTAs per cluster for series of up to max_n points: enough for about one
 // point per thread, at most 16 (8 where the device refuses 16); 0 when cluster
-// launches cannot be used.  The attributes are set once per kernel.
+// launches cannot be used.  The attributes are set once per kernel and device
+// (kernel attributes belong to the current device).
+constexpr int CLUSTER_DEVICES = 64;
 static int cluster_size_for(int64_t max_n, int slot) {
-    static std::atomic<int> caps[CLUSTER_SLOTS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
-    int cap = caps[slot].load();
+    static std::atomic<int> caps[CLUSTER_DEVICES][CLUSTER_SLOTS];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (auto &row : caps)
+            for (auto &c : row) c.store(-1);
+    });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= CLUSTER_DEVICES) {
+        cudaGetLastError();
+        return 0;   // the chunked prep needs no attributes
+    }
+    int cap = caps[dev][slot].load();
     if (cap < 0) {
         const PrepKernel k = cluster_kernel(slot);
         cap = 0;
@@ -966,7 +979,7 @@ static int cluster_size_for(int64_t max_n, int slot) {
             }
         }
         cudaGetLastError();   // clear a refused attribute
-        caps[slot].store(cap);
+        caps[dev][slot].store(cap);
     }
     if (cap == 0) return 0;
     const int64_t want = (max_n + CL_THREADS - 1) / CL_THREADS;
