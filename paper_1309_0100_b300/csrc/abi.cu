@@ -127,7 +127,7 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
 static int periodogram_core(const double *t, const double *y, const double *sigma, int64_t N, const double *base,
                             int nb, double f0, double df, int64_t nf, const fredec_opts &o, double *z,
                             double *info, int64_t *topk, double *coef, cudaStream_t st, DevBuf &ws,
-                            SingleWork &w, double *z_mirror = nullptr) {
+                            SingleWork &w, double *z_mirror = nullptr, unsigned char *host_block = nullptr) {
     const int pb = base_cols(nb, o.trend), p = padded_cols(pb);
     const int prec = o.precision;
     const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
@@ -209,7 +209,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
         if (o.statistic == FREDEC_Z_LOG)
             if (int rc = launch_log_form(w.desc, w.state, 1, nf, z, st)) return rc;
         if (topk && o.topk > 0) {   // its last kernel also copies info
-            if (int rc = launch_topk_single(z, nf, o.topk, topk, st, w.state, info)) return rc;
+            if (int rc = launch_topk_single(z, nf, o.topk, topk, st, w.state, info, w.err, host_block)) return rc;
             info = nullptr;
         }
     }
@@ -440,10 +440,20 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
         const SeriesState *state = nullptr;
         const int32_t *err = nullptr;
         bool uniform = false;
+        // the status words and the small outputs in one page-locked block: written
+        // by the last top-k kernel itself when there is one, else copied behind
+        // the device work; one synchronisation either way
+        char *pin = static_cast<char *>(pinned_scratch(PIN_HOST_CALL, 32 + (size_t)FREDEC_MAX_TOPK * 8));
+        unsigned char *pin_dev = nullptr;
+        if (pin && spec && k && topk_idx_out && nf > 0) {
+            void *dp = nullptr;
+            if (cudaHostGetDevicePointer(&dp, pin, 0) == cudaSuccess) pin_dev = static_cast<unsigned char *>(dp);
+            cudaGetLastError();
+        }
         if (spec) {
             SingleWork w;
             rc = periodogram_core(dt, dy, ds, N, db, nb, f0, df, nf, o, dz, dinfo, k ? dtop : nullptr,
-                                  coef_out ? dcoef : nullptr, st, ws, w, z_mirror);
+                                  coef_out ? dcoef : nullptr, st, ws, w, z_mirror, pin_dev);
             state = w.state;
             err = w.err;
             uniform = grid_uniform(f_grid, nf, &f0, &df);   // overlaps the device work
@@ -463,19 +473,19 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             cudaStreamSynchronize(st);
             return rc;
         }
-        // the status words and the small outputs in one page-locked block,
-        // copied behind the device work: one synchronisation
-        char *pin = static_cast<char *>(pinned_scratch(PIN_HOST_CALL, 32 + (size_t)FREDEC_MAX_TOPK * 8));
         if (!pin) {
             if ((rc = finish_host(st, state, err))) return rc;
         } else {
             int32_t *words = reinterpret_cast<int32_t *>(pin);
-            words[0] = FREDEC_OK;
-            words[1] = FREDEC_OK;
-            if (state) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[0], &state->status, 4, cudaMemcpyDeviceToHost, st));
-            if (err) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[1], err, 4, cudaMemcpyDeviceToHost, st));
-            if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 8, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
-            if (k && topk_idx_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 32, dtop, k * 8, cudaMemcpyDeviceToHost, st));
+            if (!(pin_dev && uniform)) {   // no kernel of this call writes the block any more
+                words[0] = FREDEC_OK;
+                words[1] = FREDEC_OK;
+                if (state) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[0], &state->status, 4, cudaMemcpyDeviceToHost, st));
+                if (err) FREDEC_CUDA_TRY(cudaMemcpyAsync(&words[1], err, 4, cudaMemcpyDeviceToHost, st));
+                if (info_out) FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 8, dinfo, 3 * 8, cudaMemcpyDeviceToHost, st));
+                if (k && topk_idx_out)
+                    FREDEC_CUDA_TRY(cudaMemcpyAsync(pin + 32, dtop, k * 8, cudaMemcpyDeviceToHost, st));
+            }
             FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
             if (words[0] == FREDEC_ESINGULAR)
                 return fail(FREDEC_ESINGULAR, "the base model's normal matrix is singular (duplicate base frequencies?)");

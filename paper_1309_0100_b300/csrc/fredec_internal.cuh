@@ -157,8 +157,12 @@ inline int padded_cols(int pb) { return pb | 1; }
 int launch_topk(const double *z, const int64_t *z_off, const int64_t *nf, int S, int k,
                 int64_t *idx_out, cudaStream_t st);
 // info (optional): (chi2, W, t_c) of *state, written by the last top-k kernel.
+// host (optional, with state): device address of a page-locked block that the
+// same kernel fills with [state->status, *err] (int32), (chi2, W, t_c) at +8
+// and the k indices at +32, so that a host caller needs no copies.
 int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st,
-                       const SeriesState *state = nullptr, double *info = nullptr);
+                       const SeriesState *state = nullptr, double *info = nullptr, const int32_t *err = nullptr,
+                       unsigned char *host = nullptr);
 
 // VJP (vjp.cu): dL/dy for one series on a uniform grid, all pointers device.
 int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, int64_t N, const double *base, int nb,

@@ -135,6 +135,8 @@ struct TopkArgs {
     int64_t nchunks_single;
     const SeriesState *state;  // single-series mode, optional: stage 2 copies (chi2, W, t_c) to info
     double *info;
+    const int32_t *err;        // with host: the call's bounded-wait status word (may be null)
+    unsigned char *host;       // optional page-locked block: [status, err] int32, info at +8, indices at +32
 };
 
 __global__ void __launch_bounds__(TK_THREADS) topk_stage1(TopkArgs a) {
@@ -203,6 +205,16 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
         a.info[1] = a.state->W;
         a.info[2] = a.state->tc;
     }
+    if (a.host && tid == 0) {
+        int32_t *words = reinterpret_cast<int32_t *>(a.host);
+        double *hinfo = reinterpret_cast<double *>(a.host + 8);
+        words[0] = a.state->status;
+        words[1] = a.err ? *a.err : FREDEC_OK;
+        hinfo[0] = a.state->chi2;
+        hinfo[1] = a.state->W;
+        hinfo[2] = a.state->tc;
+    }
+    int64_t *htop = a.host ? reinterpret_cast<int64_t *>(a.host + 32) : nullptr;
     if (ncand <= 512 || (a.k >= 16 && ncand <= TK_SORT)) {
         const int m = pow2_at_least((int)ncand);
         for (int q = tid; q < m; q += TK_THREADS) {
@@ -210,7 +222,10 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
             kj[q] = q < ncand ? cj[q] : -1;
         }
         block_sort(kz, kj, m);
-        for (int r = tid; r < a.k; r += TK_THREADS) a.out[(int64_t)s * a.k + r] = kj[r];
+        for (int r = tid; r < a.k; r += TK_THREADS) {
+            a.out[(int64_t)s * a.k + r] = kj[r];
+            if (htop) htop[r] = kj[r];
+        }
         return;
     }
     if (nch <= TK_THREADS) {
@@ -258,7 +273,10 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
                 }
             }
         }
-        for (int r = tid; r < a.k; r += TK_THREADS) a.out[(int64_t)s * a.k + r] = oj[r];
+        for (int r = tid; r < a.k; r += TK_THREADS) {
+            a.out[(int64_t)s * a.k + r] = oj[r];
+            if (htop) htop[r] = oj[r];
+        }
         return;
     }
     // many chunks: warp w selects the k best of [w ncand / 32, (w + 1) ncand / 32),
@@ -269,7 +287,10 @@ __global__ void __launch_bounds__(TK_THREADS) topk_stage2(TopkArgs a) {
     if (warp == 0) {
         warp_select(kz, kj, (int64_t)TK_WARPS * a.k, a.k, oz, oj);
         __syncwarp();
-        for (int r = lane; r < a.k; r += 32) a.out[(int64_t)s * a.k + r] = oj[r];
+        for (int r = lane; r < a.k; r += 32) {
+            a.out[(int64_t)s * a.k + r] = oj[r];
+            if (htop) htop[r] = oj[r];
+        }
     }
 }
 
@@ -313,7 +334,7 @@ int topk_plan_make(const int64_t *z_off_h, const int64_t *nf_h, int S, int k, in
     FREDEC_CUDA_TRY(cudaMemcpy(d_zoff, z_off_h, S * 8, cudaMemcpyHostToDevice));
     FREDEC_CUDA_TRY(cudaMemcpy(d_nf, nf_h, S * 8, cudaMemcpyHostToDevice));
     FREDEC_CUDA_TRY(cudaMemcpy(d_cs, cs.data(), nch * 4, cudaMemcpyHostToDevice));
-    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr};
+    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr, nullptr, nullptr};
     static_assert(sizeof(TopkArgs) <= 256, "args block");
     std::memcpy(args_out, &a, sizeof(a));
     return FREDEC_OK;
@@ -359,7 +380,7 @@ int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, in
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_zoff, z_off_h, S * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_nf, nf_h, S * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(d_cs, cs.data(), nch * 4, cudaMemcpyHostToDevice, st));
-    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr};
+    TopkArgs a{z, d_zoff, d_nf, d_cs, d_cb, d_coff, k, d_cz, d_cj, idx_out, 0, 0, nullptr, nullptr, nullptr, nullptr};
     topk_stage1<<<(unsigned)nch, TK_THREADS, 0, st>>>(a);
     topk_stage2<<<(unsigned)S, TK_THREADS, 0, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());
@@ -371,14 +392,14 @@ int launch_topk(const double *z, const int64_t *z_off_h, const int64_t *nf_h, in
 // Single series: chunk metadata is implicit, so nothing is uploaded from the
 // host and the launch stays asynchronous (and capturable).
 int launch_topk_single(const double *z, int64_t nf, int k, int64_t *idx_out, cudaStream_t st,
-                       const SeriesState *state, double *info) {
+                       const SeriesState *state, double *info, const int32_t *err, unsigned char *host) {
     if (k <= 0) return FREDEC_OK;
     const int64_t nch = std::max<int64_t>(1, (nf + TK_CHUNK - 1) / TK_CHUNK);
     DevBuf cand;
     if (int rc = cand.alloc(nch * k * 16, st)) return rc;
     TopkArgs a{z, nullptr, nullptr, nullptr, nullptr, nullptr, k, cand.as<uint64_t>(),
                reinterpret_cast<int64_t *>(cand.as<uint64_t>() + nch * k), idx_out, nf, nch,
-               info ? state : nullptr, state ? info : nullptr};
+               (info || host) ? state : nullptr, state ? info : nullptr, err, state ? host : nullptr};
     FREDEC_CUDA_TRY(launch_pdl(topk_stage1, dim3((unsigned)nch), dim3(TK_THREADS), 0, st, a));
     FREDEC_CUDA_TRY(launch_pdl(topk_stage2, dim3(1), dim3(TK_THREADS), 0, st, a));
     FREDEC_CUDA_TRY(cudaGetLastError());
