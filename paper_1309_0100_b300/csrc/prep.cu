@@ -419,9 +419,13 @@ constexpr int SP_THREADS = 256;
 constexpr int SP_NV = PREP_NV;
 
 // Block sum of vals[0..nv) (per-thread, may be local memory) into out[0..nv)
-// (shared); all threads see out after return.
-__device__ void block_reduce_vals(const double *vals, int nv, double *red, double *out) {
+// (shared); all threads see out after return.  NV > 0: nv = NV at compile
+// time (the loop unrolls and vals stays in registers).
+template <int NV = 0>
+__device__ __forceinline__ void block_reduce_vals(const double *vals, int nv_rt, double *red, double *out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nv = NV > 0 ? NV : nv_rt;
+#pragma unroll
     for (int q = 0; q < nv; ++q) {
         const double v = warp_sum_d(vals[q]);
         if (lane == 0) red[wid * SP_NV + q] = v;
@@ -435,16 +439,18 @@ __device__ void block_reduce_vals(const double *vals, int nv, double *red, doubl
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
-    extern __shared__ double sp_sm[];
-    double *red = sp_sm, *out = sp_sm + (SP_THREADS / 32) * SP_NV;
-    __shared__ int ok;
+// PT as for prep_cluster: the series' base of PT sinusoidal columns known at
+// compile time, or 0 for any base.
+template <int PT>
+__device__ __forceinline__ void prep_series_body(const PrepArgs &a, const SeriesDesc &d, double *red, double *out,
+                                                 int &ok) {
     const int s = blockIdx.x;
-    const SeriesDesc d = a.desc[s];
     SeriesState &st = a.state[s];
-    const int p = d.pb, nt = p * (p + 1) / 2;
+    const int p = PT > 0 ? PT : d.pb, nt = p * (p + 1) / 2, pw = PT > 0 ? PT : d.p;
+    constexpr int NT = PT * (PT + 1) / 2;
+    constexpr int PA = PT > 0 ? PT : PMAX;
     const int64_t N = d.N;
-    double v[SP_NV];
+    double v[PT > 0 ? NT + PT + 4 : SP_NV];
     // 1: W, <t>  ->  t_c and the polynomial time scale
     v[0] = v[1] = v[2] = v[3] = 0.0;
     const double t_first = a.t[d.obs_off];
@@ -456,19 +462,19 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
         v[2] += w * u;
         v[3] += w * u * u;
     }
-    block_reduce_vals(v, 4, red, out);
+    block_reduce_vals<4>(v, 4, red, out);
     const double W = out[0], tc = rint(out[1] / W), tscale = time_scale(W, out[2], out[3]);
     // 2: raw base columns, Gram Q1 -> L1
     for (int q = 0; q < nt; ++q) v[q] = 0.0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
-        double phi[PMAX];
-        base_basis(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
+        double phi[PA];
+        base_basis<PT>(a, d, tscale, a.t[d.obs_off + i] - tc, phi);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = phi[q];
         for (int r = 0; r < p; ++r)
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * phi[r] * phi[c];
     }
-    block_reduce_vals(v, nt, red, out);
+    block_reduce_vals<NT>(v, nt, red, out);
     if (threadIdx.x == 0) {
         st.W = W;
         st.tc = tc;
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     for (int q = 0; q < nt + p; ++q) v[q] = 0.0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg), yi = a.y[d.obs_off + i];
-        double x[PMAX];
+        double x[PA];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
         forward_packed(st.L1, st.R1, x, p);
         for (int q = 0; q < p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
             for (int c = 0; c <= r; ++c) v[tri(r, c)] += w * x[r] * x[c];
         for (int q = 0; q < p; ++q) v[nt + q] += w * x[q] * yi;
     }
-    block_reduce_vals(v, nt + p, red, out);
+    block_reduce_vals<NT + PT>(v, nt + p, red, out);
     if (threadIdx.x == 0) {
         for (int q = 0; q < nt; ++q) st.L2[q] = out[q];
         for (int q = 0; q < p; ++q) st.a[q] = out[nt + q];
@@ -505,17 +511,17 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     for (int q = 0; q < p; ++q) v[q] = 0.0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
-        double x[PMAX], r = a.y[d.obs_off + i];
+        double x[PA], r = a.y[d.obs_off + i];
         for (int q = 0; q < p; ++q) x[q] = a.psi[d.psi_off + (int64_t)q * N + i];
         forward_packed(st.L2, st.R2, x, p);
         for (int q = 0; q < p; ++q) {
             a.psi[d.psi_off + (int64_t)q * N + i] = x[q];
             r -= st.a[q] * x[q];
         }
-        for (int q = p; q < d.p; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
+        for (int q = p; q < pw; ++q) a.psi[d.psi_off + (int64_t)q * N + i] = 0.0;   // odd-width padding
         for (int q = 0; q < p; ++q) v[q] += w * x[q] * r;
     }
-    block_reduce_vals(v, p, red, out);
+    block_reduce_vals<PT>(v, p, red, out);
     if (threadIdx.x == 0)
         for (int q = 0; q < p; ++q) st.a2[q] = out[q];
     __syncthreads();
@@ -525,21 +531,37 @@ __global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double sg = a.sigma[d.obs_off + i], w = 1.0 / (sg * sg);
         const double tp = a.t[d.obs_off + i] - tc;
-        double r = a.y[d.obs_off + i], u[PMAX];
+        double r = a.y[d.obs_off + i], u[PA];
         for (int q = 0; q < p; ++q) {
             const double ps = a.psi[d.psi_off + (int64_t)q * N + i];
             r -= (st.a[q] + st.a2[q]) * ps;
             u[q] = w * ps;
         }
-        for (int q = p; q < d.p; ++q) u[q] = 0.0;
-        write_records(a, d, i, K, tp, w, r, u);
+        for (int q = p; q < pw; ++q) u[q] = 0.0;
+        write_records<PT>(a, d, i, K, tp, w, r, u);
         v[0] += w * r * r;
         v[1] += (double)(float)w;
     }
-    block_reduce_vals(v, 2, red, out);
+    block_reduce_vals<2>(v, 2, red, out);
     if (threadIdx.x == 0) {
         st.chi2 = out[0];
         st.Wf = out[1];
+    }
+}
+
+// One CTA per series; each series takes the body specialised for its base
+// width when it has no polynomial terms.
+__global__ void __launch_bounds__(SP_THREADS) prep_series(PrepArgs a) {
+    extern __shared__ double sp_sm[];
+    double *red = sp_sm, *out = sp_sm + (SP_THREADS / 32) * SP_NV;
+    __shared__ int ok;
+    const SeriesDesc d = a.desc[blockIdx.x];
+    switch (d.npoly == 0 ? d.pb : 0) {
+    case 1: prep_series_body<1>(a, d, red, out, ok); break;
+    case 3: prep_series_body<3>(a, d, red, out, ok); break;
+    case 5: prep_series_body<5>(a, d, red, out, ok); break;
+    case 7: prep_series_body<7>(a, d, red, out, ok); break;
+    default: prep_series_body<0>(a, d, red, out, ok); break;
     }
 }
 
