@@ -42,7 +42,7 @@ KERNELS_PER_STEP = 6
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the mixed
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
 # warps per CTA); measured with ncu (summary and command in
-# profiles/pgram_mixed_p7_config2.md).  z (8 MB) stays in L2 during the launch.
+# profiles/pgram_mixed_p7_N2000_nf1e6.md).  z (8 MB) stays in L2 during the launch.
 DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 213504 + 0}
 
 
