@@ -72,7 +72,7 @@ def reduce_max(x, ws):
 def make_rank_workload(rank):
     """Weak scaling: rank r analyses its own series (seed rep = r) on its own
     frequency band [r, r+1) x (the 1e6-point grid), so no data is exchanged."""
-    s = synth.config2(rep=rank)
+    s = synth.residual_n2000_p7(rep=rank)
     s.grid.f0 += rank * s.grid.nf * s.grid.df
     return s
 
@@ -154,7 +154,7 @@ def cpu_baseline(s, nsample):
 def run_reference(args, rank, ws):
     if rank != 0:
         return
-    s = synth.config2()
+    s = synth.residual_n2000_p7()
     nsample = 400
     times = []
     import oracle

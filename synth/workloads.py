@@ -2,20 +2,21 @@
 
 The paper analyses radial-velocity archives and an artificial two-sinusoid
 series (Section 6) that are not available here, so these generators stand in
-for them with the sizes named by the five benchmark workloads:
+for them with the sizes named by the five benchmark workloads (workload k
+draws its seeds with k):
 
-  1  single series, N=200, seasonal gaps, constant base, 20000-point grid
-  2  residual periodogram, N=2000, base = constant + 3 fixed sinusoids, 1e6 grid
-  3  4096 independent series of uneven length and grid size (batched launch)
-  4  N=1000, six sinusoids, a 16-frequency candidate pool (tuple sweep)
-  5  survey-like N=1e5 nightly cadence, base = constant + 5 sinusoids, 1e7 grid
+  1  seasonal_n200      single series, N=200, seasonal gaps, constant base, 20000-point grid
+  2  residual_n2000_p7  residual periodogram, N=2000, base = constant + 3 fixed sinusoids, 1e6 grid
+  3  batch_4096         4096 independent series of uneven length and grid size (batched launch)
+  4  pool16_n1000       N=1000, six sinusoids, a 16-frequency candidate pool (tuple sweep)
+  5  nightly_n1e5_p11   survey-like N=1e5 nightly cadence, base = constant + 5 sinusoids, 1e7 grid
 
 Everything is float64 numpy arrays.  A frequency grid is always uniform
 ``f_j = f0 + j*df`` (j = 0..nf-1) and is described by (f0, df, nf); the
 explicit array can be made with :func:`grid_array`.
 
 Only numpy's PCG64 generator is used.  Seeds follow
-``13090100 + 1000*config + rep``.
+``13090100 + 1000*k + rep`` for workload k.
 """
 from __future__ import annotations
 
@@ -26,15 +27,15 @@ import numpy as np
 
 __all__ = [
     "Series", "Grid", "Workload", "seed_for", "grid_array",
-    "config1", "config2", "config3", "config4", "config5",
-    "small_series", "uniform_series", "make_config",
+    "seasonal_n200", "residual_n2000_p7", "batch_4096", "pool16_n1000", "nightly_n1e5_p11",
+    "small_series", "uniform_series", "make_workload",
 ]
 
 SEED_BASE = 13090100
 
 
-def seed_for(config: int, rep: int = 0) -> int:
-    return SEED_BASE + 1000 * int(config) + int(rep)
+def seed_for(workload: int, rep: int = 0) -> int:
+    return SEED_BASE + 1000 * int(workload) + int(rep)
 
 
 @dataclass
@@ -83,7 +84,7 @@ def _sinusoids(rng, t, periods, amps):
     return y
 
 
-def config1(rep: int = 0) -> Series:
+def seasonal_n200(rep: int = 0) -> Series:
     """N=200 over 1000 d with seasonal gaps (t mod 365 < 240), periods 13.7 d and
     87 d (amplitudes 5 and 3), offset 1, sigma ~ LogNormal(0, 0.3); constant base;
     grid f_j = j*5e-5, j = 1..20000 (0 < f <= 1 /d)."""
@@ -100,7 +101,7 @@ def config1(rep: int = 0) -> Series:
                   true_freqs=np.array([1 / 13.7, 1 / 87.0]))
 
 
-def config2(rep: int = 0, nf: int = 1_000_000) -> Series:
+def residual_n2000_p7(rep: int = 0, nf: int = 1_000_000) -> Series:
     """N=2000 over 3000 d, sigma ~ LogNormal(0, 0.5); four sinusoids with periods
     log-uniform in [2, 500] d and amplitudes U[1, 10]; base = constant + the first
     three of them; grid f_j = j*2e-6, j = 1..1e6 (0 < f <= 2 /d)."""
@@ -115,8 +116,8 @@ def config2(rep: int = 0, nf: int = 1_000_000) -> Series:
     return Series(t, y, sigma, 1.0 / periods[:3], Grid(df, df, nf), true_freqs=1.0 / periods)
 
 
-def config3(rep: int = 0, n_series: int = 4096, nf_lo: int = 10_000, nf_hi: int = 100_000,
-            n_lo: int = 50, n_hi: int = 5000) -> Workload:
+def batch_4096(rep: int = 0, n_series: int = 4096, nf_lo: int = 10_000, nf_hi: int = 100_000,
+               n_lo: int = 50, n_hi: int = 5000) -> Workload:
     """4096 independent series: N_s ~ U{50..5000}, span T_s ~ U[100, 5000] d, uniform
     times, 0-3 injected sinusoids (periods log-uniform in [2, T_s/2], amplitudes
     U[1, 10]), sigma ~ LogNormal(0, 0.4); base = constant + the first
@@ -139,7 +140,7 @@ def config3(rep: int = 0, n_series: int = 4096, nf_lo: int = 10_000, nf_hi: int 
     return Workload("batched", out)
 
 
-def config4(rep: int = 0, N: int = 1000, n_pool: int = 16) -> Series:
+def pool16_n1000(rep: int = 0, N: int = 1000, n_pool: int = 16) -> Series:
     """N=1000 over 2000 d, sigma ~ LogNormal(0, 0.4); six sinusoids (periods
     log-uniform in [2, 500] d, amplitudes U[1, 10]).  Pool of 16: the six true
     frequencies, six yearly/daily aliases (|f +- 1/365.25|, |1 - f|) of randomly
@@ -163,7 +164,7 @@ def config4(rep: int = 0, N: int = 1000, n_pool: int = 16) -> Series:
     return Series(t, y, sigma, np.zeros(0), None, true_freqs=ftrue, pool=np.abs(pool))
 
 
-def config5(rep: int = 0, N: int = 100_000, nf: int = 10_000_000) -> Series:
+def nightly_n1e5_p11(rep: int = 0, N: int = 100_000, nf: int = 10_000_000) -> Series:
     """Survey-like series: 4000 nights, each kept with probability 0.7, with three
     60-night gaps per year at random places; points uniform inside a 0.3 d window
     of each kept night, counts chosen so that N is exact; sigma ~ LogNormal(0, 0.4);
@@ -211,5 +212,5 @@ def uniform_series(seed: int, N: int = 64, dt: float = 1.0, t0: float = 0.0) -> 
     return Series(t, y, sigma, np.zeros(0), None)
 
 
-def make_config(k: int, rep: int = 0, **kw):
-    return {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}[k](rep, **kw)
+def make_workload(k: int, rep: int = 0, **kw):
+    return {1: seasonal_n200, 2: residual_n2000_p7, 3: batch_4096, 4: pool16_n1000, 5: nightly_n1e5_p11}[k](rep, **kw)

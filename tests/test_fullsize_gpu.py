@@ -27,7 +27,7 @@ def _check_sampled(z, s, idx, tol):
 
 
 def test_config3_batch_full(F):
-    w = synth.config3()
+    w = synth.batch_4096()
     plan = F.BatchPlan(w.series, precision="mixed", topk=5)
     plan.run()
     z, top = plan.download()
@@ -46,7 +46,7 @@ def test_config3_batch_full(F):
 
 def test_config5_survey_full(F):
     import torch
-    s = synth.config5()
+    s = synth.nightly_n1e5_p11()
     dev = torch.device("cuda:0")
     tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
     t, y, sg, b = tt(s.t), tt(s.y), tt(s.sigma), tt(s.base_freqs)
@@ -83,7 +83,7 @@ def test_config4_pool_refine_sampled(F, prec, ftol, ltol):
     local minimum (the oracle's l there equals the GPU's, and the oracle's own
     refinement started there stays there) and is at least as good as the
     oracle's; such tuples must be rare."""
-    s = synth.config4()
+    s = synth.pool16_n1000()
     T = s.t.max() - s.t.min()
     rng = np.random.default_rng(4)
     masks = [m for m in rng.integers(1, 1 << 16, 400).astype(np.uint32) if bin(int(m)).count("1") <= 4][:10]

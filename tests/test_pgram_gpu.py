@@ -65,7 +65,7 @@ def test_prep_paths_long_series(F, prec, N):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_full_grid(F, prec):
-    s = synth.config1()
+    s = synth.seasonal_n200()
     f = s.grid.array()
     z, zr, top, err = _compare(F, s, f, prec)
     assert list(top) == local_max_topk(zr, 5)
@@ -77,7 +77,7 @@ def test_config2_full_size_sampled(F, prec):
     its tuner picks: 6 frequencies per thread in mixed precision, 4 in FP64,
     4 warps); the oracle evaluates a strided sample plus the neighbourhoods of
     the top-5 peaks."""
-    s = synth.config2()
+    s = synth.residual_n2000_p7()
     f = s.grid.array()
     z, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5,
                            fpt=6 if prec == "mixed" else 4, warps=4)

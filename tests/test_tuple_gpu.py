@@ -47,7 +47,7 @@ def test_pool_table_vs_oracle(F, n, N):
 
 
 def test_pool_table_config4_sampled(F):
-    s = synth.config4()
+    s = synth.pool16_n1000()
     tab = F.pool_subtuples_eval(s.t, s.y, s.sigma, s.pool)
     assert tab.size == 1 << 16
     rng = np.random.default_rng(4)
