@@ -26,7 +26,7 @@ def _check_sampled(z, s, idx, tol):
     assert np.max(err[m]) < tol, float(np.max(err[m]))
 
 
-def test_config3_batch_full(F):
+def test_batch_4096_full(F):
     w = synth.batch_4096()
     plan = F.BatchPlan(w.series, precision="mixed", topk=5)
     plan.run()
@@ -44,7 +44,7 @@ def test_config3_batch_full(F):
             assert list(top[k]) == list(t64), k
 
 
-def test_config5_survey_full(F):
+def test_nightly_n1e5_full(F):
     import torch
     s = synth.nightly_n1e5_p11()
     dev = torch.device("cuda:0")
@@ -70,7 +70,7 @@ def test_config5_survey_full(F):
 
 
 @pytest.mark.parametrize("prec,ftol,ltol", [("fp64", 1e-5, 1e-10), ("mixed", 3e-3, 1e-6)])
-def test_config4_pool_refine_sampled(F, prec, ftol, ltol):
+def test_pool16_refine_sampled(F, prec, ftol, ltol):
     """The FP64 refinement must reach the oracle's local minimum of l: equal l,
     the oracle's l at the GPU frequencies equal to the GPU's l, and frequencies
     equal to a small fraction of the resolution 1/T (small-amplitude members

@@ -64,7 +64,7 @@ def test_prep_paths_long_series(F, prec, N):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_config1_full_grid(F, prec):
+def test_seasonal_n200_full_grid(F, prec):
     s = synth.seasonal_n200()
     f = s.grid.array()
     z, zr, top, err = _compare(F, s, f, prec)
@@ -72,7 +72,7 @@ def test_config1_full_grid(F, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_config2_full_size_sampled(F, prec):
+def test_residual_n2000_full_size_sampled(F, prec):
     """Full 1e6-point grid on the GPU in the benchmark launch shape (the shapes
     its tuner picks: 6 frequencies per thread in mixed precision, 4 in FP64,
     4 warps); the oracle evaluates a strided sample plus the neighbourhoods of

@@ -46,7 +46,7 @@ def test_pool_table_vs_oracle(F, n, N):
     np.testing.assert_allclose(tab, ref, rtol=1e-10)
 
 
-def test_pool_table_config4_sampled(F):
+def test_pool_table_pool16_sampled(F):
     s = synth.pool16_n1000()
     tab = F.pool_subtuples_eval(s.t, s.y, s.sigma, s.pool)
     assert tab.size == 1 << 16
