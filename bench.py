@@ -43,7 +43,7 @@ KERNELS_PER_STEP = 6
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
 # warps per CTA); measured with ncu (summary and command in
 # profiles/pgram_mixed_p7_N2000_nf1e6.md).  z (8 MB) stays in L2 during the launch.
-DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 213504 + 0}
+DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 209152 + 0}
 
 
 def dist_setup():

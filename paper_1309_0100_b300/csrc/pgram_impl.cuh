@@ -31,15 +31,16 @@ namespace fredec {
 // (two-level summation).  The random-phase residual sums <r c>, <r s> are
 // flushed every 32 points: their FP32 rounding is amplified at low-z bins
 // (dz/z = 2 drho/rho) and sets the z error.  The other 2P+2 sums are flushed
-// every FLUSH_BLOCKS_ALL x 32 = 128 points.  Measured (largest z error against
-// the FP64 kernel, floor 1e-3 of the highest peak; kernel time on the N = 2000,
-// 1e6-frequency residual periodogram):
-//   all sums every 32 points: 1.8e-6, short series (N < 700) 5.5e-6; 1.99 ms
-//   <r c>, <r s> every 32, the rest every 128: 1.8e-6, 5.5e-6; 1.87 ms
-//   the rest every 256: 2.5e-6, 5.5e-6; 1.86 ms
+// every FLUSH_BLOCKS_ALL x 32 = 256 points.  Measured (largest z error against
+// the FP64 kernel, floor 1e-3 of the highest peak; short series N < 700 against
+// the oracle; kernel time on the N = 2000, 1e6-frequency residual periodogram):
+//   all sums every 32 points: 1.8e-6, 5.5e-6; 1.99 ms
 //   all sums every 64 points: 2.8e-6, 8e-6; 1.90 ms
+//   <r c>, <r s> every 32, the rest every 128: 1.8e-6, 5.8e-6; 1.873 ms
+//   <r c>, <r s> every 32, the rest every 256: 1.8e-6, 5.8e-6; 1.855 ms (N = 7e4: 5.4e-6, N = 1e5: 3.3e-6)
+//   <r c>, <r s> every 32, the rest every 512: 2.9e-6, 5.8e-6; 1.847 ms
 constexpr int FLUSH_POINTS = 32;
-constexpr int FLUSH_BLOCKS_ALL = 4;
+constexpr int FLUSH_BLOCKS_ALL = 8;
 
 struct PgramParams {
     const SeriesDesc *desc;
