@@ -40,7 +40,10 @@ def _compare(F, s, f, prec, topk=5, **kw):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nb,N,nf", [(0, 37, 300), (1, 129, 257), (2, 300, 1000), (3, 1000, 700), (5, 260, 333),
-                                     (7, 90, 150), (12, 64, 101)])
+                                     (7, 90, 150), (12, 64, 101),
+                                     # prep paths: one point per thread up to 16 x 128 points, then the
+                                     # per-width loop kernel (base widths 9 and 11)
+                                     (4, 777, 400), (5, 2048, 200), (5, 2049, 200)])
 def test_parity_small(F, prec, nb, N, nf):
     s = synth.small_series(100 + nb, N=N, n_base=nb, nf=nf, span=200.0, fmax=1.5)
     f = s.grid.array()
