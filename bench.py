@@ -41,8 +41,8 @@ OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (
 KERNELS_PER_STEP = 6
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the mixed
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
-# warps per CTA); measured with ncu (summary and command in
-# profiles/pgram_mixed_p7_N2000_nf1e6.md).  z (8 MB) stays in L2 during the launch.
+# warps per CTA); measured with ncu on the same command (--kernel-only).  z (8 MB)
+# stays in L2 during the launch.
 DRAM_BYTES_PER_LAUNCH = {(7, 6, 4): 209152 + 0}
 
 
@@ -286,8 +286,8 @@ def main():
     k_ms = statistics.mean(kern_ms)
     achieved = OPS_PER_TERM(p) * N * nf / (k_ms * 1e-3)
     # DRAM bytes (read + write) of one launch of this kernel at this launch
-    # shape, from an ncu capture of the same command (the profile summary for
-    # this workload under profiles/); None for shapes that were not captured
+    # shape, from an ncu capture of the same command; None for shapes that
+    # were not captured
     traffic = DRAM_BYTES_PER_LAUNCH.get((p, best["mixed"][0], best["mixed"][1]))
     # parity on a strided sample against the FP64 CPU oracle
     import oracle

@@ -46,7 +46,8 @@
  *     re-seeding of the sin/cos recurrence, the base fit and every solve in
  *     FP64, and accumulates the trigonometric sums in FP32 with blocked
  *     summation; bins whose 2x2 system is ill-conditioned are re-evaluated
- *     in FP64 (see fredec_opts.flag_tau).
+ *     with FP64-grade accuracy in float-float arithmetic (pairs of FP32
+ *     numbers, compensated sums) on the FP32 pipe (see fredec_opts.flag_tau).
  *   - Degenerate trial columns (f = 0, f equal to a base frequency): a new
  *     column whose norm after projection on the previous columns is below
  *     1e-7 of its own norm is dropped (minimum-norm least squares); z is then
@@ -86,7 +87,8 @@ typedef struct fredec_opts {
     int32_t topk;       /* number of local maxima of z to report, 0..64 (default 0) */
     int32_t fpt;        /* frequencies per thread; 0 = tuned or built-in default    */
     int32_t warps;      /* warps per CTA (point splits); 0 = tuned or default       */
-    double  flag_tau;   /* MIXED: a bin is recomputed in FP64 when a pivot of its
+    double  flag_tau;   /* MIXED: a bin is recomputed with FP64-grade accuracy
+                           (float-float sums on the FP32 pipe) when a pivot of its
                            2x2 system falls below flag_tau times its column norm.
                            0 = default (0.2); negative = never recompute.             */
     int32_t trend;      /* degree of the time polynomial that replaces the constant
@@ -296,7 +298,7 @@ int fredec_periodogram_batch(const double *t, const double *y, const double *sig
 
 /*
  * A batch plan: device-resident inputs plus the captured CUDA graph of
- * prep -> persistent periodogram -> FP64 re-evaluation -> top-k.  The plan
+ * prep -> persistent periodogram -> FP64-grade re-evaluation -> top-k.  The plan
  * copies the host inputs once (same layout as fredec_periodogram_batch) and
  * keeps them; run replays the graph on a stream and leaves z and top-k in
  * device buffers owned by the plan.

@@ -1,5 +1,5 @@
 // Public C ABI (include/fredec.h): validation, workspace and the single-series
-// periodogram pipeline  prep -> periodogram -> FP64 re-evaluation -> top-k.
+// periodogram pipeline  prep -> periodogram -> FP64-grade (float-float) re-evaluation -> top-k.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>

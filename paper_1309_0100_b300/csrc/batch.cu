@@ -2,7 +2,7 @@
 // in one plan.  The plan keeps the inputs on the device, builds the work list
 // of (series, frequency block) items (longest series first), and captures
 //   reset counters -> prep (all series) -> persistent periodogram kernel ->
-//   FP64 re-evaluation of flagged bins -> segmented top-k
+//   FP64-grade (float-float) re-evaluation of flagged bins -> segmented top-k
 // into one CUDA graph that fredec_batch_plan_run replays.  The number of warps
 // per CTA is picked at plan creation by timing the captured graph (autotuner).
 #include <algorithm>

@@ -1,5 +1,5 @@
 // fredec_periodogram_noalloc_dev: the single-series periodogram pipeline
-// (prep -> periodogram -> FP64 re-evaluation) with all of its scratch memory in
+// (prep -> periodogram -> FP64-grade re-evaluation) with all of its scratch memory in
 // one file-scope device array instead of the stream-ordered allocator.
 //
 // It exists for callers that cannot allocate device memory when they call:

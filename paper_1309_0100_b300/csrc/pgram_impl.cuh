@@ -49,8 +49,8 @@ struct PgramParams {
     double *z;                  // output base (series offsets in desc)
     double *z_mirror;           // optional second destination of z (same offsets)
     double *coef;               // optional (a_j, b_j) output, same offsets * 2
-    double flag_tau;            // mixed: FP64 re-evaluation threshold (< 0: never)
-    int64_t *flag_list;         // mixed: global z indices of bins to re-evaluate in FP64
+    double flag_tau;            // mixed: re-evaluation threshold (< 0: never)
+    int64_t *flag_list;         // mixed: global z indices of bins to re-evaluate (float-float)
     int32_t *flag_count;
     int32_t *err;               // FREDEC_ETIMEOUT on a bounded-wait timeout
     int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
@@ -120,7 +120,7 @@ __device__ __forceinline__ double solve2(double CC, double CS, double SS, double
 // The same 2x2 solve with one reciprocal, for well-conditioned bins:
 // theta = S^{-1} rho by the adjugate, z = 1/2 rho^T theta.  Returns false
 // (and leaves the outputs alone) when a pivot ratio is below tau, i.e. when
-// the bin must be re-evaluated in FP64; no divisions are spent on the test.
+// the bin must be re-evaluated with FP64-grade sums; no divisions are spent on the test.
 __device__ __forceinline__ bool solve2_fast(double CC, double CS, double SS, double vcc, double vcs, double vss,
                                             double Rc, double Rs, double tau, double *pz, double *pa, double *pb) {
     const double S11 = CC - vcc, S12 = CS - vcs, S22 = SS - vss;
@@ -414,7 +414,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         bool done = false;
         if (mixed_flags) {
             done = solve2_fast(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], prm.flag_tau, &zz, &a, &bb);
-            if (!done) {   // ill-conditioned: provisional value now, FP64 re-evaluation later
+            if (!done) {   // ill-conditioned: provisional value now, FP64-grade re-evaluation later
                 const int32_t at = atomicAdd(prm.flag_count, 1);
                 prm.flag_list[at] = d.z_off + j;
             }
