@@ -138,6 +138,19 @@ def measured_peaks():
         return {}
 
 
+def parity_vs_oracle(z, zr, ratio, chi2, tol, N):
+    """Largest relative error (floor 1e-3 of the highest z*) over the bins whose
+    2x2 system has a condition number below 1e12 (oracle column ratio >= 1e-6),
+    the largest |z - z*| / bound with the bound tol max(z*, floor) +
+    8 eps64 sqrt(N) chi2_base / ratio^2 (the rounding of an FP64 normal-equation
+    method grows as 1/ratio^2), and the number of bins left out."""
+    keep = ratio >= 1e-6
+    den = np.maximum(np.abs(zr), 1e-3 * np.max(np.abs(zr)))
+    bound = tol * den + 8.0 * 2.0 ** -52 * np.sqrt(N) * chi2 / np.maximum(ratio, 1e-6) ** 2
+    d = np.abs(z - zr)
+    return float(np.max(d[keep] / den[keep])), float(np.max(d[keep] / bound[keep])), int((~keep).sum())
+
+
 def cpu_baseline(s, nsample):
     """The oracle as it stands, single-threaded, on a strided sample of the grid."""
     import oracle
@@ -292,11 +305,9 @@ def main():
     # parity on a strided sample against the FP64 CPU oracle
     import oracle
     idx = np.unique(np.concatenate([np.arange(0, nf, nf // 200), np.asarray(top, dtype=np.int64)]))
-    zr, _, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
-    floor = 1e-3 * np.max(zr)
-    msk = ratio >= 1e-2
-    err_mixed = float(np.max(np.abs(z_mixed[idx] - zr)[msk] / np.maximum(zr, floor)[msk]))
-    err_64 = float(np.max(np.abs(z64[idx] - zr)[msk] / np.maximum(zr, floor)[msk]))
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
+    err_mixed, worst_mixed, n_excl = parity_vs_oracle(z_mixed[idx], zr, ratio, c2, 1e-5, N)
+    err_64, worst_64, _ = parity_vs_oracle(z64[idx], zr, ratio, c2, 1e-10, N)
     cpu = None if args.no_cpu_baseline else cpu_baseline(s, args.cpu_sample)
     line = {
         "metric": METRIC,
@@ -310,7 +321,10 @@ def main():
                  "launch_shape": {"fpt": best["fp64"][0], "warps": best["fp64"][1]}},
         "mixed_over_fp64": value / value64,
         "max_rel_err_vs_oracle": {"mixed": err_mixed, "fp64": err_64, "sampled_bins": int(idx.size),
-                                  "floor": "1e-3 of the highest sampled z"},
+                                  "excluded_cond_above_1e12": n_excl,
+                                  "worst_over_bound": {"mixed": worst_mixed, "fp64": worst_64},
+                                  "floor": "1e-3 of the highest sampled z",
+                                  "bound": "tol max(z*, floor) + 8 eps64 sqrt(N) chi2_base / ratio^2"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T FP32-FMA-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "pgram_kernel<mixed, P=7>", "kernel_ms": k_ms,

@@ -180,3 +180,44 @@ def test_planted_cascade_mistake_is_caught():
         if not np.array_equal(passed, _closed_form_pass(a, N, zthr)):
             caught = True
     assert caught
+
+
+# ---------------------------------------------------------------------------
+# The normalised bandwidth W = f_max T_eff, T_eff = sqrt(4 pi Var_w(t))
+# (Sect. 2), which every FAP threshold of the scan and the cascade uses, is
+# pinned by closed forms of the weighted variance, not by its own formula.
+
+def test_effective_bandwidth_equally_spaced_closed_form():
+    # n equally spaced times on [0, T] with equal weights: the discrete
+    # uniform variance T^2 (n + 1) / (12 (n - 1)); T_eff -> T sqrt(pi/3)
+    T, fmax = 2000.0, 0.7
+    for n in (2, 3, 10, 1001):
+        t = np.linspace(0.0, T, n)
+        W = oracle.effective_bandwidth(t, np.full(n, 0.3), fmax)
+        assert W == pytest.approx(fmax * np.sqrt(4 * np.pi * T * T * (n + 1) / (12.0 * (n - 1))), rel=1e-13)
+    t = np.linspace(0.0, T, 200001)
+    assert oracle.effective_bandwidth(t, np.ones(t.size), 1.0) == pytest.approx(T * np.sqrt(np.pi / 3), rel=1e-5)
+
+
+def test_effective_bandwidth_weights_closed_form():
+    # two times with weights w1 = 1/s1^2, w2 = 1/s2^2: Var_w = w1 w2 T^2 / (w1 + w2)^2
+    # (catches weights dropped, or 1/sigma used instead of 1/sigma^2)
+    T = 37.5
+    for s1, s2 in ((1.0, 1.0), (1.0, 3.0), (0.2, 5.0)):
+        w1, w2 = 1 / s1 ** 2, 1 / s2 ** 2
+        var = w1 * w2 * T * T / (w1 + w2) ** 2
+        W = oracle.effective_bandwidth([0.0, T], [s1, s2], 2.0)
+        assert W == pytest.approx(2.0 * np.sqrt(4 * np.pi * var), rel=1e-14)
+
+
+def test_effective_bandwidth_shift_and_scale():
+    # W does not depend on the time origin; it scales with f_max and with
+    # the time unit (t -> a t, f_max -> f_max / a leaves W unchanged)
+    rng = np.random.default_rng(11)
+    t = np.sort(rng.uniform(0, 500, 300))
+    sg = rng.lognormal(0, 0.5, 300)
+    W = oracle.effective_bandwidth(t, sg, 1.3)
+    assert oracle.effective_bandwidth(t + 2.45e6, sg, 1.3) == pytest.approx(W, rel=1e-9)
+    assert oracle.effective_bandwidth(t, sg, 2.6) == pytest.approx(2 * W, rel=1e-14)
+    assert oracle.effective_bandwidth(t * 24.0, sg, 1.3 / 24.0) == pytest.approx(W, rel=1e-13)
+    assert oracle.effective_bandwidth(t, 7.0 * sg, 1.3) == pytest.approx(W, rel=1e-13)   # common sigma scale

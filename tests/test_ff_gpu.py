@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import ensure_built
+from helpers import cond_parity, ensure_built
 
 pytestmark = pytest.mark.gpu
 
@@ -34,16 +34,24 @@ def test_ff_sincos_selftest(F):
 
 
 def test_flagged_bins_are_fp64_grade(F):
-    # a grid crowded around the base frequencies: many bins are flagged for
-    # re-evaluation; there the mixed result must equal the FP64 path's
+    # a grid crowded around the base frequencies and f = 0: many bins are
+    # flagged for re-evaluation (pivot ratio below 0.2, i.e. oracle ratio
+    # below about 0.45); there the mixed result must be FP64-grade, against
+    # the oracle (1e-9 plus the conditioning term) and against the FP64 path
     s = synth.small_series(77, N=2000, n_base=3, span=3000.0, nf=10, fmax=0.5)
     f = np.concatenate([g + np.linspace(-2e-4, 2e-4, 401) for g in s.base_freqs] + [np.linspace(1e-6, 2e-4, 200)])
     f = np.sort(np.abs(f))
     zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
     z64 = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="fp64")
     zmx = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="mixed")
-    flagged = (ratio < 0.05) & (ratio >= 1e-3)
-    assert flagged.sum() > 50
+    flagged = ratio < 0.3
+    assert flagged.sum() > 400 and (ratio[flagged] < 1e-2).sum() > 20
+    r = cond_parity(zmx[flagged], zr[flagged], ratio[flagged], c2, 1e-9, s.N,
+                    floor_frac=1e-3 * np.max(zr) / np.max(zr[flagged]))
+    assert r["ok"], r
+    r = cond_parity(zmx, zr, ratio, c2, 1e-5, s.N)     # every bin at the mixed bar
+    assert r["ok"], r
+    mid = (ratio < 0.05) & (ratio >= 1e-3)
     floor = 1e-3 * np.max(zr)
     den = np.maximum(np.abs(z64), floor)
-    assert np.max(np.abs(zmx - z64)[flagged] / den[flagged]) < 1e-9
+    assert np.max(np.abs(zmx - z64)[mid] / den[mid]) < 1e-9

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import ensure_built, local_max_topk, rel_err
+from helpers import cond_parity, ensure_built, local_max_topk, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -43,14 +43,19 @@ def test_trend_parity(F, prec, trend, nb, N, nf):
     zr, c2, ratio = oracle.periodogram_trend(s.t, s.y, s.sigma, s.base_freqs, trend, f, want_ratio=True)
     z, top, info = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5, want_info=True,
                                  trend=trend)
-    mask = ratio >= 1e-2
-    assert mask.mean() > 0.95
-    assert rel_err(z, zr, mask) < TOL[prec]
+    r = cond_parity(z, zr, ratio, c2, TOL[prec], s.N)
+    assert r["ok"], r
     assert info[0] == pytest.approx(c2, rel=1e-11)
     ref_top = local_max_topk(zr, 5)
     zs = sorted(zr[[j for j in ref_top if j >= 0]], reverse=True)
     if np.all(np.abs(np.diff(zs)) > 10 * TOL[prec] * zs[0]):
         assert list(top) == ref_top
+
+
+def _dlog_dz(z, chi2, N, nb, trend):
+    """d(log form)/dz = N_H / (chi2_base - 2 z): scales the conditioning term
+    of the difference form to the log form."""
+    return (N - 3 * (nb + 1) - 1 - trend) / (chi2 - 2.0 * np.asarray(z))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -63,8 +68,8 @@ def test_log_form_statistic(F, prec, trend, nb):
     zl, top = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5, trend=trend,
                             statistic="log")
     zd, topd = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, topk=5, trend=trend)
-    mask = ratio >= 1e-2
-    assert rel_err(zl, zl_ref, mask) < TOL[prec]
+    r = cond_parity(zl, zl_ref, ratio, c2, TOL[prec], s.N, cond_scale=_dlog_dz(zr, c2, s.N, nb, trend))
+    assert r["ok"], r
     assert list(top) == list(topd)     # the log form is monotone in z
 
 
@@ -74,16 +79,15 @@ def test_trend_device_generic_batch_noalloc(F):
     s = _trend_series(500, 700, 2, 2, 2000)
     f = s.grid.array()
     zr, c2, ratio = oracle.periodogram_trend(s.t, s.y, s.sigma, s.base_freqs, 2, f, want_ratio=True)
-    mask = ratio >= 1e-2
     tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=dev)
     r = F.periodogram_dev(tt(s.t), tt(s.y), tt(s.sigma), tt(s.base_freqs), s.grid.f0, s.grid.df, s.grid.nf,
                           precision="fp64", trend=2)
-    assert rel_err(r["z"].cpu().numpy(), zr, mask) < TOL["fp64"]
+    assert cond_parity(r["z"].cpu().numpy(), zr, ratio, c2, TOL["fp64"], s.N)["ok"]
     # non-uniform grid (the generic kernel)
     fg = np.sort(np.random.default_rng(1).uniform(0.001, 1.0, 500))
-    zg_r, _, rg = oracle.periodogram_trend(s.t, s.y, s.sigma, s.base_freqs, 2, fg, want_ratio=True)
+    zg_r, cg, rg = oracle.periodogram_trend(s.t, s.y, s.sigma, s.base_freqs, 2, fg, want_ratio=True)
     zg = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, fg, precision="fp64", trend=2)
-    assert rel_err(zg, zg_r, rg >= 1e-2) < TOL["fp64"]
+    assert cond_parity(zg, zg_r, rg, cg, TOL["fp64"], s.N)["ok"]
     # batch: every series with the same trend degree, log form
     ser = [_trend_series(600 + k, 150 + 97 * k, k % 3, 1, 300 + 50 * k) for k in range(5)]
     zb, zo, topb = F.periodogram_batch(ser, precision="mixed", topk=3, trend=1, statistic="log")
@@ -91,7 +95,9 @@ def test_trend_device_generic_batch_noalloc(F):
         fk = sk.grid.array()
         zk, ck, rk = oracle.periodogram_trend(sk.t, sk.y, sk.sigma, sk.base_freqs, 1, fk, want_ratio=True)
         zlk = oracle.log_form(zk, ck, sk.t.size, len(sk.base_freqs) + 1, 1)
-        assert rel_err(zb[zo[k]:zo[k] + fk.size], zlk, rk >= 1e-2) < TOL["mixed"]
+        r = cond_parity(zb[zo[k]:zo[k] + fk.size], zlk, rk, ck, TOL["mixed"], sk.N,
+                        cond_scale=_dlog_dz(zk, ck, sk.N, len(sk.base_freqs), 1))
+        assert r["ok"], (k, r)
     # the no-allocation entry point
     lib = F.lib()
     zn = torch.empty(s.grid.nf, dtype=torch.float64, device=dev)
@@ -101,7 +107,7 @@ def test_trend_device_generic_batch_noalloc(F):
                                                 len(s.base_freqs), s.grid.f0, s.grid.df, s.grid.nf,
                                                 F.ctypes.byref(o), F._dptr(zn), None, None))
     torch.cuda.synchronize()
-    assert rel_err(zn.cpu().numpy(), zr, mask) < TOL["fp64"]
+    assert cond_parity(zn.cpu().numpy(), zr, ratio, c2, TOL["fp64"], s.N)["ok"]
 
 
 @pytest.mark.parametrize("trend", [1, 3])
