@@ -192,12 +192,20 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
  * calls no allocator: all of its scratch lives in one 16 MiB device array
  * compiled into the library, held on every GPU that loads the library until
  * the process exits.
- *   - Same arguments and results as fredec_periodogram_dev without top-k
- *     (opts->topk must be 0) and without coefficients.
- *   - Scratch needed (p = 2*n_base + 1): about N*(16p + 50 + p*p/8) bytes for
- *     FREDEC_FP64; FREDEC_MIXED adds N*(4p + 32) bytes of FP32 records and
- *     8*nf bytes for its FP64 re-evaluation list.  A problem that does not
- *     fit in 16 MiB is rejected with FREDEC_EINVAL and a message giving the
+ *   - Same arguments, checks and results as fredec_periodogram_dev without
+ *     top-k (opts->topk must be 0) and without coefficients.  Every argument
+ *     is checked before anything is enqueued.
+ *   - z_out is all NaN when the base fit fails (singular base model) or when
+ *     a bounded device wait gives up (the status the other entry points
+ *     report as FREDEC_ETIMEOUT); the call itself still returns FREDEC_OK,
+ *     since nothing is read back.
+ *   - Scratch needed, in bytes, with p = 1 + trend + 2*n_base rounded up to
+ *     an odd number, c = ceil(N/32) and R(x) = x rounded up to a multiple of
+ *     256:  6912 + R(4c) + R(8c(p(p+1)/2 + p + 4)) + R(8pN) + R(rN), with
+ *     r = 8(6 + 2 ceil(p/2)) for FREDEC_FP64 and r = 4(8 + 4 ceil(p/4)) for
+ *     FREDEC_MIXED; FREDEC_MIXED with re-evaluation (flag_tau >= 0) adds
+ *     R(16 ceil((8 + 2p)/4) N) + R(8 nf + 8).  A problem that does not fit
+ *     in 16 MiB is rejected with FREDEC_EINVAL and a message giving the
  *     required and available byte counts.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -218,8 +218,8 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     return FREDEC_OK;
 }
 
-// Host-side checks shared by the entry points.
-static int check_opts(const fredec_opts *o, fredec_opts *out) {
+// Host-side checks shared by the entry points (declared in fredec_internal.cuh).
+int check_opts(const fredec_opts *o, fredec_opts *out) {
     fredec_opts_init(out);
     if (o) *out = *o;
     if (out->precision != FREDEC_FP64 && out->precision != FREDEC_MIXED)
@@ -233,7 +233,7 @@ static int check_opts(const fredec_opts *o, fredec_opts *out) {
     return FREDEC_OK;
 }
 
-static int check_sizes(int64_t N, int32_t n_base, int64_t nf, const fredec_opts &o) {
+int check_sizes(int64_t N, int32_t n_base, int64_t nf, const fredec_opts &o) {
     if (n_base < 0 || n_base > FREDEC_MAX_NBASE) return fail(FREDEC_EINVAL, "n_base must be in 0..FREDEC_MAX_NBASE");
     const int pb = base_cols(n_base, o.trend);
     if (padded_cols(pb) > PMAX) return fail(FREDEC_EINVAL, "1 + trend + 2*n_base must not exceed 25");

@@ -148,6 +148,11 @@ int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nser
 int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,
                     cudaStream_t st);
 
+// Host-side validation shared by the single-series entry points (abi.cu):
+// options (defaults when o is NULL) and sizes; FREDEC_EINVAL with a message.
+int check_opts(const fredec_opts *o, fredec_opts *out);
+int check_sizes(int64_t N, int32_t n_base, int64_t nf, const fredec_opts &o);
+
 // Base column counts for n_base sinusoids and a time polynomial of degree npoly:
 // pb real columns, padded to the odd count the periodogram kernels are built for.
 inline int base_cols(int nb, int npoly) { return 1 + npoly + 2 * nb; }

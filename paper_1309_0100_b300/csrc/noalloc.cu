@@ -14,6 +14,7 @@
 // cleared by the call itself.  Calls whose work overlaps on the GPU (different
 // streams, or different host threads, without ordering) race on the array.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "fredec_internal.cuh"
@@ -26,6 +27,12 @@ int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
+
+// The fixed part of the scratch layout (descriptor, state, two status words,
+// each in its own 256-byte block), as stated in the header's size formula.
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+static_assert(round256(sizeof(SeriesDesc)) + round256(sizeof(SeriesState)) + 2 * 256 == 6912,
+              "the header's scratch-size formula must follow the layout");
 
 // Host code must not use this name as a device address: it is a host-side
 // stand-in.  The device address comes from cudaGetSymbolAddress below.
@@ -66,14 +73,17 @@ __global__ void noalloc_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state,
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
 }
 
-__global__ void noalloc_finish(const SeriesState *state, double *z, int64_t nf, double *info) {
+// info, and NaN in z when the base fit failed (singular base) or a bounded
+// device wait gave up (FREDEC_ETIMEOUT): a z computed from a half-staged tile
+// is never returned as if it were valid.
+__global__ void noalloc_finish(const SeriesState *state, const int32_t *err, double *z, int64_t nf, double *info) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (info && i == 0) {
         info[0] = state->chi2;
         info[1] = state->W;
         info[2] = state->tc;
     }
-    if (state->status != FREDEC_OK)
+    if (state->status != FREDEC_OK || *err != FREDEC_OK)
         for (int64_t j = i; j < nf; j += (int64_t)gridDim.x * blockDim.x) z[j] = NAN;
 }
 
@@ -87,19 +97,14 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
                                               const double *base_freqs, int32_t n_base, double f0, double df,
                                               int64_t nf, const fredec_opts *opts, double *z_out, double *info_out,
                                               void *stream) {
+    // every argument is checked before anything is enqueued
     fredec_opts o;
-    fredec_opts_init(&o);
-    if (opts) o = *opts;
-    if (o.precision != FREDEC_FP64 && o.precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
+    if (int rc = check_opts(opts, &o)) return rc;
     if (o.topk != 0) return fail(FREDEC_EINVAL, "the no-allocation entry point does not compute top-k (opts.topk must be 0)");
-    if (o.trend < 0 || o.trend > FREDEC_MAX_TREND || (o.statistic != FREDEC_Z_DIFF && o.statistic != FREDEC_Z_LOG))
-        return fail(FREDEC_EINVAL, "bad opts.trend / opts.statistic");
-    if (n_base < 0 || n_base > FREDEC_MAX_NBASE || padded_cols(base_cols(n_base, o.trend)) > PMAX ||
-        N < base_cols(n_base, o.trend) + 2 || N > (1LL << 31) - 1 || nf < 0 || nf > (1LL << 31) - 1 ||
-        (o.statistic == FREDEC_Z_LOG && N - 3LL * (n_base + 1) - 1 - o.trend <= 0))
-        return fail(FREDEC_EINVAL, "bad sizes (see fredec_periodogram_dev)");
+    if (int rc = check_sizes(N, n_base, nf, o)) return rc;
     if (!t || !y || !sigma || (n_base > 0 && !base_freqs) || (nf > 0 && !z_out))
         return fail(FREDEC_EINVAL, "null pointer argument");
+    if (!std::isfinite(f0) || !std::isfinite(df)) return fail(FREDEC_EINVAL, "f0 and df must be finite");
     const cudaStream_t st = (cudaStream_t)stream;
     const int pb = base_cols(n_base, o.trend), p = padded_cols(pb);
     const int prec = o.precision;
@@ -114,6 +119,16 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     const size_t o_rec64 = fix ? take(N * (size_t)recff_bytes(p)) : 0;
     const size_t o_fl = fix ? take(nf * 8 + 8) : 0;
     const size_t o_fc = take(4), o_err = take(4);
+    PgramShape shape;
+    if (o.fpt > 0 || o.warps > 0) {
+        shape = default_shape(prec, p, N, nf);
+        if (o.fpt > 0) shape.fpt = o.fpt;
+        if (o.warps > 0) shape.warps = o.warps;
+    } else if (!tuned_shape(prec, p, N, nf, &shape)) {
+        shape = default_shape(prec, p, N, nf);
+    }
+    if (!shape_supported(prec, p, shape.fpt) || shape.warps < 1 || shape.warps > 8)
+        return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, opts.fpt, opts.warps)");
     if (off > NOALLOC_SCRATCH_BYTES)
         return fail(FREDEC_EINVAL, "fredec_periodogram_noalloc_dev: this problem needs " + std::to_string(off) +
                                        " bytes of scratch, more than the fixed " +
@@ -157,14 +172,6 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
     pp.rec = rec;
     if (int rc = run_prep_records(pp, t, y, sigma, base_freqs, prec, rec64, st)) return rc;
     if (nf > 0) {
-        PgramShape shape;
-        if (o.fpt > 0 || o.warps > 0) {
-            shape = default_shape(prec, p, N, nf);
-            if (o.fpt > 0) shape.fpt = o.fpt;
-            if (o.warps > 0) shape.warps = o.warps;
-        } else if (!tuned_shape(prec, p, N, nf, &shape)) {
-            shape = default_shape(prec, p, N, nf);
-        }
         if (int rc = launch_pgram(prec, desc, state, rec, p, (int)N, nf, shape, tau, z_out, nullptr, flag_list,
                                   flag_count, err, st))
             return rc;
@@ -174,7 +181,7 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
         if (o.statistic == FREDEC_Z_LOG)
             if (int rc = launch_log_form(desc, state, 1, nf, z_out, st)) return rc;
     }
-    noalloc_finish<<<64, 256, 0, st>>>(state, z_out, nf, info_out);
+    noalloc_finish<<<64, 256, 0, st>>>(state, err, z_out, nf, info_out);
     FREDEC_CUDA_TRY(cudaGetLastError());
     return FREDEC_OK;
 }
