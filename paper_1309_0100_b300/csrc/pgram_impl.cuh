@@ -75,9 +75,11 @@ struct PgramLayout {
     static constexpr size_t TILE_BYTES = (size_t)TILE_POINTS * RB;
     static constexpr size_t OFF_TILES = OFF_TILES_BASE;
     static constexpr size_t OFF_RED = OFF_TILES + 2 * TILE_BYTES;
-    static __host__ __device__ size_t red_bytes(int nw) {
-        return (size_t)nw * Q * F * 32 * sizeof(typename AccT<PREC>::T);
-    }
+    // warp running sums: FP64 Q x F doubles per lane; mixed Q x ceil(F/2)
+    // float2 (frequency pairs) per lane
+    static constexpr int RED_PER_WARP = PREC == FREDEC_MIXED ? Q * ((F + 1) / 2) * 32 : Q * F * 32;
+    static constexpr size_t RED_ENTRY = PREC == FREDEC_MIXED ? sizeof(float2) : sizeof(double);
+    static __host__ __device__ size_t red_bytes(int nw) { return (size_t)nw * RED_PER_WARP * RED_ENTRY; }
     static __host__ __device__ size_t smem_bytes(int nw) { return OFF_RED + red_bytes(nw); }
 };
 
@@ -177,31 +179,61 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
     pt.wr = m.w;
 }
 
-template <int P>
-__device__ __forceinline__ void mixed_sums(float c, float s, const MixedPoint<P> &pt, float (&a)[2 * P + 4]) {
-    const float wc = pt.w * c;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        a[q] = fmaf(pt.u[q], c, a[q]);
-        a[P + q] = fmaf(pt.u[q], s, a[P + q]);
-    }
-    a[2 * P] = fmaf(pt.wr, c, a[2 * P]);
-    a[2 * P + 1] = fmaf(pt.wr, s, a[2 * P + 1]);
-    a[2 * P + 2] = fmaf(wc, c, a[2 * P + 2]);
-    a[2 * P + 3] = fmaf(wc, s, a[2 * P + 3]);
-}
-
-// F consecutive frequencies of one point: sums at (c, s), then one rotation
-// by e^{i 2 pi df t'} to the next frequency.
+// Mixed accumulators: the F frequencies of a thread in pairs (k, k+1), every
+// sum of a pair in one float2 register pair, so that one packed FP32
+// instruction (FFMA2: two FMAs of one warp instruction) updates the sums of
+// both frequencies.  With F odd the last pair's second half is not used.
 template <int P, int F>
-__device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, float (&acc)[F][2 * P + 4]) {
-    float c = pt.c, s = pt.s;
+struct MixedAcc {
+    static constexpr int Q = 2 * P + 4;
+    static constexpr int NPC = (F + 1) / 2;
+    float2 a[NPC][Q];
+};
+
+// F consecutive frequencies of one point, two at a time.  The pair starts at
+// (f_{j0}, f_{j0+1}) (the seed and one step of the rotation e^{i theta},
+// theta = 2 pi df t') and advances by e^{2 i theta}; per pair the 2P+4 sums
+//     <psi_k c>, <psi_k s>, <r c>, <r s>, <c^2>, <c s>
+// take one packed FMA each, and w c one packed multiply: (2P + 9) packed
+// instructions per two frequencies, the rotation included.
+template <int P, int F>
+__device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, MixedAcc<P, F> &A) {
+    constexpr int NPC = MixedAcc<P, F>::NPC;
+    float2 c = make_float2(pt.c, fmaf(pt.c, pt.cr, -pt.s * pt.sr));
+    float2 s = make_float2(pt.s, fmaf(pt.s, pt.cr, pt.c * pt.sr));
+    const float C2 = fmaf(pt.cr, pt.cr, -pt.sr * pt.sr), S2 = 2.0f * (pt.cr * pt.sr);
+    const float2 cc = make_float2(C2, C2), ss = make_float2(S2, S2), nss = make_float2(-S2, -S2);
+    const float2 w2 = make_float2(pt.w, pt.w), wr2 = make_float2(pt.wr, pt.wr);
 #pragma unroll
-    for (int k = 0; k < F; ++k) {
-        mixed_sums<P>(c, s, pt, acc[k]);
-        if (k + 1 < F) {
-            const float cn = fmaf(c, pt.cr, -s * pt.sr);
-            s = fmaf(s, pt.cr, c * pt.sr);
+    for (int kk = 0; kk < NPC; ++kk) {
+        float2 *a = A.a[kk];
+        if ((F & 1) && kk == NPC - 1) {   // the odd last frequency on its own
+            const float wc = pt.w * c.x;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                a[q].x = fmaf(pt.u[q], c.x, a[q].x);
+                a[P + q].x = fmaf(pt.u[q], s.x, a[P + q].x);
+            }
+            a[2 * P].x = fmaf(pt.wr, c.x, a[2 * P].x);
+            a[2 * P + 1].x = fmaf(pt.wr, s.x, a[2 * P + 1].x);
+            a[2 * P + 2].x = fmaf(wc, c.x, a[2 * P + 2].x);
+            a[2 * P + 3].x = fmaf(wc, s.x, a[2 * P + 3].x);
+        } else {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const float2 uu = make_float2(pt.u[q], pt.u[q]);
+                a[q] = __ffma2_rn(uu, c, a[q]);
+                a[P + q] = __ffma2_rn(uu, s, a[P + q]);
+            }
+            a[2 * P] = __ffma2_rn(wr2, c, a[2 * P]);
+            a[2 * P + 1] = __ffma2_rn(wr2, s, a[2 * P + 1]);
+            const float2 wc = __fmul2_rn(w2, c);
+            a[2 * P + 2] = __ffma2_rn(wc, c, a[2 * P + 2]);
+            a[2 * P + 3] = __ffma2_rn(wc, s, a[2 * P + 3]);
+        }
+        if (kk + 1 < NPC) {
+            const float2 cn = __ffma2_rn(s, nss, __fmul2_rn(c, cc));
+            s = __ffma2_rn(c, ss, __fmul2_rn(s, cc));
             c = cn;
         }
     }
@@ -214,7 +246,7 @@ __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, float 
 // last point, which is not accumulated.
 template <int P, int F, int SEED>
 __device__ __forceinline__ void mixed_run(const unsigned char *p, size_t stride, int m, const SeedTableF &tab,
-                                          uint32_t j0, float (&acc)[F][2 * P + 4]) {
+                                          uint32_t j0, MixedAcc<P, F> &acc) {
     auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(p + (size_t)i * stride); };
     MixedPoint<P> pa, pb;
     mixed_load<P, SEED>(rec(0), tab, j0, pa);
@@ -266,6 +298,69 @@ __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const
 }
 
 // ---------------------------------------------------------------------------
+// Per-thread sums of pgram_block and their second summation level, the
+// warp's running sums in shared memory (red): flush() adds all first-level
+// sums into them, flush_r() only <r c>, <r s>; read() gives warp w's running
+// sum q of the lane's frequency k (epilogue).
+template <int PREC, int P, int F> struct BlockSums;
+
+template <int P, int F> struct BlockSums<FREDEC_FP64, P, F> {
+    static constexpr int Q = 2 * P + 4;
+    using R = double;
+    double a[F][Q];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < F; ++k)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) a[k][q] = 0.0;
+    }
+    template <int Q0, int Q1>
+    __device__ __forceinline__ void flush_range(R *mine, int lane) {
+#pragma unroll
+        for (int k = 0; k < F; ++k)
+#pragma unroll
+            for (int q = Q0; q < Q1; ++q) {
+                mine[(q * F + k) * 32 + lane] += a[k][q];
+                a[k][q] = 0.0;
+            }
+    }
+    __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
+    __device__ __forceinline__ void flush_r(R *mine, int lane) { flush_range<2 * P, 2 * P + 2>(mine, lane); }
+    static __device__ __forceinline__ double read(const R *red, int w, int q, int k, int ln) {
+        return red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
+    }
+};
+
+template <int P, int F> struct BlockSums<FREDEC_MIXED, P, F> {
+    static constexpr int Q = 2 * P + 4, NPC = (F + 1) / 2;
+    using R = float2;
+    MixedAcc<P, F> acc;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < NPC; ++k)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) acc.a[k][q] = make_float2(0.0f, 0.0f);
+    }
+    template <int Q0, int Q1>
+    __device__ __forceinline__ void flush_range(R *mine, int lane) {
+#pragma unroll
+        for (int k = 0; k < NPC; ++k)
+#pragma unroll
+            for (int q = Q0; q < Q1; ++q) {
+                R &m = mine[(q * NPC + k) * 32 + lane];
+                m = __fadd2_rn(m, acc.a[k][q]);
+                acc.a[k][q] = make_float2(0.0f, 0.0f);
+            }
+    }
+    __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
+    __device__ __forceinline__ void flush_r(R *mine, int lane) { flush_range<2 * P, 2 * P + 2>(mine, lane); }
+    static __device__ __forceinline__ float read(const R *red, int w, int q, int k, int ln) {
+        const float2 v = red[((size_t)w * Q + q) * NPC * 32 + (k >> 1) * 32 + ln];
+        return (k & 1) ? v.y : v.x;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // One CTA-block of 32*F frequencies of one series.
 // use0/use1: per-buffer mbarrier phase counters, identical in all threads.
 
@@ -283,7 +378,9 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     unsigned char *tiles = smem + L::OFF_TILES;
-    T *red = reinterpret_cast<T *>(smem + L::OFF_RED);
+    using BS = BlockSums<PREC, P, F>;
+    using R = typename BS::R;
+    R *red = reinterpret_cast<R *>(smem + L::OFF_RED);
     const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + OFF_TABLE);
     const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + OFF_TABLE);
 
@@ -294,7 +391,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     const int ntiles = (N + TILE_POINTS - 1) / TILE_POINTS;
 
     __syncthreads();   // previous block's epilogue is done with red / tiles
-    for (int q = lane; q < Q * F * 32; q += 32) red[(size_t)warp * Q * F * 32 + q] = T(0);
+    for (int q = lane; q < L::RED_PER_WARP; q += 32) red[(size_t)warp * L::RED_PER_WARP + q] = R{};
     if (tid == 0) {
         for (int k = 0; k < 2 && k < ntiles; ++k) {
             const unsigned n = (unsigned)min(TILE_POINTS, N - k * TILE_POINTS);
@@ -303,35 +400,10 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         }
     }
 
-    T acc[F][Q];
-#pragma unroll
-    for (int k = 0; k < F; ++k)
-#pragma unroll
-        for (int q = 0; q < Q; ++q) acc[k][q] = T(0);
-
+    BS sums;
+    sums.zero();
+    R *mine = red + (size_t)warp * L::RED_PER_WARP;
     int since = 0;   // points in the current first-level block of this warp
-    // Second summation level: block sums are added into the warp's running
-    // sums in shared memory, all of them (flush) or only <r c>, <r s> (flush_r).
-    auto flush = [&]() {
-        T *mine = red + (size_t)warp * Q * F * 32;
-#pragma unroll
-        for (int k = 0; k < F; ++k)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                mine[(q * F + k) * 32 + lane] += acc[k][q];
-                acc[k][q] = T(0);
-            }
-    };
-    auto flush_r = [&]() {
-        T *mine = red + (size_t)warp * Q * F * 32;
-#pragma unroll
-        for (int k = 0; k < F; ++k)
-#pragma unroll
-            for (int q = 2 * P; q < 2 * P + 2; ++q) {
-                mine[(q * F + k) * 32 + lane] += acc[k][q];
-                acc[k][q] = T(0);
-            }
-    };
     int nblk = 0;   // first-level blocks since the last flush of all sums
 
     for (int tile = 0; tile < ntiles; ++tile) {
@@ -351,24 +423,24 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             for (int k = 0; k < cnt;) {
                 const int take = min(cnt - k, FLUSH_POINTS - since);
                 if (prm.seed_mode == 0)
-                    mixed_run<P, F, 0>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                    mixed_run<P, F, 0>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
                 else
-                    mixed_run<P, F, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                    mixed_run<P, F, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
                 k += take;
                 since += take;
                 if (since == FLUSH_POINTS) {
                     if (++nblk == FLUSH_BLOCKS_ALL) {
-                        flush();
+                        sums.flush(mine, lane);
                         nblk = 0;
                     } else {
-                        flush_r();
+                        sums.flush_r(mine, lane);
                     }
                     since = 0;
                 }
             }
         } else {
             for (int i = warp; i < n; i += nw)
-                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, acc);
+                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, sums.a);
         }
         __syncthreads();   // all warps are done with buffer b
         if (tid == 0 && tile + 2 < ntiles) {
@@ -377,7 +449,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             bulk_g2s(tiles + b * L::TILE_BYTES, src + (size_t)(tile + 2) * L::TILE_BYTES, nn * L::RB, &bars[b]);
         }
     }
-    flush();
+    sums.flush(mine, lane);
     __syncthreads();
 
     // Epilogue: combine the warps' partial sums in FP64 and solve per frequency.
@@ -399,7 +471,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             // warps' partial sums combined in the accumulation precision (a
             // handful of terms), then one conversion to FP64 per sum
             T sq = T(0);
-            for (int w = 0; w < nw; ++w) sq += red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
+            for (int w = 0; w < nw; ++w) sq += BS::read(red, w, q, k, ln);
             S[q] = (double)sq;
         }
         double vcc = 0.0, vcs = 0.0, vss = 0.0;
@@ -460,15 +532,18 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
     __syncthreads();
 }
 
-// Minimum resident CTAs of 256 threads asked from the compiler: 2 (at most 128
-// registers, 16 warps per SM) when the F x (2P+4) accumulators leave room for
-// it, else 1.
+// Register cap of the grid kernel (which may be launched with up to 256
+// threads): mixed kernels whose F x (2P+4) accumulators fit take 128
+// registers (16 warps per SM) up to 80 accumulators and 168 (three CTAs of
+// four warps) up to 120; the others, and the FP64 kernels, are not capped.
 template <int PREC, int P, int F>
-constexpr int pgram_minb() { return (PREC == FREDEC_MIXED && F * (2 * P + 4) <= 80) ? 2 : 1; }
+constexpr int pgram_maxreg() {
+    return PREC != FREDEC_MIXED ? 255 : F * (2 * P + 4) <= 80 ? 128 : F * (2 * P + 4) <= 120 ? 168 : 255;
+}
 
 // Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
 template <int PREC, int P, int F, bool MIRROR>
-__global__ void __launch_bounds__(256, pgram_minb<PREC, P, F>()) pgram_kernel(PgramParams prm) {
+__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F>())) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
     grid_dependency_wait();   // prep's records and state
