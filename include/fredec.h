@@ -184,6 +184,46 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
                                int32_t precision, double *dldy_out, void *stream);
 
 /*
+ * Frequency derivative of the residual periodogram on the uniform grid
+ * f_j = f0 + j*df, j < nf (Section 3: the derivatives of the model of Eq. Hn,
+ * built from the t-weighted averages of Eq. avrg1), for the local maxima of
+ * Section 2 (the local test z*_loc) refined straight off the periodogram:
+ *   z_out[j]    = z(f_j) as fredec_periodogram_dev computes it;
+ *   dzdf_out[j] = dz/df at f_j = sum_i w_i r_i 2 pi t_i (b_j cos 2 pi f_j t_i
+ *                 - a_j sin 2 pi f_j t_i), r the residual of the joint fit at
+ *                 f_j and (a_j, b_j) its coefficients of cos and sin (the
+ *                 envelope theorem: the linear parameters are optimal); f in
+ *                 cycles per unit of t.  dz/df does not depend on the time
+ *                 origin.  Where a trial column is dropped (the degenerate
+ *                 columns above) the coefficient of that column is 0.
+ *   info_out[3] (may be NULL) as in fredec_periodogram_ex.
+ * opts: precision and trend as for fredec_periodogram_dev; topk must be 0,
+ * statistic FREDEC_Z_DIFF, fpt 0 (or the one compiled value: 2 mixed, 1 FP64).
+ * One pass over the observations gives both outputs (2 (2p + 4) sums per
+ * trial frequency); in mixed precision the flagged bins are re-evaluated in
+ * float-float, dz/df included.
+ * All array arguments are device pointers (base_freqs too), stream-ordered on
+ * stream as the other _dev calls; z_out and dzdf_out are NaN when the base
+ * fit fails or a bounded device wait gives up (nothing is read back).
+ * Errors (nothing enqueued): FREDEC_EINVAL for the checks of
+ * fredec_periodogram_dev and the options above; FREDEC_ENOMEM, FREDEC_ECUDA.
+ */
+int fredec_periodogram_grad_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                                const double *base_freqs, int32_t n_base,
+                                double f0, double df, int64_t nf, const fredec_opts *opts,
+                                double *z_out, double *dzdf_out, double *info_out, void *stream);
+
+/*
+ * Host-pointer variant of fredec_periodogram_grad_dev (synchronous; values
+ * validated as for fredec_periodogram; FREDEC_ESINGULAR for a singular base
+ * model, FREDEC_ETIMEOUT when a bounded device wait gave up).
+ */
+int fredec_periodogram_grad(const double *t, const double *y, const double *sigma, int64_t N,
+                            const double *base_freqs, int32_t n_base,
+                            double f0, double df, int64_t nf, const fredec_opts *opts,
+                            double *z_out, double *dzdf_out, double *info_out);
+
+/*
  * No-allocation variant of fredec_periodogram_dev (z and info only; the paper
  * has no counterpart).  For callers that cannot allocate device memory when
  * they call -- applications whose device memory is reserved up front by their
@@ -202,8 +242,8 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
  *   - Scratch needed, in bytes, with p = 1 + trend + 2*n_base rounded up to
  *     an odd number, c = ceil(N/32) and R(x) = x rounded up to a multiple of
  *     256:  6912 + R(4c) + R(8c(p(p+1)/2 + p + 4)) + R(8pN) + R(rN), with
- *     r = 8(6 + 2 ceil(p/2)) for FREDEC_FP64 and r = 4(8 + 4 ceil(p/4)) for
- *     FREDEC_MIXED; FREDEC_MIXED with re-evaluation (flag_tau >= 0) adds
+ *     r = 8(6 + 2 ceil(p/2)) for FREDEC_FP64 and r = 4(8 + 4 ceil((p + 2)/4))
+ *     for FREDEC_MIXED; FREDEC_MIXED with re-evaluation (flag_tau >= 0) adds
  *     R(16 ceil((8 + 2p)/4) N) + R(8 nf + 8).  A problem that does not fit
  *     in 16 MiB is rejected with FREDEC_EINVAL and a message giving the
  *     required and available byte counts.
@@ -248,13 +288,33 @@ int fredec_pool_subtuples_eval(const double *t, const double *y, const double *s
 
 /*
  * z and its gradient with respect to the tuple frequencies (CSR layout as in
- * fredec_tuple_eval):  dz/df_k = sum_i w_i r_i 2 pi t_i (-a_k sin + b_k cos),
+ * fredec_tuple_eval; Section 3, Eq. lsqf):
+ *     dz/df_k = sum_i w_i r_i 2 pi t_i (-a_k sin + b_k cos),
  * r the residual of the tuple's fit.  dz_df_out has the layout of tuple_freqs.
- * precision selects FP64 or FP32-accumulated sums (solves always FP64).
+ * precision: FREDEC_FP64 sums, or FREDEC_MIXED: the sums in float-float
+ * arithmetic on the FP32 pipe (pairs of FP32 numbers, compensated; FP64-grade),
+ * since plain FP32 Gram sums leave the gradient near 1e-4 relative.  Solves
+ * are always FP64.  Host pointers, synchronous; FREDEC_ESINGULAR when a
+ * tuple's normal matrix is singular (a repeated frequency).
  */
 int fredec_tuple_grad(const double *t, const double *y, const double *sigma, int64_t N,
                       const double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
                       int32_t precision, double *z_out, double *dz_df_out);
+
+/*
+ * Device-pointer, stream-ordered variant of fredec_tuple_grad (the route of
+ * the differentiable tuple statistic): t, y, sigma, tuple_freqs, z_out and
+ * dz_df_out are device pointers; tuple_offsets (n_tuples + 1 entries) is a
+ * host array, since it sizes the launch.  Sizes are checked on the host,
+ * values are not read back: a tuple whose normal matrix is singular gets NaN
+ * in z_out and in its dz_df_out entries.  Scratch from the stream-ordered
+ * allocator on stream (cudaStream_t as void*; NULL: the legacy default
+ * stream).  Errors (nothing enqueued): FREDEC_EINVAL, FREDEC_ENOMEM,
+ * FREDEC_ECUDA.
+ */
+int fredec_tuple_grad_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                          const double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
+                          int32_t precision, double *z_out, double *dz_df_out, void *stream);
 
 /*
  * Local refinement of every tuple (Section 3): up to max_iter Gauss-Newton

@@ -18,8 +18,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev",
-    "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad",
+    "FredecError", "FP64", "MIXED", "lib", "version", "periodogram", "periodogram_dev", "periodogram_grad",
+    "periodogram_grad_dev",
+    "periodogram_vjp", "periodogram_vjp_dev", "tuple_eval", "pool_subtuples_eval", "tuple_grad", "tuple_grad_dev",
     "tuple_refine", "pool_refine", "periodogram_batch", "BatchPlan", "tune", "profile_events", "pipe_peaks", "LIB_PATH",
     "fap_bound", "fap_threshold", "effective_bandwidth", "cascade", "scan", "decompose", "Z_DIFF", "Z_LOG",
 ]
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "fredec_tuple_eval": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, _c_dp, _c_dp]),
         "fredec_pool_subtuples_eval": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, _c_dp]),
         "fredec_tuple_grad": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, i32, _c_dp, _c_dp]),
+        "fredec_tuple_grad_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, _c_i64p, i64, i32, _vp, _vp, _vp]),
         "fredec_tuple_refine": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, _c_i64p, i64, i32, d, i32, _c_dp,
                                                _c_i32p]),
         "fredec_periodogram_batch": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, _c_i64p, i64, _c_dp, _c_i64p, _c_dp, _c_dp,
@@ -113,6 +115,10 @@ def lib() -> ctypes.CDLL:
         "fredec_selftest_ff_sincos": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), i64, _c_dp]),
         "fredec_periodogram_noalloc_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
                                                           ctypes.POINTER(Opts), _vp, _vp, _vp]),
+        "fredec_periodogram_grad_dev": (ctypes.c_int, [_vp, _vp, _vp, i64, _vp, i32, d, d, i64,
+                                                       ctypes.POINTER(Opts), _vp, _vp, _vp, _vp]),
+        "fredec_periodogram_grad": (ctypes.c_int, [_c_dp, _c_dp, _c_dp, i64, _c_dp, i32, d, d, i64,
+                                                   ctypes.POINTER(Opts), _c_dp, _c_dp, _c_dp]),
         "fredec_fap_bound": (d, [i32, d, d, d]),
         "fredec_fap_threshold": (d, [i32, d, d, d]),
         "fredec_effective_bandwidth": (ctypes.c_int, [_c_dp, _c_dp, i64, d, _c_dp]),
@@ -266,6 +272,42 @@ def periodogram_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, p
     return res
 
 
+def periodogram_grad(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, precision=FP64, trend=0,
+                     want_info=False):
+    """z and dz/df on the uniform grid f_j = f0 + j df (host arrays in and
+    out).  Returns (z, dzdf) or (z, dzdf, info)."""
+    t, y, sigma = map(_f64, (t, y, sigma))
+    base = _f64(base_freqs)
+    z = np.empty(max(int(nf), 1))
+    g = np.empty(max(int(nf), 1))
+    info = np.empty(3)
+    o = _opts(precision, 0, 0, 0, 0.0, trend, Z_DIFF)
+    _check(lib().fredec_periodogram_grad(_p(t), _p(y), _p(sigma), t.size, _p(base) if base.size else None,
+                                         base.size, float(f0), float(df), int(nf), ctypes.byref(o), _p(z), _p(g),
+                                         _p(info)))
+    return (z[:nf], g[:nf], info) if want_info else (z[:nf], g[:nf])
+
+
+def periodogram_grad_dev(t, y, sigma, base_freqs, f0: float, df: float, nf: int, *, precision=FP64, trend=0,
+                         warps=0, out=None, out_grad=None, stream=None):
+    """Device path of periodogram_grad (contiguous float64 CUDA tensors, torch's
+    current stream or ``stream``).  Returns dict with z, dzdf and info."""
+    import torch
+    dev = t.device
+    for x in (t, y, sigma, base_freqs):
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("periodogram_grad_dev wants contiguous float64 CUDA tensors")
+    z = out if out is not None else torch.empty(nf, dtype=torch.float64, device=dev)
+    g = out_grad if out_grad is not None else torch.empty(nf, dtype=torch.float64, device=dev)
+    info = torch.empty(3, dtype=torch.float64, device=dev)
+    o = _opts(precision, 0, 0, warps, 0.0, trend, Z_DIFF)
+    _check(lib().fredec_periodogram_grad_dev(_dptr(t), _dptr(y), _dptr(sigma), t.numel(),
+                                             _dptr(base_freqs) if base_freqs.numel() else None, base_freqs.numel(),
+                                             float(f0), float(df), int(nf), ctypes.byref(o), _dptr(z), _dptr(g),
+                                             _dptr(info), _stream(torch, stream)))
+    return {"z": z, "dzdf": g, "info": info}
+
+
 def topk_dev(z, k: int, *, stream=None):
     """Top-k local maxima of a contiguous float64 CUDA tensor z (device kernels;
     ranks by decreasing z, ties to the lower index, -1 where fewer exist)."""
@@ -336,6 +378,25 @@ def tuple_grad(t, y, sigma, tuples, *, precision=FP64):
     _check(lib().fredec_tuple_grad(_p(t), _p(y), _p(sigma), t.size, _p(flat), _p(off), len(tuples),
                                    _prec(precision), _p(z), _p(g)))
     return z[:len(tuples)], g[:int(off[-1])]
+
+
+def tuple_grad_dev(t, y, sigma, freqs, offsets, *, precision=FP64, stream=None):
+    """Device path of tuple_grad: t, y, sigma, freqs contiguous float64 CUDA
+    tensors (freqs flattened in CSR order), offsets a host int64 array or CPU
+    tensor of n_tuples + 1 entries.  Returns (z, dzdf) CUDA tensors, enqueued
+    on torch's current stream (or ``stream``)."""
+    import torch
+    for x in (t, y, sigma, freqs):
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("tuple_grad_dev wants contiguous float64 CUDA tensors")
+    off = _i64(offsets.cpu().numpy() if hasattr(offsets, "cpu") else offsets)
+    n = off.size - 1
+    z = torch.empty(max(n, 1), dtype=torch.float64, device=t.device)
+    g = torch.empty(max(freqs.numel(), 1), dtype=torch.float64, device=t.device)
+    _check(lib().fredec_tuple_grad_dev(_dptr(t), _dptr(y), _dptr(sigma), t.numel(),
+                                       _dptr(freqs) if freqs.numel() else None, _p(off), n, _prec(precision),
+                                       _dptr(z), _dptr(g), _stream(torch, stream)))
+    return z[:n], g[:freqs.numel()]
 
 
 def tuple_refine(t, y, sigma, tuples, *, max_iter=20, tol=1e-9, precision=FP64):

@@ -119,8 +119,6 @@ struct SingleWork {
     int64_t nchunks;
 };
 
-int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
-                     int precision, void *rec64, cudaStream_t st);
 
 // The device pipeline for one series on a uniform grid.  All pointers device
 // (z_mirror: optional second destination of z, e.g. page-locked host memory).
@@ -201,7 +199,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
         // the NaN fill of a failed prep rides on the re-evaluation launch when there is one
         if (fix) {
             if (int rc = launch_fixup_bins(w.desc, w.state, 1, w.rec64, p, w.flag_list, w.flag_count, nf, z, coef,
-                                           st, z_mirror, nf))
+                                           st, z_mirror, nf, nullptr, w.err))
                 return rc;
         } else {
             nan_fill_if_failed<<<64, 256, 0, st>>>(w.state, z, nf);
@@ -344,6 +342,7 @@ static int finish_host(cudaStream_t st, const SeriesState *state, const int32_t 
     if (status == FREDEC_ESINGULAR)
         return fail(FREDEC_ESINGULAR, "the base model's normal matrix is singular (duplicate base frequencies?)");
     if (e == FREDEC_ETIMEOUT) return fail(FREDEC_ETIMEOUT, "a bounded device wait gave up");
+    if (e != FREDEC_OK) return fail(FREDEC_ECUDA, "a device-side index check failed (the access was skipped)");
     return FREDEC_OK;
 }
 
@@ -490,6 +489,8 @@ int fredec_periodogram_ex(const double *t, const double *y, const double *sigma,
             if (words[0] == FREDEC_ESINGULAR)
                 return fail(FREDEC_ESINGULAR, "the base model's normal matrix is singular (duplicate base frequencies?)");
             if (words[1] == FREDEC_ETIMEOUT) return fail(FREDEC_ETIMEOUT, "a bounded device wait gave up");
+            if (words[1] != FREDEC_OK)
+                return fail(FREDEC_ECUDA, "a device-side index check failed (the access was skipped)");
         }
         const bool copies = (nf && !(uniform && z_mirror)) || (coef_out && nf);
         if (nf && !(uniform && z_mirror)) FREDEC_CUDA_TRY(cudaMemcpyAsync(z_out, dz, nf * 8, cudaMemcpyDeviceToHost, st));

@@ -16,8 +16,6 @@
 
 namespace fredec {
 
-int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
-                     int precision, void *rec64, cudaStream_t st);
 int launch_batch_p5(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
 int launch_batch_p15(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
 int launch_batch_p25(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
@@ -80,6 +78,7 @@ struct fredec_batch_plan {
         bp.prm.flag_tau = fix ? tau : -1.0;
         bp.prm.flag_list = fix ? flag_list : nullptr;
         bp.prm.flag_count = flag_count;
+        bp.prm.flag_cap = fix ? z_total : 0;
         bp.prm.err = err;
         bp.prm.seed_mode = seed_mode();
         bp.items = items;
@@ -96,7 +95,8 @@ struct fredec_batch_plan {
         if (rc) return rc;
         if (fix)
             for (int p : p_present)
-                if (int rc = launch_fixup_bins(desc, state, S, rec64, p, flag_list, flag_count, z_total, z, nullptr, st))
+                if (int rc = launch_fixup_bins(desc, state, S, rec64, p, flag_list, flag_count, z_total, z, nullptr, st,
+                                               nullptr, 0, nullptr, err))
                     return rc;
         if (statistic == FREDEC_Z_LOG)
             if (int rc = launch_log_form(desc, state, S, nf_max, z, st)) return rc;

@@ -29,11 +29,16 @@ struct FixupParams {
     double *z, *coef;
     double *z_mirror;            // optional second destination of z
     int64_t nan_nf;              // > 0 (single series): if its prep failed, z[0..nan_nf) <- NaN instead
+    double *dzdf;                // two-set records: dz/df of the re-evaluated bins
+    int64_t cap;                 // entries of list, and the number of z values
+    int32_t *err;                // optional: FREDEC_EINVAL when a listed index is out of range
 };
 
-template <int P>
+// NSET = 2: the records carry the t'-weighted values as well; the kernel
+// re-evaluates dz/df of the bin with the same float-float sums.
+template <int P, int NSET>
 __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
-    constexpr int Q = 2 * P + 4;
+    constexpr int Q0 = 2 * P + 4, Q = NSET * Q0 + (NSET == 2 ? 1 : 0);   // + <t'> with two sets
     __shared__ SeedTableFF tab;
     __shared__ ff red[FX_THREADS / 32][Q];
     __shared__ double S[Q];
@@ -44,7 +49,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
             prm.z[j] = NAN;
         return;
     }
-    const int32_t n = *prm.count;
+    const int32_t n = (int32_t)min((int64_t)*prm.count, prm.cap);
     if ((int32_t)blockIdx.x >= n) return;   // no flagged bin for this CTA
     fill_seed_table_ff(tab);
     __syncthreads();
@@ -64,9 +69,13 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
         const SeriesState &st = prm.state[s];
         if (d.p != P) continue;   // batches: another launch handles this base size
         const int64_t j = g - d.z_off;
+        if (g < 0 || g >= prm.cap || j < 0 || j >= d.nf) {   // a listed index outside the outputs
+            if (threadIdx.x == 0 && prm.err) atomicExch(prm.err, FREDEC_EINVAL);
+            continue;
+        }
         ff_acc fa[Q];
         const uint32_t *R0 = reinterpret_cast<const uint32_t *>(prm.rec64 + d.rec64_off);
-        constexpr int RW = recff_words(P);
+        constexpr int RW = recff_words(P, NSET);
         for (int i = threadIdx.x; i < d.N; i += FX_THREADS) {
             const uint32_t *R = R0 + (int64_t)i * RW;
             const uint4 h = *reinterpret_cast<const uint4 *>(R);
@@ -86,6 +95,22 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
             fa[2 * P + 1].add_prod(wr, sn);
             fa[2 * P + 2].add_prod(wc, cs);
             fa[2 * P + 3].add_prod(wc, sn);
+            if constexpr (NSET == 2) {   // the t'-weighted set: w t', w r t', w psi_k t'
+                const float *R2 = Rf + recff_words(P);
+                const ff wt = {R2[0], R2[1]}, wrt = {R2[2], R2[3]};
+                const ff wtc = ff_mul(wt, cs);
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const ff ut = {R2[4 + 2 * q], R2[5 + 2 * q]};
+                    fa[Q0 + q].add_prod(ut, cs);
+                    fa[Q0 + P + q].add_prod(ut, sn);
+                }
+                fa[Q0 + 2 * P].add_prod(wrt, cs);
+                fa[Q0 + 2 * P + 1].add_prod(wrt, sn);
+                fa[Q0 + 2 * P + 2].add_prod(wtc, cs);
+                fa[Q0 + 2 * P + 3].add_prod(wtc, sn);
+                fa[2 * Q0].add_prod(wt, {1.0f, 0.0f});   // <t'>
+            }
         }
         // the threads' double-float sums combined in float-float (warp
         // butterflies, then over the warps in a fixed order), one conversion
@@ -115,6 +140,7 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
             const double CC = S[2 * P + 2];
             double a, b, ratio;
             prm.z[g] = solve2(CC, S[2 * P + 3], st.W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &b, &ratio);
+            if constexpr (NSET == 2) prm.dzdf[g] = dz_df<P>(S, S + Q0, S[2 * Q0], a, b);
             if (prm.z_mirror) prm.z_mirror[g] = prm.z[g];
             if (prm.coef) {
                 prm.coef[2 * g] = a;
@@ -125,9 +151,9 @@ __global__ void __launch_bounds__(FX_THREADS) fixup_kernel(FixupParams prm) {
     }
 }
 
-template <int P>
+template <int P, int NSET>
 void launch_fx(const FixupParams &prm, int grid, cudaStream_t st) {
-    launch_pdl(fixup_kernel<P>, dim3(grid), dim3(FX_THREADS), 0, st, prm);
+    launch_pdl(fixup_kernel<P, NSET>, dim3(grid), dim3(FX_THREADS), 0, st, prm);
 }
 
 }  // namespace
@@ -165,15 +191,15 @@ int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nserie
 
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st, double *z_mirror, int64_t nan_nf) {
+                      cudaStream_t st, double *z_mirror, int64_t nan_nf, double *dzdf, int32_t *err) {
     FixupParams prm{desc, state, nseries, (const unsigned char *)rec64, list, count, z, coef, z_mirror,
-                    nseries == 1 ? nan_nf : 0};
+                    nseries == 1 ? nan_nf : 0, dzdf, max_items, err};
     // one wave for up to 8 bins per SM (8 CTAs of 256 threads are resident per
     // SM): the flagged count is known only on the device, and CTAs beyond it
     // exit at once
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(max_items, 1), 8LL * sm_count());
     switch (p) {
-#define C(P) case P: launch_fx<P>(prm, grid, st); break;
+#define C(P) case P: if (dzdf) launch_fx<P, 2>(prm, grid, st); else launch_fx<P, 1>(prm, grid, st); break;
         C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
         default: return fail(FREDEC_EINVAL, "unsupported base size");

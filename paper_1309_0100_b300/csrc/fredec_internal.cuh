@@ -15,24 +15,37 @@ namespace fredec {
 constexpr int PMAX = 2 * FREDEC_MAX_NBASE + 1;      // base columns (constant + cos/sin pairs)
 constexpr int NTRI = PMAX * (PMAX + 1) / 2;         // packed lower triangle
 constexpr int PREP_THREADS = 32;                     // one point per thread, one warp per prep chunk
-constexpr int TILE_POINTS = 128;                     // observation records per smem tile
+constexpr int TILE_POINTS = 128;                     // observation records per smem tile (at most)
 constexpr double DROP2 = 1e-14;                      // squared column-drop ratio (1e-7)^2
 
 // Record widths.  Mixed records (32-bit words):
 //   [0..1] phase A = frac(f0 t') as u64 turns, [2..3] phase B = frac(df t'),
-//   [4] cos(2 pi df t'), [5] sin(2 pi df t'), [6] w, [7] w r, [8..8+p) w psi_k.
+//   [4] cos(2 pi df t'), [5] sin(2 pi df t'), [6] cos(4 pi df t'),
+//   [7] sin(4 pi df t') (the two-step rotation, rounded once from FP64),
+//   then the set [w, w r, w psi_k (p)] padded to a multiple of 4 words.
 // FP64 records (64-bit words): [0] A, [1] B, [2] cos, [3] sin, [4] w, [5] w r,
 //   [6..6+p) w psi_k.  Both are padded to a multiple of 16 bytes.
-__host__ __device__ constexpr int rec32_words(int p) { return 8 + 4 * ((p + 3) / 4); }
-__host__ __device__ constexpr int rec64_words(int p) { return 6 + 2 * ((p + 1) / 2); }
-__host__ __device__ constexpr int rec_bytes(int p, int prec) {
-    return prec == FREDEC_MIXED ? 4 * rec32_words(p) : 8 * rec64_words(p);
+// Records with a second set (nset = 2, the periodogram's frequency derivative)
+// append the t'-weighted values of the weighted ones, padded the same way:
+//   mixed [w t', w r t', w psi_k t' (p)]; FP64 [w t', w r t', w psi_k t' (p)].
+__host__ __device__ constexpr int rec32_set_words(int p) { return 4 * ((p + 2 + 3) / 4); }
+__host__ __device__ constexpr int rec64_set_words(int p) { return 2 * ((p + 1) / 2); }
+__host__ __device__ constexpr int rec32_words(int p, int nset = 1) { return 8 + nset * rec32_set_words(p); }
+__host__ __device__ constexpr int rec64_words(int p, int nset = 1) {
+    return 6 + rec64_set_words(p) + (nset == 2 ? 2 + rec64_set_words(p) : 0);
+}
+__host__ __device__ constexpr int rec_bytes(int p, int prec, int nset = 1) {
+    return prec == FREDEC_MIXED ? 4 * rec32_words(p, nset) : 8 * rec64_words(p, nset);
 }
 // Float-float records for the re-evaluation of flagged mixed bins (32-bit
 // words): [0..1] phase A, [2..3] phase B (u64), then hi/lo pairs of w, w r and
-// w psi_k; padded to 16 bytes.
-__host__ __device__ constexpr int recff_words(int p) { return 4 * ((8 + 2 * p + 3) / 4); }
-__host__ __device__ constexpr int recff_bytes(int p) { return 4 * recff_words(p); }
+// w psi_k; padded to 16 bytes.  With nset = 2 hi/lo pairs of w t', w r t' and
+// w psi_k t' follow, padded the same way.
+__host__ __device__ constexpr int recff_set_words(int p) { return 4 * ((4 + 2 * p + 3) / 4); }
+__host__ __device__ constexpr int recff_words(int p, int nset = 1) {
+    return 4 * ((8 + 2 * p + 3) / 4) + (nset == 2 ? recff_set_words(p) : 0);
+}
+__host__ __device__ constexpr int recff_bytes(int p, int nset = 1) { return 4 * recff_words(p, nset); }
 
 // Per-series description (host-built, device-resident).
 struct SeriesDesc {
@@ -111,6 +124,10 @@ struct PrepPlan {
     void *rec = nullptr;             // device records
 };
 int prep_npart(int pmax);
+// The prep kernels and the per-point records (rec, and float-float records in
+// rec64 when given); nset = 2 adds the t'-weighted values to every record.
+int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
+                     const double *base, int precision, void *rec64, cudaStream_t st, int nset = 1);
 // Enqueue the prep kernels (uniform grids).  Writes state[] and records.
 int launch_prep(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
                 const double *base, int precision, cudaStream_t st);
@@ -140,9 +157,14 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
 // FP64-grade re-evaluation of the listed bins (fixup.cu); z_mirror as above.
 // nan_nf > 0 (one series): if the series' prep failed, the launch sets
 // z[0..nan_nf) to NaN instead (the NaN fill of a failed call).
+// dzdf (optional, single series): the records carry the t'-weighted set
+// (nset = 2) and dz/df of each re-evaluated bin is written there too.
+// max_items: entries of list and of z; err (optional) receives FREDEC_EINVAL
+// when a listed index lies outside them (the bin is skipped).
 int launch_fixup_bins(const SeriesDesc *desc, const SeriesState *state, int nseries, const void *rec64, int p,
                       const int64_t *list, const int32_t *count, int64_t max_items, double *z, double *coef,
-                      cudaStream_t st, double *z_mirror = nullptr, int64_t nan_nf = 0);
+                      cudaStream_t st, double *z_mirror = nullptr, int64_t nan_nf = 0, double *dzdf = nullptr,
+                      int32_t *err = nullptr);
 
 // Log form of the statistic (Eq. zpowrel) in place, per series (fixup.cu).
 int launch_log_form(const SeriesDesc *desc, const SeriesState *state, int nseries, int64_t nf_max, double *z,

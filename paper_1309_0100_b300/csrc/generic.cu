@@ -9,8 +9,6 @@
 
 namespace fredec {
 
-int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
-                     int precision, void *rec64, cudaStream_t st);
 
 namespace {
 

@@ -21,8 +21,6 @@
 
 namespace fredec {
 
-int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma, const double *base,
-                     int precision, void *rec64, cudaStream_t st);
 
 namespace {
 
@@ -176,7 +174,8 @@ extern "C" int fredec_periodogram_noalloc_dev(const double *t, const double *y, 
                                   flag_count, err, st))
             return rc;
         if (fix)
-            if (int rc = launch_fixup_bins(desc, state, 1, rec64, p, flag_list, flag_count, nf, z_out, nullptr, st))
+            if (int rc = launch_fixup_bins(desc, state, 1, rec64, p, flag_list, flag_count, nf, z_out, nullptr, st,
+                                           nullptr, 0, nullptr, err))
                 return rc;
         if (o.statistic == FREDEC_Z_LOG)
             if (int rc = launch_log_form(desc, state, 1, nf, z_out, st)) return rc;

@@ -136,6 +136,7 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
     prm.coef = coef;
     prm.flag_tau = (precision == FREDEC_MIXED && flag_list) ? flag_tau : -1.0;
     prm.flag_list = flag_list;
+    prm.flag_cap = flag_list ? nf : 0;
     prm.flag_count = flag_count;
     prm.err = err;
     prm.seed_mode = seed_mode();

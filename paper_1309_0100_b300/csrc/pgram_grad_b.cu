@@ -1,0 +1,61 @@
+// Instantiations of the two-set periodogram kernels (z and dz/df per trial
+// frequency) for base sizes 13, 15, 17, 19, 21, 23, 25; dispatched by grad.cu.
+#include "pgram_impl.cuh"
+
+namespace fredec {
+
+int launch_pgram_grad_b(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    switch (p) {
+        case 13:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 13, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 13, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 15:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 15, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 15, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 17:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 17, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 17, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 19:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 19, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 19, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 21:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 21, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 21, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 23:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 23, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 23, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+        case 25:
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 25, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+                                        : launch_pgram_t<FREDEC_FP64, 25, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
+    }
+    return -2;
+}
+
+size_t smem_pgram_grad_b(int prec, int p, int warps) {
+    switch (p) {
+        case 13:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 13, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 13, GRAD_FPT_FP64, 2>(warps);
+        case 15:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 15, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 15, GRAD_FPT_FP64, 2>(warps);
+        case 17:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 17, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 17, GRAD_FPT_FP64, 2>(warps);
+        case 19:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 19, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 19, GRAD_FPT_FP64, 2>(warps);
+        case 21:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 21, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 21, GRAD_FPT_FP64, 2>(warps);
+        case 23:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 23, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 23, GRAD_FPT_FP64, 2>(warps);
+        case 25:
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 25, GRAD_FPT_MIXED, 2>(warps)
+                                        : pgram_smem_t<FREDEC_FP64, 25, GRAD_FPT_FP64, 2>(warps);
+    }
+    return 0;
+}
+
+}  // namespace fredec

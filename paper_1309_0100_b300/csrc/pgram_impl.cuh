@@ -42,6 +42,11 @@ namespace fredec {
 constexpr int FLUSH_POINTS = 32;
 constexpr int FLUSH_BLOCKS_ALL = 8;
 
+// Frequencies per thread of the two-set kernels (z and dz/df): one frequency
+// pair (mixed) or one frequency (FP64) keeps the 2 (2P+4) sums in registers.
+constexpr int GRAD_FPT_MIXED = 2;
+constexpr int GRAD_FPT_FP64 = 1;
+
 struct PgramParams {
     const SeriesDesc *desc;
     const SeriesState *state;
@@ -52,7 +57,10 @@ struct PgramParams {
     double flag_tau;            // mixed: re-evaluation threshold (< 0: never)
     int64_t *flag_list;         // mixed: global z indices of bins to re-evaluate (float-float)
     int32_t *flag_count;
+    int64_t flag_cap;           // entries of flag_list (a full list records FREDEC_EINVAL in err)
     int32_t *err;               // FREDEC_ETIMEOUT on a bounded-wait timeout
+    double *dzdf;               // two-set kernels: dz/df per bin (same offsets as z)
+    const double *wt_sum;       // two-set kernels: <t'> = sum of the records' w t' (one series)
     int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
 };
 
@@ -68,11 +76,17 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 constexpr size_t OFF_TABLE = 128;
 constexpr size_t OFF_TILES_BASE = OFF_TABLE + sizeof(SeedTable);
 
-template <int PREC, int P, int F>
+// NSET = 2: every record carries a second set of weighted values, the
+// t'-weighted ones, and the kernel accumulates 2 (2P+4) sums per frequency.
+template <int PREC, int P, int F, int NSET = 1>
 struct PgramLayout {
-    static constexpr int Q = 2 * P + 4;
-    static constexpr int RB = rec_bytes(P, PREC);
-    static constexpr size_t TILE_BYTES = (size_t)TILE_POINTS * RB;
+    static constexpr int Q = NSET * (2 * P + 4);
+    static constexpr int RB = rec_bytes(P, PREC, NSET);
+    // records per tile: TILE_POINTS, or fewer for records above 64 bytes so
+    // that the two tiles stay within 16 KB (with the F = 10 running sums of
+    // P = 7, two CTAs then still fit an SM's shared memory)
+    static constexpr int TP = RB <= 64 ? TILE_POINTS : (8192 / RB) / 8 * 8;
+    static constexpr size_t TILE_BYTES = (size_t)TP * RB;
     static constexpr size_t OFF_TILES = OFF_TILES_BASE;
     static constexpr size_t OFF_RED = OFF_TILES + 2 * TILE_BYTES;
     // warp running sums: FP64 Q x F doubles per lane; mixed Q x ceil(F/2)
@@ -140,29 +154,66 @@ __device__ __forceinline__ bool solve2_fast(double CC, double CS, double SS, dou
     return true;
 }
 
+// dz/df of the residual periodogram at one trial frequency from its two sets
+// of sums and its joint-fit coefficients (a, b) of c and s.  By the envelope
+// theorem (the linear parameters are optimal) dz/df = <r_f dmu/df> with
+// dmu/df = 2 pi t' (b c - a s) and r_f the residual of the joint fit,
+// r_f = r - a c~ - b s~, c~ = c - sum_k <psi_k c> psi_k (the trial columns
+// projected off the orthonormal base; Section 3, the derivatives of Eq. Hn
+// through the t-weighted averages of Eq. avrg1).  S0: <psi_k c>, <psi_k s>,
+// <r c>, <r s>, <c^2>, <c s>; S1: the same sums weighted by t';
+// wt = <t'>, so that <t' s^2> = <t'> - <t' c^2>.
+template <int P>
+__device__ __forceinline__ double dz_df(const double *S0, const double *S1, double wt, double a, double b) {
+    double cc = 0.0, sc = 0.0, cs = 0.0, ss = 0.0;   // sum_k <psi_k x> <psi_k t' y>
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        cc = fma(S0[q], S1[q], cc);
+        sc = fma(S0[P + q], S1[q], sc);
+        cs = fma(S0[q], S1[P + q], cs);
+        ss = fma(S0[P + q], S1[P + q], ss);
+    }
+    const double tcc = S1[2 * P + 2], tcs = S1[2 * P + 3], tss = wt - tcc;
+    const double rtc = S1[2 * P] - a * (tcc - cc) - b * (tcs - sc);   // <r_f t' c>
+    const double rts = S1[2 * P + 1] - a * (tcs - cs) - b * (tss - ss);   // <r_f t' s>
+    return TWO_PI_D * (b * rtc - a * rts);
+}
+
 // ---------------------------------------------------------------------------
 // Inner loops: one observation record against this thread's F frequencies.
 
 // One observation record, ready for the F-step loop: the seed cos/sin at the
-// thread's first frequency, the rotation, and the weighted values.
-template <int P>
+// thread's first frequency, the one- and two-step rotations, and the weighted
+// values.  With NSET = 2 the second set holds the t'-weighted values w t',
+// w r t', w psi_k t'.
+template <int P, int NSET = 1>
 struct MixedPoint {
-    float c, s, cr, sr, w, wr;
-    float u[4 * ((P + 3) / 4)];
+    float c, s, cr, sr, c2, s2;
+    float w[NSET], wr[NSET];
+    float u[NSET][4 * ((P + 2 + 3) / 4) - 2];
 };
 
-template <int P, int SEED>
+template <int P, int SEED, int NSET = 1>
 __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, uint32_t j0,
-                                           MixedPoint<P> &pt) {
+                                           MixedPoint<P, NSET> &pt) {
+    constexpr int C4 = (P + 2 + 3) / 4;   // float4s of one set [w, w r, w psi_k]
     const uint4 h = r4[0];
     const float4 m = *reinterpret_cast<const float4 *>(r4 + 1);
 #pragma unroll
-    for (int q4 = 0; q4 < (P + 3) / 4; ++q4) {
-        const float4 v = reinterpret_cast<const float4 *>(r4 + 2)[q4];
-        pt.u[4 * q4] = v.x;
-        pt.u[4 * q4 + 1] = v.y;
-        pt.u[4 * q4 + 2] = v.z;
-        pt.u[4 * q4 + 3] = v.w;
+    for (int g = 0; g < NSET; ++g) {
+        float v[4 * C4];
+#pragma unroll
+        for (int q4 = 0; q4 < C4; ++q4) {
+            const float4 x = reinterpret_cast<const float4 *>(r4 + 2 + g * C4)[q4];
+            v[4 * q4] = x.x;
+            v[4 * q4 + 1] = x.y;
+            v[4 * q4 + 2] = x.z;
+            v[4 * q4 + 3] = x.w;
+        }
+        pt.w[g] = v[0];
+        pt.wr[g] = v[1];
+#pragma unroll
+        for (int q = 0; q < 4 * C4 - 2; ++q) pt.u[g][q] = v[2 + q];
     }
     const uint64_t A = ((uint64_t)h.y << 32) | h.x;
     const uint64_t B = ((uint64_t)h.w << 32) | h.z;
@@ -175,61 +226,65 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
     }
     pt.cr = m.x;
     pt.sr = m.y;
-    pt.w = m.z;
-    pt.wr = m.w;
+    pt.c2 = m.z;
+    pt.s2 = m.w;
 }
 
 // Mixed accumulators: the F frequencies of a thread in pairs (k, k+1), every
 // sum of a pair in one float2 register pair, so that one packed FP32
 // instruction (FFMA2: two FMAs of one warp instruction) updates the sums of
 // both frequencies.  With F odd the last pair's second half is not used.
-template <int P, int F>
+template <int P, int F, int NSET = 1>
 struct MixedAcc {
-    static constexpr int Q = 2 * P + 4;
+    static constexpr int Q = NSET * (2 * P + 4);
     static constexpr int NPC = (F + 1) / 2;
     float2 a[NPC][Q];
 };
 
 // F consecutive frequencies of one point, two at a time.  The pair starts at
 // (f_{j0}, f_{j0+1}) (the seed and one step of the rotation e^{i theta},
-// theta = 2 pi df t') and advances by e^{2 i theta}; per pair the 2P+4 sums
+// theta = 2 pi df t') and advances by e^{2 i theta} (from the record, rounded
+// once from FP64, so that the recurrence drifts by the rounding of one
+// constant per step); per pair the 2P+4 sums
 //     <psi_k c>, <psi_k s>, <r c>, <r s>, <c^2>, <c s>
 // take one packed FMA each, and w c one packed multiply: (2P + 9) packed
 // instructions per two frequencies, the rotation included.
-template <int P, int F>
-__device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, MixedAcc<P, F> &A) {
-    constexpr int NPC = MixedAcc<P, F>::NPC;
+template <int P, int F, int NSET = 1>
+__device__ __forceinline__ void mixed_accumulate(const MixedPoint<P, NSET> &pt, MixedAcc<P, F, NSET> &A) {
+    constexpr int NPC = MixedAcc<P, F, NSET>::NPC, Q0 = 2 * P + 4;
     float2 c = make_float2(pt.c, fmaf(pt.c, pt.cr, -pt.s * pt.sr));
     float2 s = make_float2(pt.s, fmaf(pt.s, pt.cr, pt.c * pt.sr));
-    const float C2 = fmaf(pt.cr, pt.cr, -pt.sr * pt.sr), S2 = 2.0f * (pt.cr * pt.sr);
-    const float2 cc = make_float2(C2, C2), ss = make_float2(S2, S2), nss = make_float2(-S2, -S2);
-    const float2 w2 = make_float2(pt.w, pt.w), wr2 = make_float2(pt.wr, pt.wr);
+    const float2 cc = make_float2(pt.c2, pt.c2), ss = make_float2(pt.s2, pt.s2), nss = make_float2(-pt.s2, -pt.s2);
 #pragma unroll
     for (int kk = 0; kk < NPC; ++kk) {
-        float2 *a = A.a[kk];
-        if ((F & 1) && kk == NPC - 1) {   // the odd last frequency on its own
-            const float wc = pt.w * c.x;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                a[q].x = fmaf(pt.u[q], c.x, a[q].x);
-                a[P + q].x = fmaf(pt.u[q], s.x, a[P + q].x);
-            }
-            a[2 * P].x = fmaf(pt.wr, c.x, a[2 * P].x);
-            a[2 * P + 1].x = fmaf(pt.wr, s.x, a[2 * P + 1].x);
-            a[2 * P + 2].x = fmaf(wc, c.x, a[2 * P + 2].x);
-            a[2 * P + 3].x = fmaf(wc, s.x, a[2 * P + 3].x);
-        } else {
+        for (int g = 0; g < NSET; ++g) {   // the set's sums; the same (c, s) for both sets
+            float2 *a = A.a[kk] + g * Q0;
+            if ((F & 1) && kk == NPC - 1) {   // the odd last frequency on its own
+                const float wc = pt.w[g] * c.x;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const float2 uu = make_float2(pt.u[q], pt.u[q]);
-                a[q] = __ffma2_rn(uu, c, a[q]);
-                a[P + q] = __ffma2_rn(uu, s, a[P + q]);
+                for (int q = 0; q < P; ++q) {
+                    a[q].x = fmaf(pt.u[g][q], c.x, a[q].x);
+                    a[P + q].x = fmaf(pt.u[g][q], s.x, a[P + q].x);
+                }
+                a[2 * P].x = fmaf(pt.wr[g], c.x, a[2 * P].x);
+                a[2 * P + 1].x = fmaf(pt.wr[g], s.x, a[2 * P + 1].x);
+                a[2 * P + 2].x = fmaf(wc, c.x, a[2 * P + 2].x);
+                a[2 * P + 3].x = fmaf(wc, s.x, a[2 * P + 3].x);
+            } else {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const float2 uu = make_float2(pt.u[g][q], pt.u[g][q]);
+                    a[q] = __ffma2_rn(uu, c, a[q]);
+                    a[P + q] = __ffma2_rn(uu, s, a[P + q]);
+                }
+                const float2 wr2 = make_float2(pt.wr[g], pt.wr[g]), w2 = make_float2(pt.w[g], pt.w[g]);
+                a[2 * P] = __ffma2_rn(wr2, c, a[2 * P]);
+                a[2 * P + 1] = __ffma2_rn(wr2, s, a[2 * P + 1]);
+                const float2 wc = __fmul2_rn(w2, c);
+                a[2 * P + 2] = __ffma2_rn(wc, c, a[2 * P + 2]);
+                a[2 * P + 3] = __ffma2_rn(wc, s, a[2 * P + 3]);
             }
-            a[2 * P] = __ffma2_rn(wr2, c, a[2 * P]);
-            a[2 * P + 1] = __ffma2_rn(wr2, s, a[2 * P + 1]);
-            const float2 wc = __fmul2_rn(w2, c);
-            a[2 * P + 2] = __ffma2_rn(wc, c, a[2 * P + 2]);
-            a[2 * P + 3] = __ffma2_rn(wc, s, a[2 * P + 3]);
         }
         if (kk + 1 < NPC) {
             const float2 cn = __ffma2_rn(s, nss, __fmul2_rn(c, cc));
@@ -244,51 +299,69 @@ __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P> &pt, MixedA
 // current point's F-step loop runs (two alternating point buffers).  The loop
 // is over pairs with no per-point branch; an even run ends by re-fetching its
 // last point, which is not accumulated.
-template <int P, int F, int SEED>
+template <int P, int F, int SEED, int NSET = 1>
 __device__ __forceinline__ void mixed_run(const unsigned char *p, size_t stride, int m, const SeedTableF &tab,
-                                          uint32_t j0, MixedAcc<P, F> &acc) {
+                                          uint32_t j0, MixedAcc<P, F, NSET> &acc) {
     auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(p + (size_t)i * stride); };
-    MixedPoint<P> pa, pb;
-    mixed_load<P, SEED>(rec(0), tab, j0, pa);
+    MixedPoint<P, NSET> pa, pb;
+    mixed_load<P, SEED, NSET>(rec(0), tab, j0, pa);
     int j = 0;
     for (; j + 2 <= m; j += 2) {
-        mixed_load<P, SEED>(rec(j + 1), tab, j0, pb);
-        mixed_accumulate<P, F>(pa, acc);
-        mixed_load<P, SEED>(rec(min(j + 2, m - 1)), tab, j0, pa);
-        mixed_accumulate<P, F>(pb, acc);
+        mixed_load<P, SEED, NSET>(rec(j + 1), tab, j0, pb);
+        mixed_accumulate<P, F, NSET>(pa, acc);
+        mixed_load<P, SEED, NSET>(rec(min(j + 2, m - 1)), tab, j0, pa);
+        mixed_accumulate<P, F, NSET>(pb, acc);
     }
-    if (j < m) mixed_accumulate<P, F>(pa, acc);
+    if (j < m) mixed_accumulate<P, F, NSET>(pa, acc);
 }
 
-template <int P, int F>
+template <int P, int F, int NSET = 1>
 __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const SeedTable &tab, uint32_t j0,
-                                           double (&acc)[F][2 * P + 4]) {
+                                           double (&acc)[F][NSET * (2 * P + 4)]) {
+    constexpr int C2 = (P + 1) / 2, Q0 = 2 * P + 4;
     const ulonglong2 h = *reinterpret_cast<const ulonglong2 *>(r2);
     const double2 rot = r2[1];
+    double w[NSET], wr[NSET], u[NSET][2 * C2];
     const double2 ww = r2[2];
-    double u[2 * ((P + 1) / 2)];
+    w[0] = ww.x;
+    wr[0] = ww.y;
 #pragma unroll
-    for (int q2 = 0; q2 < (P + 1) / 2; ++q2) {
+    for (int q2 = 0; q2 < C2; ++q2) {
         const double2 v = r2[3 + q2];
-        u[2 * q2] = v.x;
-        u[2 * q2 + 1] = v.y;
+        u[0][2 * q2] = v.x;
+        u[0][2 * q2 + 1] = v.y;
+    }
+    if constexpr (NSET == 2) {   // the t'-weighted set after the first
+        const double2 w2 = r2[3 + C2];
+        w[1] = w2.x;
+        wr[1] = w2.y;
+#pragma unroll
+        for (int q2 = 0; q2 < C2; ++q2) {
+            const double2 v = r2[4 + C2 + q2];
+            u[1][2 * q2] = v.x;
+            u[1][2 * q2 + 1] = v.y;
+        }
     }
     const uint64_t ph = h.x + (uint64_t)j0 * h.y;
     double s, c;
     seed_from_table(tab, ph, &s, &c);
-    const double cr = rot.x, sr = rot.y, w = ww.x, wr = ww.y;
+    const double cr = rot.x, sr = rot.y;
 #pragma unroll
     for (int k = 0; k < F; ++k) {
-        const double wc = w * c;
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-            acc[k][q] = fma(u[q], c, acc[k][q]);
-            acc[k][P + q] = fma(u[q], s, acc[k][P + q]);
+        for (int g = 0; g < NSET; ++g) {
+            double *a = acc[k] + g * Q0;
+            const double wc = w[g] * c;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                a[q] = fma(u[g][q], c, a[q]);
+                a[P + q] = fma(u[g][q], s, a[P + q]);
+            }
+            a[2 * P] = fma(wr[g], c, a[2 * P]);
+            a[2 * P + 1] = fma(wr[g], s, a[2 * P + 1]);
+            a[2 * P + 2] = fma(wc, c, a[2 * P + 2]);
+            a[2 * P + 3] = fma(wc, s, a[2 * P + 3]);
         }
-        acc[k][2 * P] = fma(wr, c, acc[k][2 * P]);
-        acc[k][2 * P + 1] = fma(wr, s, acc[k][2 * P + 1]);
-        acc[k][2 * P + 2] = fma(wc, c, acc[k][2 * P + 2]);
-        acc[k][2 * P + 3] = fma(wc, s, acc[k][2 * P + 3]);
         if (k + 1 < F) {
             const double cn = fma(c, cr, -s * sr);
             s = fma(s, cr, c * sr);
@@ -302,10 +375,10 @@ __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const
 // warp's running sums in shared memory (red): flush() adds all first-level
 // sums into them, flush_r() only <r c>, <r s>; read() gives warp w's running
 // sum q of the lane's frequency k (epilogue).
-template <int PREC, int P, int F> struct BlockSums;
+template <int PREC, int P, int F, int NSET> struct BlockSums;
 
-template <int P, int F> struct BlockSums<FREDEC_FP64, P, F> {
-    static constexpr int Q = 2 * P + 4;
+template <int P, int F, int NSET> struct BlockSums<FREDEC_FP64, P, F, NSET> {
+    static constexpr int Q = NSET * (2 * P + 4);
     using R = double;
     double a[F][Q];
     __device__ __forceinline__ void zero() {
@@ -316,6 +389,7 @@ template <int P, int F> struct BlockSums<FREDEC_FP64, P, F> {
     }
     template <int Q0, int Q1>
     __device__ __forceinline__ void flush_range(R *mine, int lane) {
+        static_assert(0 <= Q0 && Q0 <= Q1 && Q1 <= Q, "flush range inside the block's sums");
 #pragma unroll
         for (int k = 0; k < F; ++k)
 #pragma unroll
@@ -325,16 +399,19 @@ template <int P, int F> struct BlockSums<FREDEC_FP64, P, F> {
             }
     }
     __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
-    __device__ __forceinline__ void flush_r(R *mine, int lane) { flush_range<2 * P, 2 * P + 2>(mine, lane); }
+    __device__ __forceinline__ void flush_r(R *mine, int lane) {
+        flush_range<2 * P, 2 * P + 2>(mine, lane);
+        if constexpr (NSET == 2) flush_range<(2 * P + 4) + 2 * P, (2 * P + 4) + 2 * P + 2>(mine, lane);
+    }
     static __device__ __forceinline__ double read(const R *red, int w, int q, int k, int ln) {
         return red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
     }
 };
 
-template <int P, int F> struct BlockSums<FREDEC_MIXED, P, F> {
-    static constexpr int Q = 2 * P + 4, NPC = (F + 1) / 2;
+template <int P, int F, int NSET> struct BlockSums<FREDEC_MIXED, P, F, NSET> {
+    static constexpr int Q = NSET * (2 * P + 4), NPC = (F + 1) / 2;
     using R = float2;
-    MixedAcc<P, F> acc;
+    MixedAcc<P, F, NSET> acc;
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < NPC; ++k)
@@ -343,6 +420,7 @@ template <int P, int F> struct BlockSums<FREDEC_MIXED, P, F> {
     }
     template <int Q0, int Q1>
     __device__ __forceinline__ void flush_range(R *mine, int lane) {
+        static_assert(0 <= Q0 && Q0 <= Q1 && Q1 <= Q, "flush range inside the block's sums");
 #pragma unroll
         for (int k = 0; k < NPC; ++k)
 #pragma unroll
@@ -353,7 +431,10 @@ template <int P, int F> struct BlockSums<FREDEC_MIXED, P, F> {
             }
     }
     __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
-    __device__ __forceinline__ void flush_r(R *mine, int lane) { flush_range<2 * P, 2 * P + 2>(mine, lane); }
+    __device__ __forceinline__ void flush_r(R *mine, int lane) {
+        flush_range<2 * P, 2 * P + 2>(mine, lane);
+        if constexpr (NSET == 2) flush_range<(2 * P + 4) + 2 * P, (2 * P + 4) + 2 * P + 2>(mine, lane);
+    }
     static __device__ __forceinline__ float read(const R *red, int w, int q, int k, int ln) {
         const float2 v = red[((size_t)w * Q + q) * NPC * 32 + (k >> 1) * 32 + ln];
         return (k & 1) ? v.y : v.x;
@@ -369,16 +450,17 @@ template <int P, int F> struct BlockSums<FREDEC_MIXED, P, F> {
 // kernels are instantiated in translation units of their own
 // (pgram_mirror_*.cu): with them in the same module the kernels without a
 // mirror measured 1.5% slower, identical code notwithstanding.
-template <int PREC, int P, int F, bool MIRROR = false>
+template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 __device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                             int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
-    using L = PgramLayout<PREC, P, F>;
+    static_assert(NSET == 1 || !MIRROR, "the two-set kernels write z to device memory only");
+    using L = PgramLayout<PREC, P, F, NSET>;
     using T = typename AccT<PREC>::T;
     constexpr int Q = L::Q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     unsigned char *tiles = smem + L::OFF_TILES;
-    using BS = BlockSums<PREC, P, F>;
+    using BS = BlockSums<PREC, P, F, NSET>;
     using R = typename BS::R;
     R *red = reinterpret_cast<R *>(smem + L::OFF_RED);
     const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + OFF_TABLE);
@@ -388,13 +470,13 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     const int64_t jblock = blk * 32 * F;
     const uint32_t j0 = (uint32_t)(jblock + lane * F);
     const unsigned char *src = prm.rec + d.rec_off;
-    const int ntiles = (N + TILE_POINTS - 1) / TILE_POINTS;
+    const int ntiles = (N + L::TP - 1) / L::TP;
 
     __syncthreads();   // previous block's epilogue is done with red / tiles
     for (int q = lane; q < L::RED_PER_WARP; q += 32) red[(size_t)warp * L::RED_PER_WARP + q] = R{};
     if (tid == 0) {
         for (int k = 0; k < 2 && k < ntiles; ++k) {
-            const unsigned n = (unsigned)min(TILE_POINTS, N - k * TILE_POINTS);
+            const unsigned n = (unsigned)min(L::TP, N - k * L::TP);
             mbar_arrive_expect_tx(&bars[k], n * L::RB);
             bulk_g2s(tiles + k * L::TILE_BYTES, src + (size_t)k * L::TILE_BYTES, n * L::RB, &bars[k]);
         }
@@ -412,7 +494,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         if (!mbar_wait_bounded(&bars[b], par)) {
             if (lane == 0) atomicExch(prm.err, FREDEC_ETIMEOUT);
         }
-        const int n = min(TILE_POINTS, N - tile * TILE_POINTS);
+        const int n = min(L::TP, N - tile * L::TP);
         const unsigned char *tb = tiles + b * L::TILE_BYTES;
         if constexpr (PREC == FREDEC_MIXED) {
             // this warp's points of the tile (warp, warp + nw, ...) in runs
@@ -423,9 +505,9 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             for (int k = 0; k < cnt;) {
                 const int take = min(cnt - k, FLUSH_POINTS - since);
                 if (prm.seed_mode == 0)
-                    mixed_run<P, F, 0>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
+                    mixed_run<P, F, 0, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
                 else
-                    mixed_run<P, F, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
+                    mixed_run<P, F, 1, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
                 k += take;
                 since += take;
                 if (since == FLUSH_POINTS) {
@@ -440,11 +522,11 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             }
         } else {
             for (int i = warp; i < n; i += nw)
-                fp64_point<P, F>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, sums.a);
+                fp64_point<P, F, NSET>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, sums.a);
         }
         __syncthreads();   // all warps are done with buffer b
         if (tid == 0 && tile + 2 < ntiles) {
-            const unsigned nn = (unsigned)min(TILE_POINTS, N - (tile + 2) * TILE_POINTS);
+            const unsigned nn = (unsigned)min(L::TP, N - (tile + 2) * L::TP);
             mbar_arrive_expect_tx(&bars[b], nn * L::RB);
             bulk_g2s(tiles + b * L::TILE_BYTES, src + (size_t)(tile + 2) * L::TILE_BYTES, nn * L::RB, &bars[b]);
         }
@@ -488,13 +570,15 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             done = solve2_fast(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], prm.flag_tau, &zz, &a, &bb);
             if (!done) {   // ill-conditioned: provisional value now, FP64-grade re-evaluation later
                 const int32_t at = atomicAdd(prm.flag_count, 1);
-                prm.flag_list[at] = d.z_off + j;
+                if (at < prm.flag_cap) prm.flag_list[at] = d.z_off + j;
+                else atomicExch(prm.err, FREDEC_EINVAL);
             }
         }
         if (!done) {
             double ratio;
             zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
         }
+        if constexpr (NSET == 2) prm.dzdf[d.z_off + j] = dz_df<P>(S, S + 2 * P + 4, *prm.wt_sum, a, bb);
         if constexpr (MIRROR) zbuf[ln * F + k] = zz;
         else prm.z[d.z_off + j] = zz;
         if (prm.coef) {
@@ -535,15 +619,20 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
 // Register cap of the grid kernel (which may be launched with up to 256
 // threads): mixed kernels whose F x (2P+4) accumulators fit take 128
 // registers (16 warps per SM) up to 80 accumulators and 168 (three CTAs of
-// four warps) up to 120; the others, and the FP64 kernels, are not capped.
-template <int PREC, int P, int F>
+// four warps) up to 120 (two-set kernels: 168 up to 120 accumulators, their
+// second set of per-point values needs the registers); the others, and the
+// FP64 kernels, are not capped.
+template <int PREC, int P, int F, int NSET = 1>
 constexpr int pgram_maxreg() {
-    return PREC != FREDEC_MIXED ? 255 : F * (2 * P + 4) <= 80 ? 128 : F * (2 * P + 4) <= 120 ? 168 : 255;
+    return PREC != FREDEC_MIXED                      ? 255
+           : NSET == 1 && F * (2 * P + 4) <= 80       ? 128
+           : NSET * F * (2 * P + 4) <= 120            ? 168
+                                                      : 255;
 }
 
 // Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
-template <int PREC, int P, int F, bool MIRROR>
-__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F>())) pgram_kernel(PgramParams prm) {
+template <int PREC, int P, int F, bool MIRROR, int NSET = 1>
+__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, NSET>())) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
     grid_dependency_wait();   // prep's records and state
@@ -551,18 +640,18 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F>(
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
     uint32_t use0 = 0u, use1 = 0u;
-    pgram_block<PREC, P, F, MIRROR>(prm, d, st, blockIdx.x, smem, use0, use1);
+    pgram_block<PREC, P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
-template <int PREC, int P, int F, bool MIRROR = false>
+template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    using L = PgramLayout<PREC, P, F>;
+    using L = PgramLayout<PREC, P, F, NSET>;
     const size_t smem = L::smem_bytes(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
-    auto kern = pgram_kernel<PREC, P, F, MIRROR>;
+    auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     if (nblocks <= 0) return FREDEC_OK;
@@ -572,7 +661,7 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
     return FREDEC_OK;
 }
 
-template <int PREC, int P, int F>
-size_t pgram_smem_t(int warps) { return PgramLayout<PREC, P, F>::smem_bytes(warps); }
+template <int PREC, int P, int F, int NSET = 1>
+size_t pgram_smem_t(int warps) { return PgramLayout<PREC, P, F, NSET>::smem_bytes(warps); }
 
 }  // namespace fredec

@@ -26,8 +26,6 @@
 namespace fredec {
 
 int prep_npart(int pmax) { return pmax * (pmax + 1) / 2 + pmax + 4; }
-int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
-                     const double *base, int precision, void *rec64, cudaStream_t st);
 
 namespace {
 
@@ -42,6 +40,7 @@ struct PrepArgs {
     unsigned char *rec64;   // optional float-float records (mixed runs with re-evaluation of flagged bins)
     const double *t, *y, *sigma, *base;
     int precision;
+    int nset;               // 2: records also carry the t'-weighted values (frequency derivative)
 };
 
 constexpr int PREP_NV = NTRI + PMAX + 4;    // values summed per point, at most
@@ -311,12 +310,15 @@ __device__ __forceinline__ int64_t record_slot(int64_t i, int64_t K, int64_t N) 
     return (int64_t)(((unsigned long long)i * (unsigned long long)K) % (unsigned long long)N);
 }
 
-// Writes the records of point i of series d (residual r, w, u = w psi);
-// K = record_multiplier(d.N); PT as for base_basis (d.p = PT when PT > 0).
+// Writes the records of point i of series d (residual r, w, u = w psi; with
+// a.nset == 2 also their products with t' = tp, the t-weighted averages of
+// Eq. avrg1 that the frequency derivative needs); K = record_multiplier(d.N);
+// PT as for base_basis (d.p = PT when PT > 0).
 template <int PT = 0>
 __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, int64_t K, double tp,
                                               double w, double r, const double *u) {
     const int p = PT > 0 ? PT : d.p;
+    const int ns = a.nset;
     const int64_t slot = a.precision == FREDEC_MIXED ? record_slot(i, K, d.N) : i;
     const uint64_t A = frac_turns_u64(d.f0, tp);
     const uint64_t B = frac_turns_u64(d.df, tp);
@@ -324,40 +326,58 @@ __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDes
     sincos_turns_d(B, &sr, &cr);
     const float wf = (float)w;
     if (a.precision == FREDEC_MIXED) {
-        uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + slot * rec32_words(p);
+        uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + slot * rec32_words(p, ns);
         R[0] = (uint32_t)A;
         R[1] = (uint32_t)(A >> 32);
         R[2] = (uint32_t)B;
         R[3] = (uint32_t)(B >> 32);
         float *Rf = (float *)R;
+        double s2, c2;   // the two-step rotation from the doubled exact phase
+        sincos_turns_d(2 * B, &s2, &c2);
         Rf[4] = (float)cr;
         Rf[5] = (float)sr;
-        Rf[6] = wf;
-        Rf[7] = (float)(w * r);
-        for (int q = 0; q < p; ++q) Rf[8 + q] = (float)u[q];
-        for (int q = 8 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
+        Rf[6] = (float)c2;
+        Rf[7] = (float)s2;
+        Rf[8] = wf;
+        Rf[9] = (float)(w * r);
+        for (int q = 0; q < p; ++q) Rf[10 + q] = (float)u[q];
+        for (int q = 10 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
+        if (ns == 2) {
+            float *R2 = Rf + rec32_words(p);
+            R2[0] = (float)(w * tp);
+            R2[1] = (float)(w * r * tp);
+            for (int q = 0; q < p; ++q) R2[2 + q] = (float)(u[q] * tp);
+            for (int q = 2 + p; q < rec32_set_words(p); ++q) R2[q] = 0.f;
+        }
     }
     if (a.precision == FREDEC_MIXED && a.rec64) {   // float-float records for the re-evaluation
-        uint32_t *R = (uint32_t *)(a.rec64 + d.rec64_off) + slot * recff_words(p);
+        uint32_t *R = (uint32_t *)(a.rec64 + d.rec64_off) + slot * recff_words(p, ns);
         R[0] = (uint32_t)A;
         R[1] = (uint32_t)(A >> 32);
         R[2] = (uint32_t)B;
         R[3] = (uint32_t)(B >> 32);
         float *Rf = (float *)R;
-        auto put = [&](int at, double v) {
+        auto put = [&](float *at, double v) {
             const float hi = (float)v;
-            Rf[at] = hi;
-            Rf[at + 1] = (float)(v - (double)hi);
+            at[0] = hi;
+            at[1] = (float)(v - (double)hi);
         };
-        put(4, w);
-        put(6, w * r);
-        for (int q = 0; q < p; ++q) put(8 + 2 * q, u[q]);
+        put(Rf + 4, w);
+        put(Rf + 6, w * r);
+        for (int q = 0; q < p; ++q) put(Rf + 8 + 2 * q, u[q]);
         for (int q = 8 + 2 * p; q < recff_words(p); ++q) Rf[q] = 0.f;
+        if (ns == 2) {
+            float *R2 = Rf + recff_words(p);
+            put(R2, w * tp);
+            put(R2 + 2, w * r * tp);
+            for (int q = 0; q < p; ++q) put(R2 + 4 + 2 * q, u[q] * tp);
+            for (int q = 4 + 2 * p; q < recff_set_words(p); ++q) R2[q] = 0.f;
+        }
     }
     unsigned char *r64 = a.precision == FREDEC_FP64 ? a.rec : nullptr;
     if (r64) {
         const int64_t off64 = d.rec_off;
-        uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p);
+        uint64_t *R = (uint64_t *)(r64 + off64) + i * rec64_words(p, ns);
         R[0] = A;
         R[1] = B;
         double *Rd = (double *)R;
@@ -367,6 +387,13 @@ __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDes
         Rd[5] = w * r;
         for (int q = 0; q < p; ++q) Rd[6 + q] = u[q];
         for (int q = 6 + p; q < rec64_words(p); ++q) Rd[q] = 0.0;
+        if (ns == 2) {
+            double *R2 = Rd + rec64_words(p);
+            R2[0] = w * tp;
+            R2[1] = w * r * tp;
+            for (int q = 0; q < p; ++q) R2[2 + q] = u[q] * tp;
+            for (int q = 2 + p; q < 2 + rec64_set_words(p); ++q) R2[q] = 0.0;
+        }
     }
 }
 
@@ -1013,8 +1040,9 @@ static int cluster_size_for(int64_t max_n, int slot) {
 // As launch_prep; rec64 (optional, mixed runs) also receives float-float
 // records at each series' rec64_off.
 int run_prep_records(const PrepPlan &pp, const double *t, const double *y, const double *sigma,
-                     const double *base, int precision, void *rec64, cudaStream_t st) {
+                     const double *base, int precision, void *rec64, cudaStream_t st, int nset) {
     PrepArgs a;
+    a.nset = nset;
     a.rec64 = (unsigned char *)rec64;
     a.desc = pp.desc;
     a.state = pp.state;

@@ -132,7 +132,7 @@ def _scratch_bytes(N, n_base, nf, prec, trend=0, reeval=True):
     """The header's scratch formula of the no-allocation entry point."""
     p = (1 + trend + 2 * n_base) | 1
     c = -(-N // 32)
-    r = 8 * (6 + 2 * -(-p // 2)) if prec == "fp64" else 4 * (8 + 4 * -(-p // 4))
+    r = 8 * (6 + 2 * -(-p // 2)) if prec == "fp64" else 4 * (8 + 4 * -(-(p + 2) // 4))
     b = 6912 + _r256(4 * c) + _r256(8 * c * (p * (p + 1) // 2 + p + 4)) + _r256(8 * p * N) + _r256(r * N)
     if prec == "mixed" and reeval:
         b += _r256(16 * -(-(8 + 2 * p) // 4) * N) + _r256(8 * nf + 8)
