@@ -12,7 +12,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import FP64, _prec, periodogram_dev, periodogram_vjp_dev, tuple_grad
+from . import FP64, _prec, periodogram_dev, periodogram_vjp_dev, tuple_grad_dev
 
 
 class PeriodogramFn(torch.autograd.Function):
@@ -38,23 +38,24 @@ def periodogram_z(y, t, sigma, base, f0, df, nf, precision=FP64):
 
 
 class TupleZFn(torch.autograd.Function):
+    """Tuple frequencies (CUDA tensor, CSR order) -> z per tuple.  The forward
+    pass runs the library's tuple kernel on the device (fredec_tuple_grad_dev:
+    z and dz/df in one pass, kept for backward); the offsets stay on the host,
+    since they size the launch."""
+
     @staticmethod
     def forward(ctx, freqs, t, y, sigma, offsets, precision):
-        th, yh, sh = (x.detach().cpu().numpy() for x in (t, y, sigma))
-        off = offsets.cpu().numpy()
-        f = freqs.detach().cpu().numpy()
-        tuples = [f[off[k]:off[k + 1]] for k in range(off.size - 1)]
-        z, g = tuple_grad(th, yh, sh, tuples, precision=precision)
-        ctx.save_for_backward(torch.as_tensor(g, dtype=freqs.dtype, device=freqs.device))
-        ctx.offsets = off
-        return torch.as_tensor(z, dtype=freqs.dtype, device=freqs.device)
+        off = np.ascontiguousarray(np.asarray(offsets.cpu() if hasattr(offsets, "cpu") else offsets,
+                                              dtype=np.int64))
+        z, g = tuple_grad_dev(t, y, sigma, freqs.detach().contiguous(), off, precision=precision)
+        ctx.save_for_backward(g)
+        ctx.rep = torch.as_tensor(np.repeat(np.arange(off.size - 1), np.diff(off)), device=freqs.device)
+        return z
 
     @staticmethod
     def backward(ctx, gz):
         (g,) = ctx.saved_tensors
-        off = ctx.offsets
-        rep = torch.as_tensor(np.repeat(np.arange(off.size - 1), np.diff(off)), device=g.device)
-        return gz[rep] * g, None, None, None, None, None
+        return gz[ctx.rep] * g, None, None, None, None, None
 
 
 def tuple_z(freqs, t, y, sigma, offsets, precision=FP64):

@@ -31,6 +31,7 @@
 // cos/sin at every point are computed once (FP64 phases); the offset's
 // rotation e^{i 2 pi delta t'} is small and is applied per pass.
 #include <algorithm>
+#include <cstring>
 #include <numeric>
 #include <type_traits>
 #include <vector>
@@ -300,6 +301,15 @@ __device__ __forceinline__ void make_row(const TupleArgs &a, const TState &s, co
     for (int c = C; c < CP; ++c) put(row, c, V(0));
 }
 
+// FF tile rows are planar per block of four columns: [hi x4, lo x4], so
+// that four hi parts (or lo parts) load as one float4 and split into the
+// float2 pairs of the packed accumulation (BlockAcc<FF>).
+__device__ __forceinline__ void put_ff(float2 *row, int c, float hi, float lo) {
+    float *r = reinterpret_cast<float *>(row) + 8 * (c >> 2) + (c & 3);
+    r[0] = hi;
+    r[4] = lo;
+}
+
 // FF columns: seed (FF) rotated by the FF sin/cos of the trial offset's
 // turns delta t' (formed in FF), then the weighted products in FF.
 template <>
@@ -310,8 +320,8 @@ __device__ __forceinline__ void make_row<FF>(const TupleArgs &a, const TState &s
     const ff sw = {p0.x, p0.y}, tp = {p0.z, p0.w}, yw = {p1.x, p1.y}, swt = {p1.z, p1.w};
     const SeedTableFF &T = *static_cast<const SeedTableFF *>(tab);
     const int M = 2 * m + 1;
-    row[0] = make_float2(sw.hi, sw.lo);
-    row[M] = make_float2(yw.hi, yw.lo);
+    put_ff(row, 0, sw.hi, sw.lo);
+    put_ff(row, M, yw.hi, yw.lo);
     for (int k = 0; k < m; ++k) {
         const float4 sd = static_cast<const float4 *>(a.seeds)[(int64_t)s.pidx[k] * a.N + i];
         ff c = {sd.x, sd.y}, sn = {sd.z, sd.w};
@@ -324,15 +334,15 @@ __device__ __forceinline__ void make_row<FF>(const TupleArgs &a, const TState &s
             c = cn;
         }
         const ff c1 = ff_mul(sw, c), s1 = ff_mul(sw, sn);
-        row[1 + 2 * k] = make_float2(c1.hi, c1.lo);
-        row[2 + 2 * k] = make_float2(s1.hi, s1.lo);
+        put_ff(row, 1 + 2 * k, c1.hi, c1.lo);
+        put_ff(row, 2 + 2 * k, s1.hi, s1.lo);
         if (with_uv) {
             const ff c2 = ff_mul(swt, c), s2 = ff_mul(swt, sn);
-            row[M + 1 + 2 * k] = make_float2(c2.hi, c2.lo);
-            row[M + 2 + 2 * k] = make_float2(s2.hi, s2.lo);
+            put_ff(row, M + 1 + 2 * k, c2.hi, c2.lo);
+            put_ff(row, M + 2 + 2 * k, s2.hi, s2.lo);
         }
     }
-    for (int c = C; c < CP; ++c) row[c] = make_float2(0.f, 0.f);
+    for (int c = C; c < CP; ++c) put_ff(row, c, 0.f, 0.f);
 }
 
 __device__ __forceinline__ void load4(const float *p, float *v) {
@@ -348,14 +358,6 @@ __device__ __forceinline__ void load4(const double *p, double *v) {
     v[1] = q0.y;
     v[2] = q1.x;
     v[3] = q1.y;
-}
-
-__device__ __forceinline__ void load4(const float2 *p, float2 *v) {
-    const float4 q0 = reinterpret_cast<const float4 *>(p)[0], q1 = reinterpret_cast<const float4 *>(p)[1];
-    v[0] = make_float2(q0.x, q0.y);
-    v[1] = make_float2(q0.z, q0.w);
-    v[2] = make_float2(q1.x, q1.y);
-    v[3] = make_float2(q1.z, q1.w);
 }
 
 // Per-entry accumulators of a 4x4 Gram block.  float/double: chunk partials
@@ -390,27 +392,75 @@ template <class T> struct BlockAcc {
     }
     __device__ __forceinline__ double value(int b, int e) const { return (double)acc[b][e]; }
 };
+// Packed subtraction of two float pairs (sub.rn.f32x2), the complement of
+// __fadd2_rn; explicitly rounded like every step of the error-free
+// transformations below.
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+
+// Two double-float running sums updated by the same packed instructions: the
+// product a*b of float-float numbers enters as its rounded hi*hi part p plus
+// the exact error of that product and the two cross terms e (ff_acc::add_prod),
+// (p, e) is added by TwoSum (Knuth) and renormalised by FastTwoSum (Dekker);
+// per component this is ff_acc's arithmetic, so the sums are bit-identical.
+struct ff_acc2 {
+    float2 H = make_float2(0.f, 0.f), L = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add_prod(float2 ahi, float2 alo, float2 bhi, float2 blo) {
+        const float2 p = __fmul2_rn(ahi, bhi);
+        float2 e = __ffma2_rn(ahi, bhi, make_float2(-p.x, -p.y));
+        e = __ffma2_rn(ahi, blo, e);
+        e = __ffma2_rn(alo, bhi, e);
+        const float2 s = __fadd2_rn(H, p);                    // TwoSum(H, p)
+        const float2 bb = fsub2_rn(s, H);
+        const float2 err = __fadd2_rn(fsub2_rn(H, fsub2_rn(s, bb)), fsub2_rn(p, bb));
+        const float2 t = __fadd2_rn(err, __fadd2_rn(L, e));
+        const float2 hi = __fadd2_rn(s, t);                   // FastTwoSum(s, t)
+        L = fsub2_rn(t, fsub2_rn(hi, s));
+        H = hi;
+    }
+};
+
+// FF: the 16 entries of a 4x4 block as 8 pairs (entries 4u + 2w and
+// 4u + 2w + 1, w = 0, 1: one row column against two column columns) in
+// packed double-float sums; the planar tile rows give the hi and lo parts of
+// four columns as one float4 each.
 template <> struct BlockAcc<FF> {
-    ff_acc a[QB][16];
+    ff_acc2 a[QB][8];
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int b = 0; b < QB; ++b)
 #pragma unroll
-            for (int e = 0; e < 16; ++e) a[b][e] = ff_acc();
+            for (int e = 0; e < 8; ++e) a[b][e] = ff_acc2();
     }
     __device__ __forceinline__ void chunk(int b, const float2 *X, int rb, int cb, int g, int G, int n, int CP) {
-        const float2 *xr = X + 4 * rb, *xc = X + 4 * cb;
+        const float *xr = reinterpret_cast<const float *>(X) + 8 * rb, *xc = reinterpret_cast<const float *>(X) + 8 * cb;
         for (int p = g; p < n; p += G) {
-            float2 r[4], c[4];
-            load4(xr + (size_t)p * CP, r);
-            load4(xc + (size_t)p * CP, c);
+            const float4 rh = *reinterpret_cast<const float4 *>(xr + (size_t)p * 2 * CP);
+            const float4 rl = *reinterpret_cast<const float4 *>(xr + (size_t)p * 2 * CP + 4);
+            const float4 ch = *reinterpret_cast<const float4 *>(xc + (size_t)p * 2 * CP);
+            const float4 cl = *reinterpret_cast<const float4 *>(xc + (size_t)p * 2 * CP + 4);
+            const float rhi[4] = {rh.x, rh.y, rh.z, rh.w}, rlo[4] = {rl.x, rl.y, rl.z, rl.w};
+            const float2 chi[2] = {make_float2(ch.x, ch.y), make_float2(ch.z, ch.w)};
+            const float2 clo[2] = {make_float2(cl.x, cl.y), make_float2(cl.z, cl.w)};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                const float2 ah = make_float2(rhi[u], rhi[u]), al = make_float2(rlo[u], rlo[u]);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) a[b][4 * u + v].add_prod({r[u].x, r[u].y}, {c[v].x, c[v].y});
+                for (int w = 0; w < 2; ++w) a[b][2 * u + w].add_prod(ah, al, chi[w], clo[w]);
+            }
         }
     }
-    __device__ __forceinline__ double value(int b, int e) const { return a[b][e].value(); }
+    __device__ __forceinline__ double value(int b, int e) const {
+        const ff_acc2 &q = a[b][e >> 1];
+        return (e & 1) ? (double)q.H.y + (double)q.L.y : (double)q.H.x + (double)q.L.x;
+    }
 };
 
 __device__ __forceinline__ void block_rc(int q, int *rb, int *cb) {
@@ -694,6 +744,8 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
             if (a.z) a.z[k] = NAN;
             if (a.l_out) a.l_out[k] = NAN;
         }
+        if (a.mode == 1)
+            for (int q = tid; q < m; q += blockDim.x) a.dzdf[o0 + q] = NAN;
         return;
     }
     if (tid < 32) linear_solution(Gs, inv, M, s.theta, &s.red);
@@ -915,36 +967,113 @@ static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
     return FREDEC_OK;
 }
 
+// Device inputs of one tuple launch: the series, the pool frequencies, the
+// tuples as indices into the pool (CSR: tuple k holds pool[idx[off[k] ..
+// off[k+1])]) and the processing order (largest tuples first).
+struct TupleDevIn {
+    const double *t, *y, *sigma;
+    int64_t N;
+    const double *pool;
+    int npool;
+    const int32_t *idx;
+    const int64_t *off;
+    const int32_t *order;
+    int64_t nt;
+    int mmax;                  // largest tuple
+};
+
+// Enqueue the per-series constants, the per-point values, the pool's exact
+// cos/sin and the tuple kernel on st; scratch in ws.  Outputs (device, each
+// may be unused by the mode): z, dzdf, f_out, l_out, iters, status[nt];
+// *sp_out receives the series constants (l_0 = D).
+static int tuple_enqueue(const TupleDevIn &in, int mode, int precision, int max_iter, double tol, double *z,
+                         double *dzdf, double *f_out, double *l_out, int32_t *iters, int32_t *status,
+                         SeriesPrep **sp_out, DevBuf &ws, cudaStream_t st) {
+    const int64_t N = in.N;
+    const int npool = in.npool;
+    const size_t tsz = precision == FREDEC_MIXED ? 4 : 8;
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
+    const size_t o_sp = take(sizeof(SeriesPrep)), o_pts = take(N * 4 * tsz),
+                 o_seed = take((size_t)npool * N * 2 * tsz + 16), o_next = take(8);
+    if (int rc = ws.alloc(off, st)) return rc;
+    unsigned char *b = ws.as<unsigned char>();
+    FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 8, st));
+    SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
+    if (sp_out) *sp_out = sp;
+    series_prep<<<1, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp);
+    const unsigned pb = (unsigned)std::min<int64_t>(1024, (N + 255) / 256);
+    const unsigned sb = (unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256);
+    if (precision == FREDEC_MIXED) {
+        point_prep<float><<<pb, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp, (Pt<float> *)(b + o_pts));
+        if (npool) pool_seeds<float2><<<sb, 256, 0, st>>>(in.t, N, in.pool, npool, sp, (float2 *)(b + o_seed));
+    } else if (precision == PREC_FF) {
+        point_prep_ff<<<pb, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp, (float4 *)(b + o_pts));
+        if (npool) pool_seeds_ff<<<sb, 256, 0, st>>>(in.t, N, in.pool, npool, sp, (float4 *)(b + o_seed));
+    } else {
+        point_prep<double><<<pb, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp, (Pt<double> *)(b + o_pts));
+        if (npool) pool_seeds<double2><<<sb, 256, 0, st>>>(in.t, N, in.pool, npool, sp, (double2 *)(b + o_seed));
+    }
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    TupleArgs a{};
+    a.N = N;
+    a.sp = sp;
+    a.pts = b + o_pts;
+    a.seeds = b + o_seed;
+    a.pool = in.pool;
+    a.idx = in.idx;
+    a.off = in.off;
+    a.order = in.order;
+    a.n_tuples = in.nt;
+    a.mode = mode;
+    a.max_iter = max_iter;
+    a.tol = tol;
+    a.z = z;
+    a.dzdf = dzdf;
+    a.f_out = f_out;
+    a.l_out = l_out;
+    a.iters = iters;
+    a.status = status;
+    a.next = (int32_t *)(b + o_next);
+    a.cmax = std::max(2, mode == 0 ? 2 * in.mmax + 2 : 4 * in.mmax + 2);
+    a.chunk = tuple_chunk(precision, a.cmax);
+    if (in.nt > 0)
+        if (int rc = launch_tuples(a, precision, st)) return rc;
+    return FREDEC_OK;
+}
+
+static std::vector<int32_t> largest_first(const int64_t *off, int64_t nt) {
+    std::vector<int32_t> order(std::max<int64_t>(nt, 1));
+    std::iota(order.begin(), order.begin() + nt, 0);
+    std::stable_sort(order.begin(), order.begin() + nt,
+                     [&](int32_t p, int32_t q) { return off[p + 1] - off[p] > off[q + 1] - off[q]; });
+    return order;
+}
+
 // Tuples given as indices into a pool of frequencies (CSR: tuple k holds
 // pool[idx[off[k] .. off[k+1])]).  mode 0 z, 1 z and dz/df, 2 refinement.
 // Host inputs and outputs; synchronous.  Mixed-precision tuples whose linear
 // system was ill-conditioned anywhere on their way are redone from scratch
-// with FP64 sums (an inaccurate early step can lead a refinement into another
-// basin, which a continuation would keep).
+// with FP64-grade (float-float) sums (an inaccurate early step can lead a
+// refinement into another basin, which a continuation would keep).
 static int tuple_run(const double *t, const double *y, const double *sigma, int64_t N, const double *pool_h,
                      int npool, const std::vector<int32_t> &idx_h, const std::vector<int64_t> &off_h, int mode,
                      int precision, int max_iter, double tol, double *z_h, double *dzdf_h, double *f_h, double *l_h,
                      int32_t *iters_h, double *l0_h, cudaStream_t st) {
     const int64_t nt = (int64_t)off_h.size() - 1;
     const int64_t nflat = off_h.back();
-    const size_t tsz = precision == FREDEC_MIXED ? 4 : 8;
     int mmax = 0;
     for (int64_t k = 0; k < nt; ++k) mmax = std::max<int>(mmax, (int)(off_h[k + 1] - off_h[k]));
-    std::vector<int32_t> order(std::max<int64_t>(nt, 1));
-    std::iota(order.begin(), order.begin() + nt, 0);
-    std::stable_sort(order.begin(), order.begin() + nt, [&](int32_t p, int32_t q) {
-        return off_h[p + 1] - off_h[p] > off_h[q + 1] - off_h[q];
-    });
+    const std::vector<int32_t> order = largest_first(off_h.data(), nt);
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
-    const size_t o_in = take(3 * N * 8), o_sp = take(sizeof(SeriesPrep)), o_pool = take(npool * 8 + 8),
-                 o_pts = take(N * 4 * tsz), o_seed = take((size_t)npool * N * 2 * tsz + 16),
-                 o_idx = take(nflat * 4 + 4), o_off = take((nt + 1) * 8), o_ord = take(nt * 4 + 4),
-                 o_z = take(nt * 8 + 8), o_g = take(nflat * 8 + 8), o_f = take(nflat * 8 + 8), o_l = take(nt * 8 + 8),
-                 o_it = take(nt * 4 + 4), o_st = take(nt * 4 + 4), o_next = take(8);
-    DevBuf ws;
-    if (int rc = ws.alloc(off, st)) return rc;
-    unsigned char *b = ws.as<unsigned char>();
+    const size_t o_in = take(3 * N * 8), o_pool = take(npool * 8 + 8), o_idx = take(nflat * 4 + 4),
+                 o_off = take((nt + 1) * 8), o_ord = take(nt * 4 + 4), o_z = take(nt * 8 + 8),
+                 o_g = take(nflat * 8 + 8), o_f = take(nflat * 8 + 8), o_l = take(nt * 8 + 8),
+                 o_it = take(nt * 4 + 4), o_st = take(nt * 4 + 4);
+    DevBuf io, ws;
+    if (int rc = io.alloc(off, st)) return rc;
+    unsigned char *b = io.as<unsigned char>();
     double *dt = (double *)(b + o_in), *dy = dt + N, *ds = dy + N;
     FREDEC_CUDA_TRY(cudaMemcpyAsync(dt, t, N * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(dy, y, N * 8, cudaMemcpyHostToDevice, st));
@@ -953,49 +1082,13 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     if (nflat) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_idx, idx_h.data(), nflat * 4, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_off, off_h.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, st));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_ord, order.data(), nt * 4, cudaMemcpyHostToDevice, st));
-    FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 8, st));
-    SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
-    series_prep<<<1, 256, 0, st>>>(dt, dy, ds, N, sp);
-    const unsigned pb = (unsigned)std::min<int64_t>(1024, (N + 255) / 256);
-    const unsigned sb = (unsigned)std::min<int64_t>(4096, ((int64_t)npool * N + 255) / 256);
-    if (precision == FREDEC_MIXED) {
-        point_prep<float><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<float> *)(b + o_pts));
-        if (npool) pool_seeds<float2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
-                                                          (float2 *)(b + o_seed));
-    } else if (precision == PREC_FF) {
-        point_prep_ff<<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (float4 *)(b + o_pts));
-        if (npool) pool_seeds_ff<<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
-                                                     (float4 *)(b + o_seed));
-    } else {
-        point_prep<double><<<pb, 256, 0, st>>>(dt, dy, ds, N, sp, (Pt<double> *)(b + o_pts));
-        if (npool) pool_seeds<double2><<<sb, 256, 0, st>>>(dt, N, (const double *)(b + o_pool), npool, sp,
-                                                           (double2 *)(b + o_seed));
-    }
-    FREDEC_CUDA_TRY(cudaGetLastError());
-    TupleArgs a{};
-    a.N = N;
-    a.sp = sp;
-    a.pts = b + o_pts;
-    a.seeds = b + o_seed;
-    a.pool = (const double *)(b + o_pool);
-    a.idx = (const int32_t *)(b + o_idx);
-    a.off = (const int64_t *)(b + o_off);
-    a.order = (const int32_t *)(b + o_ord);
-    a.n_tuples = nt;
-    a.mode = mode;
-    a.max_iter = max_iter;
-    a.tol = tol;
-    a.z = (double *)(b + o_z);
-    a.dzdf = (double *)(b + o_g);
-    a.f_out = (double *)(b + o_f);
-    a.l_out = (double *)(b + o_l);
-    a.iters = (int32_t *)(b + o_it);
-    a.status = (int32_t *)(b + o_st);
-    a.next = (int32_t *)(b + o_next);
-    a.cmax = std::max(2, mode == 0 ? 2 * mmax + 2 : 4 * mmax + 2);
-    a.chunk = tuple_chunk(precision, a.cmax);
-    if (nt > 0)
-        if (int rc = launch_tuples(a, precision, st)) return rc;
+    TupleDevIn in{dt, dy, ds, N, (const double *)(b + o_pool), npool, (const int32_t *)(b + o_idx),
+                  (const int64_t *)(b + o_off), (const int32_t *)(b + o_ord), nt, mmax};
+    SeriesPrep *sp = nullptr;
+    if (int rc = tuple_enqueue(in, mode, precision, max_iter, tol, (double *)(b + o_z), (double *)(b + o_g),
+                               (double *)(b + o_f), (double *)(b + o_l), (int32_t *)(b + o_it),
+                               (int32_t *)(b + o_st), &sp, ws, st))
+        return rc;
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int32_t> status(std::max<int64_t>(nt, 1));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpy(status.data(), b + o_st, nt * 4, cudaMemcpyDeviceToHost));
@@ -1171,12 +1264,53 @@ int fredec_tuple_grad(const double *t, const double *y, const double *sigma, int
     std::vector<double> g(std::max<int64_t>(nflat, 1));
     TStream ts;
     FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&ts.s, cudaStreamNonBlocking));
-    int rc = tuple_run(t, y, sigma, N, tuple_freqs, (int)nflat, idx, off, 1, precision, 0, 0.0, z_out, g.data(),
-                       nullptr, nullptr, nullptr, nullptr, ts.s);
+    // mixed precision: float-float (compensated FP32-pipe) sums, FP64 solves;
+    // plain FP32 Gram sums leave the gradient at about 1e-4 relative
+    int rc = tuple_run(t, y, sigma, N, tuple_freqs, (int)nflat, idx, off, 1,
+                       precision == FREDEC_MIXED ? PREC_FF : precision, 0, 0.0, z_out, g.data(), nullptr, nullptr,
+                       nullptr, nullptr, ts.s);
     if (rc) return rc;
     // the kernel returns <d r> with d = dmu/df; dz/df = -1/2 dchi2/df = <r dmu/df>
     for (int64_t q = 0; q < nflat; ++q) dz_df_out[q] = g[q];
     return FREDEC_OK;
+}
+
+int fredec_tuple_grad_dev(const double *t, const double *y, const double *sigma, int64_t N,
+                          const double *tuple_freqs, const int64_t *tuple_offsets, int64_t n_tuples,
+                          int32_t precision, double *z_out, double *dz_df_out, void *stream) {
+    if (precision != FREDEC_FP64 && precision != FREDEC_MIXED) return fail(FREDEC_EINVAL, "bad precision");
+    if (!t || !y || !sigma || N < 1 || n_tuples < 0 || (n_tuples > 0 && (!tuple_offsets || !z_out)))
+        return fail(FREDEC_EINVAL, "bad arguments");
+    if (n_tuples > 0 && tuple_offsets[0] != 0) return fail(FREDEC_EINVAL, "tuple_offsets[0] must be 0");
+    int mmax = 0;
+    for (int64_t k = 0; k < n_tuples; ++k) {
+        const int64_t m = tuple_offsets[k + 1] - tuple_offsets[k];
+        if (m < 0 || m > FREDEC_MAX_TUPLE) return fail(FREDEC_EINVAL, "tuple sizes must be in 0..FREDEC_MAX_TUPLE");
+        if (N < 2 * m + 2) return fail(FREDEC_EINVAL, "N must exceed 2m+1 for every tuple");
+        mmax = std::max<int>(mmax, (int)m);
+    }
+    const int64_t nflat = n_tuples ? tuple_offsets[n_tuples] : 0;
+    if (nflat > 0 && (!tuple_freqs || !dz_df_out)) return fail(FREDEC_EINVAL, "null frequencies or dz_df_out");
+    if (n_tuples == 0) return FREDEC_OK;
+    const cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> idx(std::max<int64_t>(nflat, 1));
+    for (int64_t q = 0; q < nflat; ++q) idx[q] = (int32_t)q;
+    const std::vector<int32_t> order = largest_first(tuple_offsets, n_tuples);
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
+    const size_t o_idx = take(nflat * 4 + 4), o_off = take((n_tuples + 1) * 8), o_ord = take(n_tuples * 4),
+                 o_st = take(n_tuples * 4);
+    DevBuf io, ws;
+    if (int rc = io.alloc(off, st)) return rc;
+    unsigned char *b = io.as<unsigned char>();
+    // pageable sources: each copy returns once its data is staged
+    if (nflat) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_idx, idx.data(), nflat * 4, cudaMemcpyHostToDevice, st));
+    FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_off, tuple_offsets, (n_tuples + 1) * 8, cudaMemcpyHostToDevice, st));
+    FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_ord, order.data(), n_tuples * 4, cudaMemcpyHostToDevice, st));
+    TupleDevIn in{t, y, sigma, N, tuple_freqs, (int)nflat, (const int32_t *)(b + o_idx), (const int64_t *)(b + o_off),
+                  (const int32_t *)(b + o_ord), n_tuples, mmax};
+    return tuple_enqueue(in, 1, precision == FREDEC_MIXED ? PREC_FF : precision, 0, 0.0, z_out, dz_df_out, nullptr,
+                         nullptr, nullptr, (int32_t *)(b + o_st), nullptr, ws, st);
 }
 
 int fredec_pool_refine(const double *t, const double *y, const double *sigma, int64_t N, const double *pool,
