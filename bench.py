@@ -164,6 +164,170 @@ def cpu_baseline(s, nsample):
                       f"one thread, {dt:.1f} s"}
 
 
+def _oracle_shard(args):
+    """One worker of the parallel CPU baseline: the oracle on a shard of the
+    sampled frequencies (runs in a spawned process)."""
+    import oracle
+    t, y, sigma, base, f = args
+    oracle.periodogram(t, y, sigma, base, f)
+    return f.size
+
+
+def cpu_baseline_parallel(s, nsample):
+    """The same oracle as independent processes over shards of the same
+    strided sample, one per available host core (spawned: no GPU context
+    is forked)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    f = s.grid.array()
+    idx = np.linspace(0, f.size - 1, nsample).astype(np.int64)
+    shards = [(s.t, s.y, s.sigma, s.base_freqs, f[idx[r::cores]]) for r in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_shard, [(s.t[:8], s.y[:8], s.sigma[:8], s.base_freqs[:1], f[:2])] * cores)   # start-up
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_shard, shards))
+        dt = time.perf_counter() - t0
+    return {"value": s.N * done / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"same series, the same {nsample} strided trial frequencies split over {cores} processes "
+                      f"(one per host core), {dt:.1f} s"}
+
+
+def _timed(stream, fn, reps, flush):
+    """CUDA-event time (ms) of each of reps calls of fn on stream, L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    out = []
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def bench_batch(F, peak_ops, flush):
+    """The 4096-series batch (uneven N, base sizes and grids): one replay of
+    the plan's captured graph (prep, persistent periodogram kernel,
+    re-evaluation of flagged bins, top-5) per step; parity on sampled series."""
+    import torch
+    import oracle
+    w = synth.batch_4096()
+    plan = F.BatchPlan(w.series, precision="mixed", topk=5)
+    stream = torch.cuda.Stream()
+    for _ in range(2):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    ms = _timed(stream, lambda: plan.run(stream), 4, flush)
+    ops = sum(OPS_PER_TERM(2 * len(s.base_freqs) + 1) * s.N * s.grid.nf for s in w.series)
+    z, top = plan.download()
+    rng = np.random.default_rng(3)
+    errs, worst, excl = [], [], 0
+    for k in rng.choice(len(w.series), 6, replace=False):
+        s = w.series[k]
+        zk = z[plan.z_offsets[k]:plan.z_offsets[k] + s.grid.nf]
+        idx = np.unique(np.concatenate([np.linspace(0, s.grid.nf - 1, 20).astype(int), top[k][top[k] >= 0]]))
+        zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
+        e, wst, n = parity_vs_oracle(zk[idx], zr, ratio, c2, 1e-5, s.N)
+        errs.append(e)
+        worst.append(wst)
+        excl += n
+    plan.close()
+    t_ms = statistics.median(ms)
+    return {"value": plan.terms / (t_ms * 1e-3), "unit": "terms/s", "ms_per_replay": t_ms, "replays": len(ms),
+            "series": len(w.series), "terms": plan.terms,
+            "roofline_frac": ops / (t_ms * 1e-3) / peak_ops,
+            "roofline_note": "2p+9 FP32 ops per term of every series over the whole replay (prep, top-k and "
+                             "re-evaluation included) against the unit-count FP32 peak",
+            "max_rel_err_vs_oracle": max(errs), "worst_over_bound": max(worst), "excluded_cond_above_1e12": excl,
+            "sample": "6 random series x (20 strided bins + their top-5 peaks)"}
+
+
+def bench_nightly(F, peak_ops, flush):
+    """The N = 1e5, 1e7-frequency survey-like series (p = 11), mixed: the
+    whole single-series step per call, its periodogram kernel timed by the
+    library's events; then the adjoint dL/dy for all points."""
+    import torch
+    import oracle
+    s = synth.nightly_n1e5_p11()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tt = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    t, y, sg, b = tt(s.t), tt(s.y), tt(s.sigma), tt(s.base_freqs)
+    nf = s.grid.nf
+    z = torch.empty(nf, dtype=torch.float64, device=dev)
+    coef = torch.empty((nf, 2), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream()
+    res = {}
+
+    def step():
+        res.update(F.periodogram_dev(t, y, sg, b, s.grid.f0, s.grid.df, nf, precision="mixed", topk=5, out=z,
+                                     want_coef=True, stream=stream))
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    kev[0].record(stream)
+    kev[1].record(stream)
+    kms = []
+
+    def kstep():
+        F.profile_events(*kev)
+        step()
+        F.profile_events(None, None)
+
+    ms = []
+    for _ in range(3):
+        ms += _timed(stream, kstep, 1, flush)
+        kms.append(kev[0].elapsed_time(kev[1]))
+    top = res["topk"].cpu().numpy()
+    zh = z.cpu().numpy()
+    idx = np.unique(np.concatenate([np.linspace(0, nf - 1, 12).astype(int)] + [np.arange(j - 1, j + 2) for j in top[:2]]))
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
+    err, worst, excl = parity_vs_oracle(zh[idx], zr, ratio, c2, 1e-5, s.N)
+    v = tt(np.random.default_rng(1).standard_normal(nf))
+    vjp_ms = _timed(stream, lambda: F.periodogram_vjp_dev(t, y, sg, b, s.grid.f0, s.grid.df, nf, res["coef"],
+                                                          res["info"], v, precision="mixed", stream=stream), 2, flush)
+    t_ms, k_ms = statistics.median(ms), statistics.median(kms)
+    p = 2 * len(s.base_freqs) + 1
+    return {"value": s.N * nf / (t_ms * 1e-3), "unit": "terms/s", "ms_per_step": t_ms, "steps": len(ms),
+            "kernel_ms": k_ms, "roofline_frac": OPS_PER_TERM(p) * s.N * nf / (k_ms * 1e-3) / peak_ops,
+            "max_rel_err_vs_oracle": err, "worst_over_bound": worst, "excluded_cond_above_1e12": excl,
+            "sample": "12 strided bins and the neighbourhoods of the two highest peaks",
+            "vjp": {"value": s.N * nf / (statistics.median(vjp_ms) * 1e-3), "unit": "terms/s",
+                    "ms_per_call": statistics.median(vjp_ms), "what": "dL/dy for all 1e5 points, v ~ N(0,1) on "
+                                                                        "all 1e7 bins"}}
+
+
+def bench_pool16():
+    """All 65535 non-empty subtuples of the 16-frequency pool (N = 1000)
+    refined by Gauss-Newton (at most 20 steps, mixed; the host API call,
+    transfers and the float-float redo of ill-conditioned tuples included)."""
+    import paper_1309_0100_b300 as F
+    import oracle
+    s = synth.pool16_n1000()
+    masks = np.arange(1, 1 << 16, dtype=np.uint32)
+    F.pool_refine(s.t, s.y, s.sigma, s.pool, masks[:64], max_iter=20, precision="mixed")   # warm-up
+    times, it = [], None
+    for _ in range(2):
+        t0 = time.perf_counter()
+        mk, f, l, it = F.pool_refine(s.t, s.y, s.sigma, s.pool, masks, max_iter=20, precision="mixed")
+        times.append(time.perf_counter() - t0)
+    m = np.array([bin(int(x)).count("1") for x in masks])
+    work = int(np.sum((it.astype(np.int64) + 1) * m)) * s.N
+    dt = min(times)
+    rng = np.random.default_rng(4)
+    lerr = 0.0
+    for q in rng.choice(masks.size, 6, replace=False):
+        sel = [k for k in range(16) if int(masks[q]) >> k & 1]
+        lerr = max(lerr, abs(oracle.tuple_l(s.t, s.y, s.sigma, f[q, sel]) - l[q]) / l[q])
+    return {"seconds": dt, "tuples": int(masks.size), "value": work / dt, "unit": "terms/s",
+            "terms": work, "terms_note": "sum over tuples of (accepted Gauss-Newton steps + 1) x m x N "
+                                         "(rejected half steps not counted)",
+            "max_rel_err_l_vs_oracle_at_gpu_freqs": lerr, "sample": "6 random subtuples"}
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return
@@ -197,6 +361,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the batch, survey-series and pool-refinement lines")
     ap.add_argument("--cpu-sample", type=int, default=30000)
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling runs: fixed launch shape, mixed steps only (no tuning, FP64, e2e or CPU legs)")
@@ -309,6 +475,12 @@ def main():
     err_mixed, worst_mixed, n_excl = parity_vs_oracle(z_mixed[idx], zr, ratio, c2, 1e-5, N)
     err_64, worst_64, _ = parity_vs_oracle(z64[idx], zr, ratio, c2, 1e-10, N)
     cpu = None if args.no_cpu_baseline else cpu_baseline(s, args.cpu_sample)
+    cpu_par = None if args.no_cpu_baseline else cpu_baseline_parallel(s, args.cpu_sample)
+    others = {}
+    if not args.no_other_workloads:
+        others["batch_4096"] = bench_batch(F, peak_ops, flush)
+        others["nightly_n1e5_p11"] = bench_nightly(F, peak_ops, flush)
+        others["pool16_refine"] = bench_pool16()
     line = {
         "metric": METRIC,
         "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -332,6 +504,8 @@ def main():
                      "peak_source": f"148 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (unit counts x max clock)",
                      "measured_pipe_rates": {k: v / 1e12 for k, v in pipe.items()}},
         "cpu_baseline": cpu,
+        "cpu_baseline_parallel": cpu_par,
+        "other_workloads": others,
         "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": int(8 * (3 * N + nb)),
                 "d2h_bytes_per_step": int(8 * nf + 8 * 5)},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
