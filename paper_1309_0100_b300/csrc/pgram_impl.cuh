@@ -75,6 +75,7 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // F) so that persistent kernels switching between (P, F) fill it once.
 constexpr size_t OFF_TABLE = 128;
 constexpr size_t OFF_TILES_BASE = OFF_TABLE + sizeof(SeedTable);
+static_assert(sizeof(SeedTableF) <= sizeof(SeedTable), "both seed tables fit the table region");
 
 // NSET = 2: every record carries a second set of weighted values, the
 // t'-weighted ones, and the kernel accumulates 2 (2P+4) sums per frequency.
