@@ -383,7 +383,9 @@ int fredec_batch_plan_run(fredec_batch_plan *plan, void *stream);
 /* Device pointers to the plan's outputs (valid until destroy). */
 int fredec_batch_plan_outputs(fredec_batch_plan *plan, double **z_dev, int64_t **topk_dev,
                               int64_t *z_total, int64_t *terms);
-/* Copy the outputs to host buffers (synchronous). Either may be NULL. */
+/* Copy the outputs to host buffers (synchronous). Either may be NULL.
+ * FREDEC_ESINGULAR when a series' base model is singular, FREDEC_ETIMEOUT
+ * when a bounded device wait of the last replay gave up. */
 int fredec_batch_plan_download(fredec_batch_plan *plan, double *z_out, int64_t *topk_idx_out);
 void fredec_batch_plan_destroy(fredec_batch_plan *plan);
 

@@ -57,6 +57,7 @@ struct fredec_batch_plan {
     int enqueue(cudaStream_t st, int w) {
         FREDEC_CUDA_TRY(cudaMemsetAsync(counter, 0, 8, st));
         FREDEC_CUDA_TRY(cudaMemsetAsync(flag_count, 0, 4, st));
+        FREDEC_CUDA_TRY(cudaMemsetAsync(err, 0, 4, st));   // status of this replay
         PrepPlan pp;
         pp.S = S;
         pp.max_n = max_n;
@@ -349,6 +350,10 @@ int fredec_batch_plan_download(fredec_batch_plan *plan, double *z_out, int64_t *
     for (int s = 0; s < plan->S; ++s)
         if (status[s] != FREDEC_OK)
             return fail(FREDEC_ESINGULAR, "series " + std::to_string(s) + ": base normal matrix is singular");
+    int32_t e = FREDEC_OK;   // the last replay's bounded waits and index checks
+    FREDEC_CUDA_TRY(cudaMemcpy(&e, plan->err, 4, cudaMemcpyDeviceToHost));
+    if (e == FREDEC_ETIMEOUT) return fail(FREDEC_ETIMEOUT, "a bounded device wait gave up");
+    if (e != FREDEC_OK) return fail(FREDEC_ECUDA, "a device-side index check failed (the access was skipped)");
     if (z_out) FREDEC_CUDA_TRY(cudaMemcpy(z_out, plan->z, plan->z_total * 8, cudaMemcpyDeviceToHost));
     if (topk_idx_out && plan->topk > 0)
         FREDEC_CUDA_TRY(cudaMemcpy(topk_idx_out, plan->topk_out, (size_t)plan->S * plan->topk * 8,

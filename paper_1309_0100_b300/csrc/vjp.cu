@@ -26,6 +26,7 @@ constexpr int VJ_THREADS = 128;
 constexpr int VJ_PT = 8;            // points per thread (measured: 5% faster than 4 on 1e5 points x 1e7 bins)
 constexpr int VJ_TILE = 2048;       // frequencies staged per shared-memory tile
 constexpr int VJ_SEG = 32;          // re-seed every 32 frequencies
+static_assert(VJ_PT % 2 == 0, "the mixed kernel takes the points in pairs");
 
 __global__ void vjp_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int32_t *cs, int64_t nchunks) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,33 +38,41 @@ __global__ void vjp_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) cs[q] = 0;
 }
 
-// (v_j a_j, v_j b_j) per frequency, in the accumulation precision.
-template <class T>
-__global__ void vjp_coef(const double *coef, const double *v, int64_t nf, T *ab) {
+// (v_j a_j, v_j b_j) per frequency (FP64 path).
+__global__ void vjp_coef(const double *coef, const double *v, int64_t nf, double *ab) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x) {
-        ab[2 * j] = (T)(v[j] * coef[2 * j]);
-        ab[2 * j + 1] = (T)(v[j] * coef[2 * j + 1]);
+        ab[2 * j] = v[j] * coef[2 * j];
+        ab[2 * j + 1] = v[j] * coef[2 * j + 1];
     }
 }
 
-// g partials: block (x: points, y: frequency chunk).  Records are the FP64
-// records of the prep (phases A, B).  gpart[chunk * N + i].
-template <class T>
-__global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, const unsigned char *rec64,
-                                                       const T *ab, int64_t chunk_len, double *gpart) {
-    __shared__ __align__(16) T sab[2 * VJ_TILE];
-    __shared__ SeedTable tab;
+// Mixed path: (v_j a_j, v_j a_j, v_j b_j, v_j b_j) per frequency, the
+// duplicated pairs that the packed instructions of vjp_trig_mixed take.
+__global__ void vjp_coef_pairs(const double *coef, const double *v, int64_t nf, float4 *ab) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x) {
+        const float a = (float)(v[j] * coef[2 * j]), b = (float)(v[j] * coef[2 * j + 1]);
+        ab[j] = make_float4(a, a, b, b);
+    }
+}
+
+// g partials of the mixed path: as vjp_trig with FP32 values, the thread's
+// VJ_PT points in pairs held in float2 registers and updated by packed FP32
+// instructions: per frequency and pair, acc += a c + b s (two FFMA2) and the
+// rotation of (c, s) (two FMUL2, two FFMA2) -- half the warp instructions of
+// the scalar loop, the same arithmetic per component.
+__global__ void __launch_bounds__(VJ_THREADS) vjp_trig_mixed(const SeriesDesc *desc, const unsigned char *rec64,
+                                                             const float4 *ab, int64_t chunk_len, double *gpart) {
+    constexpr int NP = VJ_PT / 2;
+    __shared__ __align__(16) float4 sab[VJ_TILE];
     __shared__ SeedTableF tabf;
-    if constexpr (sizeof(T) == 8) fill_seed_table(tab); else fill_seed_table_f(tabf);
+    fill_seed_table_f(tabf);
     const SeriesDesc d = *desc;
-    const int p = d.p;
-    const int rw = rec64_words(p);
+    const int rw = rec64_words(d.p);
     const int64_t j_begin = (int64_t)blockIdx.y * chunk_len;
     const int64_t j_end = std::min<int64_t>(d.nf, j_begin + chunk_len);
     uint64_t A[VJ_PT], B[VJ_PT];
-    T cr[VJ_PT], sr[VJ_PT];
-    double g[VJ_PT];            // FP64 path: running sum
-    float ghi[VJ_PT], glo[VJ_PT];   // FP32 path: float-float running sum (no FP64-pipe conversions)
+    float2 cr[NP], sr[NP], nsr[NP];
+    float ghi[VJ_PT], glo[VJ_PT];   // float-float running sums (no FP64-pipe conversions)
     int64_t idx[VJ_PT];
 #pragma unroll
     for (int q = 0; q < VJ_PT; ++q) {
@@ -73,11 +82,98 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
         const uint64_t *R = reinterpret_cast<const uint64_t *>(rec64) + ic * rw;
         A[q] = R[0];
         B[q] = R[1];
-        cr[q] = (T)reinterpret_cast<const double *>(R)[2];
-        sr[q] = (T)reinterpret_cast<const double *>(R)[3];
-        g[q] = 0.0;
+        const float c1 = (float)reinterpret_cast<const double *>(R)[2], s1 = (float)reinterpret_cast<const double *>(R)[3];
+        if (q & 1) {
+            cr[q / 2].y = c1;
+            sr[q / 2].y = s1;
+            nsr[q / 2].y = -s1;
+        } else {
+            cr[q / 2].x = c1;
+            sr[q / 2].x = s1;
+            nsr[q / 2].x = -s1;
+        }
         ghi[q] = 0.f;
         glo[q] = 0.f;
+    }
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += VJ_TILE) {
+        const int nt = (int)std::min<int64_t>(VJ_TILE, j_end - j0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) sab[k] = ab[j0 + k];
+        __syncthreads();
+        for (int seg = 0; seg < nt; seg += VJ_SEG) {
+            const int ns = min(VJ_SEG, nt - seg);
+            float2 c[NP], s[NP], acc[NP];
+#pragma unroll
+            for (int q = 0; q < VJ_PT; ++q) {
+                const uint64_t ph = A[q] + (uint64_t)(j0 + seg) * B[q];
+                float ss, cc;
+                seed_from_table_f(tabf, (uint32_t)(ph >> 32), &ss, &cc);
+                if (q & 1) {
+                    c[q / 2].y = cc;
+                    s[q / 2].y = ss;
+                } else {
+                    c[q / 2].x = cc;
+                    s[q / 2].x = ss;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc[q] = make_float2(0.f, 0.f);
+            auto step = [&](int k) {
+                const float4 w = sab[seg + k];
+                const float2 a = make_float2(w.x, w.y), b = make_float2(w.z, w.w);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    acc[q] = __ffma2_rn(a, c[q], __ffma2_rn(b, s[q], acc[q]));
+                    const float2 cn = __ffma2_rn(c[q], cr[q], __fmul2_rn(s[q], nsr[q]));
+                    s[q] = __ffma2_rn(s[q], cr[q], __fmul2_rn(c[q], sr[q]));
+                    c[q] = cn;
+                }
+            };
+            if (ns == VJ_SEG) {   // full segments: no loop bookkeeping
+#pragma unroll
+                for (int k = 0; k < VJ_SEG; ++k) step(k);
+            } else {
+                for (int k = 0; k < ns; ++k) step(k);
+            }
+#pragma unroll
+            for (int q = 0; q < VJ_PT; ++q) {   // float-float running sum of the segment sums (TwoSum)
+                const float a = (q & 1) ? acc[q / 2].y : acc[q / 2].x;
+                const float h = ghi[q], sum = h + a, bp = sum - h;
+                glo[q] += (h - (sum - bp)) + (a - bp);
+                ghi[q] = sum;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < VJ_PT; ++q)
+        if (idx[q] < d.N) gpart[(int64_t)blockIdx.y * d.N + idx[q]] = (double)ghi[q] + (double)glo[q];
+}
+
+// g partials of the FP64 path: block (x: points, y: frequency chunk).  Records
+// are the FP64 records of the prep (phases A, B).  gpart[chunk * N + i].
+__global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, const unsigned char *rec64,
+                                                       const double *ab, int64_t chunk_len, double *gpart) {
+    __shared__ __align__(16) double sab[2 * VJ_TILE];
+    __shared__ SeedTable tab;
+    fill_seed_table(tab);
+    const SeriesDesc d = *desc;
+    const int rw = rec64_words(d.p);
+    const int64_t j_begin = (int64_t)blockIdx.y * chunk_len;
+    const int64_t j_end = std::min<int64_t>(d.nf, j_begin + chunk_len);
+    uint64_t A[VJ_PT], B[VJ_PT];
+    double cr[VJ_PT], sr[VJ_PT], g[VJ_PT];
+    int64_t idx[VJ_PT];
+#pragma unroll
+    for (int q = 0; q < VJ_PT; ++q) {
+        const int64_t i = ((int64_t)blockIdx.x * VJ_PT + q) * VJ_THREADS + threadIdx.x;
+        idx[q] = i;
+        const int64_t ic = i < d.N ? i : d.N - 1;
+        const uint64_t *R = reinterpret_cast<const uint64_t *>(rec64) + ic * rw;
+        A[q] = R[0];
+        B[q] = R[1];
+        cr[q] = reinterpret_cast<const double *>(R)[2];
+        sr[q] = reinterpret_cast<const double *>(R)[3];
+        g[q] = 0.0;
     }
     for (int64_t j0 = j_begin; j0 < j_end; j0 += VJ_TILE) {
         const int nt = (int)std::min<int64_t>(VJ_TILE, j_end - j0);
@@ -86,29 +182,18 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
         __syncthreads();
         for (int seg = 0; seg < nt; seg += VJ_SEG) {
             const int ns = min(VJ_SEG, nt - seg);
-            T c[VJ_PT], s[VJ_PT], acc[VJ_PT];
+            double c[VJ_PT], s[VJ_PT], acc[VJ_PT];
 #pragma unroll
             for (int q = 0; q < VJ_PT; ++q) {
-                const uint64_t ph = A[q] + (uint64_t)(j0 + seg) * B[q];
-                if constexpr (sizeof(T) == 8) {
-                    double ss, cc;
-                    seed_from_table(tab, ph, &ss, &cc);
-                    c[q] = cc;
-                    s[q] = ss;
-                } else {
-                    float ss, cc;
-                    seed_from_table_f(tabf, (uint32_t)(ph >> 32), &ss, &cc);
-                    c[q] = cc;
-                    s[q] = ss;
-                }
-                acc[q] = T(0);
+                seed_from_table(tab, A[q] + (uint64_t)(j0 + seg) * B[q], &s[q], &c[q]);
+                acc[q] = 0.0;
             }
             auto step = [&](int k) {
-                const T a = sab[2 * (seg + k)], b = sab[2 * (seg + k) + 1];
+                const double a = sab[2 * (seg + k)], b = sab[2 * (seg + k) + 1];
 #pragma unroll
                 for (int q = 0; q < VJ_PT; ++q) {
                     acc[q] = fma(a, c[q], fma(b, s[q], acc[q]));
-                    const T cn = fma(c[q], cr[q], -s[q] * sr[q]);
+                    const double cn = fma(c[q], cr[q], -s[q] * sr[q]);
                     s[q] = fma(s[q], cr[q], c[q] * sr[q]);
                     c[q] = cn;
                 }
@@ -120,22 +205,12 @@ __global__ void __launch_bounds__(VJ_THREADS) vjp_trig(const SeriesDesc *desc, c
                 for (int k = 0; k < ns; ++k) step(k);
             }
 #pragma unroll
-            for (int q = 0; q < VJ_PT; ++q) {
-                if constexpr (sizeof(T) == 8) {
-                    g[q] += acc[q];
-                } else {   // float-float running sum of the FP32 segment sums (TwoSum)
-                    const float h = ghi[q], sum = h + acc[q], bp = sum - h;
-                    glo[q] += (h - (sum - bp)) + (acc[q] - bp);
-                    ghi[q] = sum;
-                }
-            }
+            for (int q = 0; q < VJ_PT; ++q) g[q] += acc[q];
         }
     }
 #pragma unroll
-    for (int q = 0; q < VJ_PT; ++q) {
-        if constexpr (sizeof(T) == 4) g[q] = (double)ghi[q] + (double)glo[q];
+    for (int q = 0; q < VJ_PT; ++q)
         if (idx[q] < d.N) gpart[(int64_t)blockIdx.y * d.N + idx[q]] = g[q];
-    }
 }
 
 // Sum the frequency-chunk partials of g (in chunk order) and form the base
@@ -208,13 +283,13 @@ int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, i
     gy = std::min<int64_t>(gy, std::max<int64_t>(1, (nf + VJ_TILE - 1) / VJ_TILE));
     const int64_t chunk_len = (nf + gy - 1) / gy;
     const int gamma_blocks = (int)std::min<int64_t>(256, (N + 255) / 256);
-    const size_t abw = precision == FREDEC_MIXED ? 4 : 8;
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
     const size_t o_desc = take(sizeof(SeriesDesc)), o_state = take(sizeof(SeriesState));
     const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
     const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * (size_t)rec_bytes(p, FREDEC_FP64));
-    const size_t o_ab = take(2 * nf * abw + 16), o_g = take(gy * N * 8);
+    // 16 bytes per frequency: (a, b) doubles, or (a, a, b, b) floats (mixed)
+    const size_t o_ab = take(16 * nf + 16), o_g = take(gy * N * 8);
     const size_t o_gp = take(gamma_blocks * PMAX * 8), o_gm = take(PMAX * 8), o_cnt = take(4);
     DevBuf ws;
     if (int rc = ws.alloc(off, st)) return rc;
@@ -249,13 +324,13 @@ int launch_vjp_pipeline(const double *t, const double *y, const double *sigma, i
     if (int rc = run_prep_records(pp, t, y, sigma, base, FREDEC_FP64, nullptr, st)) return rc;
     const dim3 grid((unsigned)gx, (unsigned)gy);
     if (precision == FREDEC_MIXED) {
-        vjp_coef<float><<<256, 256, 0, st>>>(coef, v, nf, (float *)(b + o_ab));
-        vjp_trig<float><<<grid, VJ_THREADS, 0, st>>>(desc, b + o_rec, (const float *)(b + o_ab), chunk_len,
-                                                     (double *)(b + o_g));
+        vjp_coef_pairs<<<256, 256, 0, st>>>(coef, v, nf, (float4 *)(b + o_ab));
+        vjp_trig_mixed<<<grid, VJ_THREADS, 0, st>>>(desc, b + o_rec, (const float4 *)(b + o_ab), chunk_len,
+                                                    (double *)(b + o_g));
     } else {
-        vjp_coef<double><<<256, 256, 0, st>>>(coef, v, nf, (double *)(b + o_ab));
-        vjp_trig<double><<<grid, VJ_THREADS, 0, st>>>(desc, b + o_rec, (const double *)(b + o_ab), chunk_len,
-                                                      (double *)(b + o_g));
+        vjp_coef<<<256, 256, 0, st>>>(coef, v, nf, (double *)(b + o_ab));
+        vjp_trig<<<grid, VJ_THREADS, 0, st>>>(desc, b + o_rec, (const double *)(b + o_ab), chunk_len,
+                                              (double *)(b + o_g));
     }
     vjp_gamma<<<gamma_blocks, 256, 0, st>>>(desc, (const double *)(b + o_psi), t, sigma, (double *)(b + o_g), (int)gy,
                                             (double *)(b + o_gp), (double *)(b + o_gm), (uint32_t *)(b + o_cnt));

@@ -44,8 +44,16 @@ def test_batch_4096_full(F):
         idx = np.unique(np.concatenate([np.linspace(0, s.grid.nf - 1, 24).astype(int), top[k][top[k] >= 0]]))
         _check_sampled(zk, s, idx, 1e-5)
         z64, t64 = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array(), precision="fp64", topk=5)
-        zs = sorted(z64[t64], reverse=True)
-        if np.all(-np.diff(zs) > 1e-4 * zs[0]):
+        # the peak indices must agree where the ranking is not a near-tie: the
+        # peaks' heights apart by more than the path tolerance, each peak clear
+        # of its neighbours, and every peak bin well conditioned (near f = 0
+        # and the base frequencies the 2x2 system amplifies rounding)
+        ts = [j for j in t64 if j >= 0]
+        zs = sorted(z64[ts], reverse=True)
+        clear = all(min(abs(z64[j] - z64[n]) for n in (j - 1, j + 1) if 0 <= n < z64.size) > 1e-4 * z64[j]
+                    for j in ts)
+        _, _, rat = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[ts], want_ratio=True)
+        if np.all(-np.diff(zs) > 1e-4 * zs[0]) and clear and np.all(rat > 0.1):
             assert list(top[k]) == list(t64), k
 
 
