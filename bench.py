@@ -353,10 +353,17 @@ def bench_grad(F, peak_ops, flush):
                       "bins the kernel does not re-evaluate (ratio > 0.45), the bound over all"}
 
 
-def bench_pool16():
+def bench_pool16(peak_ops):
     """All 65535 non-empty subtuples of the 16-frequency pool (N = 1000)
     refined by Gauss-Newton (at most 20 steps, mixed; the host API call,
-    transfers and the float-float redo of ill-conditioned tuples included)."""
+    transfers and the float-float redo of ill-conditioned tuples included).
+    Roofline: the FP32 work of one pass over the points for a tuple of m
+    frequencies is the Gram of its 4m + 2 columns ((4m+2)(4m+3)/2 FMAs a
+    point) plus their generation (8 operations a frequency: rotation and
+    weighting of cos, sin, t' cos, t' sin), counted for the passes of the
+    accepted steps (plus the first) of every tuple, against the unit-count
+    FP32 peak; rejected half steps and the float-float redo are not counted
+    as work."""
     import paper_1309_0100_b300 as F
     import oracle
     s = synth.pool16_n1000()
@@ -369,6 +376,7 @@ def bench_pool16():
         times.append(time.perf_counter() - t0)
     m = np.array([bin(int(x)).count("1") for x in masks])
     work = int(np.sum((it.astype(np.int64) + 1) * m)) * s.N
+    ops = float(np.sum((it.astype(np.float64) + 1) * ((4 * m + 2) * (4 * m + 3) / 2 + 8 * m))) * s.N
     dt = min(times)
     rng = np.random.default_rng(4)
     lerr = 0.0
@@ -379,6 +387,8 @@ def bench_pool16():
     return {"seconds": dt, "tuples": int(masks.size), "value": work / dt, "unit": "terms/s",
             "terms": work, "terms_note": "sum over tuples of (accepted Gauss-Newton steps + 1) x m x N "
                                          "(rejected half steps not counted)",
+            "roofline_frac": ops / dt / peak_ops,
+            "roofline_note": "FP32 Gram and column operations of the counted passes against the unit-count FP32 peak",
             "max_err_l_vs_oracle_at_gpu_freqs": lerr, "err_unit": "of l_0 (FP32 sums resolve l to about 3e-7 of "
                                                                    "l_0)", "sample": "6 random subtuples"}
 
@@ -535,7 +545,7 @@ def main():
     if not args.no_other_workloads:
         others["batch_4096"] = bench_batch(F, peak_ops, flush)
         others["nightly_n1e5_p11"] = bench_nightly(F, peak_ops, flush)
-        others["pool16_refine"] = bench_pool16()
+        others["pool16_refine"] = bench_pool16(peak_ops)
         others["residual_n2000_p7_dzdf"] = bench_grad(F, peak_ops, flush)
     line = {
         "metric": METRIC,

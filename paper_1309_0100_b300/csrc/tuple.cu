@@ -5,9 +5,11 @@
 //   local refinement (Section 3, Eq. lsqf): Gauss-Newton on f with the linear
 //   parameters refitted at every step.
 //
-// One CTA per tuple (persistent CTAs, largest tuples first).  A pass over the
-// points builds the weighted columns of a chunk of points in shared memory
-// (one point per thread) and
+// One CTA per tuple (persistent CTAs, largest tuples first), one launch per
+// range of three tuple sizes with shared memory and CTA width sized for the
+// range, the ranges on concurrent streams.  A pass over the points builds the
+// weighted columns of a chunk of points in shared memory (one point per
+// thread) and
 // accumulates their Gram matrix: every thread owns 4x4 blocks of the lower
 // triangle and runs over the chunk's points with float4 shared loads; when a
 // tuple has fewer blocks than threads the points are split among groups of
@@ -364,12 +366,17 @@ __device__ __forceinline__ void load4(const double *p, double *v) {
 // added into running sums.  FF: double-float running sums (ff_acc), each
 // product r c of hi/lo pairs entering as its rounded hi*hi part plus the exact
 // rounding error of that product and the two cross terms.
-template <class T> struct BlockAcc {
+// 4x4 blocks per thread: QB, or 1 for float-float sums, whose accumulators
+// take four registers an entry (more threads per tuple instead, and more
+// resident warps to hide the latency of their dependent chains).
+template <class T> constexpr int qb_of() { return std::is_same<T, FF>::value ? 1 : QB; }
+
+template <class T, int Q = QB> struct BlockAcc {
     using V = typename TP<T>::pt;
-    V acc[QB][16];
+    V acc[Q][16];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int b = 0; b < QB; ++b)
+        for (int b = 0; b < Q; ++b)
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[b][e] = V(0);
     }
@@ -378,6 +385,7 @@ template <class T> struct BlockAcc {
 #pragma unroll
         for (int e = 0; e < 16; ++e) part[e] = V(0);
         const V *xr = X + 4 * rb, *xc = X + 4 * cb;
+#pragma unroll 4
         for (int p = g; p < n; p += G) {
             V r[4], c[4];
             load4(xr + (size_t)p * CP, r);
@@ -431,11 +439,11 @@ struct ff_acc2 {
 // 4u + 2w + 1, w = 0, 1: one row column against two column columns) in
 // packed double-float sums; the planar tile rows give the hi and lo parts of
 // four columns as one float4 each.
-template <> struct BlockAcc<FF> {
-    ff_acc2 a[QB][8];
+template <int Q> struct BlockAcc<FF, Q> {
+    ff_acc2 a[Q][8];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int b = 0; b < QB; ++b)
+        for (int b = 0; b < Q; ++b)
 #pragma unroll
             for (int e = 0; e < 8; ++e) a[b][e] = ff_acc2();
     }
@@ -475,20 +483,22 @@ __device__ __forceinline__ void block_rc(int q, int *rb, int *cb) {
 template <class T>
 __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, double *Gs, unsigned char *R, int m,
                           bool with_uv) {
+    constexpr int QBT = qb_of<T>();
     const int M = 2 * m + 1, C = with_uv ? M + 1 + 2 * m : M + 1, CP = (C + 3) & ~3;
     const int nb = CP / 4, nblk = nb * (nb + 1) / 2;
     const int tid = threadIdx.x, L = blockDim.x;
-    int G = 1, g = 0, nq = 0, rb[QB], cb[QB], qid = 0;
+    int G = 1, g = 0, nq = 0, rb[QBT], cb[QBT], qid = 0;
     if (nblk <= L) {
         G = L / nblk;
         g = tid / nblk;
         qid = tid % nblk;
         nq = tid < G * nblk ? 1 : 0;
         block_rc(qid, &rb[0], &cb[0]);
-        rb[1] = cb[1] = 0;
+#pragma unroll
+        for (int b = 1; b < QBT; ++b) rb[b] = cb[b] = 0;
     } else {
 #pragma unroll
-        for (int b = 0; b < QB; ++b) {
+        for (int b = 0; b < QBT; ++b) {
             const int q = tid + b * L;
             rb[b] = cb[b] = 0;
             if (q < nblk) {
@@ -497,7 +507,7 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
             }
         }
     }
-    BlockAcc<T> acc;
+    BlockAcc<T, QBT> acc;
     acc.zero();
     using Tile = typename TP<T>::tile;
     Tile *X = reinterpret_cast<Tile *>(R);
@@ -507,13 +517,13 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
         for (int p = tid; p < n; p += L) make_row<T>(a, s, tab, i0 + p, m, with_uv, C, CP, X + (size_t)p * CP);
         __syncthreads();
 #pragma unroll
-        for (int b = 0; b < QB; ++b)
+        for (int b = 0; b < QBT; ++b)
             if (b < nq) acc.chunk(b, X, rb[b], cb[b], g, G, n, CP);
     }
     __syncthreads();
     if (G == 1) {
 #pragma unroll
-        for (int b = 0; b < QB; ++b)
+        for (int b = 0; b < QBT; ++b)
             if (b < nq)
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -540,36 +550,46 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
 }
 
 // In-place right-looking Cholesky of the packed C x C matrix by the whole CTA.
-// Thread 0 takes each pivot (check, square root, reciprocal; the reciprocal
-// diagonal is kept in inv[] for the substitutions), the CTA scales the column
-// and updates the trailing triangle (threads over its entries).
-// Pivots 0..nchk-1 must keep more than 1e-13 of their original diagonal; the
-// index of the first that does not is left in s.fail_at (C when all do).
-// s.ratio = the smallest pivot ratio among the first nlin pivots.  Later
-// pivots (the data column) are factored without a check.
-__device__ void chol_cta(double *A, double *d0, double *inv, int C, int nlin, int nchk, TState &s) {
+// The reciprocals of the original diagonal are formed first, in parallel
+// (rd0[]), so that a pivot's check is one multiplication.  Thread 0 takes each
+// pivot (check, reciprocal square root; the reciprocal diagonal is kept in
+// inv[] for the substitutions): pivot j + 1 as soon as its own part of
+// pivot j's trailing update has produced it (entry (j+1, j+1) is that
+// update's first entry, always thread 0's), while the other threads finish
+// theirs -- two barriers a pivot.  The CTA scales the column and updates the
+// trailing triangle (threads over its entries).  Pivots 0..nchk-1 must keep
+// more than 1e-13 of their original diagonal; the index of the first that
+// does not is left in s.fail_at (C when all do).  s.ratio = the smallest
+// pivot ratio among the first nlin pivots.  Later pivots (the data column)
+// are factored without a check.
+__device__ void chol_cta(double *A, double *rd0, double *inv, int C, int nlin, int nchk, TState &s) {
     const int tid = threadIdx.x, L = blockDim.x;
-    for (int j = tid; j < C; j += L) d0[j] = A[tri(j, j)];
+    for (int j = tid; j < C; j += L) {
+        const double v = A[tri(j, j)];
+        rd0[j] = v > 0.0 ? 1.0 / v : -1.0;
+    }
+    __syncthreads();
+    auto pivot = [&](int j) {   // thread 0
+        const double d = A[tri(j, j)];
+        if (j < nchk) {
+            const double r = rd0[j] > 0.0 ? d * rd0[j] : -1.0;
+            if (j < nlin) s.ratio = fmin(s.ratio, r);
+            if (!(r > 1e-13)) s.fail_at = j;
+        }
+        // one FP64 reciprocal square root per pivot (no division): 1/L_jj,
+        // and L_jj = d / sqrt(d)
+        const double il = d > 0.0 ? rsqrt(d) : 0.0;
+        A[tri(j, j)] = d * il;
+        inv[j] = il;
+    };
     if (tid == 0) {
         s.fail_at = C;
         s.ratio = 1.0;
+        if (C > 0) pivot(0);
     }
     __syncthreads();
     for (int j = 0; j < C; ++j) {
-        if (tid == 0) {
-            const double d = A[tri(j, j)];
-            if (j < nchk) {
-                if (j < nlin) s.ratio = fmin(s.ratio, d0[j] > 0.0 ? d / d0[j] : -1.0);
-                if (!(d > 1e-13 * d0[j]) || !(d0[j] > 0.0)) s.fail_at = j;
-            }
-            // one FP64 reciprocal square root per pivot (no division): 1/L_jj,
-            // and L_jj = d / sqrt(d)
-            const double il = d > 0.0 ? rsqrt(d) : 0.0;
-            A[tri(j, j)] = d * il;
-            inv[j] = il;
-        }
-        __syncthreads();
-        if (s.fail_at < C) break;
+        if (s.fail_at <= j) break;
         const double iv = inv[j];
         for (int i = j + 1 + tid; i < C; i += L) A[tri(i, j)] *= iv;
         __syncthreads();
@@ -580,6 +600,7 @@ __device__ void chol_cta(double *A, double *d0, double *inv, int C, int nlin, in
             while (tri(ii, 0) > e) --ii;
             const int i = j + 1 + ii, k = j + 1 + (e - tri(ii, 0));
             A[tri(i, k)] -= A[tri(i, j)] * A[tri(k, j)];
+            if (e == 0) pivot(j + 1);
         }
         __syncthreads();
     }
@@ -662,15 +683,27 @@ __device__ bool extend_cta(const double *H, const double *invL, int M, int m, co
                 (bk * bl * Hs(uk, ul) - bk * al * Hs(uk, ul + 1) - ak * bl * Hs(uk + 1, ul) + ak * al * Hs(uk + 1, ul + 1));
     }
     __syncthreads();
-    // X = L^{-1} <phi d>: column k of X is row k of Xs; rows eliminated in order
-    for (int r = 0; r < M; ++r) {
-        const double ir = invL[r];
-        for (int k = tid; k < m; k += L) Xs[k * M + r] *= ir;
+    // X = L^{-1} <phi d>: column k of X is row k of Xs; rows eliminated four
+    // at a time (the four-row diagonal block by one thread per column, then
+    // the rows below by all threads), in the order of the row-by-row
+    // elimination for every entry
+    for (int r0 = 0; r0 < M; r0 += 4) {
+        const int nr = M - r0 < 4 ? M - r0 : 4;
+        for (int k = tid; k < m; k += L) {
+            double *x = Xs + (size_t)k * M;
+            for (int u = 0; u < nr; ++u) {
+                const int r = r0 + u;
+                x[r] *= invL[r];
+                for (int v = u + 1; v < nr; ++v) x[r0 + v] -= H[tri(r0 + v, r)] * x[r];
+            }
+        }
         __syncthreads();
-        const int rest = M - r - 1;
+        const int rest = M - r0 - nr;
         for (int e = tid; e < m * rest; e += L) {
-            const int k = e / rest, rr = r + 1 + (e - k * rest);
-            Xs[k * M + rr] -= H[tri(rr, r)] * Xs[k * M + r];
+            const int k = e / rest, rr = r0 + nr + (e - k * rest);
+            double v = Xs[k * M + rr];
+            for (int u = 0; u < nr; ++u) v -= H[tri(rr, r0 + u)] * Xs[k * M + r0 + u];
+            Xs[k * M + rr] = v;
         }
         __syncthreads();
     }
@@ -817,8 +850,12 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
 // NT threads per CTA: 64 when two 4x4 blocks per thread cover the widest Gram
 // of the launch (more tuples per SM, so one tuple's serial FP64 solve leaves
 // fewer warps idle), else 128.
+template <class T> constexpr int tuple_min_blocks(int nt) {
+    return (std::is_same<T, FF>::value ? 608 : TP<T>::mixed ? 512 : 384) / nt;
+}
+
 template <class T, int NT>
-__global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_kernel(TupleArgs a) {
+__global__ void __launch_bounds__(NT, tuple_min_blocks<T>(NT)) tuple_kernel(TupleArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int CP = (a.cmax + 3) & ~3;
     size_t o = 0;
@@ -854,7 +891,7 @@ __global__ void __launch_bounds__(NT, (TP<T>::mixed ? 512 : 384) / NT) tuple_ker
 
 static_assert(sizeof(SeedTable) == sizeof(SeedTableFF), "the FF passes reuse the FP64 table's space");
 
-size_t tuple_smem(int prec, int cmax, int chunk) {
+size_t tuple_smem(int prec, int cmax, int chunk, int nt) {
     const size_t tsz = prec == FREDEC_MIXED ? 4 : 8;
     const int CP = (cmax + 3) & ~3;
     size_t o = prec == FREDEC_MIXED ? sizeof(SeedTableF) : sizeof(SeedTable);
@@ -863,7 +900,7 @@ size_t tuple_smem(int prec, int cmax, int chunk) {
     o = (o + 15) & ~(size_t)15;
     o += sizeof(double) * (size_t)cmax * (cmax + 1) / 2 + 2 * sizeof(double) * (size_t)cmax;
     o = (o + 15) & ~(size_t)15;
-    o += std::max<size_t>((size_t)chunk * CP * tsz, (size_t)WT_THREADS * 16 * 8);
+    o += std::max<size_t>((size_t)chunk * CP * tsz, (size_t)nt * 16 * 8);
     return o;
 }
 
@@ -951,25 +988,66 @@ __global__ void __launch_bounds__(32 * PM_WARPS) pool_mask_kernel(const double *
 
 // Host side -------------------------------------------------------------------
 
-static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
-    const size_t smem = tuple_smem(precision, a.cmax, a.chunk);
-    const int nb = ((a.cmax + 3) & ~3) / 4;
-    const int nt = nb * (nb + 1) / 2 <= QB * 64 ? 64 : WT_THREADS;
-    auto kern = precision == FREDEC_MIXED ? (nt == 64 ? tuple_kernel<float, 64> : tuple_kernel<float, WT_THREADS>)
-                : precision == PREC_FF    ? (nt == 64 ? tuple_kernel<FF, 64> : tuple_kernel<FF, WT_THREADS>)
-                                          : (nt == 64 ? tuple_kernel<double, 64> : tuple_kernel<double, WT_THREADS>);
+// Threads of the CTA kernel: the width whose lanes the Gram blocks of the
+// launch's widest tuple use best (64, 96 or 128 threads with QB blocks a
+// thread for FP32 sums; 64 to 256 threads with one block each for
+// float-float sums).  FP64 sums always take 128: their pass is bound by the
+// FP64 pipes, which four warps spread over all four SM sub-partitions.
+static int cta_threads(int precision, int cmax) {
+    const int nb = ((cmax + 3) & ~3) / 4, nblk = nb * (nb + 1) / 2;
+    if (precision == FREDEC_FP64) return WT_THREADS;
+    const bool ff = precision == PREC_FF;
+    const int qb = ff ? 1 : QB;
+    int best = ff ? 256 : WT_THREADS;
+    double best_u = -1.0;
+    for (int L : {64, 96, 128, 160, 192, 256}) {
+        if ((!ff && L > WT_THREADS) || nblk > qb * L) continue;
+        const double u = nblk <= L ? (double)(L / nblk * nblk) / L : (double)nblk / (L * ((nblk + L - 1) / L));
+        if (u > best_u + 1e-9) {
+            best_u = u;
+            best = L;
+        }
+    }
+    return best;
+}
+
+template <class T, int NT>
+static int launch_tuples_t(const TupleArgs &a, size_t smem, cudaStream_t st) {
+    auto kern = tuple_kernel<T, NT>;
     FREDEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FREDEC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+    FREDEC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     const int64_t grid = std::min<int64_t>(std::max<int64_t>(a.n_tuples, 1), (int64_t)std::max(per_sm, 1) * sm_count());
-    kern<<<(unsigned)grid, nt, smem, st>>>(a);
+    kern<<<(unsigned)grid, NT, smem, st>>>(a);
     FREDEC_CUDA_TRY(cudaGetLastError());
     return FREDEC_OK;
 }
 
+static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
+    const int nt = cta_threads(precision, a.cmax);
+    const size_t smem = tuple_smem(precision, a.cmax, a.chunk, nt);
+    if (precision == FREDEC_FP64) return launch_tuples_t<double, WT_THREADS>(a, smem, st);
+    if (precision == FREDEC_MIXED) {
+        if (nt == 64) return launch_tuples_t<float, 64>(a, smem, st);
+        if (nt == 96) return launch_tuples_t<float, 96>(a, smem, st);
+        return launch_tuples_t<float, 128>(a, smem, st);
+    }
+    switch (nt) {
+    case 64: return launch_tuples_t<FF, 64>(a, smem, st);
+    case 96: return launch_tuples_t<FF, 96>(a, smem, st);
+    case 128: return launch_tuples_t<FF, 128>(a, smem, st);
+    case 160: return launch_tuples_t<FF, 160>(a, smem, st);
+    case 192: return launch_tuples_t<FF, 192>(a, smem, st);
+    default: return launch_tuples_t<FF, 256>(a, smem, st);
+    }
+}
+
+constexpr int MAX_RANGES = 32;             // size ranges (and work counters) of one enqueue
+
 // Device inputs of one tuple launch: the series, the pool frequencies, the
 // tuples as indices into the pool (CSR: tuple k holds pool[idx[off[k] ..
-// off[k+1])]) and the processing order (largest tuples first).
+// off[k+1])]) and the processing order (largest tuples first), with host
+// copies of the offsets and the order (the launches are split by size).
 struct TupleDevIn {
     const double *t, *y, *sigma;
     int64_t N;
@@ -980,7 +1058,78 @@ struct TupleDevIn {
     const int32_t *order;
     int64_t nt;
     int mmax;                  // largest tuple
+    const int64_t *off_h;      // host: off
+    const int32_t *order_h;    // host: order
 };
+
+// Columns of a tuple of m frequencies in a pass of the mode.
+static int tuple_cols(int mode, int m) { return std::max(2, mode == 0 ? 2 * m + 2 : 4 * m + 2); }
+
+// Side streams of the size-range launches, one set per host thread and
+// device, created on first use and kept.
+constexpr int RANGE_STREAMS = 4;
+static int range_streams(cudaStream_t **out) {
+    static thread_local cudaStream_t cached[16][RANGE_STREAMS] = {};
+    int dev = 0;
+    FREDEC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 16) return fail(FREDEC_ECUDA, "device index out of range for the tuple streams");
+    for (int i = 0; i < RANGE_STREAMS; ++i)
+        if (!cached[dev][i]) FREDEC_CUDA_TRY(cudaStreamCreateWithFlags(&cached[dev][i], cudaStreamNonBlocking));
+    *out = cached[dev];
+    return FREDEC_OK;
+}
+
+// The tuples in processing order (sizes do not increase along it), one
+// launch per range of three sizes, each with the shared memory and the CTA
+// width of its largest tuple (a launch sized for the largest tuple of all
+// leaves most lanes of the small ones idle) and a work counter of its own
+// (a.next[r], zeroed by the caller).  The launches go to RANGE_STREAMS streams
+// forked from st and joined back into it, so that one range's last tuples
+// overlap the next range's first.
+static int launch_tuple_ranges(const TupleArgs &a0, const TupleDevIn &in, int precision, cudaStream_t st) {
+    auto size_at = [&](int64_t q) { const int32_t k = in.order_h[q]; return (int)(in.off_h[k + 1] - in.off_h[k]); };
+    cudaStream_t *side = nullptr;
+    if (int rc = range_streams(&side)) return rc;
+    cudaEvent_t fork, join[RANGE_STREAMS];
+    FREDEC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    FREDEC_CUDA_TRY(cudaEventRecord(fork, st));
+    bool used[RANGE_STREAMS] = {};
+    int rc = FREDEC_OK, r = 0;
+    for (int64_t lo = 0; lo < in.nt && !rc; ++r) {
+        const int mtop = size_at(lo), mbot = std::max(0, mtop - 2);
+        int64_t hi = lo;
+        while (hi < in.nt && size_at(hi) >= mbot) ++hi;
+        if (r >= MAX_RANGES) {
+            rc = fail(FREDEC_ECUDA, "too many tuple size ranges");
+            break;
+        }
+        TupleArgs a = a0;
+        a.order = in.order + lo;
+        a.n_tuples = hi - lo;
+        a.cmax = tuple_cols(a.mode, mtop);
+        a.chunk = tuple_chunk(precision, a.cmax);
+        a.next = a0.next + r;
+        const int si = r % RANGE_STREAMS;
+        if (!used[si]) {
+            used[si] = true;
+            if (cudaStreamWaitEvent(side[si], fork, 0) != cudaSuccess) {
+                rc = fail(FREDEC_ECUDA, "stream wait");
+                break;
+            }
+        }
+        rc = launch_tuples(a, precision, side[si]);
+        lo = hi;
+    }
+    for (int i = 0; i < RANGE_STREAMS; ++i) {   // join every forked stream, also after a failure
+        if (!used[i]) continue;
+        cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+        cudaEventRecord(join[i], side[i]);
+        cudaStreamWaitEvent(st, join[i], 0);
+        cudaEventDestroy(join[i]);
+    }
+    cudaEventDestroy(fork);
+    return rc;
+}
 
 // Enqueue the per-series constants, the per-point values, the pool's exact
 // cos/sin and the tuple kernel on st; scratch in ws.  Outputs (device, each
@@ -995,10 +1144,10 @@ static int tuple_enqueue(const TupleDevIn &in, int mode, int precision, int max_
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
     const size_t o_sp = take(sizeof(SeriesPrep)), o_pts = take(N * 4 * tsz),
-                 o_seed = take((size_t)npool * N * 2 * tsz + 16), o_next = take(8);
+                 o_seed = take((size_t)npool * N * 2 * tsz + 16), o_next = take(4 * MAX_RANGES);
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();
-    FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 8, st));
+    FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 4 * MAX_RANGES, st));
     SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
     if (sp_out) *sp_out = sp;
     series_prep<<<1, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp);
@@ -1035,10 +1184,12 @@ static int tuple_enqueue(const TupleDevIn &in, int mode, int precision, int max_
     a.iters = iters;
     a.status = status;
     a.next = (int32_t *)(b + o_next);
-    a.cmax = std::max(2, mode == 0 ? 2 * in.mmax + 2 : 4 * in.mmax + 2);
+    a.cmax = tuple_cols(mode, in.mmax);
     a.chunk = tuple_chunk(precision, a.cmax);
-    if (in.nt > 0)
-        if (int rc = launch_tuples(a, precision, st)) return rc;
+    if (in.nt > 0) {
+        const int rc = mode <= 2 ? launch_tuple_ranges(a, in, precision, st) : launch_tuples(a, precision, st);
+        if (rc) return rc;
+    }
     return FREDEC_OK;
 }
 
@@ -1083,7 +1234,7 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_off, off_h.data(), (nt + 1) * 8, cudaMemcpyHostToDevice, st));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_ord, order.data(), nt * 4, cudaMemcpyHostToDevice, st));
     TupleDevIn in{dt, dy, ds, N, (const double *)(b + o_pool), npool, (const int32_t *)(b + o_idx),
-                  (const int64_t *)(b + o_off), (const int32_t *)(b + o_ord), nt, mmax};
+                  (const int64_t *)(b + o_off), (const int32_t *)(b + o_ord), nt, mmax, off_h.data(), order.data()};
     SeriesPrep *sp = nullptr;
     if (int rc = tuple_enqueue(in, mode, precision, max_iter, tol, (double *)(b + o_z), (double *)(b + o_g),
                                (double *)(b + o_f), (double *)(b + o_l), (int32_t *)(b + o_it),
@@ -1308,7 +1459,7 @@ int fredec_tuple_grad_dev(const double *t, const double *y, const double *sigma,
     FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_off, tuple_offsets, (n_tuples + 1) * 8, cudaMemcpyHostToDevice, st));
     FREDEC_CUDA_TRY(cudaMemcpyAsync(b + o_ord, order.data(), n_tuples * 4, cudaMemcpyHostToDevice, st));
     TupleDevIn in{t, y, sigma, N, tuple_freqs, (int)nflat, (const int32_t *)(b + o_idx), (const int64_t *)(b + o_off),
-                  (const int32_t *)(b + o_ord), n_tuples, mmax};
+                  (const int32_t *)(b + o_ord), n_tuples, mmax, tuple_offsets, order.data()};
     return tuple_enqueue(in, 1, precision == FREDEC_MIXED ? PREC_FF : precision, 0, 0.0, z_out, dz_df_out, nullptr,
                          nullptr, nullptr, (int32_t *)(b + o_st), nullptr, ws, st);
 }

@@ -125,3 +125,51 @@ def test_tuple_refine_vs_oracle(F, prec):
         ftol = (1e-7 if prec == "fp64" else 1e-4) / T
         assert np.max(np.abs(gf - rf)) < ftol, (gf - rf) * T
         assert gl == pytest.approx(rl, rel=1e-10 if prec == "fp64" else 1e-6)
+
+
+def _separated(rng, m, lo=0.02, step=0.028):
+    """m frequencies on a jittered grid (well apart at the series' resolution)."""
+    base = lo + step * np.sort(rng.choice(20, m, replace=False))
+    return list(base + rng.uniform(-0.004, 0.004, m))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_many_tuples_every_size_vs_oracle(F, prec):
+    """Eight tuples of every size 1..20: the warp-per-tuple kernels run over
+    several size ranges, with one sweep of the Gram blocks or several, and
+    with groups of lanes splitting the points for the smallest Grams.  z and
+    dz/df against the oracle."""
+    t, y, s, fr = _series(6, N=500, span=300.0)
+    rng = np.random.default_rng(7)
+    tuples = [_separated(rng, m) for m in range(1, 21) for _ in range(8)]
+    z, g = F.tuple_grad(t, y, s, tuples, precision=prec)
+    zr, gr = oracle.tuple_grad(t, y, s, tuples)
+    np.testing.assert_allclose(z, zr, rtol=1e-10)
+    k = 0
+    for tp in tuples:
+        m = len(tp)
+        gk, gkr = g[k:k + m], gr[k:k + m]
+        assert np.max(np.abs(gk - gkr)) <= 1e-8 * np.max(np.abs(gkr)), (prec, m)
+        k += m
+    ze, _ = F.tuple_eval(t, y, s, tuples)
+    np.testing.assert_allclose(ze, zr, rtol=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_long_series_few_tuples_cta_kernel(F, prec):
+    """A long series with a few tuples takes the CTA-per-tuple kernel (the
+    whole CTA on one tuple's pass): z, dz/df and refinement against the
+    oracle."""
+    t, y, s, fr = _series(7, N=10000, span=2000.0)
+    T = t.max() - t.min()
+    tuples = [[fr[0] + 0.02 / T], [fr[0], fr[1] - 0.03 / T], [fr[0], fr[1], fr[2] + 0.01 / T, fr[3]]]
+    z, g = F.tuple_grad(t, y, s, tuples, precision=prec)
+    zr, gr = oracle.tuple_grad(t, y, s, tuples)
+    np.testing.assert_allclose(z, zr, rtol=1e-10)
+    assert np.max(np.abs(g - gr)) <= 1e-8 * np.max(np.abs(gr))
+    starts = [[fr[0] + 0.2 / T], [fr[0] - 0.15 / T, fr[1] + 0.25 / T]]
+    got_f, got_l, _ = F.tuple_refine(t, y, s, starts, max_iter=30, tol=1e-10, precision=prec)
+    for st, gf, gl in zip(starts, got_f, got_l):
+        rf, rl, _ = oracle.tuple_refine(t, y, s, st, max_iter=60, tol=1e-12)
+        assert np.max(np.abs(gf - rf)) < (1e-7 if prec == "fp64" else 1e-4) / T, (gf - rf) * T
+        assert gl == pytest.approx(rl, rel=1e-10 if prec == "fp64" else 1e-6)
