@@ -309,6 +309,70 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
 }
 
 // ---------------------------------------------------------------------------
+// Fifth-generation tensor cores (tcgen05, inline PTX; one CTA, cta_group::1):
+// tensor-memory allocation, bf16 MMAs accumulating in FP32 in tensor memory,
+// loads from tensor memory.
+
+// Shared-memory matrix descriptor of a K-major bf16 operand in the 128-byte
+// swizzled layout: rows of 64 elements (128 bytes), 8-row groups 1024 bytes
+// apart, the 16-byte chunk j of row r stored at chunk j ^ (r % 8); the
+// operand starts in a 1024-byte aligned group, and a K step of 16 elements
+// advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Byte offset of element (row r, k) of such an operand (k < 64).
+__device__ __forceinline__ int umma_sw128_offset(int r, int k) {
+    return r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1);
+}
+// Instruction descriptor of kind::f16: bf16 x bf16 -> FP32, A and B K-major,
+// D of M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Whole warp: allocate ncols columns (a power of two, 32..512) of tensor
+// memory; the address goes to *slot (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {   // whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// One thread: D (tensor memory) = A B^T (+ D when acc), operands by descriptor.
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)acc)
+        : "memory");
+}
+// One thread: the mbarrier receives one arrival when this thread's earlier
+// MMAs have completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// Whole warp: 16 consecutive 32-bit columns of each lane's tensor-memory row
+// (taddr: lane offset in the upper 16 bits, the warp's quarter of the lanes).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *out) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(v[j]);
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic block reductions (fixed shuffle tree, fixed warp order).
 
 __device__ __forceinline__ double warp_sum_d(double v) {

@@ -64,7 +64,26 @@ constexpr double TUPLE_TAU = 1e-2;
 struct SeriesPrep {            // per-series constants (device)
     double W, ybar, tc, D;     // sum w, weighted mean of y, time origin, <(y - ybar)^2> = l_0
     double span;               // max t - min t
+    // column scales of the tensor-core Gram: 2^E with |value| < 2^(E-1) for
+    // the columns built on 1/sigma (the constant, cos, sin), (y - ybar)/sigma
+    // and (t - t_c)/sigma (the t-weighted cos, sin)
+    int e_sw, e_yw, e_swt;
 };
+
+__device__ __forceinline__ double block_max_d(double v, double *scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < nw; ++i) r = fmax(r, scratch[i]);
+    return r;
+}
+
+// 2^E > 2 b (1 + 2^-20): values bounded by b scaled by 2^-E lie in (-1/2, 1/2).
+__device__ __forceinline__ int scale_exponent(double b) { return b > 0.0 ? ilogb(b * (1.0 + 0x1p-20)) + 2 : 0; }
 
 // Weighted mean of y and centred time origin; D = <(y-ybar)^2>.  One CTA.
 __global__ void series_prep(const double *t, const double *y, const double *sigma, int64_t N, SeriesPrep *out) {
@@ -89,13 +108,17 @@ __global__ void series_prep(const double *t, const double *y, const double *sigm
         smin[threadIdx.x >> 5] = mn;
         smax[threadIdx.x >> 5] = mx;
     }
-    const double ybar = Wy / W;
-    double D = 0;
+    const double ybar = Wy / W, tc = rint(Wt / W);
+    double D = 0, bsw = 0, byw = 0, bswt = 0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
-        const double w = 1.0 / (sigma[i] * sigma[i]);
+        const double w = 1.0 / (sigma[i] * sigma[i]), sw = 1.0 / sigma[i];
         D += w * (y[i] - ybar) * (y[i] - ybar);
+        bsw = fmax(bsw, sw);
+        byw = fmax(byw, fabs((y[i] - ybar) * sw));
+        bswt = fmax(bswt, fabs((t[i] - tc) * sw));
     }
     D = block_sum_d(D, sc);   // (its barriers also publish smin/smax)
+    const double mx_sw = block_max_d(bsw, sc), mx_yw = block_max_d(byw, sc), mx_swt = block_max_d(bswt, sc);
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
             mn = fmin(mn, smin[w]);
@@ -105,8 +128,11 @@ __global__ void series_prep(const double *t, const double *y, const double *sigm
         mx = fmax(mx, smax[0]);
         out->W = W;
         out->ybar = ybar;
-        out->tc = rint(Wt / W);
+        out->tc = tc;
         out->D = D;
+        out->e_sw = scale_exponent(mx_sw);
+        out->e_yw = scale_exponent(mx_yw);
+        out->e_swt = scale_exponent(mx_swt);
         out->span = mx - mn > 0 ? mx - mn : 1.0;
     }
 }
@@ -221,6 +247,7 @@ struct TupleArgs {
     double *gram_out;          // mode 3: packed Gram of [1, c_k, s_k, y]
     int chunk;                 // points per shared tile
     int cmax;                  // most columns of any tuple of the launch
+    int32_t *err;              // FREDEC_ETIMEOUT from a bounded wait of the tensor-core kernel
 };
 
 struct TState {
@@ -549,6 +576,294 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core Gram of the float-float passes: error-free splitting of the
+// columns into bf16 digits (Ozaki, Ogita, Oishi and Rump 2012, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication").
+//
+// A column value x (a float pair) scaled by the power of two 2^-E of its
+// column class (|x| 2^-E < 1/2) is rounded to 49 bits and written exactly as
+// seven signed base-128 digits, x 2^-E = sum_k d_k 2^(-7(k+1)) + r with
+// |d_k| <= 64 and |r| <= 2^-50: bf16 values, whose products are exact, and
+// FP32 sums of up to 2^24 / (7 * 2^12) = 585 such products are exact too.
+// The tensor cores accumulate one level d = s + t of the digit pairs at a
+// time, D_d(i, j) = sum over points and s + t = d of d_s(i) d_t(j), in FP32
+// in tensor memory; every TC_WIN chunks (512 points) the levels are combined
+// in float-float arithmetic, sum_d 2^(-7d) D_d, into per-entry float-float
+// sums, and the Gram entry is 2^(E_i + E_j - 14) times the total.  Pairs with
+// s + t > 6 (below 2^-49 of the column scales) are left out.  Points enter in
+// chunks of 64 (one 128-byte swizzled row of bf16 per Gram column), two
+// buffers of digit tiles so that the MMAs of one chunk overlap the column
+// generation of the next.
+
+constexpr int TC_DIG = 7;                              // digits per value
+constexpr int TC_LEVELS = TC_DIG;                      // digit-pair levels kept: s + t <= TC_DIG - 1
+constexpr int TC_K = 64;                               // points per chunk
+constexpr int TC_WIN = 8;                              // chunks per exact window: 7 * 512 * 2^12 < 2^24
+constexpr int TC_ROWS = 64;                            // MMA M: Gram columns of one tile, at most 64
+constexpr size_t TC_TILE = (size_t)TC_ROWS * 128;      // one digit tile (bytes)
+constexpr size_t TC_BUF = TC_DIG * TC_TILE;            // the digit tiles of one chunk
+constexpr int TC_THREADS = 256;
+constexpr int TC_MIN_COLS = 40;                        // narrower Grams stay on the CUDA cores
+constexpr uint32_t TC_TMEM_COLS = 512;                 // TC_LEVELS x N (N <= 64) columns
+static_assert(TC_WIN * TC_K * TC_LEVELS * 4096 < (1 << 24), "a window's digit sums must stay exact in FP32");
+static_assert(TC_LEVELS * TC_ROWS <= (int)TC_TMEM_COLS, "tensor memory holds every level");
+
+struct TcState {
+    unsigned char *dig;        // 2 buffers of TC_DIG tiles, 1024-byte aligned
+    float2 *acc;               // float-float sums of the packed lower triangle
+    uint64_t *bar;             // one mbarrier per buffer
+    int32_t *err;              // FREDEC_ETIMEOUT when an MMA completion was not seen
+    uint32_t tmem;             // tensor-memory base: level d at columns d N .. d N + N - 1
+    uint32_t phase[2];         // parity of the next completion, per buffer
+    bool pend[2];              // a commit not yet waited for, per buffer
+};
+
+// Waits (bounded) for the MMAs committed to buffer b, if any.
+__device__ __forceinline__ void tc_wait(TcState &t, int b) {
+    if (!t.pend[b]) return;
+    if (!mbar_wait_bounded(&t.bar[b], t.phase[b]) && threadIdx.x == 0) atomicExch(t.err, FREDEC_ETIMEOUT);
+    t.phase[b] ^= 1u;
+    t.pend[b] = false;
+}
+
+// bf16 bits of a small integer (|d| <= 64): float(d) by the 1.5 * 2^23
+// offset, whose low 16 bits are then zero.
+__device__ __forceinline__ uint16_t small_int_bf16(int d) {
+    return (uint16_t)(__float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16);
+}
+
+// The seven digits of (h + l) sc 2^-49 (sc = 2^(49 - E)) into row c, point
+// slot k of the digit tiles.  h sc and l sc are exact (power-of-two scaling);
+// their sum, rounded to an integer, is the 49-bit fixed-point value Q,
+// |Q| < 2^48, split as Q = q1 2^28 + q0 (|q0| <= 2^27) and then into digits of
+// weights 2^42, 2^35, ..., 2^0 by rounding divisions.
+__device__ __forceinline__ void put_digits(unsigned char *tiles, int c, int k, float h, float l, float sc) {
+    const long long Q = __float2ll_rn(h * sc) + __float2ll_rn(l * sc);
+    const int q1 = (int)((Q + (1LL << 27)) >> 28);
+    int r = (int)(Q - (long long)q1 * (1LL << 28));
+    int d[TC_DIG];
+    int u = q1;
+    d[0] = (u + (1 << 13)) >> 14;
+    u -= d[0] * (1 << 14);
+    d[1] = (u + (1 << 6)) >> 7;
+    d[2] = u - d[1] * (1 << 7);
+    d[3] = (r + (1 << 20)) >> 21;
+    r -= d[3] * (1 << 21);
+    d[4] = (r + (1 << 13)) >> 14;
+    r -= d[4] * (1 << 14);
+    d[5] = (r + (1 << 6)) >> 7;
+    d[6] = r - d[5] * (1 << 7);
+    const int off = umma_sw128_offset(c, k);
+#pragma unroll
+    for (int q = 0; q < TC_DIG; ++q) *reinterpret_cast<uint16_t *>(tiles + q * TC_TILE + off) = small_int_bf16(d[q]);
+}
+__device__ __forceinline__ void put_zero_digits(unsigned char *tiles, int c, int k) {
+    const int off = umma_sw128_offset(c, k);
+#pragma unroll
+    for (int q = 0; q < TC_DIG; ++q) *reinterpret_cast<uint16_t *>(tiles + q * TC_TILE + off) = 0;
+}
+
+// The float-float columns of point i (make_row<FF>'s values) as digits in
+// point slot k: this thread's share, the frequencies part - 1, part - 1 +
+// nparts, ... (mod nparts; part 0 also takes the constant and the data
+// column, and the frequencies that leave it the lightest share); zeros past
+// the last point.
+__device__ __forceinline__ void tc_columns(const TupleArgs &a, const TState &s, const SeedTableFF &T, int64_t i, int k,
+                                           int part, int nparts, int m, bool with_uv, unsigned char *tiles,
+                                           float sc_sw, float sc_yw, float sc_swt) {
+    const int M = 2 * m + 1;
+    if (i >= a.N) {
+        if (part == 0) {
+            put_zero_digits(tiles, 0, k);
+            put_zero_digits(tiles, M, k);
+        }
+        for (int q = (part + nparts - 1) % nparts; q < m; q += nparts) {
+            put_zero_digits(tiles, 1 + 2 * q, k);
+            put_zero_digits(tiles, 2 + 2 * q, k);
+            if (with_uv) {
+                put_zero_digits(tiles, M + 1 + 2 * q, k);
+                put_zero_digits(tiles, M + 2 + 2 * q, k);
+            }
+        }
+        return;
+    }
+    const float4 *P4 = static_cast<const float4 *>(a.pts) + 2 * i;
+    const float4 p0 = P4[0], p1 = P4[1];
+    const ff sw = {p0.x, p0.y}, tp = {p0.z, p0.w}, yw = {p1.x, p1.y}, swt = {p1.z, p1.w};
+    if (part == 0) {
+        put_digits(tiles, 0, k, sw.hi, sw.lo, sc_sw);
+        put_digits(tiles, M, k, yw.hi, yw.lo, sc_yw);
+    }
+    for (int q = (part + nparts - 1) % nparts; q < m; q += nparts) {
+        const float4 sd = static_cast<const float4 *>(a.seeds)[(int64_t)s.pidx[q] * a.N + i];
+        ff c = {sd.x, sd.y}, sn = {sd.z, sd.w};
+        const float2 dl = s.trialff[q];
+        if (dl.x != 0.0f) {
+            ff ds, dc;
+            ff_sincos_ff_turns(T, ff_mul({dl.x, dl.y}, tp), &ds, &dc);
+            const ff cn = ff_sub(ff_mul(c, dc), ff_mul(sn, ds));
+            sn = ff_add(ff_mul(sn, dc), ff_mul(c, ds));
+            c = cn;
+        }
+        const ff c1 = ff_mul(sw, c), s1 = ff_mul(sw, sn);
+        put_digits(tiles, 1 + 2 * q, k, c1.hi, c1.lo, sc_sw);
+        put_digits(tiles, 2 + 2 * q, k, s1.hi, s1.lo, sc_sw);
+        if (with_uv) {
+            const ff c2 = ff_mul(swt, c), s2 = ff_mul(swt, sn);
+            put_digits(tiles, M + 1 + 2 * q, k, c2.hi, c2.lo, sc_swt);
+            put_digits(tiles, M + 2 + 2 * q, k, s2.hi, s2.lo, sc_swt);
+        }
+    }
+}
+
+// The window's levels into the float-float sums (all threads).  With M = 64
+// the Gram row r sits in tensor-memory lane 32 (r / 16) + r % 16: warp w
+// reads the lanes of its quarter q = w % 4 (rows 16q .. 16q + 15 in lanes
+// 0..15) and the 16-column blocks b with b % 2 == w / 4 that hold entries
+// j <= r.
+__device__ void tc_readout(TcState &t, int C, int N) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, half = w >> 2;
+    const int row = 16 * q + (lane & 15);
+    const bool live = lane < 16 && row < C;
+    const int top = min(C, 16 * q + 16);                    // rows of this quarter end below top
+    const int nb = 16 * q < C ? (top + 15) / 16 : 0;        // column blocks with j < top
+    for (int b = half; b < nb; b += 2) {
+        float hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0.0f;
+        float scale = 1.0f;
+        for (int d = 0; d < TC_LEVELS; ++d) {
+            float v[16];
+            tmem_ld16(t.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * N + 16 * b), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {   // (hi, lo) += v 2^(-7d), exact scaling
+                const ff s = ff_two_sum(hi[j], v[j] * scale);
+                const ff r = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, lo[j]));
+                hi[j] = r.hi;
+                lo[j] = r.lo;
+            }
+            scale *= 0x1p-7f;
+        }
+        if (live)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = 16 * b + j;
+                if (col <= row) {
+                    float2 &e = t.acc[tri(row, col)];
+                    const ff sum = ff_add({e.x, e.y}, {hi[j], lo[j]});
+                    e = make_float2(sum.hi, sum.lo);
+                }
+            }
+    }
+}
+
+// One pass over all points on the tensor cores: the FP64 Gram (packed, C x C,
+// C <= 64) of the float-float columns at the trial offsets.
+__device__ void gram_pass_tc(const TupleArgs &a, const TState &s, const void *tab, double *Gs, TcState &t, int m,
+                             bool with_uv) {
+    const int M = 2 * m + 1, C = with_uv ? M + 1 + 2 * m : M + 1, N = (C + 15) & ~15;
+    const int ne = C * (C + 1) / 2, tid = threadIdx.x, L = blockDim.x;
+    for (int e = tid; e < ne; e += L) t.acc[e] = make_float2(0.0f, 0.0f);
+    const SeriesPrep &sp = *a.sp;
+    const float sc_sw = exp2f((float)(49 - sp.e_sw)), sc_yw = exp2f((float)(49 - sp.e_yw)),
+                sc_swt = exp2f((float)(49 - sp.e_swt));
+    const SeedTableFF &T = *static_cast<const SeedTableFF *>(tab);
+    const int nparts = L / TC_K, part = tid / TC_K, k = tid % TC_K;
+    const int nch = (int)((a.N + TC_K - 1) / TC_K);
+    const uint32_t idesc = umma_idesc_bf16(TC_ROWS, N);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int buf = ch & 1;
+        unsigned char *tiles = t.dig + buf * TC_BUF;
+        const bool wstart = ch % TC_WIN == 0;
+        tc_wait(t, buf);                                    // the MMAs of chunk ch - 2 are done with the buffer
+        if (wstart && ch > 0) {                             // the previous window is complete: read it out
+            tc_wait(t, buf ^ 1);
+            tc_fence_after();
+            tc_readout(t, C, N);
+            tc_fence_before();
+            __syncthreads();
+        }
+        tc_columns(a, s, T, (int64_t)ch * TC_K + k, k, part, nparts, m, with_uv, tiles, sc_sw, sc_yw, sc_swt);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            // descriptors differ only in the start address (its field holds
+            // address / 16): tile sd, K step ks at + (sd TC_TILE + 32 ks) / 16
+            const uint64_t d0 = umma_desc_sw128(smem_u32(tiles));
+            for (int d = 0; d < TC_LEVELS; ++d)
+                for (int sd = 0; sd <= d; ++sd) {
+                    const uint64_t da = d0 + (uint64_t)(sd * (TC_TILE >> 4)), db = d0 + (uint64_t)((d - sd) * (TC_TILE >> 4));
+#pragma unroll
+                    for (int ks = 0; ks < TC_K / 16; ++ks)
+                        umma_bf16(t.tmem + (uint32_t)(d * N), da + 2u * ks, db + 2u * ks, idesc,
+                                  !(wstart && sd == 0 && ks == 0));
+                }
+            umma_commit(&t.bar[buf]);
+        }
+        t.pend[buf] = true;
+    }
+    tc_wait(t, 0);
+    tc_wait(t, 1);
+    tc_fence_after();
+    tc_readout(t, C, N);
+    tc_fence_before();
+    __syncthreads();
+    const int eM = M;
+    for (int e = tid; e < ne; e += L) {
+        int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (tri(i + 1, 0) <= e) ++i;
+        while (tri(i, 0) > e) --i;
+        const int j = e - tri(i, 0);
+        auto ex = [&](int c) { return c == eM ? sp.e_yw : c > eM ? sp.e_swt : sp.e_sw; };
+        const float2 v = t.acc[e];
+        Gs[e] = ldexp((double)v.x + (double)v.y, ex(i) + ex(j) - 14);
+    }
+    __syncthreads();
+    // a completion not seen: the pass's sums are unknown; a NaN first pivot
+    // makes the tuple's outputs NaN (the host reports FREDEC_ETIMEOUT)
+    if (tid == 0 && *(volatile int32_t *)t.err != 0) Gs[0] = NAN;
+    __syncthreads();
+}
+
+// Shared memory of the tensor-core kernel (offsets from a 1024-byte aligned
+// base): the two buffers of digit tiles, the float-float seed table, the
+// tuple state, the FP64 Gram with its diagonal scratch, the extension's
+// scratch, the float-float Gram sums, two mbarriers and the tensor-memory
+// address.
+struct TcLayout {
+    size_t tab, state, gram, d0, inv, R, acc, bar, slot, bytes;
+};
+__host__ __device__ inline size_t tc_al16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline TcLayout tc_layout(int cmax) {
+    TcLayout L{};
+    const size_t ntri = (size_t)cmax * (cmax + 1) / 2, mm = (size_t)(cmax > 2 ? (cmax - 2) / 4 : 0),
+                 M = 2 * mm + 1;
+    size_t o = 2 * TC_BUF;
+    L.tab = o;
+    o = tc_al16(o + sizeof(SeedTableFF));
+    L.state = o;
+    o = tc_al16(o + sizeof(TState));
+    L.gram = o;
+    o += 8 * ntri;
+    L.d0 = o;
+    o += 8 * (size_t)cmax;
+    L.inv = o;
+    o = tc_al16(o + 8 * (size_t)cmax);
+    L.R = o;
+    o = tc_al16(o + 8 * (mm * M + mm * (mm + 1) / 2 + 2 * mm) + 16);
+    L.acc = o;
+    o = tc_al16(o + 8 * ntri);
+    L.bar = o;
+    o += 16;
+    L.slot = o;
+    o += 16;
+    L.bytes = o + 1024;   // room to align the base
+    return L;
+}
+
 // In-place right-looking Cholesky of the packed C x C matrix by the whole CTA.
 // The reciprocals of the original diagonal are formed first, in parallel
 // (rd0[]), so that a pivot's check is one multiplication.  Thread 0 takes each
@@ -744,9 +1059,9 @@ __device__ void set_trial(TState &s, int m, const double *src_delta, const doubl
     }
 }
 
-template <class T>
+template <class T, bool TC = false>
 __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, double *Gs, double *d0, double *inv,
-                           unsigned char *R, int64_t k) {
+                           unsigned char *R, int64_t k, TcState *tc = nullptr) {
     const int tid = threadIdx.x;
     const int64_t o0 = a.off[k];
     if (tid == 0) s.m = (int)(a.off[k + 1] - o0);
@@ -764,7 +1079,11 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
     const bool mixed = TP<T>::mixed;
     const bool uv = a.mode == 1 || a.mode == 2;
     double *W = reinterpret_cast<double *>(R);   // extension scratch (free after a pass)
-    gram_pass<T>(a, s, tab, Gs, R, m, uv);
+    auto pass = [&](bool with_uv) {
+        if constexpr (TC) gram_pass_tc(a, s, tab, Gs, *tc, m, with_uv);
+        else gram_pass<T>(a, s, tab, Gs, R, m, with_uv);
+    };
+    pass(uv);
     if (a.mode == 3) {
         for (int e = tid; e < (M + 1) * (M + 2) / 2; e += blockDim.x) a.gram_out[e] = Gs[e];
         if (tid == 0) a.status[k] = 0;
@@ -807,7 +1126,7 @@ __device__ void tuple_work(const TupleArgs &a, TState &s, const void *tab, doubl
     while (have_step && it < a.max_iter) {
         set_trial(s, m, s.delta, s.step, h);
         __syncthreads();
-        gram_pass<T>(a, s, tab, Gs, R, m, true);
+        pass(true);
         chol_cta(Gs, d0, inv, M + 1, M, M, s);
         const bool lin_ok = s.fail_at >= M;
         if (lin_ok && tid < 32) linear_solution(Gs, inv, M, s.x, &s.redx);
@@ -887,6 +1206,46 @@ __global__ void __launch_bounds__(NT, tuple_min_blocks<T>(NT)) tuple_kernel(Tupl
         tuple_work<T>(a, s, tab, Gs, d0, inv, R, a.order ? (int64_t)a.order[q] : q);
         __syncthreads();
     }
+}
+
+// Float-float passes with the tensor-core Gram (modes 0-2, at most TC_ROWS
+// columns): TC_THREADS threads and the SM's tensor memory per CTA, one CTA
+// per SM.
+__global__ void __launch_bounds__(TC_THREADS, 1) tuple_kernel_tc(TupleArgs a) {
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
+    const TcLayout Lt = tc_layout(a.cmax);
+    void *tab = base + Lt.tab;
+    TState &s = *reinterpret_cast<TState *>(base + Lt.state);
+    double *Gs = reinterpret_cast<double *>(base + Lt.gram);
+    double *d0 = reinterpret_cast<double *>(base + Lt.d0);
+    double *inv = reinterpret_cast<double *>(base + Lt.inv);
+    unsigned char *R = base + Lt.R;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Lt.bar);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(base + Lt.slot);
+    fill_seed_table_ff(*static_cast<SeedTableFF *>(tab));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(slot, TC_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    TcState t{base, reinterpret_cast<float2 *>(base + Lt.acc), bar, a.err, *slot, {0u, 0u}, {false, false}};
+    __shared__ int64_t cur;
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int64_t q = cur;
+        if (q >= a.n_tuples) break;
+        tuple_work<FF, true>(a, s, tab, Gs, d0, inv, R, a.order ? (int64_t)a.order[q] : q, &t);
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(t.tmem, TC_TMEM_COLS);
 }
 
 static_assert(sizeof(SeedTable) == sizeof(SeedTableFF), "the FF passes reuse the FP64 table's space");
@@ -1023,7 +1382,27 @@ static int launch_tuples_t(const TupleArgs &a, size_t smem, cudaStream_t st) {
     return FREDEC_OK;
 }
 
+// The tensor-core float-float kernel, one CTA per SM; -1 when its shared
+// memory does not fit.
+static int launch_tuples_tc(const TupleArgs &a, cudaStream_t st) {
+    const size_t smem = tc_layout(a.cmax).bytes;
+    if (smem > 227 * 1024) return -1;
+    FREDEC_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t grid = std::min<int64_t>(std::max<int64_t>(a.n_tuples, 1), (int64_t)sm_count());
+    tuple_kernel_tc<<<(unsigned)grid, TC_THREADS, smem, st>>>(a);
+    FREDEC_CUDA_TRY(cudaGetLastError());
+    return FREDEC_OK;
+}
+
 static int launch_tuples(TupleArgs a, int precision, cudaStream_t st) {
+    // the tensor cores pay off from about 40 columns on: the Gram grows as
+    // C^2, the column generation and digit split as C (measured per size
+    // range on the 16-frequency pool: 2.6x faster at 13-15 frequencies,
+    // 1.2x at 10-12, slower below)
+    if (precision == PREC_FF && a.mode <= 2 && a.cmax > TC_MIN_COLS && a.cmax <= TC_ROWS && a.err) {
+        const int rc = launch_tuples_tc(a, st);
+        if (rc != -1) return rc;
+    }
     const int nt = cta_threads(precision, a.cmax);
     const size_t smem = tuple_smem(precision, a.cmax, a.chunk, nt);
     if (precision == FREDEC_FP64) return launch_tuples_t<double, WT_THREADS>(a, smem, st);
@@ -1137,17 +1516,19 @@ static int launch_tuple_ranges(const TupleArgs &a0, const TupleDevIn &in, int pr
 // *sp_out receives the series constants (l_0 = D).
 static int tuple_enqueue(const TupleDevIn &in, int mode, int precision, int max_iter, double tol, double *z,
                          double *dzdf, double *f_out, double *l_out, int32_t *iters, int32_t *status,
-                         SeriesPrep **sp_out, DevBuf &ws, cudaStream_t st) {
+                         SeriesPrep **sp_out, DevBuf &ws, cudaStream_t st, int32_t **err_out = nullptr) {
     const int64_t N = in.N;
     const int npool = in.npool;
     const size_t tsz = precision == FREDEC_MIXED ? 4 : 8;
     size_t off = 0;
     auto take = [&](size_t n) { size_t at = off; off = (off + n + 255) / 256 * 256; return at; };
     const size_t o_sp = take(sizeof(SeriesPrep)), o_pts = take(N * 4 * tsz),
-                 o_seed = take((size_t)npool * N * 2 * tsz + 16), o_next = take(4 * MAX_RANGES);
+                 o_seed = take((size_t)npool * N * 2 * tsz + 16), o_next = take(4 * MAX_RANGES), o_err = take(8);
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();
     FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_next, 0, 4 * MAX_RANGES, st));
+    FREDEC_CUDA_TRY(cudaMemsetAsync(b + o_err, 0, 8, st));
+    if (err_out) *err_out = (int32_t *)(b + o_err);
     SeriesPrep *sp = (SeriesPrep *)(b + o_sp);
     if (sp_out) *sp_out = sp;
     series_prep<<<1, 256, 0, st>>>(in.t, in.y, in.sigma, N, sp);
@@ -1184,6 +1565,7 @@ static int tuple_enqueue(const TupleDevIn &in, int mode, int precision, int max_
     a.iters = iters;
     a.status = status;
     a.next = (int32_t *)(b + o_next);
+    a.err = (int32_t *)(b + o_err);
     a.cmax = tuple_cols(mode, in.mmax);
     a.chunk = tuple_chunk(precision, a.cmax);
     if (in.nt > 0) {
@@ -1236,11 +1618,15 @@ static int tuple_run(const double *t, const double *y, const double *sigma, int6
     TupleDevIn in{dt, dy, ds, N, (const double *)(b + o_pool), npool, (const int32_t *)(b + o_idx),
                   (const int64_t *)(b + o_off), (const int32_t *)(b + o_ord), nt, mmax, off_h.data(), order.data()};
     SeriesPrep *sp = nullptr;
+    int32_t *derr = nullptr;
     if (int rc = tuple_enqueue(in, mode, precision, max_iter, tol, (double *)(b + o_z), (double *)(b + o_g),
                                (double *)(b + o_f), (double *)(b + o_l), (int32_t *)(b + o_it),
-                               (int32_t *)(b + o_st), &sp, ws, st))
+                               (int32_t *)(b + o_st), &sp, ws, st, &derr))
         return rc;
     FREDEC_CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t herr = 0;
+    if (derr) FREDEC_CUDA_TRY(cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost));
+    if (herr) return fail(FREDEC_ETIMEOUT, "a bounded wait of the tensor-core tuple kernel gave up");
     std::vector<int32_t> status(std::max<int64_t>(nt, 1));
     if (nt) FREDEC_CUDA_TRY(cudaMemcpy(status.data(), b + o_st, nt * 4, cudaMemcpyDeviceToHost));
     for (int64_t k = 0; k < nt; ++k)

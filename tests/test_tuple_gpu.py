@@ -173,3 +173,25 @@ def test_long_series_few_tuples_cta_kernel(F, prec):
         rf, rl, _ = oracle.tuple_refine(t, y, s, st, max_iter=60, tol=1e-12)
         assert np.max(np.abs(gf - rf)) < (1e-7 if prec == "fp64" else 1e-4) / T, (gf - rf) * T
         assert gl == pytest.approx(rl, rel=1e-10 if prec == "fp64" else 1e-6)
+
+
+def test_tensor_core_gram_wide_weight_range(F):
+    """Tuples of 11 to 15 frequencies (Grams of 46 to 62 columns: the
+    float-float passes on the tensor cores, columns split into bf16 digits
+    relative to each column's largest value) on a series whose 1/sigma spans
+    two decades, so that most values sit far below their column's scale: z and
+    dz/df of the mixed path against the oracle."""
+    rng = np.random.default_rng(11)
+    N = 600
+    t = np.sort(rng.uniform(0, 400.0, N))
+    sigma = 10.0 ** rng.uniform(-1.0, 1.0, N)
+    y = 3.0 + 2.0 * np.sin(2 * np.pi * 0.05 * t) + 1.5 * np.cos(2 * np.pi * 0.17 * t) + sigma * rng.standard_normal(N)
+    tuples = [_separated(rng, m) for m in (11, 12, 13, 14, 15) for _ in range(3)]
+    z, g = F.tuple_grad(t, y, sigma, tuples, precision="mixed")
+    zr, gr = oracle.tuple_grad(t, y, sigma, tuples)
+    np.testing.assert_allclose(z, zr, rtol=1e-10)
+    k = 0
+    for tp in tuples:
+        m = len(tp)
+        assert np.max(np.abs(g[k:k + m] - gr[k:k + m])) <= 1e-8 * np.max(np.abs(gr[k:k + m])), m
+        k += m
