@@ -198,7 +198,8 @@ int fredec_periodogram_vjp_dev(const double *t, const double *y, const double *s
  *                 columns above) the coefficient of that column is 0.
  *   info_out[3] (may be NULL) as in fredec_periodogram_ex.
  * opts: precision and trend as for fredec_periodogram_dev; topk must be 0,
- * statistic FREDEC_Z_DIFF, fpt 0 (or the one compiled value: 2 mixed, 1 FP64).
+ * statistic FREDEC_Z_DIFF, fpt 0 (or the one compiled value: mixed 4 for up to
+ * 7 base columns (p <= 7, trend columns included), 2 above; FP64 1).
  * One pass over the observations gives both outputs (2 (2p + 4) sums per
  * trial frequency); in mixed precision the flagged bins are re-evaluated in
  * float-float, dz/df included.

@@ -96,7 +96,7 @@ int grad_core(const double *t, const double *y, const double *sigma, int64_t N, 
     const int prec = o.precision;
     const double tau = o.flag_tau == 0.0 ? 0.2 : o.flag_tau;
     const bool fix = prec == FREDEC_MIXED && tau >= 0.0;
-    const int fpt = prec == FREDEC_MIXED ? GRAD_FPT_MIXED : GRAD_FPT_FP64;
+    const int fpt = prec == FREDEC_MIXED ? grad_fpt_mixed(p) : GRAD_FPT_FP64;
     const int warps = o.warps > 0 ? o.warps : (N < 256 ? 2 : 4);
     const int64_t nchunks = (N + PREP_THREADS - 1) / PREP_THREADS;
     size_t off = 0;
@@ -187,7 +187,8 @@ int check_grad_args(const fredec_opts *opts, fredec_opts *o, int64_t N, int32_t 
     if (o->topk != 0) return fail(FREDEC_EINVAL, "the derivative entry points do not compute top-k (opts.topk must be 0)");
     if (o->statistic != FREDEC_Z_DIFF)
         return fail(FREDEC_EINVAL, "the derivative entry points compute the difference form (opts.statistic)");
-    const int fpt = o->precision == FREDEC_MIXED ? GRAD_FPT_MIXED : GRAD_FPT_FP64;
+    const int p = padded_cols(base_cols(n_base, o->trend));
+    const int fpt = o->precision == FREDEC_MIXED ? grad_fpt_mixed(p) : GRAD_FPT_FP64;
     if (o->fpt != 0 && o->fpt != fpt)
         return fail(FREDEC_EINVAL, "opts.fpt must be 0 or " + std::to_string(fpt) + " for the derivative kernels");
     if (int rc = check_sizes(N, n_base, nf, *o)) return rc;

@@ -7,22 +7,22 @@ namespace fredec {
 int launch_pgram_grad_a(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
     switch (p) {
         case 1:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 1, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 1, grad_fpt_mixed(1), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 1, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
         case 3:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 3, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 3, grad_fpt_mixed(3), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 3, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
         case 5:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 5, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 5, grad_fpt_mixed(5), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 5, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
         case 7:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 7, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 7, grad_fpt_mixed(7), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 7, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
         case 9:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 9, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 9, grad_fpt_mixed(9), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 9, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
         case 11:
-            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 11, GRAD_FPT_MIXED, false, 2>(prm, nblocks, warps, st)
+            return prec == FREDEC_MIXED ? launch_pgram_t<FREDEC_MIXED, 11, grad_fpt_mixed(11), false, 2>(prm, nblocks, warps, st)
                                         : launch_pgram_t<FREDEC_FP64, 11, GRAD_FPT_FP64, false, 2>(prm, nblocks, warps, st);
     }
     return -2;
@@ -31,22 +31,22 @@ int launch_pgram_grad_a(int prec, int p, const PgramParams &prm, int64_t nblocks
 size_t smem_pgram_grad_a(int prec, int p, int warps) {
     switch (p) {
         case 1:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 1, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 1, grad_fpt_mixed(1), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 1, GRAD_FPT_FP64, 2>(warps);
         case 3:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 3, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 3, grad_fpt_mixed(3), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 3, GRAD_FPT_FP64, 2>(warps);
         case 5:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 5, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 5, grad_fpt_mixed(5), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 5, GRAD_FPT_FP64, 2>(warps);
         case 7:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 7, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 7, grad_fpt_mixed(7), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 7, GRAD_FPT_FP64, 2>(warps);
         case 9:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 9, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 9, grad_fpt_mixed(9), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 9, GRAD_FPT_FP64, 2>(warps);
         case 11:
-            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 11, GRAD_FPT_MIXED, 2>(warps)
+            return prec == FREDEC_MIXED ? pgram_smem_t<FREDEC_MIXED, 11, grad_fpt_mixed(11), 2>(warps)
                                         : pgram_smem_t<FREDEC_FP64, 11, GRAD_FPT_FP64, 2>(warps);
     }
     return 0;

@@ -42,9 +42,14 @@ namespace fredec {
 constexpr int FLUSH_POINTS = 32;
 constexpr int FLUSH_BLOCKS_ALL = 8;
 
-// Frequencies per thread of the two-set kernels (z and dz/df): one frequency
-// pair (mixed) or one frequency (FP64) keeps the 2 (2P+4) sums in registers.
-constexpr int GRAD_FPT_MIXED = 2;
+// Frequencies per thread of the two-set kernels (z and dz/df): mixed, two
+// frequency pairs for bases of up to 7 columns (2 (2P+4) float2 sums a pair in
+// registers: 218 registers at P = 7; 0.643 of the FP32 peak against 0.562
+// with one pair) and one pair for wider bases (the second pair, reached by
+// the two-step rotation, carries rounding that the t'-weighted dz/df sums
+// amplify: 1.2e-4 at P = 11 on a 300-point series, above the 1e-4 bar);
+// FP64, one frequency.
+__host__ __device__ constexpr int grad_fpt_mixed(int p) { return p <= 7 ? 4 : 2; }
 constexpr int GRAD_FPT_FP64 = 1;
 
 struct PgramParams {
