@@ -36,6 +36,7 @@ WORKLOAD = "residual periodogram, N=2000, base = constant + 3 sinusoids (p=7), u
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq*obs terms/s, mixed vs FP64 on 1 B300, at stated max rel err vs FP64 oracle"
 OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (rotation 4, sums 2p+4, w*c 1)
+VJP_OPS_PER_TERM = 6                   # adjoint: rotation 4, a cos + b sin 2
 # Library kernels per mixed step (ncu launch list of this workload): initialisation, prep,
 # periodogram, re-evaluation of flagged bins, top-k stages 1 and 2.
 KERNELS_PER_STEP = 6
@@ -296,8 +297,11 @@ def bench_nightly(F, peak_ops, flush):
             "max_rel_err_vs_oracle": err, "worst_over_bound": worst, "excluded_cond_above_1e12": excl,
             "sample": "12 strided bins and the neighbourhoods of the two highest peaks",
             "vjp": {"value": s.N * nf / (statistics.median(vjp_ms) * 1e-3), "unit": "terms/s",
-                    "ms_per_call": statistics.median(vjp_ms), "what": "dL/dy for all 1e5 points, v ~ N(0,1) on "
-                                                                        "all 1e7 bins"}}
+                    "ms_per_call": statistics.median(vjp_ms),
+                    "roofline_frac": VJP_OPS_PER_TERM * s.N * nf / (statistics.median(vjp_ms) * 1e-3) / peak_ops,
+                    "ops_per_term": VJP_OPS_PER_TERM,
+                    "what": "dL/dy for all 1e5 points, v ~ N(0,1) on all 1e7 bins (whole call against the "
+                            "unit-count FP32 peak)"}}
 
 
 def bench_grad(F, peak_ops, flush):
