@@ -303,10 +303,6 @@ __device__ __forceinline__ void tuple_cs(const TupleArgs &a, const TState &s, co
 // and avrg2 from which the derivative columns are formed).
 __device__ __forceinline__ void put(float *row, int c, float v) { row[c] = v; }
 __device__ __forceinline__ void put(double *row, int c, double v) { row[c] = v; }
-__device__ __forceinline__ void put(float2 *row, int c, double v) {   // exact split hi + lo
-    const float hi = __double2float_rn(v);
-    row[c] = make_float2(hi, __double2float_rn(v - (double)hi));
-}
 
 template <class T>
 __device__ __forceinline__ void make_row(const TupleArgs &a, const TState &s, const void *tab, int64_t i, int m,
@@ -1469,9 +1465,17 @@ static int launch_tuple_ranges(const TupleArgs &a0, const TupleDevIn &in, int pr
     auto size_at = [&](int64_t q) { const int32_t k = in.order_h[q]; return (int)(in.off_h[k + 1] - in.off_h[k]); };
     cudaStream_t *side = nullptr;
     if (int rc = range_streams(&side)) return rc;
-    cudaEvent_t fork, join[RANGE_STREAMS];
-    FREDEC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    FREDEC_CUDA_TRY(cudaEventRecord(fork, st));
+    cudaEvent_t ev[RANGE_STREAMS + 1] = {};   // the fork, then one join per side stream
+    for (int i = 0; i <= RANGE_STREAMS; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return fail(FREDEC_ECUDA, "event creation for the tuple streams");
+        }
+    cudaEvent_t fork = ev[0];
+    if (cudaEventRecord(fork, st) != cudaSuccess) {
+        for (int i = 0; i <= RANGE_STREAMS; ++i) cudaEventDestroy(ev[i]);
+        return fail(FREDEC_ECUDA, "fork event");
+    }
     bool used[RANGE_STREAMS] = {};
     int rc = FREDEC_OK, r = 0;
     for (int64_t lo = 0; lo < in.nt && !rc; ++r) {
@@ -1499,14 +1503,11 @@ static int launch_tuple_ranges(const TupleArgs &a0, const TupleDevIn &in, int pr
         rc = launch_tuples(a, precision, side[si]);
         lo = hi;
     }
-    for (int i = 0; i < RANGE_STREAMS; ++i) {   // join every forked stream, also after a failure
-        if (!used[i]) continue;
-        cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
-        cudaEventRecord(join[i], side[i]);
-        cudaStreamWaitEvent(st, join[i], 0);
-        cudaEventDestroy(join[i]);
-    }
-    cudaEventDestroy(fork);
+    for (int i = 0; i < RANGE_STREAMS; ++i)   // join every forked stream, also after a failure
+        if (used[i] && (cudaEventRecord(ev[1 + i], side[i]) != cudaSuccess ||
+                        cudaStreamWaitEvent(st, ev[1 + i], 0) != cudaSuccess) && !rc)
+            rc = fail(FREDEC_ECUDA, "join of the tuple streams");
+    for (int i = 0; i <= RANGE_STREAMS; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 
