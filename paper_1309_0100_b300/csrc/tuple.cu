@@ -600,7 +600,8 @@ constexpr int TC_WIN = 8;                              // chunks per exact windo
 constexpr int TC_ROWS = 64;                            // MMA M: Gram columns of one tile, at most 64
 constexpr size_t TC_TILE = (size_t)TC_ROWS * 128;      // one digit tile (bytes)
 constexpr size_t TC_BUF = TC_DIG * TC_TILE;            // the digit tiles of one chunk
-constexpr int TC_THREADS = 256;
+constexpr int TC_WORKERS = 256;                        // column generation, readouts (4 threads a point)
+constexpr int TC_THREADS = TC_WORKERS + 32;            // and one warp that issues the MMAs
 constexpr int TC_MIN_COLS = 40;                        // narrower Grams stay on the CUDA cores
 constexpr uint32_t TC_TMEM_COLS = 512;                 // TC_LEVELS x N (N <= 64) columns
 static_assert(TC_WIN * TC_K * TC_LEVELS * 4096 < (1 << 24), "a window's digit sums must stay exact in FP32");
@@ -720,6 +721,7 @@ __device__ __forceinline__ void tc_columns(const TupleArgs &a, const TState &s, 
 // 0..15) and the 16-column blocks b with b % 2 == w / 4 that hold entries
 // j <= r.
 __device__ void tc_readout(TcState &t, int C, int N) {
+    if (threadIdx.x >= TC_WORKERS) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, half = w >> 2;
     const int row = 16 * q + (lane & 15);
     const bool live = lane < 16 && row < C;
@@ -766,7 +768,8 @@ __device__ void gram_pass_tc(const TupleArgs &a, const TState &s, const void *ta
     const float sc_sw = exp2f((float)(49 - sp.e_sw)), sc_yw = exp2f((float)(49 - sp.e_yw)),
                 sc_swt = exp2f((float)(49 - sp.e_swt));
     const SeedTableFF &T = *static_cast<const SeedTableFF *>(tab);
-    const int nparts = L / TC_K, part = tid / TC_K, k = tid % TC_K;
+    const int nparts = TC_WORKERS / TC_K, part = tid / TC_K, k = tid % TC_K;
+    const bool worker = tid < TC_WORKERS, issuer = tid == TC_WORKERS;
     const int nch = (int)((a.N + TC_K - 1) / TC_K);
     const uint32_t idesc = umma_idesc_bf16(TC_ROWS, N);
     for (int ch = 0; ch < nch; ++ch) {
@@ -781,10 +784,13 @@ __device__ void gram_pass_tc(const TupleArgs &a, const TState &s, const void *ta
             tc_fence_before();
             __syncthreads();
         }
-        tc_columns(a, s, T, (int64_t)ch * TC_K + k, k, part, nparts, m, with_uv, tiles, sc_sw, sc_yw, sc_swt);
+        if (worker)
+            tc_columns(a, s, T, (int64_t)ch * TC_K + k, k, part, nparts, m, with_uv, tiles, sc_sw, sc_yw, sc_swt);
         fence_proxy_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        // the issuing warp queues this chunk's MMAs while the workers go on
+        // to the next chunk's columns
+        if (issuer) {
             tc_fence_after();
             // descriptors differ only in the start address (its field holds
             // address / 16): tile sd, K step ks at + (sd TC_TILE + 32 ks) / 16
@@ -1205,8 +1211,9 @@ __global__ void __launch_bounds__(NT, tuple_min_blocks<T>(NT)) tuple_kernel(Tupl
 }
 
 // Float-float passes with the tensor-core Gram (modes 0-2, at most TC_ROWS
-// columns): TC_THREADS threads and the SM's tensor memory per CTA, one CTA
-// per SM.
+// columns): TC_THREADS threads (TC_WORKERS for the columns and readouts, the
+// last warp's first lane issuing the MMAs; all of them in the solves) and the
+// SM's tensor memory per CTA, one CTA per SM.
 __global__ void __launch_bounds__(TC_THREADS, 1) tuple_kernel_tc(TupleArgs a) {
     extern __shared__ __align__(16) unsigned char tc_raw[];
     unsigned char *base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
