@@ -582,29 +582,36 @@ __device__ void gram_pass(const TupleArgs &a, const TState &s, const void *tab, 
 // column class (|x| 2^-E < 1/2) is rounded to 49 bits and written exactly as
 // seven signed base-128 digits, x 2^-E = sum_k d_k 2^(-7(k+1)) + r with
 // |d_k| <= 64 and |r| <= 2^-50: bf16 values, whose products are exact, and
-// FP32 sums of up to 2^24 / (7 * 2^12) = 585 such products are exact too.
-// The tensor cores accumulate one level d = s + t of the digit pairs at a
-// time, D_d(i, j) = sum over points and s + t = d of d_s(i) d_t(j), in FP32
-// in tensor memory; every TC_WIN chunks (512 points) the levels are combined
-// in float-float arithmetic, sum_d 2^(-7d) D_d, into per-entry float-float
-// sums, and the Gram entry is 2^(E_i + E_j - 14) times the total.  Pairs with
-// s + t > 6 (below 2^-49 of the column scales) are left out.  Points enter in
-// chunks of 64 (one 128-byte swizzled row of bf16 per Gram column), two
-// buffers of digit tiles so that the MMAs of one chunk overlap the column
-// generation of the next.
+// FP32 sums of up to 2^24 / 2^12 = 4096 such products are exact too.
+// Level d = s + t of the digit pairs, D_d(i, j) = sum over points and
+// s + t = d of d_s(i) d_t(j), is accumulated in FP32 in tensor memory by
+// MMAs of M = 128 whose A operand is two digit tiles stacked, s and s + 1
+// (s even; the tiles are adjacent in shared memory, a zero tile after the
+// seventh), against tile t: rows 0..63 of accumulator region s + t receive
+// the pair (s, t) (level s + t), rows 64..127 the pair (s + 1, t) (level
+// s + t + 1), so 16 MMAs cover the 28 pairs with s + t <= 6 (a region's row
+// receives at most 4 pairs).  Every TC_WIN chunks (512 points) the levels
+// are combined in float-float arithmetic, sum_d 2^(-7d) D_d, into per-entry
+// float-float sums, and the Gram entry is 2^(E_i + E_j - 14) times the
+// total.  Pairs with s + t > 6 (below 2^-49 of the column scales) are left
+// out.  Points enter in chunks of 64 (one 128-byte swizzled row of bf16 per
+// Gram column), two buffers of digit tiles so that the MMAs of one chunk
+// overlap the column generation of the next.
 
 constexpr int TC_DIG = 7;                              // digits per value
 constexpr int TC_LEVELS = TC_DIG;                      // digit-pair levels kept: s + t <= TC_DIG - 1
 constexpr int TC_K = 64;                               // points per chunk
 constexpr int TC_WIN = 8;                              // chunks per exact window: 7 * 512 * 2^12 < 2^24
-constexpr int TC_ROWS = 64;                            // MMA M: Gram columns of one tile, at most 64
+constexpr int TC_ROWS = 64;                            // Gram columns of one tile, at most 64
+constexpr int TC_M = 2 * TC_ROWS;                      // MMA M: two digit tiles stacked
 constexpr size_t TC_TILE = (size_t)TC_ROWS * 128;      // one digit tile (bytes)
-constexpr size_t TC_BUF = TC_DIG * TC_TILE;            // the digit tiles of one chunk
+constexpr int TC_TILES = TC_DIG + 1;                   // the digit tiles of a chunk and a zero tile
+constexpr size_t TC_BUF = TC_TILES * TC_TILE;          // one buffer of tiles
 constexpr int TC_WORKERS = 256;                        // column generation, readouts (4 threads a point)
 constexpr int TC_THREADS = TC_WORKERS + 32;            // and one warp that issues the MMAs
 constexpr int TC_MIN_COLS = 40;                        // narrower Grams stay on the CUDA cores
 constexpr uint32_t TC_TMEM_COLS = 512;                 // TC_LEVELS x N (N <= 64) columns
-static_assert(TC_WIN * TC_K * TC_LEVELS * 4096 < (1 << 24), "a window's digit sums must stay exact in FP32");
+static_assert(TC_WIN * TC_K * 4 * 4096 < (1 << 24), "a window's digit sums must stay exact in FP32");
 static_assert(TC_LEVELS * TC_ROWS <= (int)TC_TMEM_COLS, "tensor memory holds every level");
 
 struct TcState {
@@ -715,45 +722,49 @@ __device__ __forceinline__ void tc_columns(const TupleArgs &a, const TState &s, 
     }
 }
 
-// The window's levels into the float-float sums (all threads).  With M = 64
-// the Gram row r sits in tensor-memory lane 32 (r / 16) + r % 16: warp w
-// reads the lanes of its quarter q = w % 4 (rows 16q .. 16q + 15 in lanes
-// 0..15) and the 16-column blocks b with b % 2 == w / 4 that hold entries
-// j <= r.
+// The window's levels into the float-float sums (the workers).  With M = 128
+// tensor-memory lane l of region r holds Gram row l % 64 of level r + l / 64.
+// Warp w reads the lanes of its quarter q = w % 4 (rows 32 (q % 2) .. + 31,
+// one level up for q >= 2) and the 16-column blocks b with b % 2 == w / 4
+// that hold entries j <= row; the upper quarters add theirs after the lower
+// ones (both update the same entries).
 __device__ void tc_readout(TcState &t, int C, int N) {
     if (threadIdx.x >= TC_WORKERS) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, half = w >> 2;
-    const int row = 16 * q + (lane & 15);
-    const bool live = lane < 16 && row < C;
-    const int top = min(C, 16 * q + 16);                    // rows of this quarter end below top
-    const int nb = 16 * q < C ? (top + 15) / 16 : 0;        // column blocks with j < top
-    for (int b = half; b < nb; b += 2) {
-        float hi[16], lo[16];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, half = w >> 2, up = q >> 1;
+    const int r0 = 32 * (q & 1), row = r0 + lane;
+    const bool live = row < C;
+    const int nb = r0 < C ? (min(C, r0 + 32) + 15) / 16 : 0;   // column blocks with j < the quarter's last row
+    for (int phase = 0; phase < 2; ++phase) {
+        if (phase == up)
+            for (int b = half; b < nb; b += 2) {
+                float hi[16], lo[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0.0f;
-        float scale = 1.0f;
-        for (int d = 0; d < TC_LEVELS; ++d) {
-            float v[16];
-            tmem_ld16(t.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * N + 16 * b), v);
+                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0.0f;
+                float scale = up ? 0x1p-7f : 1.0f;
+                for (int d = 0; d < TC_LEVELS; ++d) {
+                    float v[16];
+                    tmem_ld16(t.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * N + 16 * b), v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {   // (hi, lo) += v 2^(-7d), exact scaling
-                const ff s = ff_two_sum(hi[j], v[j] * scale);
-                const ff r = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, lo[j]));
-                hi[j] = r.hi;
-                lo[j] = r.lo;
-            }
-            scale *= 0x1p-7f;
-        }
-        if (live)
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = 16 * b + j;
-                if (col <= row) {
-                    float2 &e = t.acc[tri(row, col)];
-                    const ff sum = ff_add({e.x, e.y}, {hi[j], lo[j]});
-                    e = make_float2(sum.hi, sum.lo);
+                    for (int j = 0; j < 16; ++j) {   // (hi, lo) += v 2^(-7 level), exact scaling
+                        const ff s = ff_two_sum(hi[j], v[j] * scale);
+                        const ff r = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, lo[j]));
+                        hi[j] = r.hi;
+                        lo[j] = r.lo;
+                    }
+                    scale *= 0x1p-7f;
                 }
+                if (live)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = 16 * b + j;
+                        if (col <= row) {
+                            float2 &e = t.acc[tri(row, col)];
+                            const ff sum = ff_add({e.x, e.y}, {hi[j], lo[j]});
+                            e = make_float2(sum.hi, sum.lo);
+                        }
+                    }
             }
+        asm volatile("bar.sync 1, %0;" ::"r"(TC_WORKERS) : "memory");   // the workers only
     }
 }
 
@@ -771,7 +782,7 @@ __device__ void gram_pass_tc(const TupleArgs &a, const TState &s, const void *ta
     const int nparts = TC_WORKERS / TC_K, part = tid / TC_K, k = tid % TC_K;
     const bool worker = tid < TC_WORKERS, issuer = tid == TC_WORKERS;
     const int nch = (int)((a.N + TC_K - 1) / TC_K);
-    const uint32_t idesc = umma_idesc_bf16(TC_ROWS, N);
+    const uint32_t idesc = umma_idesc_bf16(TC_M, N);
     for (int ch = 0; ch < nch; ++ch) {
         const int buf = ch & 1;
         unsigned char *tiles = t.dig + buf * TC_BUF;
@@ -793,15 +804,16 @@ __device__ void gram_pass_tc(const TupleArgs &a, const TState &s, const void *ta
         if (issuer) {
             tc_fence_after();
             // descriptors differ only in the start address (its field holds
-            // address / 16): tile sd, K step ks at + (sd TC_TILE + 32 ks) / 16
+            // address / 16): tile u, K step ks at + (u TC_TILE + 32 ks) / 16;
+            // A = tiles sa, sa + 1 (128 rows), B = tile tb, into region sa + tb
             const uint64_t d0 = umma_desc_sw128(smem_u32(tiles));
-            for (int d = 0; d < TC_LEVELS; ++d)
-                for (int sd = 0; sd <= d; ++sd) {
-                    const uint64_t da = d0 + (uint64_t)(sd * (TC_TILE >> 4)), db = d0 + (uint64_t)((d - sd) * (TC_TILE >> 4));
+            for (int sa = 0; sa < TC_DIG; sa += 2)
+                for (int tb = 0; sa + tb < TC_LEVELS; ++tb) {
+                    const uint64_t da = d0 + (uint64_t)(sa * (TC_TILE >> 4)), db = d0 + (uint64_t)(tb * (TC_TILE >> 4));
 #pragma unroll
                     for (int ks = 0; ks < TC_K / 16; ++ks)
-                        umma_bf16(t.tmem + (uint32_t)(d * N), da + 2u * ks, db + 2u * ks, idesc,
-                                  !(wstart && sd == 0 && ks == 0));
+                        umma_bf16(t.tmem + (uint32_t)((sa + tb) * N), da + 2u * ks, db + 2u * ks, idesc,
+                                  !(wstart && sa == 0 && ks == 0));
                 }
             umma_commit(&t.bar[buf]);
         }
@@ -1233,6 +1245,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tuple_kernel_tc(TupleArgs a) {
         fence_mbar_init();
     }
     if (threadIdx.x < 32) tmem_alloc(slot, TC_TMEM_COLS);
+    // the zero tile after each buffer's seven digit tiles (the upper half of
+    // the last stacked A operand)
+    for (int b = 0; b < 2; ++b)
+        for (size_t o = threadIdx.x * 16; o < TC_TILE; o += (size_t)blockDim.x * 16)
+            *reinterpret_cast<uint4 *>(base + b * TC_BUF + TC_DIG * TC_TILE + o) = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
