@@ -35,7 +35,8 @@ import synth  # noqa: E402
 WORKLOAD = "residual periodogram, N=2000, base = constant + 3 sinusoids (p=7), uniform grid nf=1e6 (0<f<=2 /d)"
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq*obs terms/s, mixed vs FP64 on 1 B300, at stated max rel err vs FP64 oracle"
-OPS_PER_TERM = lambda p: 2 * p + 9     # FMA-pipe operations per freq*obs term (rotation 4, sums 2p+4, w*c 1)
+OPS_PER_TERM = lambda p: 2 * p + 8     # FMA-pipe operations per freq*obs term (rotation 4, sums 2p+4 of sqrt(w)-scaled cos/sin)
+GRAD_OPS_PER_TERM = lambda p: 4 * p + 13   # z and dz/df: the 2p+8 above, then 2p+4 t'-weighted sums and t' (s c) 1
 VJP_OPS_PER_TERM = 6                   # adjoint: rotation 4, a cos + b sin 2
 # Library kernels per mixed step (ncu launch list of this workload): initialisation, prep,
 # periodogram, re-evaluation of flagged bins, top-k stages 1 and 2.
@@ -44,7 +45,7 @@ KERNELS_PER_STEP = 6
 # periodogram kernel on this workload, keyed by (p, frequencies per thread,
 # warps per CTA); measured with ncu on the same command (--kernel-only).  z (8 MB)
 # stays in L2 during the launch.
-DRAM_BYTES_PER_LAUNCH = {(7, 10, 4): 255488}
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def dist_setup():
@@ -239,7 +240,7 @@ def bench_batch(F, peak_ops, flush):
     return {"value": plan.terms / (t_ms * 1e-3), "unit": "terms/s", "ms_per_replay": t_ms, "replays": len(ms),
             "series": len(w.series), "terms": plan.terms,
             "roofline_frac": ops / (t_ms * 1e-3) / peak_ops,
-            "roofline_note": "2p+9 FP32 ops per term of every series over the whole replay (prep, top-k and "
+            "roofline_note": "2p+8 FP32 ops per term of every series over the whole replay (prep, top-k and "
                              "re-evaluation included) against the unit-count FP32 peak",
             "max_rel_err_vs_oracle": max(errs), "worst_over_bound": max(worst), "excluded_cond_above_1e12": excl,
             "sample": "6 random series x (20 strided bins + their top-5 peaks)"}
@@ -349,8 +350,8 @@ def bench_grad(F, peak_ops, flush):
     bound = 1e-4 * den + 8.0 * 2e-15 * np.sqrt(s.N) * 2 * np.pi * T * c2 / np.maximum(ratio, 1e-6) ** 2
     d = np.abs(gh[idx] - gr)
     return {"value": s.N * nf / (t_ms * 1e-3), "unit": "terms/s", "ms_per_step": t_ms, "kernel_ms": k_ms,
-            "roofline_frac": (4 * p + 14) * s.N * nf / (k_ms * 1e-3) / peak_ops,
-            "ops_per_term": 4 * p + 14,
+            "roofline_frac": GRAD_OPS_PER_TERM(p) * s.N * nf / (k_ms * 1e-3) / peak_ops,
+            "ops_per_term": GRAD_OPS_PER_TERM(p),
             "max_rel_err_dzdf_vs_oracle": float(np.max((d / den)[keep & (ratio > 0.45)])),
             "worst_over_bound": float(np.max((d / bound)[keep])), "excluded_cond_above_1e12": int((~keep).sum()),
             "sample": "60 strided bins, floor 1e-3 of the largest sampled |dz/df|; the relative error over the "

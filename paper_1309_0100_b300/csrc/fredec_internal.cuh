@@ -22,13 +22,26 @@ constexpr double DROP2 = 1e-14;                      // squared column-drop rati
 //   [0..1] phase A = frac(f0 t') as u64 turns, [2..3] phase B = frac(df t'),
 //   [4] cos(2 pi df t'), [5] sin(2 pi df t'), [6] cos(4 pi df t'),
 //   [7] sin(4 pi df t') (the two-step rotation, rounded once from FP64),
-//   then the set [w, w r, w psi_k (p)] padded to a multiple of 4 words.
+//   then the set [s, s r, s psi_k (p)] padded to a multiple of 4 words, with
+//   s = sqrt(w) rounded to FP32: the mixed kernels scale each point's cos/sin
+//   by s, so that s psi_k (s c) = w psi_k c and (s c)^2 = s^2 c^2; the weight
+//   they integrate is s^2 (rec_weight).
 // FP64 records (64-bit words): [0] A, [1] B, [2] cos, [3] sin, [4] w, [5] w r,
 //   [6..6+p) w psi_k.  Both are padded to a multiple of 16 bytes.
 // Records with a second set (nset = 2, the periodogram's frequency derivative)
 // append the t'-weighted values of the weighted ones, padded the same way:
-//   mixed [w t', w r t', w psi_k t' (p)]; FP64 [w t', w r t', w psi_k t' (p)].
+//   mixed [t', s r t', s psi_k t' (p)] (t' multiplies the scaled (s c)^2 and
+//   (s c)(s s) sums); FP64 [w t', w r t', w psi_k t' (p)].
 __host__ __device__ constexpr int rec32_set_words(int p) { return 4 * ((p + 2 + 3) / 4); }
+#ifdef __CUDACC__
+// s = sqrt(w) as the mixed records carry it, and the weight s^2 that the
+// mixed kernels integrate in place of w.
+__device__ __forceinline__ double rec_sqrt_w(double w) { return (double)__double2float_rn(sqrt(w)); }
+__device__ __forceinline__ double rec_weight(double w) {
+    const double s = rec_sqrt_w(w);
+    return s * s;
+}
+#endif
 __host__ __device__ constexpr int rec64_set_words(int p) { return 2 * ((p + 1) / 2); }
 __host__ __device__ constexpr int rec32_words(int p, int nset = 1) { return 8 + nset * rec32_set_words(p); }
 __host__ __device__ constexpr int rec64_words(int p, int nset = 1) {
@@ -66,7 +79,7 @@ struct SeriesDesc {
 // Per-series results of the prep kernels.
 struct SeriesState {
     double W;            // sum of weights (FP64)
-    double Wf;           // sum of FP32-rounded weights (what the mixed kernel integrates)
+    double Wf;           // sum of s^2, s = sqrt(w) rounded to FP32 (the weight the mixed kernels integrate)
     double tc;           // time origin
     double chi2;         // l(f') of the base model
     double Swt;          // sum w t (scratch)

@@ -41,9 +41,10 @@ __global__ void grad_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state, in
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
 }
 
-// <t'> = sum of the records' w t' values (the first word of the second set),
-// exactly the values the periodogram kernel integrates (FP32 in mixed
-// records); the order of the points does not matter.  One CTA, fixed-order
+// <t'> = sum of the records' w t' values (FP64 records: the first word of
+// the second set; mixed records: that word, t', times the square of the
+// first word of the first set, s = sqrt(w)), exactly the values the
+// periodogram kernel integrates; the order of the points does not matter.  One CTA, fixed-order
 // reduction (deterministic).
 __global__ void wt_sum_kernel(const unsigned char *rec, int64_t N, int p, int prec, double *out) {
     __shared__ double sc[32];
@@ -51,7 +52,10 @@ __global__ void wt_sum_kernel(const unsigned char *rec, int64_t N, int p, int pr
     if (prec == FREDEC_MIXED) {
         const int rw = rec32_words(p, 2), at = rec32_words(p);
         const float *R = reinterpret_cast<const float *>(rec);
-        for (int64_t i = threadIdx.x; i < N; i += blockDim.x) v += (double)R[i * rw + at];
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+            const double s = (double)R[i * rw + 8];
+            v += (double)R[i * rw + at] * s * s;
+        }
     } else {
         const int rw = rec64_words(p, 2), at = rec64_words(p);
         const double *R = reinterpret_cast<const double *>(rec);

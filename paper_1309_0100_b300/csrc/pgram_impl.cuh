@@ -189,9 +189,10 @@ __device__ __forceinline__ double dz_df(const double *S0, const double *S1, doub
 // Inner loops: one observation record against this thread's F frequencies.
 
 // One observation record, ready for the F-step loop: the seed cos/sin at the
-// thread's first frequency, the one- and two-step rotations, and the weighted
-// values.  With NSET = 2 the second set holds the t'-weighted values w t',
-// w r t', w psi_k t'.
+// thread's first frequency, scaled by s = sqrt(w), the one- and two-step
+// rotations, and the values that multiply the scaled cos/sin: s r, s psi_k
+// (w[0] = s itself).  With NSET = 2 the second set holds t' (w[1], the
+// factor of the t'-weighted (s c)^2 and (s c)(s s) sums), s r t', s psi_k t'.
 template <int P, int NSET = 1>
 struct MixedPoint {
     float c, s, cr, sr, c2, s2;
@@ -230,6 +231,8 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
         const float ang = (float)(int32_t)(ph >> 32) * TWO_PI_OVER_2_32;
         __sincosf(ang, &pt.s, &pt.c);
     }
+    pt.c *= pt.w[0];   // the point's cos/sin scaled by s = sqrt(w)
+    pt.s *= pt.w[0];
     pt.cr = m.x;
     pt.sr = m.y;
     pt.c2 = m.z;
@@ -251,10 +254,12 @@ struct MixedAcc {
 // (f_{j0}, f_{j0+1}) (the seed and one step of the rotation e^{i theta},
 // theta = 2 pi df t') and advances by e^{2 i theta} (from the record, rounded
 // once from FP64, so that the recurrence drifts by the rounding of one
-// constant per step); per pair the 2P+4 sums
+// constant per step); with the cos/sin scaled by s = sqrt(w), per pair the
+// 2P+4 sums
 //     <psi_k c>, <psi_k s>, <r c>, <r s>, <c^2>, <c s>
-// take one packed FMA each, and w c one packed multiply: (2P + 9) packed
-// instructions per two frequencies, the rotation included.
+// take one packed FMA each ((s psi_k)(s c), ..., (s c)(s c), (s c)(s s)):
+// (2P + 8) packed instructions per two frequencies, the rotation included.
+// The second set's <t' c^2>, <t' c s> take one packed multiply more (t' s c).
 template <int P, int F, int NSET = 1>
 __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P, NSET> &pt, MixedAcc<P, F, NSET> &A) {
     constexpr int NPC = MixedAcc<P, F, NSET>::NPC, Q0 = 2 * P + 4;
@@ -267,7 +272,7 @@ __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P, NSET> &pt, 
         for (int g = 0; g < NSET; ++g) {   // the set's sums; the same (c, s) for both sets
             float2 *a = A.a[kk] + g * Q0;
             if ((F & 1) && kk == NPC - 1) {   // the odd last frequency on its own
-                const float wc = pt.w[g] * c.x;
+                const float wc = g == 0 ? c.x : pt.w[g] * c.x;
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
                     a[q].x = fmaf(pt.u[g][q], c.x, a[q].x);
@@ -287,7 +292,7 @@ __device__ __forceinline__ void mixed_accumulate(const MixedPoint<P, NSET> &pt, 
                 const float2 wr2 = make_float2(pt.wr[g], pt.wr[g]), w2 = make_float2(pt.w[g], pt.w[g]);
                 a[2 * P] = __ffma2_rn(wr2, c, a[2 * P]);
                 a[2 * P + 1] = __ffma2_rn(wr2, s, a[2 * P + 1]);
-                const float2 wc = __fmul2_rn(w2, c);
+                const float2 wc = g == 0 ? c : __fmul2_rn(w2, c);
                 a[2 * P + 2] = __ffma2_rn(wc, c, a[2 * P + 2]);
                 a[2 * P + 3] = __ffma2_rn(wc, s, a[2 * P + 3]);
             }

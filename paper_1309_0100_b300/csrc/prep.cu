@@ -312,7 +312,8 @@ __device__ __forceinline__ int64_t record_slot(int64_t i, int64_t K, int64_t N) 
 
 // Writes the records of point i of series d (residual r, w, u = w psi; with
 // a.nset == 2 also their products with t' = tp, the t-weighted averages of
-// Eq. avrg1 that the frequency derivative needs); K = record_multiplier(d.N);
+// Eq. avrg1 that the frequency derivative needs; mixed records carry them
+// divided by sqrt(w), the scale of the kernel's cos/sin); K = record_multiplier(d.N);
 // PT as for base_basis (d.p = PT when PT > 0).
 template <int PT = 0>
 __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDesc &d, int64_t i, int64_t K, double tp,
@@ -324,8 +325,8 @@ __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDes
     const uint64_t B = frac_turns_u64(d.df, tp);
     double sr, cr;
     sincos_turns_d(B, &sr, &cr);
-    const float wf = (float)w;
     if (a.precision == FREDEC_MIXED) {
+        const double sw = sqrt(w), isw = sw > 0.0 ? 1.0 / sw : 0.0;
         uint32_t *R = (uint32_t *)(a.rec + d.rec_off) + slot * rec32_words(p, ns);
         R[0] = (uint32_t)A;
         R[1] = (uint32_t)(A >> 32);
@@ -338,15 +339,15 @@ __device__ __forceinline__ void write_records(const PrepArgs &a, const SeriesDes
         Rf[5] = (float)sr;
         Rf[6] = (float)c2;
         Rf[7] = (float)s2;
-        Rf[8] = wf;
-        Rf[9] = (float)(w * r);
-        for (int q = 0; q < p; ++q) Rf[10 + q] = (float)u[q];
+        Rf[8] = (float)rec_sqrt_w(w);
+        Rf[9] = (float)(sw * r);
+        for (int q = 0; q < p; ++q) Rf[10 + q] = (float)(u[q] * isw);
         for (int q = 10 + p; q < rec32_words(p); ++q) Rf[q] = 0.f;
         if (ns == 2) {
             float *R2 = Rf + rec32_words(p);
-            R2[0] = (float)(w * tp);
-            R2[1] = (float)(w * r * tp);
-            for (int q = 0; q < p; ++q) R2[2 + q] = (float)(u[q] * tp);
+            R2[0] = (float)tp;
+            R2[1] = (float)(sw * r * tp);
+            for (int q = 0; q < p; ++q) R2[2 + q] = (float)(u[q] * isw * tp);
             for (int q = 2 + p; q < rec32_set_words(p); ++q) R2[q] = 0.f;
         }
     }
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_k5(PrepArgs a) {
         for (int q = p; q < d.p; ++q) u[q] = 0.0;
         write_records(a, d, i, record_multiplier(d.N), tp, w, r, u);
         v[0] = w * r * r;
-        v[1] = (double)(float)w;
+        v[1] = rec_weight(w);
     }
     store_partials(a, chunk, v, 2, prep_sm);
     if (arrive_last(st, 4, d.nchunks)) {
@@ -567,7 +568,7 @@ __device__ __forceinline__ void prep_series_body(const PrepArgs &a, const Series
         for (int q = p; q < pw; ++q) u[q] = 0.0;
         write_records<PT>(a, d, i, K, tp, w, r, u);
         v[0] += w * r * r;
-        v[1] += (double)(float)w;
+        v[1] += rec_weight(w);
     }
     block_reduce_vals<2>(v, 2, red, out);
     if (threadIdx.x == 0) {
@@ -787,7 +788,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster(PrepArgs a) {
             for (int q = p; q < pw; ++q) u[q] = 0.0;
             write_records<PT>(a, d, i, K, tp, w, r, u);
             v[0] += w * r * r;
-            v[1] += (double)(float)w;
+            v[1] += rec_weight(w);
         }
         cluster_reduce<2>(v, 2, sm, ph);
         if (lead) {
@@ -932,7 +933,7 @@ __global__ void __launch_bounds__(CL_THREADS) prep_cluster_one(PrepArgs a) {
             }
             write_records<PT>(a, d, i, sm.K, ti - tc, w, r2, uu);
             v[0] += w * r2 * r2;
-            v[1] += (double)(float)w;
+            v[1] += rec_weight(w);
         }
         cluster_reduce<2>(v, 2, sm, ph);
         if (lead) {
