@@ -200,11 +200,11 @@ struct MixedPoint {
     float u[NSET][4 * ((P + 2 + 3) / 4) - 2];
 };
 
-template <int P, int SEED, int NSET = 1>
-__device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, uint32_t j0,
-                                           MixedPoint<P, NSET> &pt) {
-    constexpr int C4 = (P + 2 + 3) / 4;   // float4s of one set [w, w r, w psi_k]
-    const uint4 h = r4[0];
+// The record's rotations and the values that multiply the scaled cos/sin
+// (everything but the seed).
+template <int P, int NSET = 1>
+__device__ __forceinline__ void mixed_load_values(const uint4 *__restrict__ r4, MixedPoint<P, NSET> &pt) {
+    constexpr int C4 = (P + 2 + 3) / 4;   // float4s of one set [s, s r, s psi_k]
     const float4 m = *reinterpret_cast<const float4 *>(r4 + 1);
 #pragma unroll
     for (int g = 0; g < NSET; ++g) {
@@ -222,6 +222,17 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
 #pragma unroll
         for (int q = 0; q < 4 * C4 - 2; ++q) pt.u[g][q] = v[2 + q];
     }
+    pt.cr = m.x;
+    pt.sr = m.y;
+    pt.c2 = m.z;
+    pt.s2 = m.w;
+}
+
+template <int P, int SEED, int NSET = 1>
+__device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const SeedTableF &tab, uint32_t j0,
+                                           MixedPoint<P, NSET> &pt) {
+    mixed_load_values<P, NSET>(r4, pt);
+    const uint4 h = r4[0];
     const uint64_t A = ((uint64_t)h.y << 32) | h.x;
     const uint64_t B = ((uint64_t)h.w << 32) | h.z;
     const uint64_t ph = A + (uint64_t)j0 * B;          // exact phase (turns * 2^64) at f_{j0}
@@ -233,10 +244,6 @@ __device__ __forceinline__ void mixed_load(const uint4 *__restrict__ r4, const S
     }
     pt.c *= pt.w[0];   // the point's cos/sin scaled by s = sqrt(w)
     pt.s *= pt.w[0];
-    pt.cr = m.x;
-    pt.sr = m.y;
-    pt.c2 = m.z;
-    pt.s2 = m.w;
 }
 
 // Mixed accumulators: the F frequencies of a thread in pairs (k, k+1), every
@@ -627,6 +634,205 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Single-series mixed kernels with CTA-level second-level sums.  The 2P+2
+// slow sums (<psi_k c>, <psi_k s>, <c^2>, <c s>) of all warps go into ONE
+// running array per CTA: every KS tiles, at the tile barrier, the warps add
+// their register sums in nw steps separated by CTA barriers, warp w adding
+// in step s the slow sums b with b % nw == (w + s) % nw, so that no two
+// warps touch the same entries in a step and the order of the additions is
+// fixed (deterministic).  The residual sums <r c>, <r s> keep per-warp
+// running sums, flushed every FLUSH_POINTS points as in pgram_block.  This
+// takes the warps' running sums from (2P+4) nw to 2P+2 + 2 nw rows of
+// 32 F floats (92 -> 31 KB at P = 7, F = 10, four warps; with two warps a
+// CTA four CTAs fit an SM, where per-warp sums allowed three).  A tile holds
+// 32 points per warp: one run of the software-pipelined point loop per flush
+// of the residual sums (measured at P = 7, F = 10, four warps: 64-point tiles
+// 1.749 ms, 96 1.724 ms, 128 1.690 ms, against 1.704 ms with per-warp
+// running sums).
+template <int P, int F>
+struct PgramCsLayout {
+    static constexpr int Q = 2 * P + 4, QS = 2 * P + 2, NPC = (F + 1) / 2;
+    static constexpr int RB = rec_bytes(P, FREDEC_MIXED, 1);
+    static __host__ __device__ int tile_points(int nw) { return 32 * nw; }
+    static __host__ __device__ size_t tile_bytes(int nw) { return (size_t)tile_points(nw) * RB; }
+    static constexpr size_t OFF_TILES = OFF_TILES_BASE;
+    // two record tiles; also z of the CTA's 32 F frequencies (mirror kernels)
+    static __host__ __device__ size_t rr_off(int nw) {
+        const size_t t = 2 * tile_bytes(nw), zs = 32 * F * sizeof(double);
+        return align_up(OFF_TILES + (t > zs ? t : zs), 16);
+    }
+    static constexpr size_t RR_PER_WARP = (size_t)2 * NPC * 32;      // float2 entries
+    static __host__ __device__ size_t rs_off(int nw) { return rr_off(nw) + (size_t)nw * RR_PER_WARP * sizeof(float2); }
+    static constexpr size_t RS_ENTRIES = (size_t)QS * NPC * 32;
+    static __host__ __device__ size_t smem_bytes(int nw) { return rs_off(nw) + RS_ENTRIES * sizeof(float2); }
+    // the sum index q of slow sum b
+    static __host__ __device__ constexpr int slow_q(int b) { return b < 2 * P ? b : b + 2; }
+};
+
+template <int P, int F, bool MIRROR>
+__device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
+                                               int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
+    using L = PgramCsLayout<P, F>;
+    constexpr int Q = L::Q, QS = L::QS, NPC = L::NPC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *tiles = smem + L::OFF_TILES;
+    float2 *rr = reinterpret_cast<float2 *>(smem + L::rr_off(nw));
+    float2 *rs = reinterpret_cast<float2 *>(smem + L::rs_off(nw));
+    const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + OFF_TABLE);
+
+    const int N = d.N;
+    const int64_t jblock = blk * 32 * F;
+    const uint32_t j0 = (uint32_t)(jblock + lane * F);
+    const unsigned char *src = prm.rec + d.rec_off;
+    const int TP = L::tile_points(nw);
+    const size_t TB = L::tile_bytes(nw);
+    const int ntiles = (N + TP - 1) / TP;
+    const int ks = FLUSH_BLOCKS_ALL;   // tiles between slow flushes: 32 FLUSH_BLOCKS_ALL points per warp
+
+    __syncthreads();   // previous block's epilogue is done with the sums and tiles
+    // each thread clears the residual entries it flushes into; the slow sums
+    // are first touched after a tile barrier
+    for (int q = lane; q < (int)L::RR_PER_WARP; q += 32) rr[(size_t)warp * L::RR_PER_WARP + q] = make_float2(0.f, 0.f);
+    for (int q = tid; q < (int)L::RS_ENTRIES; q += blockDim.x) rs[q] = make_float2(0.f, 0.f);
+    auto issue = [&](int k, uint64_t *bar) {
+        const unsigned n = (unsigned)min(TP, N - k * TP);
+        mbar_arrive_expect_tx(bar, n * L::RB);
+        bulk_g2s(tiles + (k & 1) * TB, src + (size_t)k * TB, n * L::RB, bar);
+    };
+    if (tid == 0)
+        for (int k = 0; k < 2 && k < ntiles; ++k) issue(k, &bars[k]);
+
+    MixedAcc<P, F, 1> acc;
+#pragma unroll
+    for (int k = 0; k < NPC; ++k)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc.a[k][q] = make_float2(0.0f, 0.0f);
+    float2 *mine = rr + (size_t)warp * L::RR_PER_WARP;
+    auto flush_r = [&]() {
+#pragma unroll
+        for (int k = 0; k < NPC; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float2 &m = mine[(j * NPC + k) * 32 + lane];
+                m = __fadd2_rn(m, acc.a[k][2 * P + j]);
+                acc.a[k][2 * P + j] = make_float2(0.0f, 0.0f);
+            }
+    };
+    auto flush_slow = [&]() {   // all threads; nw steps, a CTA barrier after each
+        for (int s = 0; s < nw; ++s) {
+            const int slice = (warp + s) % nw;
+#pragma unroll
+            for (int b = 0; b < QS; ++b)
+                if (b % nw == slice)
+#pragma unroll
+                    for (int k = 0; k < NPC; ++k) {
+                        float2 &m = rs[(b * NPC + k) * 32 + lane];
+                        m = __fadd2_rn(m, acc.a[k][L::slow_q(b)]);
+                        acc.a[k][L::slow_q(b)] = make_float2(0.0f, 0.0f);
+                    }
+            __syncthreads();
+        }
+    };
+    int since = 0;   // points of this warp since the last flush of the residual sums
+
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int b = tile & 1;
+        const uint32_t par = b ? (use1++ & 1u) : (use0++ & 1u);
+        if (!mbar_wait_bounded(&bars[b], par)) {
+            if (lane == 0) atomicExch(prm.err, FREDEC_ETIMEOUT);
+        }
+        const int n = min(TP, N - tile * TP);
+        const unsigned char *tb = tiles + b * TB;
+        const int cnt = n > warp ? (n - warp + nw - 1) / nw : 0;
+        const unsigned char *pw = tb + (size_t)warp * L::RB;
+        const size_t stride = (size_t)nw * L::RB;
+        for (int k = 0; k < cnt;) {
+            const int take = min(cnt - k, FLUSH_POINTS - since);
+            if (prm.seed_mode == 0)
+                mixed_run<P, F, 0, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+            else
+                mixed_run<P, F, 1, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+            k += take;
+            since += take;
+            if (since == FLUSH_POINTS) {
+                flush_r();
+                since = 0;
+            }
+        }
+        __syncthreads();   // all warps are done with buffer b
+        if (tid == 0 && tile + 2 < ntiles) issue(tile + 2, &bars[b]);
+        if ((tile + 1) % ks == 0 && tile + 1 < ntiles) flush_slow();
+    }
+    flush_r();
+    flush_slow();
+
+    // Epilogue: the slow sums are the CTA's, the residual sums the warps'
+    // (added in FP32); FP64 solve per frequency.
+    double *zbuf = reinterpret_cast<double *>(tiles);
+    const double W = st.Wf;
+    const int64_t nf = d.nf;
+    const bool mixed_flags = prm.flag_tau >= 0.0;
+    auto rd = [&](const float2 *a, int k, int ln) {
+        const float2 v = a[(k >> 1) * 32 + ln];
+        return (k & 1) ? v.y : v.x;
+    };
+    for (int fs = tid; fs < 32 * F; fs += blockDim.x) {
+        const int k = fs >> 5, ln = fs & 31;
+        const int64_t j = jblock + (int64_t)ln * F + k;
+        if (j >= nf) continue;
+        double S[Q];
+#pragma unroll
+        for (int bq = 0; bq < QS; ++bq) S[L::slow_q(bq)] = (double)rd(rs + (size_t)bq * NPC * 32, k, ln);
+#pragma unroll
+        for (int jr = 0; jr < 2; ++jr) {
+            float v = 0.0f;
+            for (int w = 0; w < nw; ++w) v += rd(rr + (size_t)w * L::RR_PER_WARP + (size_t)jr * NPC * 32, k, ln);
+            S[2 * P + jr] = (double)v;
+        }
+        double vcc = 0.0, vcs = 0.0, vss = 0.0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            vcc = fma(S[q], S[q], vcc);
+            vcs = fma(S[q], S[P + q], vcs);
+            vss = fma(S[P + q], S[P + q], vss);
+        }
+        const double CC = S[2 * P + 2], CS = S[2 * P + 3];
+        double a, bb, zz;
+        bool done = false;
+        if (mixed_flags) {
+            done = solve2_fast(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], prm.flag_tau, &zz, &a, &bb);
+            if (!done) {   // ill-conditioned: provisional value now, FP64-grade re-evaluation later
+                const int32_t at = atomicAdd(prm.flag_count, 1);
+                if (at < prm.flag_cap) prm.flag_list[at] = d.z_off + j;
+                else atomicExch(prm.err, FREDEC_EINVAL);
+            }
+        }
+        if (!done) {
+            double ratio;
+            zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
+        }
+        if constexpr (MIRROR) zbuf[ln * F + k] = zz;
+        else prm.z[d.z_off + j] = zz;
+        if (prm.coef) {
+            prm.coef[2 * (d.z_off + j)] = a;
+            prm.coef[2 * (d.z_off + j) + 1] = bb;
+        }
+    }
+    if constexpr (MIRROR) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        for (int i = tid; i < 32 * F; i += blockDim.x) {
+            const int64_t j = jblock + i;
+            if (j < nf) {
+                prm.z[d.z_off + j] = zbuf[i];
+                prm.z_mirror[d.z_off + j] = zbuf[i];
+            }
+        }
+    }
+}
+
 // Register cap of the grid kernel (which may be launched with up to 256
 // threads): mixed kernels whose F x (2P+4) accumulators fit take 128
 // registers (16 warps per SM) up to 80 accumulators and 168 (three CTAs of
@@ -642,6 +848,11 @@ constexpr int pgram_maxreg() {
 }
 
 // Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
+// The single-series mixed one-set kernels keep CTA-level slow sums
+// (pgram_block_cs).
+template <int PREC, int NSET>
+constexpr bool pgram_cs() { return PREC == FREDEC_MIXED && NSET == 1; }
+
 template <int PREC, int P, int F, bool MIRROR, int NSET = 1>
 __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, NSET>())) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -651,15 +862,18 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
     uint32_t use0 = 0u, use1 = 0u;
-    pgram_block<PREC, P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
+    if constexpr (pgram_cs<PREC, NSET>())
+        pgram_block_cs<P, F, MIRROR>(prm, d, st, blockIdx.x, smem, use0, use1);
+    else
+        pgram_block<PREC, P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    using L = PgramLayout<PREC, P, F, NSET>;
-    const size_t smem = L::smem_bytes(warps);
+    const size_t smem = pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F>::smem_bytes(warps)
+                                               : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
     auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET>;
@@ -673,6 +887,9 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
 }
 
 template <int PREC, int P, int F, int NSET = 1>
-size_t pgram_smem_t(int warps) { return PgramLayout<PREC, P, F, NSET>::smem_bytes(warps); }
+size_t pgram_smem_t(int warps) {
+    return pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F>::smem_bytes(warps)
+                                  : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
+}
 
 }  // namespace fredec

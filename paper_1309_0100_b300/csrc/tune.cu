@@ -101,13 +101,13 @@ extern "C" int fredec_tune(int32_t precision, int32_t n_base, int64_t N, int64_t
         synth_kernel<<<256, 256, 0, st>>>(t, y, s, base, N, n_base);
         int fpts[4];
         const int nfpt = compiled_fpts(precision, p, fpts);
-        const int warps_opts[3] = {2, 4, 8};
+        const int warps_opts[4] = {1, 2, 4, 8};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         for (int a = 0; a < nfpt && !rc; ++a)
-            for (int b = 0; b < 3 && !rc; ++b) {
+            for (int b = 0; b < 4 && !rc; ++b) {
                 fredec_opts o;
                 fredec_opts_init(&o);
                 o.precision = precision;
