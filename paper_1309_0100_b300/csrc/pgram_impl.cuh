@@ -649,11 +649,12 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
 // 32 points per warp: one run of the software-pipelined point loop per flush
 // of the residual sums (measured at P = 7, F = 10, four warps: 64-point tiles
 // 1.749 ms, 96 1.724 ms, 128 1.690 ms, against 1.704 ms with per-warp
-// running sums).
-template <int P, int F>
+// running sums).  With NSET = 2 (z and dz/df) both sets are split the same
+// way: 2 (2P+2) slow sums, 4 residual sums.
+template <int P, int F, int NSET = 1>
 struct PgramCsLayout {
-    static constexpr int Q = 2 * P + 4, QS = 2 * P + 2, NPC = (F + 1) / 2;
-    static constexpr int RB = rec_bytes(P, FREDEC_MIXED, 1);
+    static constexpr int Q0 = 2 * P + 4, Q = NSET * Q0, QS = NSET * (2 * P + 2), NPC = (F + 1) / 2;
+    static constexpr int RB = rec_bytes(P, FREDEC_MIXED, NSET);
     static __host__ __device__ int tile_points(int nw) { return 32 * nw; }
     static __host__ __device__ size_t tile_bytes(int nw) { return (size_t)tile_points(nw) * RB; }
     static constexpr size_t OFF_TILES = OFF_TILES_BASE;
@@ -662,18 +663,22 @@ struct PgramCsLayout {
         const size_t t = 2 * tile_bytes(nw), zs = 32 * F * sizeof(double);
         return align_up(OFF_TILES + (t > zs ? t : zs), 16);
     }
-    static constexpr size_t RR_PER_WARP = (size_t)2 * NPC * 32;      // float2 entries
+    static constexpr size_t RR_PER_WARP = (size_t)2 * NSET * NPC * 32;   // float2 entries
     static __host__ __device__ size_t rs_off(int nw) { return rr_off(nw) + (size_t)nw * RR_PER_WARP * sizeof(float2); }
     static constexpr size_t RS_ENTRIES = (size_t)QS * NPC * 32;
     static __host__ __device__ size_t smem_bytes(int nw) { return rs_off(nw) + RS_ENTRIES * sizeof(float2); }
-    // the sum index q of slow sum b
-    static __host__ __device__ constexpr int slow_q(int b) { return b < 2 * P ? b : b + 2; }
+    // the sum index q of slow sum b and of residual sum j
+    static __host__ __device__ constexpr int slow_q(int b) {
+        return (b / (2 * P + 2)) * Q0 + (b % (2 * P + 2) < 2 * P ? b % (2 * P + 2) : b % (2 * P + 2) + 2);
+    }
+    static __host__ __device__ constexpr int fast_q(int j) { return (j / 2) * Q0 + 2 * P + j % 2; }
 };
 
-template <int P, int F, bool MIRROR>
+template <int P, int F, bool MIRROR, int NSET = 1>
 __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                                int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
-    using L = PgramCsLayout<P, F>;
+    static_assert(NSET == 1 || !MIRROR, "the two-set kernels write z to device memory only");
+    using L = PgramCsLayout<P, F, NSET>;
     constexpr int Q = L::Q, QS = L::QS, NPC = L::NPC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -704,7 +709,7 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
     if (tid == 0)
         for (int k = 0; k < 2 && k < ntiles; ++k) issue(k, &bars[k]);
 
-    MixedAcc<P, F, 1> acc;
+    MixedAcc<P, F, NSET> acc;
 #pragma unroll
     for (int k = 0; k < NPC; ++k)
 #pragma unroll
@@ -714,10 +719,10 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
 #pragma unroll
         for (int k = 0; k < NPC; ++k)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 2 * NSET; ++j) {
                 float2 &m = mine[(j * NPC + k) * 32 + lane];
-                m = __fadd2_rn(m, acc.a[k][2 * P + j]);
-                acc.a[k][2 * P + j] = make_float2(0.0f, 0.0f);
+                m = __fadd2_rn(m, acc.a[k][L::fast_q(j)]);
+                acc.a[k][L::fast_q(j)] = make_float2(0.0f, 0.0f);
             }
     };
     auto flush_slow = [&]() {   // all threads; nw steps, a CTA barrier after each
@@ -751,9 +756,9 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
         for (int k = 0; k < cnt;) {
             const int take = min(cnt - k, FLUSH_POINTS - since);
             if (prm.seed_mode == 0)
-                mixed_run<P, F, 0, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                mixed_run<P, F, 0, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
             else
-                mixed_run<P, F, 1, 1>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
+                mixed_run<P, F, 1, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, acc);
             k += take;
             since += take;
             if (since == FLUSH_POINTS) {
@@ -786,10 +791,10 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
 #pragma unroll
         for (int bq = 0; bq < QS; ++bq) S[L::slow_q(bq)] = (double)rd(rs + (size_t)bq * NPC * 32, k, ln);
 #pragma unroll
-        for (int jr = 0; jr < 2; ++jr) {
+        for (int jr = 0; jr < 2 * NSET; ++jr) {
             float v = 0.0f;
             for (int w = 0; w < nw; ++w) v += rd(rr + (size_t)w * L::RR_PER_WARP + (size_t)jr * NPC * 32, k, ln);
-            S[2 * P + jr] = (double)v;
+            S[L::fast_q(jr)] = (double)v;
         }
         double vcc = 0.0, vcs = 0.0, vss = 0.0;
 #pragma unroll
@@ -813,6 +818,7 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
             double ratio;
             zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
         }
+        if constexpr (NSET == 2) prm.dzdf[d.z_off + j] = dz_df<P>(S, S + L::Q0, *prm.wt_sum, a, bb);
         if constexpr (MIRROR) zbuf[ln * F + k] = zz;
         else prm.z[d.z_off + j] = zz;
         if (prm.coef) {
@@ -848,10 +854,9 @@ constexpr int pgram_maxreg() {
 }
 
 // Grid kernel: one CTA per block of 32*F frequencies of the series desc[0].
-// The single-series mixed one-set kernels keep CTA-level slow sums
-// (pgram_block_cs).
+// The single-series mixed kernels keep CTA-level slow sums (pgram_block_cs).
 template <int PREC, int NSET>
-constexpr bool pgram_cs() { return PREC == FREDEC_MIXED && NSET == 1; }
+constexpr bool pgram_cs() { return PREC == FREDEC_MIXED; }
 
 template <int PREC, int P, int F, bool MIRROR, int NSET = 1>
 __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, NSET>())) pgram_kernel(PgramParams prm) {
@@ -863,7 +868,7 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     if (st.status != FREDEC_OK) return;
     uint32_t use0 = 0u, use1 = 0u;
     if constexpr (pgram_cs<PREC, NSET>())
-        pgram_block_cs<P, F, MIRROR>(prm, d, st, blockIdx.x, smem, use0, use1);
+        pgram_block_cs<P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
     else
         pgram_block<PREC, P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
@@ -872,7 +877,7 @@ constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    const size_t smem = pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F>::smem_bytes(warps)
+    const size_t smem = pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F, NSET>::smem_bytes(warps)
                                                : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
@@ -888,7 +893,7 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
 
 template <int PREC, int P, int F, int NSET = 1>
 size_t pgram_smem_t(int warps) {
-    return pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F>::smem_bytes(warps)
+    return pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F, NSET>::smem_bytes(warps)
                                   : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
 }
 
