@@ -463,15 +463,12 @@ template <int P, int F, int NSET> struct BlockSums<FREDEC_MIXED, P, F, NSET> {
 // One CTA-block of 32*F frequencies of one series.
 // use0/use1: per-buffer mbarrier phase counters, identical in all threads.
 
-// MIRROR: z also goes to prm.z_mirror (page-locked host memory), staged in
-// shared memory so that the host-memory stores are contiguous.  The mirror
-// kernels are instantiated in translation units of their own
-// (pgram_mirror_*.cu): with them in the same module the kernels without a
-// mirror measured 1.5% slower, identical code notwithstanding.
-template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
+// The block routine of the FP64 kernels and of the batched kernels (per-warp
+// running sums of every sum); the single-series mixed kernels use
+// pgram_block_cs below.
+template <int PREC, int P, int F, int NSET = 1>
 __device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                             int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
-    static_assert(NSET == 1 || !MIRROR, "the two-set kernels write z to device memory only");
     using L = PgramLayout<PREC, P, F, NSET>;
     using T = typename AccT<PREC>::T;
     constexpr int Q = L::Q;
@@ -552,12 +549,7 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     sums.flush(mine, lane);
     __syncthreads();
 
-    // Epilogue: combine the warps' partial sums in FP64 and solve per frequency.
-    // With a mirror (page-locked host memory) z is staged in the now idle
-    // record tiles and written out contiguously: scattered 8-byte stores to
-    // host memory would stall the epilogue.
-    double *zbuf = reinterpret_cast<double *>(tiles);
-    static_assert(32 * F * sizeof(double) <= 2 * L::TILE_BYTES, "z staging fits the record tiles");
+    // Epilogue: combine the warps' partial sums and solve per frequency.
     const double W = (PREC == FREDEC_MIXED) ? st.Wf : st.W;
     const int64_t nf = d.nf;
     const bool mixed_flags = (PREC == FREDEC_MIXED) && prm.flag_tau >= 0.0;
@@ -597,24 +589,10 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
         }
         if constexpr (NSET == 2) prm.dzdf[d.z_off + j] = dz_df<P>(S, S + 2 * P + 4, *prm.wt_sum, a, bb);
-        if constexpr (MIRROR) zbuf[ln * F + k] = zz;
-        else prm.z[d.z_off + j] = zz;
+        prm.z[d.z_off + j] = zz;
         if (prm.coef) {
             prm.coef[2 * (d.z_off + j)] = a;
             prm.coef[2 * (d.z_off + j) + 1] = bb;
-        }
-    }
-    if constexpr (MIRROR) {
-        // the staging stores are ordered before the next block's TMA copies
-        // into the same tiles (persistent kernels) by each writer's fence
-        fence_proxy_async_smem();
-        __syncthreads();
-        for (int i = tid; i < 32 * F; i += blockDim.x) {
-            const int64_t j = jblock + i;
-            if (j < nf) {
-                prm.z[d.z_off + j] = zbuf[i];
-                prm.z_mirror[d.z_off + j] = zbuf[i];
-            }
         }
     }
 }
@@ -674,6 +652,11 @@ struct PgramCsLayout {
     static __host__ __device__ constexpr int fast_q(int j) { return (j / 2) * Q0 + 2 * P + j % 2; }
 };
 
+// MIRROR: z also goes to prm.z_mirror (page-locked host memory), staged in
+// shared memory so that the host-memory stores are contiguous.  The mirror
+// kernels are instantiated in translation units of their own
+// (pgram_mirror_*.cu): with them in the same module the kernels without a
+// mirror measured 1.5% slower, identical code notwithstanding.
 template <int P, int F, bool MIRROR, int NSET = 1>
 __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                                int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
@@ -870,7 +853,7 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     if constexpr (pgram_cs<PREC, NSET>())
         pgram_block_cs<P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
     else
-        pgram_block<PREC, P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
+        pgram_block<PREC, P, F, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;

@@ -1,6 +1,6 @@
 // Mixed-precision periodogram kernels that also write z to a page-locked host
 // mirror (pgram_impl.cuh, MIRROR), P = 7, 9, 11.  Kept out of the
-// pgram_p*.cu units: see the note at pgram_block.
+// pgram_p*.cu units: see the note at pgram_block_cs.
 #include "pgram_impl.cuh"
 
 namespace fredec {

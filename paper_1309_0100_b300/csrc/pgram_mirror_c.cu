@@ -1,6 +1,6 @@
 // Mixed-precision periodogram kernels that also write z to a page-locked host
 // mirror (pgram_impl.cuh, MIRROR), P = 13, 15, 17, 19, 21, 23, 25.  Kept out of the
-// pgram_p*.cu units: see the note at pgram_block.
+// pgram_p*.cu units: see the note at pgram_block_cs.
 #include "pgram_impl.cuh"
 
 namespace fredec {
