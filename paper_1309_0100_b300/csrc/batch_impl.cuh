@@ -33,7 +33,17 @@ __device__ __forceinline__ void batch_item(const BatchParams &bp, const SeriesDe
         }
         return;
     }
-    pgram_block<PREC, P, F>(bp.prm, d, st, blk, smem, use0, use1);
+    if constexpr (PREC == FREDEC_MIXED)
+        pgram_block_cs<P, F, false>(bp.prm, d, st, blk, smem, use0, use1);
+    else
+        pgram_block<PREC, P, F>(bp.prm, d, st, blk, smem, use0, use1);
+}
+
+// Shared memory of one batch item's block routine.
+template <int PREC, int P>
+size_t batch_item_smem(int warps) {
+    constexpr int F = batch_fpt(PREC, P);
+    return PREC == FREDEC_MIXED ? PgramCsLayout<P, F>::smem_bytes(warps) : PgramLayout<PREC, P, F>::smem_bytes(warps);
 }
 
 // Resident CTAs of 128 threads asked from the compiler: 3 for the small-base
@@ -72,10 +82,10 @@ template <int PREC, int PMAXC>
 size_t batch_smem(int warps) {
     size_t m = 0;
     auto upd = [&](size_t v) { m = v > m ? v : m; };
-    upd(PgramLayout<PREC, 1, batch_fpt(PREC, 1)>::smem_bytes(warps));
-    upd(PgramLayout<PREC, 3, batch_fpt(PREC, 3)>::smem_bytes(warps));
-    upd(PgramLayout<PREC, 5, batch_fpt(PREC, 5)>::smem_bytes(warps));
-#define C(P) if (PMAXC >= P) upd(PgramLayout<PREC, P, batch_fpt(PREC, P)>::smem_bytes(warps));
+    upd(batch_item_smem<PREC, 1>(warps));
+    upd(batch_item_smem<PREC, 3>(warps));
+    upd(batch_item_smem<PREC, 5>(warps));
+#define C(P) if (PMAXC >= P) upd(batch_item_smem<PREC, P>(warps));
     C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
     return m;
