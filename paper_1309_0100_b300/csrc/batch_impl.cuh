@@ -43,7 +43,8 @@ __device__ __forceinline__ void batch_item(const BatchParams &bp, const SeriesDe
 template <int PREC, int P>
 size_t batch_item_smem(int warps) {
     constexpr int F = batch_fpt(PREC, P);
-    return PREC == FREDEC_MIXED ? PgramCsLayout<P, F>::smem_bytes(warps) : PgramLayout<PREC, P, F>::smem_bytes(warps);
+    if constexpr (PREC == FREDEC_MIXED) return PgramCsLayout<P, F>::smem_bytes(warps);
+    else return PgramLayout<PREC, P, F>::smem_bytes(warps);
 }
 
 // Resident CTAs of 128 threads asked from the compiler: 3 for the small-base

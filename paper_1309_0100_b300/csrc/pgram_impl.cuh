@@ -69,10 +69,6 @@ struct PgramParams {
     int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
 };
 
-template <int PREC> struct AccT;
-template <> struct AccT<FREDEC_MIXED> { using T = float; };
-template <> struct AccT<FREDEC_FP64> { using T = double; };
-
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared memory of a CTA: [mbarriers | seed table | 2 record tiles | warp
@@ -82,24 +78,23 @@ constexpr size_t OFF_TABLE = 128;
 constexpr size_t OFF_TILES_BASE = OFF_TABLE + sizeof(SeedTable);
 static_assert(sizeof(SeedTableF) <= sizeof(SeedTable), "both seed tables fit the table region");
 
-// NSET = 2: every record carries a second set of weighted values, the
-// t'-weighted ones, and the kernel accumulates 2 (2P+4) sums per frequency.
+// Shared memory of the FP64 kernels (pgram_block).  NSET = 2: every record
+// carries a second set of weighted values, the t'-weighted ones, and the
+// kernel accumulates 2 (2P+4) sums per frequency.
 template <int PREC, int P, int F, int NSET = 1>
 struct PgramLayout {
+    static_assert(PREC == FREDEC_FP64, "the mixed kernels use PgramCsLayout");
     static constexpr int Q = NSET * (2 * P + 4);
     static constexpr int RB = rec_bytes(P, PREC, NSET);
     // records per tile: TILE_POINTS, or fewer for records above 64 bytes so
-    // that the two tiles stay within 16 KB (with the F = 10 running sums of
-    // P = 7, two CTAs then still fit an SM's shared memory)
+    // that the two tiles stay within 16 KB
     static constexpr int TP = RB <= 64 ? TILE_POINTS : (8192 / RB) / 8 * 8;
     static constexpr size_t TILE_BYTES = (size_t)TP * RB;
     static constexpr size_t OFF_TILES = OFF_TILES_BASE;
     static constexpr size_t OFF_RED = OFF_TILES + 2 * TILE_BYTES;
-    // warp running sums: FP64 Q x F doubles per lane; mixed Q x ceil(F/2)
-    // float2 (frequency pairs) per lane
-    static constexpr int RED_PER_WARP = PREC == FREDEC_MIXED ? Q * ((F + 1) / 2) * 32 : Q * F * 32;
-    static constexpr size_t RED_ENTRY = PREC == FREDEC_MIXED ? sizeof(float2) : sizeof(double);
-    static __host__ __device__ size_t red_bytes(int nw) { return (size_t)nw * RED_PER_WARP * RED_ENTRY; }
+    // warp running sums: Q x F doubles per lane
+    static constexpr int RED_PER_WARP = Q * F * 32;
+    static __host__ __device__ size_t red_bytes(int nw) { return (size_t)nw * RED_PER_WARP * sizeof(double); }
     static __host__ __device__ size_t smem_bytes(int nw) { return OFF_RED + red_bytes(nw); }
 };
 
@@ -389,97 +384,22 @@ __device__ __forceinline__ void fp64_point(const double2 *__restrict__ r2, const
 }
 
 // ---------------------------------------------------------------------------
-// Per-thread sums of pgram_block and their second summation level, the
-// warp's running sums in shared memory (red): flush() adds all first-level
-// sums into them, flush_r() only <r c>, <r s>; read() gives warp w's running
-// sum q of the lane's frequency k (epilogue).
-template <int PREC, int P, int F, int NSET> struct BlockSums;
-
-template <int P, int F, int NSET> struct BlockSums<FREDEC_FP64, P, F, NSET> {
-    static constexpr int Q = NSET * (2 * P + 4);
-    using R = double;
-    double a[F][Q];
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < F; ++k)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) a[k][q] = 0.0;
-    }
-    template <int Q0, int Q1>
-    __device__ __forceinline__ void flush_range(R *mine, int lane) {
-        static_assert(0 <= Q0 && Q0 <= Q1 && Q1 <= Q, "flush range inside the block's sums");
-#pragma unroll
-        for (int k = 0; k < F; ++k)
-#pragma unroll
-            for (int q = Q0; q < Q1; ++q) {
-                mine[(q * F + k) * 32 + lane] += a[k][q];
-                a[k][q] = 0.0;
-            }
-    }
-    __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
-    __device__ __forceinline__ void flush_r(R *mine, int lane) {
-        flush_range<2 * P, 2 * P + 2>(mine, lane);
-        if constexpr (NSET == 2) flush_range<(2 * P + 4) + 2 * P, (2 * P + 4) + 2 * P + 2>(mine, lane);
-    }
-    static __device__ __forceinline__ double read(const R *red, int w, int q, int k, int ln) {
-        return red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
-    }
-};
-
-template <int P, int F, int NSET> struct BlockSums<FREDEC_MIXED, P, F, NSET> {
-    static constexpr int Q = NSET * (2 * P + 4), NPC = (F + 1) / 2;
-    using R = float2;
-    MixedAcc<P, F, NSET> acc;
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < NPC; ++k)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) acc.a[k][q] = make_float2(0.0f, 0.0f);
-    }
-    template <int Q0, int Q1>
-    __device__ __forceinline__ void flush_range(R *mine, int lane) {
-        static_assert(0 <= Q0 && Q0 <= Q1 && Q1 <= Q, "flush range inside the block's sums");
-#pragma unroll
-        for (int k = 0; k < NPC; ++k)
-#pragma unroll
-            for (int q = Q0; q < Q1; ++q) {
-                R &m = mine[(q * NPC + k) * 32 + lane];
-                m = __fadd2_rn(m, acc.a[k][q]);
-                acc.a[k][q] = make_float2(0.0f, 0.0f);
-            }
-    }
-    __device__ __forceinline__ void flush(R *mine, int lane) { flush_range<0, Q>(mine, lane); }
-    __device__ __forceinline__ void flush_r(R *mine, int lane) {
-        flush_range<2 * P, 2 * P + 2>(mine, lane);
-        if constexpr (NSET == 2) flush_range<(2 * P + 4) + 2 * P, (2 * P + 4) + 2 * P + 2>(mine, lane);
-    }
-    static __device__ __forceinline__ float read(const R *red, int w, int q, int k, int ln) {
-        const float2 v = red[((size_t)w * Q + q) * NPC * 32 + (k >> 1) * 32 + ln];
-        return (k & 1) ? v.y : v.x;
-    }
-};
-
-// ---------------------------------------------------------------------------
-// One CTA-block of 32*F frequencies of one series.
-// use0/use1: per-buffer mbarrier phase counters, identical in all threads.
-
-// The block routine of the FP64 kernels and of the batched kernels (per-warp
-// running sums of every sum); the single-series mixed kernels use
-// pgram_block_cs below.
+// One CTA-block of 32*F frequencies of one series, FP64 (the FP64 grid,
+// two-set and batched kernels): each lane's F x Q sums in FP64 registers over
+// all points, then the warps' running sums in shared memory (red) combined
+// per frequency.  use0/use1: per-buffer mbarrier phase counters, identical in
+// all threads.
 template <int PREC, int P, int F, int NSET = 1>
 __device__ __forceinline__ void pgram_block(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                             int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
+    static_assert(PREC == FREDEC_FP64, "the mixed kernels use pgram_block_cs");
     using L = PgramLayout<PREC, P, F, NSET>;
-    using T = typename AccT<PREC>::T;
     constexpr int Q = L::Q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     unsigned char *tiles = smem + L::OFF_TILES;
-    using BS = BlockSums<PREC, P, F, NSET>;
-    using R = typename BS::R;
-    R *red = reinterpret_cast<R *>(smem + L::OFF_RED);
+    double *red = reinterpret_cast<double *>(smem + L::OFF_RED);
     const SeedTable &tab = *reinterpret_cast<const SeedTable *>(smem + OFF_TABLE);
-    const SeedTableF &tabf = *reinterpret_cast<const SeedTableF *>(smem + OFF_TABLE);
 
     const int N = d.N;
     const int64_t jblock = blk * 32 * F;
@@ -488,7 +408,6 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
     const int ntiles = (N + L::TP - 1) / L::TP;
 
     __syncthreads();   // previous block's epilogue is done with red / tiles
-    for (int q = lane; q < L::RED_PER_WARP; q += 32) red[(size_t)warp * L::RED_PER_WARP + q] = R{};
     if (tid == 0) {
         for (int k = 0; k < 2 && k < ntiles; ++k) {
             const unsigned n = (unsigned)min(L::TP, N - k * L::TP);
@@ -497,11 +416,11 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         }
     }
 
-    BS sums;
-    sums.zero();
-    R *mine = red + (size_t)warp * L::RED_PER_WARP;
-    int since = 0;   // points in the current first-level block of this warp
-    int nblk = 0;   // first-level blocks since the last flush of all sums
+    double acc[F][Q];
+#pragma unroll
+    for (int k = 0; k < F; ++k)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[k][q] = 0.0;
 
     for (int tile = 0; tile < ntiles; ++tile) {
         const int b = tile & 1;
@@ -511,34 +430,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         }
         const int n = min(L::TP, N - tile * L::TP);
         const unsigned char *tb = tiles + b * L::TILE_BYTES;
-        if constexpr (PREC == FREDEC_MIXED) {
-            // this warp's points of the tile (warp, warp + nw, ...) in runs
-            // that end on the first-level block boundaries
-            const int cnt = n > warp ? (n - warp + nw - 1) / nw : 0;
-            const unsigned char *pw = tb + (size_t)warp * L::RB;
-            const size_t stride = (size_t)nw * L::RB;
-            for (int k = 0; k < cnt;) {
-                const int take = min(cnt - k, FLUSH_POINTS - since);
-                if (prm.seed_mode == 0)
-                    mixed_run<P, F, 0, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
-                else
-                    mixed_run<P, F, 1, NSET>(pw + (size_t)k * stride, stride, take, tabf, j0, sums.acc);
-                k += take;
-                since += take;
-                if (since == FLUSH_POINTS) {
-                    if (++nblk == FLUSH_BLOCKS_ALL) {
-                        sums.flush(mine, lane);
-                        nblk = 0;
-                    } else {
-                        sums.flush_r(mine, lane);
-                    }
-                    since = 0;
-                }
-            }
-        } else {
-            for (int i = warp; i < n; i += nw)
-                fp64_point<P, F, NSET>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, sums.a);
-        }
+        for (int i = warp; i < n; i += nw)
+            fp64_point<P, F, NSET>(reinterpret_cast<const double2 *>(tb + (size_t)i * L::RB), tab, j0, acc);
         __syncthreads();   // all warps are done with buffer b
         if (tid == 0 && tile + 2 < ntiles) {
             const unsigned nn = (unsigned)min(L::TP, N - (tile + 2) * L::TP);
@@ -546,13 +439,16 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             bulk_g2s(tiles + b * L::TILE_BYTES, src + (size_t)(tile + 2) * L::TILE_BYTES, nn * L::RB, &bars[b]);
         }
     }
-    sums.flush(mine, lane);
+    double *mine = red + (size_t)warp * L::RED_PER_WARP;
+#pragma unroll
+    for (int k = 0; k < F; ++k)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) mine[(q * F + k) * 32 + lane] = acc[k][q];
     __syncthreads();
 
-    // Epilogue: combine the warps' partial sums and solve per frequency.
-    const double W = (PREC == FREDEC_MIXED) ? st.Wf : st.W;
+    // Epilogue: combine the warps' sums and solve per frequency.
+    const double W = st.W;
     const int64_t nf = d.nf;
-    const bool mixed_flags = (PREC == FREDEC_MIXED) && prm.flag_tau >= 0.0;
     for (int fs = tid; fs < 32 * F; fs += blockDim.x) {
         const int k = fs >> 5, ln = fs & 31;
         const int64_t j = jblock + (int64_t)ln * F + k;
@@ -560,11 +456,9 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
         double S[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            // warps' partial sums combined in the accumulation precision (a
-            // handful of terms), then one conversion to FP64 per sum
-            T sq = T(0);
-            for (int w = 0; w < nw; ++w) sq += BS::read(red, w, q, k, ln);
-            S[q] = (double)sq;
+            double sq = 0.0;
+            for (int w = 0; w < nw; ++w) sq += red[((size_t)w * Q + q) * F * 32 + k * 32 + ln];
+            S[q] = sq;
         }
         double vcc = 0.0, vcs = 0.0, vss = 0.0;
 #pragma unroll
@@ -574,20 +468,8 @@ __device__ __forceinline__ void pgram_block(const PgramParams &prm, const Series
             vss = fma(S[P + q], S[P + q], vss);
         }
         const double CC = S[2 * P + 2], CS = S[2 * P + 3];
-        double a, bb, zz;
-        bool done = false;
-        if (mixed_flags) {
-            done = solve2_fast(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], prm.flag_tau, &zz, &a, &bb);
-            if (!done) {   // ill-conditioned: provisional value now, FP64-grade re-evaluation later
-                const int32_t at = atomicAdd(prm.flag_count, 1);
-                if (at < prm.flag_cap) prm.flag_list[at] = d.z_off + j;
-                else atomicExch(prm.err, FREDEC_EINVAL);
-            }
-        }
-        if (!done) {
-            double ratio;
-            zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
-        }
+        double a, bb, ratio;
+        const double zz = solve2(CC, CS, W - CC, vcc, vcs, vss, S[2 * P], S[2 * P + 1], &a, &bb, &ratio);
         if constexpr (NSET == 2) prm.dzdf[d.z_off + j] = dz_df<P>(S, S + 2 * P + 4, *prm.wt_sum, a, bb);
         prm.z[d.z_off + j] = zz;
         if (prm.coef) {
@@ -858,10 +740,15 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
+template <int PREC, int P, int F, int NSET = 1>
+size_t pgram_smem_t(int warps) {
+    if constexpr (pgram_cs<PREC, NSET>()) return PgramCsLayout<P, F, NSET>::smem_bytes(warps);
+    else return PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
+}
+
 template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    const size_t smem = pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F, NSET>::smem_bytes(warps)
-                                               : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
+    const size_t smem = pgram_smem_t<PREC, P, F, NSET>(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
     auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET>;
@@ -872,12 +759,6 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram launch: ") + cudaGetErrorString(e));
     return FREDEC_OK;
-}
-
-template <int PREC, int P, int F, int NSET = 1>
-size_t pgram_smem_t(int warps) {
-    return pgram_cs<PREC, NSET>() ? PgramCsLayout<P, F, NSET>::smem_bytes(warps)
-                                  : PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
 }
 
 }  // namespace fredec
