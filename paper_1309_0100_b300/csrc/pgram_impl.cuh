@@ -27,8 +27,9 @@
 
 namespace fredec {
 
-// Mixed path: FP32 block sums are flushed into the warp's shared running sums
-// (two-level summation).  The random-phase residual sums <r c>, <r s> are
+// Mixed path: FP32 block sums are flushed into FP32 running sums in shared
+// memory (two-level summation; per warp for <r c>, <r s>, one array per CTA
+// for the others: pgram_block_cs).  The random-phase residual sums <r c>, <r s> are
 // flushed every 32 points: their FP32 rounding is amplified at low-z bins
 // (dz/z = 2 drho/rho) and sets the z error.  The other 2P+2 sums are flushed
 // every FLUSH_BLOCKS_ALL x 32 = 256 points.  Measured (largest z error against
@@ -495,14 +496,15 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
 }
 
 // ---------------------------------------------------------------------------
-// Single-series mixed kernels with CTA-level second-level sums.  The 2P+2
-// slow sums (<psi_k c>, <psi_k s>, <c^2>, <c s>) of all warps go into ONE
-// running array per CTA: every KS tiles, at the tile barrier, the warps add
-// their register sums in nw steps separated by CTA barriers, warp w adding
-// in step s the slow sums b with b % nw == (w + s) % nw, so that no two
-// warps touch the same entries in a step and the order of the additions is
-// fixed (deterministic).  The residual sums <r c>, <r s> keep per-warp
-// running sums, flushed every FLUSH_POINTS points as in pgram_block.  This
+// Mixed kernels (single-series, two-set and batched) with CTA-level
+// second-level sums.  The 2P+2 slow sums (<psi_k c>, <psi_k s>, <c^2>,
+// <c s>) of all warps go into ONE running array per CTA: every
+// FLUSH_BLOCKS_ALL tiles (256 points per warp), at the tile barrier, the
+// warps add their register sums in nw steps separated by CTA barriers, warp
+// w adding in step s the slow sums b with b % nw == (w + s) % nw, so that no
+// two warps touch the same entries in a step and the order of the additions
+// is fixed (deterministic).  The residual sums <r c>, <r s> keep per-warp
+// running sums, flushed every FLUSH_POINTS points.  This
 // takes the warps' running sums from (2P+4) nw to 2P+2 + 2 nw rows of
 // 32 F floats (92 -> 31 KB at P = 7, F = 10, four warps; with two warps a
 // CTA four CTAs fit an SM, where per-warp sums allowed three).  A tile holds
