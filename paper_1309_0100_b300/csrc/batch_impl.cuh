@@ -8,11 +8,16 @@
 
 namespace fredec {
 
-// Frequencies per thread used by the batch kernels for each base size: the
-// largest that keeps a thread at about 128 registers (mixed) or the FP64
-// default.
+// Frequencies per thread used by the batch kernels for each base size (mixed:
+// p = 1, 3, 5 the widest that the 168 registers of three resident CTAs hold
+// without spills; measured on the 4096-series workload, p = 1, 3, 5:
+// 12 / 8 / 4 309.8 ms a replay, 16 / 12 / 6 286.8 ms, 20 / 12 / 6 284.8 ms;
+// 20 / 14 / 8 and 24 / 16 / 8 spill; p = 7 stays at 4, where 6 moved short
+// series past the single-series results by more than the mixed bar) or the
+// FP64 default.
 __host__ __device__ constexpr int batch_fpt(int prec, int p) {
-    return prec == FREDEC_MIXED ? (p == 1 ? 12 : p == 3 ? 8 : p <= 7 ? 4 : p <= 11 ? 3 : p <= 15 ? 2 : 1) : (p <= 5 ? 2 : 1);
+    return prec == FREDEC_MIXED ? (p == 1 ? 20 : p == 3 ? 12 : p == 5 ? 6 : p <= 7 ? 4 : p <= 11 ? 3 : p <= 15 ? 2 : 1)
+                                : (p <= 5 ? 2 : 1);
 }
 
 struct BatchParams {
