@@ -93,11 +93,12 @@ int compiled_fpts(int precision, int p, int *out) {
 }
 
 // Widest mixed shape worth taking for series of at most SHORT_N points, by p
-// = 1, 3, ..., 13 (measured with the autotuner at N = 2000, nf = 1e6: the
+// = 1, 3, ..., 13 (the autotuner's choices at N = 300, nf = 1e6: the
 // per-CTA epilogue weighs more against a short point loop, and the widest
-// shapes run fewer CTAs per SM); longer series take the widest compiled shape.
-constexpr int64_t SHORT_N = 4096;
-constexpr int SHORT_MIXED_FPT[7] = {12, 8, 14, 6, 8, 6, 4};
+// shapes run fewer CTAs per SM); longer series take the widest compiled shape
+// (the autotuner's choice for every p at N = 2000).
+constexpr int64_t SHORT_N = 1024;
+constexpr int SHORT_MIXED_FPT[7] = {12, 8, 8, 6, 8, 4, 4};
 
 // Built-in default (without a tuned entry): the largest compiled F (fewest
 // re-seeds; for short mixed series at most SHORT_MIXED_FPT) and 4 warps,
