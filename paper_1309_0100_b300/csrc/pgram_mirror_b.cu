@@ -13,9 +13,9 @@ int launch_pgram_mirror_b(int p, int F, const PgramParams &prm, int64_t nblocks,
     if (p == 9 && F == 3) return launch_pgram_t<FREDEC_MIXED, 9, 3, true>(prm, nblocks, warps, st);
     if (p == 9 && F == 5) return launch_pgram_t<FREDEC_MIXED, 9, 5, true>(prm, nblocks, warps, st);
     if (p == 9 && F == 8) return launch_pgram_t<FREDEC_MIXED, 9, 8, true>(prm, nblocks, warps, st);
-    if (p == 11 && F == 3) return launch_pgram_t<FREDEC_MIXED, 11, 3, true>(prm, nblocks, warps, st);
     if (p == 11 && F == 4) return launch_pgram_t<FREDEC_MIXED, 11, 4, true>(prm, nblocks, warps, st);
     if (p == 11 && F == 6) return launch_pgram_t<FREDEC_MIXED, 11, 6, true>(prm, nblocks, warps, st);
+    if (p == 11 && F == 8) return launch_pgram_t<FREDEC_MIXED, 11, 8, true>(prm, nblocks, warps, st);
     for (int q : {7, 9, 11})
         if (p == q) return -1;
     return -2;

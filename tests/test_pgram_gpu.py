@@ -195,20 +195,21 @@ def test_mixed_shapes_odd_widths_long_series(F, nb):
     shapes) on a series long enough for several flushes of the CTA-level
     slow sums at every CTA width (2600 points: 82 tiles of one warp, 11 of
     eight) and a ragged last tile: every shape meets the bound against the
-    oracle on every bin and agrees with the others."""
+    oracle on every bin, and any two shapes agree within twice it (each is
+    within the bound of the oracle; their summation orders differ)."""
     s = synth.small_series(40 + nb, N=2600, n_base=nb, nf=1500, span=400.0, fmax=1.2)
     f = s.grid.array()
     zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
     p = 2 * nb + 1
     first = None
-    for fpt in {9: (3, 5, 8), 11: (3, 4, 6)}[p]:   # the compiled mixed shapes of these widths
+    for fpt in {9: (3, 5, 8), 11: (4, 6, 8)}[p]:   # the compiled mixed shapes of these widths
         for warps in (1, 2, 4, 8):
             z = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="mixed", fpt=fpt, warps=warps)
             _assert_cond(z, zr, ratio, c2, "mixed", s.N, (fpt, warps))
             if first is None:
                 first = z
             else:
-                r = cond_parity(z, first, ratio, c2, TOL["mixed"], s.N)
+                r = cond_parity(z, first, ratio, c2, 2 * TOL["mixed"], s.N)
                 assert r["ok"], (fpt, warps, r)
 
 
