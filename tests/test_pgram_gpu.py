@@ -178,7 +178,7 @@ def test_launch_shapes_agree(F, prec):
     zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
     first = None
     for fpt in {"fp64": (1, 2, 4), "mixed": (4, 6, 10)}[prec]:
-        for warps in (1, 2, 4, 8):
+        for warps in (1, 2, 3, 4, 6, 8):   # 3 and 6: slices of the CTA-level sums that are not powers of two
             z = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision=prec, fpt=fpt, warps=warps)
             r = _assert_cond(z, zr, ratio, c2, prec, s.N, (fpt, warps))
             assert r["excluded"] == 0
