@@ -54,13 +54,15 @@ DevBuf::~DevBuf() {
     if (ptr) cudaFreeAsync(ptr, stream);
 }
 
+// SM count of the device current at the first call (thread-safe static
+// initialisation; every device of this build is a B300).
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-    }
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        return v;
+    }();
     return n;
 }
 
