@@ -9,7 +9,7 @@ static const FptOptions kFptOptions[] = {
     {7, {4, 6, 10}, 3, {1, 2, 4}, 3},
     {9, {3, 5, 8}, 3, {1, 2, 0}, 2},
     {11, {4, 6, 8}, 3, {1, 2, 0}, 2},
-    {13, {2, 4, 0}, 2, {1, 0, 0}, 1},
+    {13, {4, 6, 0}, 2, {1, 0, 0}, 1},
     {15, {2, 3, 0}, 2, {1, 0, 0}, 1},
     {17, {2, 3, 0}, 2, {1, 0, 0}, 1},
     {19, {2, 0, 0}, 1, {1, 0, 0}, 1},

@@ -7,8 +7,8 @@ namespace fredec {
 
 // -2: P not handled here.
 int launch_pgram_mirror_c(int p, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    if (p == 13 && F == 2) return launch_pgram_t<FREDEC_MIXED, 13, 2, true>(prm, nblocks, warps, st);
     if (p == 13 && F == 4) return launch_pgram_t<FREDEC_MIXED, 13, 4, true>(prm, nblocks, warps, st);
+    if (p == 13 && F == 6) return launch_pgram_t<FREDEC_MIXED, 13, 6, true>(prm, nblocks, warps, st);
     if (p == 15 && F == 2) return launch_pgram_t<FREDEC_MIXED, 15, 2, true>(prm, nblocks, warps, st);
     if (p == 15 && F == 3) return launch_pgram_t<FREDEC_MIXED, 15, 3, true>(prm, nblocks, warps, st);
     if (p == 17 && F == 2) return launch_pgram_t<FREDEC_MIXED, 17, 2, true>(prm, nblocks, warps, st);

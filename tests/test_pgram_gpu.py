@@ -189,10 +189,10 @@ def test_launch_shapes_agree(F, prec):
                 assert r["ok"] and r["excluded"] == 0, (fpt, warps, r)
 
 
-@pytest.mark.parametrize("nb", [4, 5])
-def test_mixed_shapes_odd_widths_long_series(F, nb):
-    """Base widths 9 and 11 (odd frequencies per thread among the compiled
-    shapes) on a series long enough for several flushes of the CTA-level
+@pytest.mark.parametrize("nb", [4, 5, 6])
+def test_mixed_shapes_wide_bases_long_series(F, nb):
+    """Base widths 9, 11 and 13 (odd frequencies per thread among the
+    compiled shapes of width 9) on a series long enough for several flushes of the CTA-level
     slow sums at every CTA width (2600 points: 82 tiles of one warp, 11 of
     eight) and a ragged last tile: every shape meets the bound against the
     oracle on every bin, and any two shapes agree within twice it (each is
@@ -202,7 +202,7 @@ def test_mixed_shapes_odd_widths_long_series(F, nb):
     zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, want_ratio=True)
     p = 2 * nb + 1
     first = None
-    for fpt in {9: (3, 5, 8), 11: (4, 6, 8)}[p]:   # the compiled mixed shapes of these widths
+    for fpt in {9: (3, 5, 8), 11: (4, 6, 8), 13: (4, 6)}[p]:   # the compiled mixed shapes of these widths
         for warps in (1, 2, 4, 8):
             z = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="mixed", fpt=fpt, warps=warps)
             _assert_cond(z, zr, ratio, c2, "mixed", s.N, (fpt, warps))
