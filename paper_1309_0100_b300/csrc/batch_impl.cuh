@@ -13,10 +13,12 @@ namespace fredec {
 // without spills; measured on the 4096-series workload, p = 1, 3, 5:
 // 12 / 8 / 4 309.8 ms a replay, 16 / 12 / 6 286.8 ms, 20 / 12 / 6 284.8 ms;
 // 20 / 14 / 8 and 24 / 16 / 8 spill; p = 7 stays at 4, where 6 moved short
-// series past the single-series results by more than the mixed bar) or the
-// FP64 default.
+// series past the single-series results by more than the mixed bar; p >= 13
+// take 2, in a kernel of 240 registers without spills: with F = 1 for p >= 17,
+// one unpacked FMA per sum and a seed per frequency, 512 series of p = 13..25
+// took 168.6 ms a replay, with F = 2 126.6 ms) or the FP64 default.
 __host__ __device__ constexpr int batch_fpt(int prec, int p) {
-    return prec == FREDEC_MIXED ? (p == 1 ? 20 : p == 3 ? 12 : p == 5 ? 6 : p <= 7 ? 4 : p <= 11 ? 3 : p <= 15 ? 2 : 1)
+    return prec == FREDEC_MIXED ? (p == 1 ? 20 : p == 3 ? 12 : p == 5 ? 6 : p <= 7 ? 4 : p <= 11 ? 3 : 2)
                                 : (p <= 5 ? 2 : 1);
 }
 

@@ -95,9 +95,14 @@ int compiled_fpts(int precision, int p, int *out) {
 // = 1, 3, ..., 13 (the autotuner's choices at N = 300, nf = 1e6: the
 // per-CTA epilogue weighs more against a short point loop, and the widest
 // shapes run fewer CTAs per SM); longer series take the widest compiled shape
-// (the autotuner's choice for every p at N = 2000).
+// (the autotuner's choice for every p <= 13 at N = 2000).  From p = 15 on,
+// mixed series of any length take F = 2: F = 3 holds 3 of its 4 frequency
+// slots and ran slower at both lengths (kernel ms, nf = 1e6, 4 warps: p = 15
+// 3.50 against 3.68 at N = 2000, 0.61 against 0.68 at N = 300; p = 17 3.83
+// against 4.20, 0.67 against 0.79).
 constexpr int64_t SHORT_N = 1024;
 constexpr int SHORT_MIXED_FPT[7] = {12, 8, 8, 6, 8, 4, 4};
+constexpr int WIDE_MIXED_FPT = 2;
 
 // Built-in default (without a tuned entry): the largest compiled F (fewest
 // re-seeds; for short mixed series at most SHORT_MIXED_FPT) and 4 warps,
@@ -110,6 +115,8 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
     int n = precision == FREDEC_MIXED ? o->nmixed : o->nfp64;
     if (precision == FREDEC_MIXED && N <= SHORT_N && p <= 13)
         while (n > 1 && v[n - 1] > SHORT_MIXED_FPT[(p - 1) / 2]) --n;
+    if (precision == FREDEC_MIXED && p >= 15)
+        while (n > 1 && v[n - 1] > WIDE_MIXED_FPT) --n;
     s.fpt = v[n - 1];
     const int64_t want = 2LL * sm_count();
     for (int i = n - 1; i > 0; --i) {
