@@ -166,6 +166,7 @@ int grad_core(const double *t, const double *y, const double *sigma, int64_t N, 
         prm.flag_count = flag_count;
         prm.err = err;
         prm.seed_mode = seed_mode();
+        prm.comp = pgram_comp(N, warps);
         prm.dzdf = dzdf;
         prm.wt_sum = wt;
         const int64_t nblocks = (nf + 32LL * fpt - 1) / (32LL * fpt);

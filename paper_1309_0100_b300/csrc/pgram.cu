@@ -130,7 +130,6 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,
                  int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef, int64_t *flag_list,
                  int32_t *flag_count, int32_t *err, cudaStream_t st, double *z_mirror) {
-    (void)N;
     if (!shape_supported(precision, p, shape.fpt))
         return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, frequencies per thread)");
     if (shape.warps < 1 || shape.warps > 8) return fail(FREDEC_EINVAL, "warps per CTA must be in 1..8");
@@ -147,6 +146,7 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
     prm.flag_count = flag_count;
     prm.err = err;
     prm.seed_mode = seed_mode();
+    prm.comp = pgram_comp(N, shape.warps);
     const int64_t nblocks = (nf + 32LL * shape.fpt - 1) / (32LL * shape.fpt);
     cudaEvent_t e0, e1;
     profile_events(&e0, &e1);

@@ -29,7 +29,8 @@ namespace fredec {
 
 // Mixed path: FP32 block sums are flushed into FP32 running sums in shared
 // memory (two-level summation; per warp for <r c>, <r s>, one array per CTA
-// for the others: pgram_block_cs).  The random-phase residual sums <r c>, <r s> are
+// for the others: pgram_block_cs; on long series a third, compensated level
+// for <r c>, <r s>: COMP below).  The random-phase residual sums <r c>, <r s> are
 // flushed every 32 points: their FP32 rounding is amplified at low-z bins
 // (dz/z = 2 drho/rho) and sets the z error.  The other 2P+2 sums are flushed
 // every FLUSH_BLOCKS_ALL x 32 = 256 points.  Measured (largest z error against
@@ -40,8 +41,27 @@ namespace fredec {
 //   <r c>, <r s> every 32, the rest every 128: 1.8e-6, 5.8e-6; 1.873 ms
 //   <r c>, <r s> every 32, the rest every 256: 1.8e-6, 5.8e-6; 1.855 ms (N = 7e4: 5.4e-6, N = 1e5: 3.3e-6)
 //   <r c>, <r s> every 32, the rest every 512: 2.9e-6, 5.8e-6; 1.847 ms
+//   with COMP (below) at N = 1e5, p = 11 and N = 7e4, p = 7: 99th percentile
+//   of the error over 290 bins 6.1e-6 -> 1.4e-6 and 4.8e-6 -> 1.1e-6, median
+//   5.3e-7 -> 1.7e-7 and 4.8e-7 -> 1.8e-7 (the largest errors, 6.0e-6 and
+//   5.5e-6, are at nearly degenerate bins that the float-float re-evaluation
+//   serves, within their bound); short series unchanged (the FP32 cos/sin of
+//   the first level sets their error)
 constexpr int FLUSH_POINTS = 32;
 constexpr int FLUSH_BLOCKS_ALL = 8;
+
+// Long series: a warp's FP32 running residual sums take one flush per tile,
+// and their rounding grows as sqrt(flushes).  The COMP kernels move them,
+// every FLUSH_BLOCKS_ALL tiles, into CTA-level totals with Kahan compensation
+// (kahan_add2), so that no FP32 running sum takes more than FLUSH_BLOCKS_ALL
+// plain additions.  They serve series with more than COMP_MIN_FLUSHES tiles
+// (N > 8192 with four warps).  On shorter series the running sums take few
+// flushes and the plain kernels run: the compensated variant measured 1.7%
+// slower on the N = 2000, p = 7, F = 10 kernel (a different schedule of the
+// point loop, not the additions themselves: a plain-add variant of the same
+// structure measured the same); on N = 1e5 it runs as fast as the plain one.
+constexpr int COMP_MIN_FLUSHES = 64;
+inline bool pgram_comp(int64_t N, int warps) { return (N + 32LL * warps - 1) / (32LL * warps) > COMP_MIN_FLUSHES; }
 
 // Frequencies per thread of the two-set kernels (z and dz/df): mixed, two
 // frequency pairs for bases of up to 7 columns (2 (2P+4) float2 sums a pair in
@@ -68,6 +88,7 @@ struct PgramParams {
     double *dzdf;               // two-set kernels: dz/df per bin (same offsets as z)
     const double *wt_sum;       // two-set kernels: <t'> = sum of the records' w t' (one series)
     int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
+    int comp;                   // mixed: compensated residual totals (pgram_comp)
 };
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -252,6 +273,19 @@ struct MixedAcc {
     static constexpr int NPC = (F + 1) / 2;
     float2 a[NPC][Q];
 };
+
+// Compensated (Kahan) addition of v to the running sum m with compensation
+// c, two lanes at a time: c holds the low-order part lost by the earlier
+// additions, so that m - c carries the total to within a few roundings
+// whatever the number of additions.  a - b is formed as fma(b, -1, a), one
+// rounding.
+__device__ __forceinline__ void kahan_add2(float2 &m, float2 &c, float2 v) {
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    const float2 y = __ffma2_rn(c, neg1, v);
+    const float2 t = __fadd2_rn(m, y);
+    c = __ffma2_rn(y, neg1, __ffma2_rn(m, neg1, t));
+    m = t;
+}
 
 // F consecutive frequencies of one point, two at a time.  The pair starts at
 // (f_{j0}, f_{j0+1}) (the seed and one step of the rotation e^{i theta},
@@ -513,7 +547,7 @@ __device__ __forceinline__ void pgram_cta_init(unsigned char *smem) {
 // 1.749 ms, 96 1.724 ms, 128 1.690 ms, against 1.704 ms with per-warp
 // running sums).  With NSET = 2 (z and dz/df) both sets are split the same
 // way: 2 (2P+2) slow sums, 4 residual sums.
-template <int P, int F, int NSET = 1>
+template <int P, int F, int NSET = 1, bool COMP = false>
 struct PgramCsLayout {
     static constexpr int Q0 = 2 * P + 4, Q = NSET * Q0, QS = NSET * (2 * P + 2), NPC = (F + 1) / 2;
     static constexpr int RB = rec_bytes(P, FREDEC_MIXED, NSET);
@@ -525,9 +559,12 @@ struct PgramCsLayout {
         const size_t t = 2 * tile_bytes(nw), zs = 32 * F * sizeof(double);
         return align_up(OFF_TILES + (t > zs ? t : zs), 16);
     }
-    static constexpr size_t RR_PER_WARP = (size_t)2 * NSET * NPC * 32;   // float2 entries
+    static constexpr int QR = 2 * NSET;   // residual sums
+    static constexpr size_t RR_PER_WARP = (size_t)QR * NPC * 32;   // float2 entries
     static __host__ __device__ size_t rs_off(int nw) { return rr_off(nw) + (size_t)nw * RR_PER_WARP * sizeof(float2); }
-    static constexpr size_t RS_ENTRIES = (size_t)QS * NPC * 32;
+    // CTA array: QS slow-sum rows, then with COMP QR residual-total rows and
+    // QR rows of their compensation terms; a row is NPC * 32 float2 entries
+    static constexpr size_t RS_ENTRIES = (size_t)(QS + (COMP ? 2 * QR : 0)) * NPC * 32;
     static __host__ __device__ size_t smem_bytes(int nw) { return rs_off(nw) + RS_ENTRIES * sizeof(float2); }
     // the sum index q of slow sum b and of residual sum j
     static __host__ __device__ constexpr int slow_q(int b) {
@@ -541,11 +578,11 @@ struct PgramCsLayout {
 // kernels are instantiated in translation units of their own
 // (pgram_mirror_*.cu): with them in the same module the kernels without a
 // mirror measured 1.5% slower, identical code notwithstanding.
-template <int P, int F, bool MIRROR, int NSET = 1>
+template <int P, int F, bool MIRROR, int NSET = 1, bool COMP = false>
 __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
                                                int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
     static_assert(NSET == 1 || !MIRROR, "the two-set kernels write z to device memory only");
-    using L = PgramCsLayout<P, F, NSET>;
+    using L = PgramCsLayout<P, F, NSET, COMP>;
     constexpr int Q = L::Q, QS = L::QS, NPC = L::NPC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -604,6 +641,18 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
                         m = __fadd2_rn(m, acc.a[k][L::slow_q(b)]);
                         acc.a[k][L::slow_q(b)] = make_float2(0.0f, 0.0f);
                     }
+            if constexpr (COMP) {   // the warp's residual running sums (at most
+                                    // FLUSH_BLOCKS_ALL flushes) into the CTA's compensated totals
+#pragma unroll 1
+                for (int j = 0; j < L::QR; ++j)
+                    if ((QS + j) % nw == slice)
+#pragma unroll 1
+                        for (int k = 0; k < NPC; ++k) {
+                            float2 &v = mine[(j * NPC + k) * 32 + lane];
+                            kahan_add2(rs[((QS + j) * NPC + k) * 32 + lane], rs[((QS + L::QR + j) * NPC + k) * 32 + lane], v);
+                            v = make_float2(0.0f, 0.0f);
+                        }
+            }
             __syncthreads();
         }
     };
@@ -640,8 +689,9 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
     flush_r();
     flush_slow();
 
-    // Epilogue: the slow sums are the CTA's, the residual sums the warps'
-    // (added in FP32); FP64 solve per frequency.
+    // Epilogue: the slow sums (and with COMP the residual totals) from the
+    // CTA array, else the residual sums from the warps'; FP64 solve per
+    // frequency.
     double *zbuf = reinterpret_cast<double *>(tiles);
     const double W = st.Wf;
     const int64_t nf = d.nf;
@@ -658,10 +708,15 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
 #pragma unroll
         for (int bq = 0; bq < QS; ++bq) S[L::slow_q(bq)] = (double)rd(rs + (size_t)bq * NPC * 32, k, ln);
 #pragma unroll
-        for (int jr = 0; jr < 2 * NSET; ++jr) {
-            float v = 0.0f;
-            for (int w = 0; w < nw; ++w) v += rd(rr + (size_t)w * L::RR_PER_WARP + (size_t)jr * NPC * 32, k, ln);
-            S[L::fast_q(jr)] = (double)v;
+        for (int jr = 0; jr < L::QR; ++jr) {
+            if constexpr (COMP) {   // total minus its compensation, rounded once to FP32
+                S[L::fast_q(jr)] = (double)(rd(rs + (size_t)(QS + jr) * NPC * 32, k, ln) -
+                                            rd(rs + (size_t)(QS + L::QR + jr) * NPC * 32, k, ln));
+            } else {   // the warps' running sums, added in FP32
+                float v = 0.0f;
+                for (int w = 0; w < nw; ++w) v += rd(rr + (size_t)w * L::RR_PER_WARP + (size_t)jr * NPC * 32, k, ln);
+                S[L::fast_q(jr)] = (double)v;
+            }
         }
         double vcc = 0.0, vcs = 0.0, vss = 0.0;
 #pragma unroll
@@ -725,7 +780,7 @@ constexpr int pgram_maxreg() {
 template <int PREC, int NSET>
 constexpr bool pgram_cs() { return PREC == FREDEC_MIXED; }
 
-template <int PREC, int P, int F, bool MIRROR, int NSET = 1>
+template <int PREC, int P, int F, bool MIRROR, int NSET = 1, bool COMP = false>
 __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, NSET>())) pgram_kernel(PgramParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
@@ -735,25 +790,25 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     if (st.status != FREDEC_OK) return;
     uint32_t use0 = 0u, use1 = 0u;
     if constexpr (pgram_cs<PREC, NSET>())
-        pgram_block_cs<P, F, MIRROR, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
+        pgram_block_cs<P, F, MIRROR, NSET, COMP>(prm, d, st, blockIdx.x, smem, use0, use1);
     else
         pgram_block<PREC, P, F, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
-template <int PREC, int P, int F, int NSET = 1>
+template <int PREC, int P, int F, int NSET = 1, bool COMP = false>
 size_t pgram_smem_t(int warps) {
-    if constexpr (pgram_cs<PREC, NSET>()) return PgramCsLayout<P, F, NSET>::smem_bytes(warps);
+    if constexpr (pgram_cs<PREC, NSET>()) return PgramCsLayout<P, F, NSET, COMP>::smem_bytes(warps);
     else return PgramLayout<PREC, P, F, NSET>::smem_bytes(warps);
 }
 
-template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
-int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    const size_t smem = pgram_smem_t<PREC, P, F, NSET>(warps);
+template <int PREC, int P, int F, bool MIRROR, int NSET, bool COMP>
+int launch_pgram_k(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    const size_t smem = pgram_smem_t<PREC, P, F, NSET, COMP>(warps);
     if (smem > SMEM_LIMIT) return fail(FREDEC_EINVAL, "launch shape needs more than 227 KB of shared memory");
     if ((prm.z_mirror != nullptr) != MIRROR) return fail(FREDEC_EINVAL, "z mirror and kernel variant differ");
-    auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET>;
+    auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     if (nblocks <= 0) return FREDEC_OK;
@@ -761,6 +816,16 @@ int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram launch: ") + cudaGetErrorString(e));
     return FREDEC_OK;
+}
+
+// The mixed kernels with compensated residual totals serve series whose warps
+// would otherwise add more than COMP_MIN_FLUSHES flushes into their FP32
+// running sums (prm.comp, set by the launcher).
+template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
+int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+    if constexpr (PREC == FREDEC_MIXED)
+        if (prm.comp) return launch_pgram_k<PREC, P, F, MIRROR, NSET, true>(prm, nblocks, warps, st);
+    return launch_pgram_k<PREC, P, F, MIRROR, NSET, false>(prm, nblocks, warps, st);
 }
 
 }  // namespace fredec
