@@ -16,12 +16,12 @@
 
 namespace fredec {
 
-int launch_batch_p5(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
-int launch_batch_p15(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
-int launch_batch_p25(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st);
-int batch_occupancy_p5(int prec, int warps);
-int batch_occupancy_p15(int prec, int warps);
-int batch_occupancy_p25(int prec, int warps);
+int launch_batch_p5(int prec, const BatchParams &bp, int warps, int grid, bool comp, cudaStream_t st);
+int launch_batch_p15(int prec, const BatchParams &bp, int warps, int grid, bool comp, cudaStream_t st);
+int launch_batch_p25(int prec, const BatchParams &bp, int warps, int grid, bool comp, cudaStream_t st);
+int batch_occupancy_p5(int prec, int warps, bool comp);
+int batch_occupancy_p15(int prec, int warps, bool comp);
+int batch_occupancy_p25(int prec, int warps, bool comp);
 size_t topk_plan_size(int S, int64_t nch, int k);
 int topk_plan_bytes(const int64_t *nf_h, int S, int k, int64_t *nchunks_out);
 int topk_plan_make(const int64_t *z_off_h, const int64_t *nf_h, int S, int k, int64_t *idx_out, const double *z,
@@ -85,14 +85,16 @@ struct fredec_batch_plan {
         bp.items = items;
         bp.n_items = n_items;
         bp.counter = counter;
-        // the smallest compiled class of base sizes that covers the batch
-        const int occ = pmax <= 5    ? batch_occupancy_p5(precision, w)
-                        : pmax <= 15 ? batch_occupancy_p15(precision, w)
-                                     : batch_occupancy_p25(precision, w);
+        // the smallest compiled class of base sizes that covers the batch;
+        // compensated residual totals when its longest series needs them
+        const bool comp = pgram_comp(max_n, w);
+        const int occ = pmax <= 5    ? batch_occupancy_p5(precision, w, comp)
+                        : pmax <= 15 ? batch_occupancy_p15(precision, w, comp)
+                                     : batch_occupancy_p25(precision, w, comp);
         const int grid = std::max(1, occ * sm_count());
-        const int rc = pmax <= 5    ? launch_batch_p5(precision, bp, w, grid, st)
-                       : pmax <= 15 ? launch_batch_p15(precision, bp, w, grid, st)
-                                    : launch_batch_p25(precision, bp, w, grid, st);
+        const int rc = pmax <= 5    ? launch_batch_p5(precision, bp, w, grid, comp, st)
+                       : pmax <= 15 ? launch_batch_p15(precision, bp, w, grid, comp, st)
+                                    : launch_batch_p25(precision, bp, w, grid, comp, st);
         if (rc) return rc;
         if (fix)
             for (int p : p_present)

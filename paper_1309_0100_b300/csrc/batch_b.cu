@@ -3,14 +3,14 @@
 
 namespace fredec {
 
-int launch_batch_p15(int prec, const BatchParams &bp, int warps, int grid, cudaStream_t st) {
-    return prec == FREDEC_MIXED ? launch_batch_t<FREDEC_MIXED, 15>(bp, warps, grid, st)
-                                : launch_batch_t<FREDEC_FP64, 15>(bp, warps, grid, st);
+int launch_batch_p15(int prec, const BatchParams &bp, int warps, int grid, bool comp, cudaStream_t st) {
+    return prec == FREDEC_MIXED ? launch_batch_t<FREDEC_MIXED, 15>(bp, warps, grid, comp, st)
+                                : launch_batch_t<FREDEC_FP64, 15>(bp, warps, grid, comp, st);
 }
 
-int batch_occupancy_p15(int prec, int warps) {
-    return prec == FREDEC_MIXED ? batch_blocks_per_sm<FREDEC_MIXED, 15>(warps)
-                                : batch_blocks_per_sm<FREDEC_FP64, 15>(warps);
+int batch_occupancy_p15(int prec, int warps, bool comp) {
+    return prec == FREDEC_MIXED ? batch_blocks_per_sm<FREDEC_MIXED, 15>(warps, comp)
+                                : batch_blocks_per_sm<FREDEC_FP64, 15>(warps, comp);
 }
 
 }  // namespace fredec

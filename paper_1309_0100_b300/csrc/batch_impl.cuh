@@ -29,7 +29,7 @@ struct BatchParams {
     unsigned long long *counter;
 };
 
-template <int PREC, int P>
+template <int PREC, int P, bool COMP>
 __device__ __forceinline__ void batch_item(const BatchParams &bp, const SeriesDesc &d, const SeriesState &st,
                                            int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
     constexpr int F = batch_fpt(PREC, P);
@@ -41,16 +41,16 @@ __device__ __forceinline__ void batch_item(const BatchParams &bp, const SeriesDe
         return;
     }
     if constexpr (PREC == FREDEC_MIXED)
-        pgram_block_cs<P, F, false>(bp.prm, d, st, blk, smem, use0, use1);
+        pgram_block_cs<P, F, false, 1, COMP>(bp.prm, d, st, blk, smem, use0, use1);
     else
         pgram_block<PREC, P, F>(bp.prm, d, st, blk, smem, use0, use1);
 }
 
 // Shared memory of one batch item's block routine.
-template <int PREC, int P>
+template <int PREC, int P, bool COMP>
 size_t batch_item_smem(int warps) {
     constexpr int F = batch_fpt(PREC, P);
-    if constexpr (PREC == FREDEC_MIXED) return PgramCsLayout<P, F>::smem_bytes(warps);
+    if constexpr (PREC == FREDEC_MIXED) return PgramCsLayout<P, F, 1, COMP>::smem_bytes(warps);
     else return PgramLayout<PREC, P, F>::smem_bytes(warps);
 }
 
@@ -59,7 +59,9 @@ size_t batch_item_smem(int warps) {
 template <int PMAXC>
 constexpr int batch_minb() { return PMAXC <= 5 ? 3 : 2; }
 
-template <int PREC, int PMAXC>
+// COMP: compensated residual totals (mixed; plans holding a series of more
+// than COMP_MIN_FLUSHES tiles per warp).
+template <int PREC, int PMAXC, bool COMP>
 __global__ void __launch_bounds__(128, batch_minb<PMAXC>()) pgram_batch_kernel(BatchParams bp) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long cur;
@@ -74,10 +76,10 @@ __global__ void __launch_bounds__(128, batch_minb<PMAXC>()) pgram_batch_kernel(B
         const SeriesDesc d = bp.prm.desc[w.x];
         const SeriesState &st = bp.prm.state[w.x];
         switch (d.p) {
-            case 1: batch_item<PREC, 1>(bp, d, st, w.y, smem, use0, use1); break;
-            case 3: batch_item<PREC, 3>(bp, d, st, w.y, smem, use0, use1); break;
-            case 5: batch_item<PREC, 5>(bp, d, st, w.y, smem, use0, use1); break;
-#define C(P) case P: if constexpr (PMAXC >= P) batch_item<PREC, P>(bp, d, st, w.y, smem, use0, use1); break;
+            case 1: batch_item<PREC, 1, COMP>(bp, d, st, w.y, smem, use0, use1); break;
+            case 3: batch_item<PREC, 3, COMP>(bp, d, st, w.y, smem, use0, use1); break;
+            case 5: batch_item<PREC, 5, COMP>(bp, d, st, w.y, smem, use0, use1); break;
+#define C(P) case P: if constexpr (PMAXC >= P) batch_item<PREC, P, COMP>(bp, d, st, w.y, smem, use0, use1); break;
             C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
             default: break;
@@ -86,37 +88,52 @@ __global__ void __launch_bounds__(128, batch_minb<PMAXC>()) pgram_batch_kernel(B
     }
 }
 
-template <int PREC, int PMAXC>
+template <int PREC, int PMAXC, bool COMP>
 size_t batch_smem(int warps) {
     size_t m = 0;
     auto upd = [&](size_t v) { m = v > m ? v : m; };
-    upd(batch_item_smem<PREC, 1>(warps));
-    upd(batch_item_smem<PREC, 3>(warps));
-    upd(batch_item_smem<PREC, 5>(warps));
-#define C(P) if (PMAXC >= P) upd(batch_item_smem<PREC, P>(warps));
+    upd(batch_item_smem<PREC, 1, COMP>(warps));
+    upd(batch_item_smem<PREC, 3, COMP>(warps));
+    upd(batch_item_smem<PREC, 5, COMP>(warps));
+#define C(P) if (PMAXC >= P) upd(batch_item_smem<PREC, P, COMP>(warps));
     C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
     return m;
 }
 
-template <int PREC, int PMAXC>
-int launch_batch_t(const BatchParams &bp, int warps, int grid, cudaStream_t st) {
-    const size_t smem = batch_smem<PREC, PMAXC>(warps);
-    auto kern = pgram_batch_kernel<PREC, PMAXC>;
+template <int PREC, int PMAXC, bool COMP>
+int launch_batch_k(const BatchParams &bp, int warps, int grid, cudaStream_t st) {
+    const size_t smem = batch_smem<PREC, PMAXC, COMP>(warps);
+    auto kern = pgram_batch_kernel<PREC, PMAXC, COMP>;
     FREDEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, warps * 32, smem, st>>>(bp);
     FREDEC_CUDA_TRY(cudaGetLastError());
     return FREDEC_OK;
 }
 
-template <int PREC, int PMAXC>
-int batch_blocks_per_sm(int warps) {
+template <int PREC, int PMAXC, bool COMP>
+int batch_blocks_per_sm_k(int warps) {
     int n = 0;
-    const size_t smem = batch_smem<PREC, PMAXC>(warps);
-    auto kern = pgram_batch_kernel<PREC, PMAXC>;
+    const size_t smem = batch_smem<PREC, PMAXC, COMP>(warps);
+    auto kern = pgram_batch_kernel<PREC, PMAXC, COMP>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, warps * 32, smem) != cudaSuccess || n < 1) n = 1;
     return n;
+}
+
+// The FP64 kernels have no compensated variant (their sums are FP64).
+template <int PREC, int PMAXC>
+int launch_batch_t(const BatchParams &bp, int warps, int grid, bool comp, cudaStream_t st) {
+    if constexpr (PREC == FREDEC_MIXED)
+        if (comp) return launch_batch_k<PREC, PMAXC, true>(bp, warps, grid, st);
+    return launch_batch_k<PREC, PMAXC, false>(bp, warps, grid, st);
+}
+
+template <int PREC, int PMAXC>
+int batch_blocks_per_sm(int warps, bool comp) {
+    if constexpr (PREC == FREDEC_MIXED)
+        if (comp) return batch_blocks_per_sm_k<PREC, PMAXC, true>(warps);
+    return batch_blocks_per_sm_k<PREC, PMAXC, false>(warps);
 }
 
 }  // namespace fredec
