@@ -74,7 +74,8 @@ size_t pgram_smem(int p, int prec, int F, int warps);
 namespace {
 
 __global__ void init_series_kernel(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int32_t *chunk_series,
-                                   int64_t nchunks, int32_t *flag_count, int32_t *err) {
+                                   int64_t nchunks, int32_t *flag_count, int32_t *err, int32_t *tail_cnt = nullptr,
+                                   int n_tail = 0) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *desc = v;
@@ -84,6 +85,7 @@ __global__ void init_series_kernel(SeriesDesc *desc, SeriesDesc v, SeriesState *
         if (err) *err = FREDEC_OK;
     }
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
+    for (int64_t q = i; q < n_tail; q += (int64_t)gridDim.x * blockDim.x) tail_cnt[q] = 0;
 }
 
 __global__ void info_kernel(const SeriesState *state, double *info) {
@@ -119,6 +121,9 @@ struct SingleWork {
     int32_t *flag_count;
     int32_t *err;
     int64_t nchunks;
+    float2 *tail_part;   // tail split of the periodogram launch (mixed)
+    int32_t *tail_cnt;
+    int tail_gcap;
 };
 
 
@@ -143,7 +148,18 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     const size_t o_cs = take(nchunks * 4), o_part = take(nchunks * prep_npart(p) * 8);
     const size_t o_psi = take((size_t)p * N * 8), o_rec = take(N * rb);
     const size_t o_rec64 = fix ? take(N * rbff) : 0;
+    PgramShape shape;
+    if (o.fpt > 0 || o.warps > 0) {
+        shape = default_shape(prec, p, N, nf);
+        if (o.fpt > 0) shape.fpt = o.fpt;
+        if (o.warps > 0) shape.warps = o.warps;
+    } else if (!tuned_shape(prec, p, N, nf, &shape)) {
+        shape = default_shape(prec, p, N, nf);
+    }
+    int tail_gcap = 0;
+    const size_t tail_bytes = nf > 0 ? pgram_tail_bytes(prec, p, shape.fpt, &tail_gcap) : 0;
     const size_t o_fl = take(nflag * 8 + 8), o_fc = take(4), o_err = take(4);
+    const size_t o_tp = tail_bytes ? take(tail_bytes) : 0, o_tc = tail_bytes ? take((size_t)tail_gcap * 4) : 0;
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();
     w.desc = (SeriesDesc *)(b + o_desc);
@@ -157,6 +173,9 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     w.flag_count = (int32_t *)(b + o_fc);
     w.err = (int32_t *)(b + o_err);
     w.nchunks = nchunks;
+    w.tail_part = tail_bytes ? (float2 *)(b + o_tp) : nullptr;
+    w.tail_cnt = tail_bytes ? (int32_t *)(b + o_tc) : nullptr;
+    w.tail_gcap = tail_bytes ? tail_gcap : 0;
 
     SeriesDesc d{};
     d.f0 = f0;
@@ -169,7 +188,7 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     d.npoly = o.trend;
     d.nchunks = (int32_t)nchunks;
     init_series_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
-        w.desc, d, w.state, w.chunk_series, nchunks, w.flag_count, w.err);
+        w.desc, d, w.state, w.chunk_series, nchunks, w.flag_count, w.err, w.tail_cnt, w.tail_gcap);
     FREDEC_CUDA_TRY(cudaGetLastError());
 
     PrepPlan pp;
@@ -186,17 +205,9 @@ static int periodogram_core(const double *t, const double *y, const double *sigm
     pp.rec = w.rec;
     if (int rc = run_prep_records(pp, t, y, sigma, base, prec, fix ? w.rec64 : nullptr, st)) return rc;
 
-    PgramShape shape;
-    if (o.fpt > 0 || o.warps > 0) {
-        shape = default_shape(prec, p, N, nf);
-        if (o.fpt > 0) shape.fpt = o.fpt;
-        if (o.warps > 0) shape.warps = o.warps;
-    } else if (!tuned_shape(prec, p, N, nf, &shape)) {
-        shape = default_shape(prec, p, N, nf);
-    }
     if (nf > 0) {
         if (int rc = launch_pgram(prec, w.desc, w.state, w.rec, p, (int)N, nf, shape, tau, z, coef, w.flag_list,
-                                  w.flag_count, w.err, st, z_mirror))
+                                  w.flag_count, w.err, st, z_mirror, w.tail_part, w.tail_cnt, w.tail_gcap))
             return rc;
         // the NaN fill of a failed prep rides on the re-evaluation launch when there is one
         if (fix) {

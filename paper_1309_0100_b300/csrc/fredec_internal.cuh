@@ -166,7 +166,12 @@ void *pinned_scratch(int slot, size_t bytes);
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev,
                  const void *rec, int p, int N, int64_t nf, PgramShape shape, double flag_tau,
                  double *z, double *coef, int64_t *flag_list, int32_t *flag_count, int32_t *err,
-                 cudaStream_t st, double *z_mirror = nullptr);
+                 cudaStream_t st, double *z_mirror = nullptr, float2 *tail_part = nullptr,
+                 int32_t *tail_cnt = nullptr, int tail_gcap = 0);
+// Bytes of the tail-split arrays of a mixed single-series launch of shape fpt
+// (partial sums; 0 for FP64) and the tail CTAs they hold (*gcap); the tiles
+// counters take 4 bytes per tail CTA more and must be zero at launch.
+size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap);
 // FP64-grade re-evaluation of the listed bins (fixup.cu); z_mirror as above.
 // nan_nf > 0 (one series): if the series' prep failed, the launch sets
 // z[0..nan_nf) to NaN instead (the NaN fill of a failed call).

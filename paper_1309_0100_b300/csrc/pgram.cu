@@ -30,27 +30,28 @@ void set_profile_events(cudaEvent_t a, cudaEvent_t b) { g_ev0 = a; g_ev1 = b; }
 void profile_events(cudaEvent_t *a, cudaEvent_t *b) { *a = g_ev0; *b = g_ev1; }
 
 #define FREDEC_DECL_P(P)                                                                              \
-    int launch_pgram_p##P(int, int, const PgramParams &, int64_t, int, cudaStream_t);               \
+    int launch_pgram_p##P(int, int, const PgramParams &, int64_t, int, cudaStream_t, const TailParams *); \
     size_t smem_pgram_p##P(int, int, int);
 FREDEC_DECL_P(1) FREDEC_DECL_P(3) FREDEC_DECL_P(5) FREDEC_DECL_P(7) FREDEC_DECL_P(9) FREDEC_DECL_P(11)
 FREDEC_DECL_P(13) FREDEC_DECL_P(15) FREDEC_DECL_P(17) FREDEC_DECL_P(19) FREDEC_DECL_P(21)
 FREDEC_DECL_P(23) FREDEC_DECL_P(25)
 #undef FREDEC_DECL_P
 
-int launch_pgram_mirror_a(int, int, const PgramParams &, int64_t, int, cudaStream_t);
-int launch_pgram_mirror_b(int, int, const PgramParams &, int64_t, int, cudaStream_t);
-int launch_pgram_mirror_c(int, int, const PgramParams &, int64_t, int, cudaStream_t);
+int launch_pgram_mirror_a(int, int, const PgramParams &, int64_t, int, cudaStream_t, const TailParams *);
+int launch_pgram_mirror_b(int, int, const PgramParams &, int64_t, int, cudaStream_t, const TailParams *);
+int launch_pgram_mirror_c(int, int, const PgramParams &, int64_t, int, cudaStream_t, const TailParams *);
 
-static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+static int dispatch(int p, int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                    const TailParams *tail) {
     if (prm.z_mirror) {   // mixed precision only (pgram_mirror_*.cu)
         if (prec != FREDEC_MIXED) return -1;
-        int rc = launch_pgram_mirror_a(p, F, prm, nblocks, warps, st);
-        if (rc == -2) rc = launch_pgram_mirror_b(p, F, prm, nblocks, warps, st);
-        if (rc == -2) rc = launch_pgram_mirror_c(p, F, prm, nblocks, warps, st);
+        int rc = launch_pgram_mirror_a(p, F, prm, nblocks, warps, st, tail);
+        if (rc == -2) rc = launch_pgram_mirror_b(p, F, prm, nblocks, warps, st, tail);
+        if (rc == -2) rc = launch_pgram_mirror_c(p, F, prm, nblocks, warps, st, tail);
         return rc == -2 ? -1 : rc;
     }
     switch (p) {
-#define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, st);
+#define C(P) case P: return launch_pgram_p##P(prec, F, prm, nblocks, warps, st, tail);
         C(1) C(3) C(5) C(7) C(9) C(11) C(13) C(15) C(17) C(19) C(21) C(23) C(25)
 #undef C
     }
@@ -127,9 +128,19 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
     return s;
 }
 
+// Two slots of (2p+4) ceil(F/2) 32 float2 partial sums per tail CTA, up to two
+// tail CTAs per SM.
+size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap) {
+    *gcap = 0;
+    if (precision != FREDEC_MIXED || fpt < 1) return 0;
+    *gcap = 2 * sm_count();
+    return (size_t)2 * *gcap * (2 * p + 4) * ((fpt + 1) / 2) * 32 * sizeof(float2);
+}
+
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,
                  int N, int64_t nf, PgramShape shape, double flag_tau, double *z, double *coef, int64_t *flag_list,
-                 int32_t *flag_count, int32_t *err, cudaStream_t st, double *z_mirror) {
+                 int32_t *flag_count, int32_t *err, cudaStream_t st, double *z_mirror, float2 *tail_part,
+                 int32_t *tail_cnt, int tail_gcap) {
     if (!shape_supported(precision, p, shape.fpt))
         return fail(FREDEC_EINVAL, "no compiled kernel for this (precision, p, frequencies per thread)");
     if (shape.warps < 1 || shape.warps > 8) return fail(FREDEC_EINVAL, "warps per CTA must be in 1..8");
@@ -147,11 +158,18 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
     prm.err = err;
     prm.seed_mode = seed_mode();
     prm.comp = pgram_comp(N, shape.warps);
+    TailParams tail{};
+    if (precision == FREDEC_MIXED && tail_part && tail_cnt && tail_gcap > 0) {
+        tail.part = tail_part;
+        tail.cnt = tail_cnt;
+        tail.gcap = tail_gcap;
+        tail.n_points = N;
+    }
     const int64_t nblocks = (nf + 32LL * shape.fpt - 1) / (32LL * shape.fpt);
     cudaEvent_t e0, e1;
     profile_events(&e0, &e1);
     if (e0) cudaEventRecord(e0, st);
-    const int rc = dispatch(p, precision, shape.fpt, prm, nblocks, shape.warps, st);
+    const int rc = dispatch(p, precision, shape.fpt, prm, nblocks, shape.warps, st, tail.part ? &tail : nullptr);
     if (e1) cudaEventRecord(e1, st);
     return rc < 0 ? fail(FREDEC_EINVAL, "kernel dispatch failed") : rc;
 }

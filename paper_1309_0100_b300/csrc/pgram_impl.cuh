@@ -22,6 +22,9 @@
 // point at each thread's first frequency from the exact fixed-point phase.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
+
 #include "device_util.cuh"
 #include "fredec_internal.cuh"
 
@@ -61,6 +64,11 @@ constexpr int FLUSH_BLOCKS_ALL = 8;
 // point loop, not the additions themselves: a plain-add variant of the same
 // structure measured the same); on N = 1e5 it runs as fast as the plain one.
 constexpr int COMP_MIN_FLUSHES = 64;
+
+// A block of the tail of a launch is shared by at most TAIL_MAX_PARTS CTAs
+// (the launcher gives every tail CTA at least tiles / (TAIL_MAX_PARTS - 1) of
+// them).
+constexpr int TAIL_MAX_PARTS = 9;
 inline bool pgram_comp(int64_t N, int warps) { return (N + 32LL * warps - 1) / (32LL * warps) > COMP_MIN_FLUSHES; }
 
 // Frequencies per thread of the two-set kernels (z and dz/df): mixed, two
@@ -89,6 +97,17 @@ struct PgramParams {
     const double *wt_sum;       // two-set kernels: <t'> = sum of the records' w t' (one series)
     int seed_mode;              // mixed: 0 = table-driven FP32 sin/cos seed, 1 = MUFU __sincosf
     int comp;                   // mixed: compensated residual totals (pgram_comp)
+};
+
+// Mixed, one series: the last part-filled wave of blocks split over a wave of
+// CTAs (pgram_tail_kernel).  A separate kernel argument: a larger PgramParams
+// changed the main kernel's register allocation and slowed it by 1.5%.
+struct TailParams {
+    float2 *part;     // partial sums, 2 slots per tail CTA
+    int32_t *cnt;     // tiles done per tail block (zero at launch)
+    int gcap;         // tail CTAs the two arrays hold
+    int n_points;     // the series' N (host copy)
+    int64_t b0;       // first block of the tail (set by the launcher)
 };
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -573,14 +592,91 @@ struct PgramCsLayout {
     static __host__ __device__ constexpr int fast_q(int j) { return (j / 2) * Q0 + 2 * P + j % 2; }
 };
 
+// Tail of a single-series launch (pgram_tail_kernel): the blocks from
+// TailParams::b0 on are cut into their tiles, U = blocks x tiles units in all,
+// and tail CTA g of G takes the units [u0(g), u0(g + 1)), u0(g) = g U / G, in
+// (block, tile) order: every CTA has the same work, so the last wave of a
+// launch ends together instead of leaving SMs idle.  A block that CTAs share
+// is completed by the CTA whose tiles complete its count; no CTA waits for
+// another.
+__host__ __device__ inline int64_t tail_u0(int64_t g, int64_t U, int64_t G) { return g * U / G; }
+
+// After a part of block blk (ntl of its ntiles tiles) has been summed: write
+// this CTA's partial sums, the slow-sum rows and the residual rows (the warps'
+// running sums added in warp order; with COMP total minus compensation), to
+// its slot (2 g for the first block of its range, 2 g + 1 for the last), and
+// count the tiles.  The CTA that completes the count adds the parts in the
+// order of the CTAs that hold them (deterministic) into its own shared-memory
+// sums, laid out as the epilogue reads them, and returns true.
+template <int P, int F, int NSET, bool COMP>
+__device__ bool tail_exchange(const PgramParams &prm, const TailParams &tp, int64_t blk, int ntiles, int ntl, float2 *rr,
+                              float2 *rs) {
+    using L = PgramCsLayout<P, F, NSET, COMP>;
+    constexpr int SE = L::QS * L::NPC * 32, RE = L::QR * L::NPC * 32, PE = SE + RE;
+    __shared__ int s_last, s_nslot, s_slot[TAIL_MAX_PARTS];
+    const int tid = threadIdx.x, nw = blockDim.x >> 5;
+    const int64_t G = gridDim.x, g = blockIdx.x;
+    const int64_t nblocks = (prm.desc[0].nf + 32 * F - 1) / (32 * F);
+    const int64_t U = (nblocks - tp.b0) * ntiles, ub = (blk - tp.b0) * ntiles, ue = ub + ntiles;
+    const int64_t mine = 2 * g + (tail_u0(g, U, G) < ub ? 1 : 0);
+    float2 *dst = tp.part + (size_t)mine * PE;
+    for (int e = tid; e < SE; e += blockDim.x) dst[e] = rs[e];
+    for (int e = tid; e < RE; e += blockDim.x) {
+        float2 v;
+        if constexpr (COMP) {
+            const float2 m = rs[SE + e], c = rs[SE + RE + e];
+            v = make_float2(m.x - c.x, m.y - c.y);
+        } else {
+            v = make_float2(0.0f, 0.0f);
+            for (int w = 0; w < nw; ++w) v = __fadd2_rn(v, rr[(size_t)w * L::RR_PER_WARP + e]);
+        }
+        dst[SE + e] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();   // the partial before the count
+        const int old = atomicAdd(tp.cnt + (blk - tp.b0), ntl);
+        s_last = old + ntl == ntiles;
+        if (s_last) {
+            __threadfence();   // the other parts after the count
+            int64_t h = ub * G / U;   // the CTA holding the block's first unit
+            while (h + 1 < G && tail_u0(h + 1, U, G) <= ub) ++h;
+            while (h > 0 && tail_u0(h, U, G) > ub) --h;
+            int n = 0;
+            for (; h < G && tail_u0(h, U, G) < ue && n < TAIL_MAX_PARTS; ++h)
+                s_slot[n++] = (int)(2 * h + (tail_u0(h, U, G) < ub ? 1 : 0));
+            s_nslot = n;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    const int n = s_nslot;
+    for (int e = tid; e < PE; e += blockDim.x) {
+        float2 v = make_float2(0.0f, 0.0f);
+        for (int i = 0; i < n; ++i) v = __fadd2_rn(v, __ldcg(tp.part + (size_t)s_slot[i] * PE + e));
+        if (e < SE) {
+            rs[e] = v;
+        } else if constexpr (COMP) {
+            rs[e] = v;
+            rs[RE + e] = make_float2(0.0f, 0.0f);
+        } else {
+            rr[e - SE] = v;   // warp 0's running sums; the other warps' are zero
+            for (int w = 1; w < nw; ++w) rr[(size_t)w * L::RR_PER_WARP + e - SE] = make_float2(0.0f, 0.0f);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // MIRROR: z also goes to prm.z_mirror (page-locked host memory), staged in
 // shared memory so that the host-memory stores are contiguous.  The mirror
 // kernels are instantiated in translation units of their own
 // (pgram_mirror_*.cu): with them in the same module the kernels without a
 // mirror measured 1.5% slower, identical code notwithstanding.
-template <int P, int F, bool MIRROR, int NSET = 1, bool COMP = false>
+template <int P, int F, bool MIRROR, int NSET = 1, bool COMP = false, bool TAIL = false>
 __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const SeriesDesc &d, const SeriesState &st,
-                                               int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1) {
+                                               int64_t blk, unsigned char *smem, uint32_t &use0, uint32_t &use1,
+                                               int t_begin = 0, int t_end = 0, const TailParams *tp = nullptr) {
     static_assert(NSET == 1 || !MIRROR, "the two-set kernels write z to device memory only");
     using L = PgramCsLayout<P, F, NSET, COMP>;
     constexpr int Q = L::Q, QS = L::QS, NPC = L::NPC;
@@ -599,6 +695,8 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
     const size_t TB = L::tile_bytes(nw);
     const int ntiles = (N + TP - 1) / TP;
     const int ks = FLUSH_BLOCKS_ALL;   // tiles between slow flushes: 32 FLUSH_BLOCKS_ALL points per warp
+    // tiles [tb, te) of the block (TAIL: a part of it)
+    const int tbeg = TAIL ? t_begin : 0, tend = TAIL ? t_end : ntiles;
 
     __syncthreads();   // previous block's epilogue is done with the sums and tiles
     // each thread clears the residual entries it flushes into; the slow sums
@@ -608,10 +706,10 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
     auto issue = [&](int k, uint64_t *bar) {
         const unsigned n = (unsigned)min(TP, N - k * TP);
         mbar_arrive_expect_tx(bar, n * L::RB);
-        bulk_g2s(tiles + (k & 1) * TB, src + (size_t)k * TB, n * L::RB, bar);
+        bulk_g2s(tiles + ((k - tbeg) & 1) * TB, src + (size_t)k * TB, n * L::RB, bar);
     };
     if (tid == 0)
-        for (int k = 0; k < 2 && k < ntiles; ++k) issue(k, &bars[k]);
+        for (int k = tbeg; k < tbeg + 2 && k < tend; ++k) issue(k, &bars[(k - tbeg) & 1]);
 
     MixedAcc<P, F, NSET> acc;
 #pragma unroll
@@ -658,8 +756,8 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
     };
     int since = 0;   // points of this warp since the last flush of the residual sums
 
-    for (int tile = 0; tile < ntiles; ++tile) {
-        const int b = tile & 1;
+    for (int tile = tbeg; tile < tend; ++tile) {
+        const int b = (tile - tbeg) & 1;
         const uint32_t par = b ? (use1++ & 1u) : (use0++ & 1u);
         if (!mbar_wait_bounded(&bars[b], par)) {
             if (lane == 0) atomicExch(prm.err, FREDEC_ETIMEOUT);
@@ -683,11 +781,14 @@ __device__ __forceinline__ void pgram_block_cs(const PgramParams &prm, const Ser
             }
         }
         __syncthreads();   // all warps are done with buffer b
-        if (tid == 0 && tile + 2 < ntiles) issue(tile + 2, &bars[b]);
-        if ((tile + 1) % ks == 0 && tile + 1 < ntiles) flush_slow();
+        if (tid == 0 && tile + 2 < tend) issue(tile + 2, &bars[b]);
+        if ((tile + 1 - tbeg) % ks == 0 && tile + 1 < tend) flush_slow();
     }
     flush_r();
     flush_slow();
+    if constexpr (TAIL)
+        if ((tbeg != 0 || tend != ntiles) && !tail_exchange<P, F, NSET, COMP>(prm, *tp, blk, ntiles, tend - tbeg, rr, rs))
+            return;   // another CTA completes the block
 
     // Epilogue: the slow sums (and with COMP the residual totals) from the
     // CTA array, else the residual sums from the warps'; FP64 solve per
@@ -785,6 +886,7 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
     grid_dependency_wait();   // prep's records and state
+    allow_dependents();       // the tail kernel's CTAs may start as this grid's drain
     const SeriesDesc d = prm.desc[0];
     const SeriesState &st = prm.state[0];
     if (st.status != FREDEC_OK) return;
@@ -793,6 +895,38 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
         pgram_block_cs<P, F, MIRROR, NSET, COMP>(prm, d, st, blockIdx.x, smem, use0, use1);
     else
         pgram_block<PREC, P, F, NSET>(prm, d, st, blockIdx.x, smem, use0, use1);
+}
+
+// The tail of a mixed single-series launch: tail CTA g sums the tiles
+// [u0(g), u0(g + 1)) of the blocks from tp.b0 on (tail_exchange).
+template <int PREC, int P, int F, bool MIRROR, bool COMP>
+__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 1>())) pgram_tail_kernel(PgramParams prm,
+                                                                                                TailParams tp) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    pgram_cta_init<PREC>(smem);
+    // No wait here: this grid starts once every CTA of the main launch has
+    // passed its own wait for prep (allow_dependents), so the records are in
+    // place; its CTAs fill the SMs that the main launch's last wave frees.
+    const SeriesDesc d = prm.desc[0];
+    const SeriesState &st = prm.state[0];
+    if (st.status != FREDEC_OK) {
+        grid_dependency_wait();
+        return;
+    }
+    const int TP = 32 * (int)(blockDim.x >> 5), ntiles = (d.N + TP - 1) / TP;
+    const int64_t nblocks = (d.nf + 32 * F - 1) / (32 * F);
+    const int64_t U = (nblocks - tp.b0) * ntiles, G = gridDim.x;
+    const int64_t u1 = tail_u0((int64_t)blockIdx.x + 1, U, G);
+    uint32_t use0 = 0u, use1 = 0u;
+    for (int64_t u = tail_u0(blockIdx.x, U, G); u < u1;) {
+        const int64_t blk = tp.b0 + u / ntiles;
+        const int t0 = (int)(u % ntiles), t1 = t0 + (u1 - u) < ntiles ? (int)(t0 + (u1 - u)) : ntiles;
+        pgram_block_cs<P, F, MIRROR, 1, COMP, true>(prm, d, st, blk, smem, use0, use1, t0, t1, &tp);
+        u += t1 - t0;
+    }
+    // this grid ends after the main launch, so that a kernel that waits for
+    // it (the re-evaluation of flagged bins) sees both launches' z
+    grid_dependency_wait();
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
@@ -818,11 +952,55 @@ int launch_pgram_k(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
     return FREDEC_OK;
 }
 
+// Mixed single-series launch with a tail split: the main kernel takes the
+// whole waves of blocks (resident CTAs per SM x SMs), pgram_tail_kernel the
+// rest, spread evenly over up to a wave of CTAs, when that rest fills less
+// than 90% of a wave.  Measured on the N = 2000, p = 7 series with F = 10 and
+// four warps (two CTAs per SM): 947,200 frequencies (10 whole waves) 1.514 ms,
+// 1e6 (10.56 waves) 1.657 ms, 1,041,920 (11 waves) 1.663 ms: a part-filled
+// last wave costs a whole one.
+template <int P, int F, bool MIRROR, bool COMP>
+int launch_pgram_split(const PgramParams &prm, const TailParams &tail, int64_t nblocks, int warps, cudaStream_t st) {
+    constexpr int PREC = FREDEC_MIXED;
+    static std::atomic<int> occ_cache[9];
+    const size_t smem = pgram_smem_t<PREC, P, F, 1, COMP>(warps);
+    int occ = warps >= 1 && warps <= 8 ? occ_cache[warps].load() : 0;
+    if (occ == 0 && smem <= SMEM_LIMIT) {
+        auto kern = pgram_kernel<PREC, P, F, MIRROR, 1, COMP>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem) == cudaSuccess && occ > 0)
+            occ_cache[warps].store(occ);
+        else
+            occ = 0, (void)cudaGetLastError();
+    }
+    const int64_t slots = (int64_t)occ * sm_count();
+    const int64_t full = slots > 0 ? nblocks / slots * slots : 0, rem = nblocks - full;
+    const int64_t ntiles = ((int64_t)tail.n_points + 32 * warps - 1) / (32 * warps);
+    const int64_t U = rem * ntiles, min_units = (ntiles + TAIL_MAX_PARTS - 2) / (TAIL_MAX_PARTS - 1);
+    const int64_t G = std::min<int64_t>(std::min<int64_t>(slots, tail.gcap), U / std::max<int64_t>(min_units, 1));
+    if (full == 0 || rem == 0 || rem > tail.gcap || rem * 10 > slots * 9 || G < 1)
+        return launch_pgram_k<PREC, P, F, MIRROR, 1, COMP>(prm, nblocks, warps, st);
+    if (int rc = launch_pgram_k<PREC, P, F, MIRROR, 1, COMP>(prm, full, warps, st)) return rc;
+    TailParams tp = tail;
+    tp.b0 = full;
+    auto kern = pgram_tail_kernel<PREC, P, F, MIRROR, COMP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = launch_pdl(kern, dim3((unsigned)G), dim3(warps * 32), smem, st, prm, tp);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FREDEC_ECUDA, std::string("pgram tail launch: ") + cudaGetErrorString(e));
+    return FREDEC_OK;
+}
+
 // The mixed kernels with compensated residual totals serve series whose warps
 // would otherwise add more than COMP_MIN_FLUSHES flushes into their FP32
 // running sums (prm.comp, set by the launcher).
 template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
-int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
+int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                   const TailParams *tail = nullptr) {
+    if constexpr (PREC == FREDEC_MIXED && NSET == 1)
+        if (tail && tail->part)
+            return prm.comp ? launch_pgram_split<P, F, MIRROR, true>(prm, *tail, nblocks, warps, st)
+                            : launch_pgram_split<P, F, MIRROR, false>(prm, *tail, nblocks, warps, st);
     if constexpr (PREC == FREDEC_MIXED)
         if (prm.comp) return launch_pgram_k<PREC, P, F, MIRROR, NSET, true>(prm, nblocks, warps, st);
     return launch_pgram_k<PREC, P, F, MIRROR, NSET, false>(prm, nblocks, warps, st);

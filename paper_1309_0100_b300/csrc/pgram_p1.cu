@@ -3,12 +3,13 @@
 
 namespace fredec {
 
-int launch_pgram_p1(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    if (prec == FREDEC_MIXED && F == 12) return launch_pgram_t<FREDEC_MIXED, 1, 12>(prm, nblocks, warps, st);
-    if (prec == FREDEC_MIXED && F == 20) return launch_pgram_t<FREDEC_MIXED, 1, 20>(prm, nblocks, warps, st);
-    if (prec == FREDEC_MIXED && F == 32) return launch_pgram_t<FREDEC_MIXED, 1, 32>(prm, nblocks, warps, st);
-    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 1, 2>(prm, nblocks, warps, st);
-    if (prec == FREDEC_FP64 && F == 4) return launch_pgram_t<FREDEC_FP64, 1, 4>(prm, nblocks, warps, st);
+int launch_pgram_p1(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                     const TailParams *tail) {
+    if (prec == FREDEC_MIXED && F == 12) return launch_pgram_t<FREDEC_MIXED, 1, 12>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_MIXED && F == 20) return launch_pgram_t<FREDEC_MIXED, 1, 20>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_MIXED && F == 32) return launch_pgram_t<FREDEC_MIXED, 1, 32>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 1, 2>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_FP64 && F == 4) return launch_pgram_t<FREDEC_FP64, 1, 4>(prm, nblocks, warps, st, tail);
     return -1;
 }
 

@@ -3,12 +3,13 @@
 
 namespace fredec {
 
-int launch_pgram_p9(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    if (prec == FREDEC_MIXED && F == 3) return launch_pgram_t<FREDEC_MIXED, 9, 3>(prm, nblocks, warps, st);
-    if (prec == FREDEC_MIXED && F == 5) return launch_pgram_t<FREDEC_MIXED, 9, 5>(prm, nblocks, warps, st);
-    if (prec == FREDEC_MIXED && F == 8) return launch_pgram_t<FREDEC_MIXED, 9, 8>(prm, nblocks, warps, st);
-    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 9, 1>(prm, nblocks, warps, st);
-    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 9, 2>(prm, nblocks, warps, st);
+int launch_pgram_p9(int prec, int F, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                     const TailParams *tail) {
+    if (prec == FREDEC_MIXED && F == 3) return launch_pgram_t<FREDEC_MIXED, 9, 3>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_MIXED && F == 5) return launch_pgram_t<FREDEC_MIXED, 9, 5>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_MIXED && F == 8) return launch_pgram_t<FREDEC_MIXED, 9, 8>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_FP64 && F == 1) return launch_pgram_t<FREDEC_FP64, 9, 1>(prm, nblocks, warps, st, tail);
+    if (prec == FREDEC_FP64 && F == 2) return launch_pgram_t<FREDEC_FP64, 9, 2>(prm, nblocks, warps, st, tail);
     return -1;
 }
 

@@ -91,6 +91,35 @@ def test_mixed_long_series_error_distribution(F, N, nb):
     assert np.median(e) < 4e-7 and np.quantile(e, 0.99) < 3e-6, (np.median(e), np.quantile(e, 0.99))
 
 
+@pytest.mark.parametrize("N,nb,fpt,warps,nf", [(2000, 3, 10, 4, 1_000_000), (2000, 3, 6, 4, 300_000),
+                                               (2000, 3, 4, 2, 150_000), (777, 1, 12, 1, 123_457),
+                                               (70000, 3, 6, 4, 100_000)])
+def test_tail_split(F, N, nb, fpt, warps, nf):
+    """Grids whose last wave of CTAs is part-filled run their last blocks as an
+    even split of the blocks' tiles over a wave of tail CTAs; a CTA that
+    completes a shared block adds the parts in a fixed order (the last case
+    with compensated residual totals).  The bins of the tail (and a sample of
+    the rest) agree with the oracle, and two calls agree bit for bit."""
+    import torch
+    s = synth.small_series(61 + nb, N=N, n_base=nb, nf=nf, span=3000.0, fmax=2.0)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda:0")
+    t, y, sg, b = (dev(a) for a in (s.t, s.y, s.sigma, s.base_freqs))
+    zs = []
+    for _ in range(2):
+        z = torch.empty(nf, dtype=torch.float64, device="cuda:0")
+        F.periodogram_dev(t, y, sg, b, s.grid.f0, s.grid.df, nf, precision="mixed", fpt=fpt, warps=warps, out=z)
+        zs.append(z.cpu().numpy())
+    assert np.array_equal(zs[0], zs[1])
+    tail = int(0.12 * nf)
+    ns = 60 if N > 10000 else 240
+    idx = np.unique(np.concatenate([np.linspace(nf - tail, nf - 1, ns).astype(int),
+                                    np.linspace(0, nf - tail - 1, ns // 4).astype(int)]))
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, s.grid.array()[idx], want_ratio=True)
+    r = cond_parity(zs[0][idx], zr, ratio, c2, TOL["mixed"], s.N,
+                    floor_frac=1e-3 * np.max(zs[0]) / max(np.max(zr), 1e-300))
+    assert r["ok"], r
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_seasonal_n200_full_grid(F, prec):
     s = synth.seasonal_n200()
