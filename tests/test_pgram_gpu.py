@@ -99,7 +99,9 @@ def test_tail_split(F, N, nb, fpt, warps, nf):
     even split of the blocks' tiles over a wave of tail CTAs; a CTA that
     completes a shared block adds the parts in a fixed order (the last case
     with compensated residual totals).  The bins of the tail (and a sample of
-    the rest) agree with the oracle, and two calls agree bit for bit."""
+    the rest) agree with the oracle, two calls agree bit for bit, and so do the
+    host-pointer calls with a pageable and a page-locked z_out (whose kernels
+    write z to host memory themselves)."""
     import torch
     s = synth.small_series(61 + nb, N=N, n_base=nb, nf=nf, span=3000.0, fmax=2.0)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda:0")
@@ -110,6 +112,11 @@ def test_tail_split(F, N, nb, fpt, warps, nf):
         F.periodogram_dev(t, y, sg, b, s.grid.f0, s.grid.df, nf, precision="mixed", fpt=fpt, warps=warps, out=z)
         zs.append(z.cpu().numpy())
     assert np.array_equal(zs[0], zs[1])
+    f = s.grid.array()
+    zh = F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="mixed", fpt=fpt, warps=warps)
+    pinned = torch.full((nf,), -1.0, dtype=torch.float64).pin_memory().numpy()
+    F.periodogram(s.t, s.y, s.sigma, s.base_freqs, f, precision="mixed", fpt=fpt, warps=warps, out=pinned)
+    assert np.array_equal(pinned, zh)
     tail = int(0.12 * nf)
     ns = 60 if N > 10000 else 240
     idx = np.unique(np.concatenate([np.linspace(nf - tail, nf - 1, ns).astype(int),
