@@ -169,9 +169,10 @@ int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *s
                  cudaStream_t st, double *z_mirror = nullptr, float2 *tail_part = nullptr,
                  int32_t *tail_cnt = nullptr, int tail_gcap = 0);
 // Bytes of the tail-split arrays of a mixed single-series launch of shape fpt
-// (partial sums; 0 for FP64) and the tail CTAs they hold (*gcap); the tiles
-// counters take 4 bytes per tail CTA more and must be zero at launch.
-size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap);
+// with nset sets of sums (partial sums; 0 for FP64) and the tail CTAs they
+// hold (*gcap); the tiles counters take 4 bytes per tail CTA more and must be
+// zero at launch.
+size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap, int nset = 1);
 // FP64-grade re-evaluation of the listed bins (fixup.cu); z_mirror as above.
 // nan_nf > 0 (one series): if the series' prep failed, the launch sets
 // z[0..nan_nf) to NaN instead (the NaN fill of a failed call).

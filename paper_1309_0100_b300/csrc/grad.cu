@@ -23,13 +23,15 @@
 
 namespace fredec {
 
-int launch_pgram_grad_a(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st);
-int launch_pgram_grad_b(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st);
+int launch_pgram_grad_a(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                        const TailParams *tail);
+int launch_pgram_grad_b(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                        const TailParams *tail);
 
 namespace {
 
 __global__ void grad_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state, int32_t *chunk_series, int64_t nchunks,
-                          int32_t *flag_count, int32_t *err) {
+                          int32_t *flag_count, int32_t *err, int32_t *tail_cnt, int n_tail) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *desc = v;
@@ -39,6 +41,7 @@ __global__ void grad_init(SeriesDesc *desc, SeriesDesc v, SeriesState *state, in
         *err = FREDEC_OK;
     }
     for (int64_t q = i; q < nchunks; q += (int64_t)gridDim.x * blockDim.x) chunk_series[q] = 0;
+    for (int64_t q = i; q < n_tail; q += (int64_t)gridDim.x * blockDim.x) tail_cnt[q] = 0;
 }
 
 // <t'> = sum of the records' w t' values (FP64 records: the first word of
@@ -81,9 +84,10 @@ __global__ void grad_finish(const SeriesState *state, const int32_t *err, double
         }
 }
 
-int launch_pgram_grad(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st) {
-    int rc = launch_pgram_grad_a(prec, p, prm, nblocks, warps, st);
-    if (rc == -2) rc = launch_pgram_grad_b(prec, p, prm, nblocks, warps, st);
+int launch_pgram_grad(int prec, int p, const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
+                      const TailParams *tail) {
+    int rc = launch_pgram_grad_a(prec, p, prm, nblocks, warps, st, tail);
+    if (rc == -2) rc = launch_pgram_grad_b(prec, p, prm, nblocks, warps, st, tail);
     return rc == -2 ? fail(FREDEC_EINVAL, "no two-set kernel for this base size") : rc;
 }
 
@@ -111,6 +115,9 @@ int grad_core(const double *t, const double *y, const double *sigma, int64_t N, 
     const size_t o_rec64 = fix ? take(N * (size_t)recff_bytes(p, 2)) : 0;
     const size_t o_fl = fix ? take(nf * 8 + 8) : 0;
     const size_t o_fc = take(4), o_err = take(4), o_wt = take(8);
+    int tail_gcap = 0;
+    const size_t tail_bytes = nf > 0 ? pgram_tail_bytes(prec, p, fpt, &tail_gcap, 2) : 0;
+    const size_t o_tp = tail_bytes ? take(tail_bytes) : 0, o_tc = tail_bytes ? take((size_t)tail_gcap * 4) : 0;
     if (int rc = ws.alloc(off, st)) return rc;
     unsigned char *b = ws.as<unsigned char>();
     SeriesDesc *desc = (SeriesDesc *)(b + o_desc);
@@ -136,7 +143,8 @@ int grad_core(const double *t, const double *y, const double *sigma, int64_t N, 
     d.npoly = o.trend;
     d.nchunks = (int32_t)nchunks;
     grad_init<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (nchunks + 255) / 256)), 256, 0, st>>>(
-        desc, d, state, cs, nchunks, flag_count, err);
+        desc, d, state, cs, nchunks, flag_count, err, tail_bytes ? (int32_t *)(b + o_tc) : nullptr,
+        tail_bytes ? tail_gcap : 0);
     FREDEC_CUDA_TRY(cudaGetLastError());
     PrepPlan pp;
     pp.S = 1;
@@ -173,7 +181,14 @@ int grad_core(const double *t, const double *y, const double *sigma, int64_t N, 
         cudaEvent_t e0, e1;
         profile_events(&e0, &e1);
         if (e0) cudaEventRecord(e0, st);
-        if (int rc = launch_pgram_grad(prec, p, prm, nblocks, warps, st))
+        TailParams tail{};   // the tail split of the last part-filled wave (mixed)
+        if (tail_bytes) {
+            tail.part = (float2 *)(b + o_tp);
+            tail.cnt = (int32_t *)(b + o_tc);
+            tail.gcap = tail_gcap;
+            tail.n_points = (int)N;
+        }
+        if (int rc = launch_pgram_grad(prec, p, prm, nblocks, warps, st, tail_bytes ? &tail : nullptr))
             return fail(rc, std::string("two-set periodogram kernel: ") + fredec_last_error());
         if (e1) cudaEventRecord(e1, st);
         if (fix)

@@ -128,13 +128,13 @@ PgramShape default_shape(int precision, int p, int64_t N, int64_t nf) {
     return s;
 }
 
-// Two slots of (2p+4) ceil(F/2) 32 float2 partial sums per tail CTA, up to two
-// tail CTAs per SM.
-size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap) {
+// Two slots of nset (2p+4) ceil(F/2) 32 float2 partial sums per tail CTA, up to
+// two tail CTAs per SM.
+size_t pgram_tail_bytes(int precision, int p, int fpt, int *gcap, int nset) {
     *gcap = 0;
     if (precision != FREDEC_MIXED || fpt < 1) return 0;
     *gcap = 2 * sm_count();
-    return (size_t)2 * *gcap * (2 * p + 4) * ((fpt + 1) / 2) * 32 * sizeof(float2);
+    return (size_t)2 * *gcap * nset * (2 * p + 4) * ((fpt + 1) / 2) * 32 * sizeof(float2);
 }
 
 int launch_pgram(int precision, const SeriesDesc *desc_dev, const SeriesState *state_dev, const void *rec, int p,

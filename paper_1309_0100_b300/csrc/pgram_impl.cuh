@@ -899,8 +899,8 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
 
 // The tail of a mixed single-series launch: tail CTA g sums the tiles
 // [u0(g), u0(g + 1)) of the blocks from tp.b0 on (tail_exchange).
-template <int PREC, int P, int F, bool MIRROR, bool COMP>
-__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 1>())) pgram_tail_kernel(PgramParams prm,
+template <int PREC, int P, int F, bool MIRROR, int NSET, bool COMP>
+__global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, NSET>())) pgram_tail_kernel(PgramParams prm,
                                                                                                 TailParams tp) {
     extern __shared__ __align__(128) unsigned char smem[];
     pgram_cta_init<PREC>(smem);
@@ -921,7 +921,7 @@ __global__ void __launch_bounds__(256, 1) __maxnreg__((pgram_maxreg<PREC, P, F, 
     for (int64_t u = tail_u0(blockIdx.x, U, G); u < u1;) {
         const int64_t blk = tp.b0 + u / ntiles;
         const int t0 = (int)(u % ntiles), t1 = t0 + (u1 - u) < ntiles ? (int)(t0 + (u1 - u)) : ntiles;
-        pgram_block_cs<P, F, MIRROR, 1, COMP, true>(prm, d, st, blk, smem, use0, use1, t0, t1, &tp);
+        pgram_block_cs<P, F, MIRROR, NSET, COMP, true>(prm, d, st, blk, smem, use0, use1, t0, t1, &tp);
         u += t1 - t0;
     }
     // this grid ends after the main launch, so that a kernel that waits for
@@ -954,19 +954,24 @@ int launch_pgram_k(const PgramParams &prm, int64_t nblocks, int warps, cudaStrea
 
 // Mixed single-series launch with a tail split: the main kernel takes the
 // whole waves of blocks (resident CTAs per SM x SMs), pgram_tail_kernel the
-// rest, spread evenly over up to a wave of CTAs, when that rest fills less
-// than 90% of a wave.  Measured on the N = 2000, p = 7 series with F = 10 and
-// four warps (two CTAs per SM): 947,200 frequencies (10 whole waves) 1.514 ms,
-// 1e6 (10.56 waves) 1.657 ms, 1,041,920 (11 waves) 1.663 ms: a part-filled
-// last wave costs a whole one.
-template <int P, int F, bool MIRROR, bool COMP>
+// rest, spread evenly over up to a wave of CTAs.  Measured on the N = 2000,
+// p = 7 series with F = 10 and four warps (two CTAs per SM): 947,200
+// frequencies (10 whole waves) 1.514 ms, 1e6 (10.56 waves) 1.657 ms, 1,041,920
+// (11 waves) 1.663 ms: a part-filled last wave that puts two CTAs on some SMs
+// costs a whole one (split: 1.620 ms).  The split pays when the rest puts more
+// than one CTA on some SM, or leaves fewer than 3 warps per SM on average (1e6
+// frequencies with two warps: 1.678 -> 1.647 ms; z and dz/df at F = 4, 117
+// blocks left, two warps: 3.321 -> 3.271 ms); with one 4-warp CTA on each of
+// 117 SMs the lone CTAs already run faster than shared ones, and the split
+// cost 1.1% (3.273 -> 3.310 ms).  Not when the rest fills 90% of a wave.
+template <int P, int F, bool MIRROR, int NSET, bool COMP>
 int launch_pgram_split(const PgramParams &prm, const TailParams &tail, int64_t nblocks, int warps, cudaStream_t st) {
     constexpr int PREC = FREDEC_MIXED;
     static std::atomic<int> occ_cache[9];
-    const size_t smem = pgram_smem_t<PREC, P, F, 1, COMP>(warps);
+    const size_t smem = pgram_smem_t<PREC, P, F, NSET, COMP>(warps);
     int occ = warps >= 1 && warps <= 8 ? occ_cache[warps].load() : 0;
     if (occ == 0 && smem <= SMEM_LIMIT) {
-        auto kern = pgram_kernel<PREC, P, F, MIRROR, 1, COMP>;
+        auto kern = pgram_kernel<PREC, P, F, MIRROR, NSET, COMP>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem) == cudaSuccess && occ > 0)
             occ_cache[warps].store(occ);
@@ -978,12 +983,14 @@ int launch_pgram_split(const PgramParams &prm, const TailParams &tail, int64_t n
     const int64_t ntiles = ((int64_t)tail.n_points + 32 * warps - 1) / (32 * warps);
     const int64_t U = rem * ntiles, min_units = (ntiles + TAIL_MAX_PARTS - 2) / (TAIL_MAX_PARTS - 1);
     const int64_t G = std::min<int64_t>(std::min<int64_t>(slots, tail.gcap), U / std::max<int64_t>(min_units, 1));
-    if (full == 0 || rem == 0 || rem > tail.gcap || rem * 10 > slots * 9 || G < 1)
-        return launch_pgram_k<PREC, P, F, MIRROR, 1, COMP>(prm, nblocks, warps, st);
-    if (int rc = launch_pgram_k<PREC, P, F, MIRROR, 1, COMP>(prm, full, warps, st)) return rc;
+    const int64_t sms = sm_count();
+    const bool pays = rem > sms || rem * warps < 3 * sms;   // see above
+    if (full == 0 || rem == 0 || rem > tail.gcap || rem * 10 > slots * 9 || G < 1 || !pays)
+        return launch_pgram_k<PREC, P, F, MIRROR, NSET, COMP>(prm, nblocks, warps, st);
+    if (int rc = launch_pgram_k<PREC, P, F, MIRROR, NSET, COMP>(prm, full, warps, st)) return rc;
     TailParams tp = tail;
     tp.b0 = full;
-    auto kern = pgram_tail_kernel<PREC, P, F, MIRROR, COMP>;
+    auto kern = pgram_tail_kernel<PREC, P, F, MIRROR, NSET, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = launch_pdl(kern, dim3((unsigned)G), dim3(warps * 32), smem, st, prm, tp);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -997,10 +1004,10 @@ int launch_pgram_split(const PgramParams &prm, const TailParams &tail, int64_t n
 template <int PREC, int P, int F, bool MIRROR = false, int NSET = 1>
 int launch_pgram_t(const PgramParams &prm, int64_t nblocks, int warps, cudaStream_t st,
                    const TailParams *tail = nullptr) {
-    if constexpr (PREC == FREDEC_MIXED && NSET == 1)
+    if constexpr (PREC == FREDEC_MIXED)
         if (tail && tail->part)
-            return prm.comp ? launch_pgram_split<P, F, MIRROR, true>(prm, *tail, nblocks, warps, st)
-                            : launch_pgram_split<P, F, MIRROR, false>(prm, *tail, nblocks, warps, st);
+            return prm.comp ? launch_pgram_split<P, F, MIRROR, NSET, true>(prm, *tail, nblocks, warps, st)
+                            : launch_pgram_split<P, F, MIRROR, NSET, false>(prm, *tail, nblocks, warps, st);
     if constexpr (PREC == FREDEC_MIXED)
         if (prm.comp) return launch_pgram_k<PREC, P, F, MIRROR, NSET, true>(prm, nblocks, warps, st);
     return launch_pgram_k<PREC, P, F, MIRROR, NSET, false>(prm, nblocks, warps, st);

@@ -181,6 +181,29 @@ def test_grad_full_size_sampled(F):
                 assert g[j - 1] > 0 > g[j + 1] or g[j - 1] >= 0 >= g[j + 1], (prec, j)
 
 
+def test_grad_tail_split(F):
+    """A two-set launch whose last wave of CTAs is part-filled (1954 blocks of
+    128 frequencies on two CTAs per SM) runs its last blocks as an even split
+    of their tiles over a wave of tail CTAs: z and dz/df on the bins of the
+    tail agree with the oracle, and two calls agree bit for bit."""
+    s = synth.small_series(715, N=2000, n_base=3, nf=250_000, span=3000.0, fmax=2.0)
+    f = s.grid.array()
+    T = s.t.max() - s.t.min()
+    runs = [F.periodogram_grad(s.t, s.y, s.sigma, s.base_freqs, s.grid.f0, s.grid.df, s.grid.nf, precision="mixed")
+            for _ in range(2)]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    z, g = runs[0]
+    tail = int(0.12 * f.size)
+    idx = np.unique(np.concatenate([np.linspace(f.size - tail, f.size - 1, 200).astype(int),
+                                    np.linspace(0, f.size - tail - 1, 50).astype(int)]))
+    zr, c2, ratio = oracle.periodogram(s.t, s.y, s.sigma, s.base_freqs, f[idx], want_ratio=True)
+    gr = oracle.periodogram_grad(s.t, s.y, s.sigma, s.base_freqs, f[idx])
+    rz = cond_parity(z[idx], zr, ratio, c2, TOL_Z["mixed"], s.N)
+    assert rz["ok"], rz
+    rg = grad_parity(g[idx], gr, ratio, c2, T, s.N, TOL_G["mixed"], eps=EPS_FF)
+    assert rg["ok"], rg
+
+
 def test_grad_argument_checks(F):
     import ctypes
     s = synth.small_series(714, N=100, n_base=2, nf=50)

@@ -92,7 +92,7 @@ def test_mixed_long_series_error_distribution(F, N, nb):
 
 
 @pytest.mark.parametrize("N,nb,fpt,warps,nf", [(2000, 3, 10, 4, 1_000_000), (2000, 3, 6, 4, 300_000),
-                                               (2000, 3, 4, 2, 150_000), (777, 1, 12, 1, 123_457),
+                                               (2000, 3, 10, 2, 1_000_000), (777, 1, 12, 4, 300_000),
                                                (70000, 3, 6, 4, 100_000)])
 def test_tail_split(F, N, nb, fpt, warps, nf):
     """Grids whose last wave of CTAs is part-filled run their last blocks as an
