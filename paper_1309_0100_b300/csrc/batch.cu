@@ -87,7 +87,7 @@ struct fredec_batch_plan {
         bp.counter = counter;
         // the smallest compiled class of base sizes that covers the batch;
         // compensated residual totals when its longest series needs them
-        const bool comp = pgram_comp(max_n, w);
+        const bool comp = batch_comp(max_n, w);
         const int occ = pmax <= 5    ? batch_occupancy_p5(precision, w, comp)
                         : pmax <= 15 ? batch_occupancy_p15(precision, w, comp)
                                      : batch_occupancy_p25(precision, w, comp);

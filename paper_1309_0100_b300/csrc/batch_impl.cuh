@@ -54,6 +54,19 @@ size_t batch_item_smem(int warps) {
     else return PgramLayout<PREC, P, F>::smem_bytes(warps);
 }
 
+// Batch plans take the kernels with compensated residual totals (COMP) from
+// BATCH_COMP_MIN_FLUSHES tiles per warp on, not from COMP_MIN_FLUSHES as single
+// series do: their four extra rows of shared memory (10 KB at F = 20) take the
+// p <= 5 class from six to five CTAs per SM.  The first 256 series of the
+// 4096-series workload (N up to 5000, 79 tiles on two-warp CTAs) took 16.34 ms
+// a launch with COMP against 15.96 ms without; at 79 flushes the plain FP32
+// running sums stay near the error of the block sums (their rounding grows as
+// the square root of the flushes: the bound broke at 780).
+constexpr int BATCH_COMP_MIN_FLUSHES = 256;
+inline bool batch_comp(int64_t max_n, int warps) {
+    return (max_n + 32LL * warps - 1) / (32LL * warps) > BATCH_COMP_MIN_FLUSHES;
+}
+
 // Resident CTAs of 128 threads asked from the compiler: 3 for the small-base
 // class (about 170 registers), 2 when large base sizes are compiled in.
 template <int PMAXC>

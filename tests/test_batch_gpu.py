@@ -91,7 +91,7 @@ def test_batch_large_base_classes(F):
 
 
 def test_batch_long_series_error_distribution(F):
-    """A plan holding series of more than 64 tiles per warp runs the batch
+    """A plan holding series of more than 256 tiles per warp runs the batch
     kernel with compensated residual totals: the long series of the plan keep
     the error distribution of the single-series kernels (median below 4e-7,
     99th percentile below 3e-6 of the floor-relative error; measured 2.0e-7
