@@ -54,6 +54,20 @@ def test_device_path_singular_base_gives_nan(F, prec, topk):
         assert r["topk"].cpu().tolist() == [-1] * topk
 
 
+def test_split_launch_singular_base_gives_nan(F):
+    """A grid large enough for the tail split of the mixed launch (1e6
+    frequencies at F = 10 with four warps): with a singular base model both
+    periodogram launches return at once and the whole of z is NaN."""
+    import torch
+    s = synth.small_series(4, N=2000, n_base=3, nf=1_000_000, span=3000.0, fmax=2.0)
+    tt = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+    r = F.periodogram_dev(tt(s.t), tt(s.y), tt(s.sigma), tt([0.1, 0.1, 0.2]), s.grid.f0, s.grid.df, s.grid.nf,
+                          precision="mixed", topk=3, fpt=10, warps=4)
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(r["z"].cpu().numpy()))
+    assert r["topk"].cpu().tolist() == [-1] * 3
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_device_path_info_with_and_without_topk(F, prec):
     # info comes from the top-k launch when there is one, else from its own kernel
