@@ -370,6 +370,19 @@ template <int P, int F, int SEED, int NSET = 1>
 __device__ __forceinline__ void mixed_run(const unsigned char *p, size_t stride, int m, const SeedTableF &tab,
                                           uint32_t j0, MixedAcc<P, F, NSET> &acc) {
     auto rec = [&](int i) { return reinterpret_cast<const uint4 *>(p + (size_t)i * stride); };
+    if constexpr (NSET == 2 && P >= 23) {
+        // two-set kernels of the widest bases: 2 (2P+4) float2 sums leave no
+        // room for a second point in flight; one point at a time spills less
+        // (P = 25: 1984 -> 1148 bytes) and runs faster (z and dz/df, N = 2000,
+        // 1e6 frequencies: P = 25 27.7 -> 15.0 ms, P = 23 11.74 -> 11.36 ms;
+        // P = 21 kept the two points: 9.51 against 9.62 ms)
+        for (int j = 0; j < m; ++j) {
+            MixedPoint<P, NSET> pc;
+            mixed_load<P, SEED, NSET>(rec(j), tab, j0, pc);
+            mixed_accumulate<P, F, NSET>(pc, acc);
+        }
+        return;
+    }
     MixedPoint<P, NSET> pa, pb;
     mixed_load<P, SEED, NSET>(rec(0), tab, j0, pa);
     int j = 0;
