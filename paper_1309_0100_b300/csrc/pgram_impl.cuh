@@ -375,7 +375,8 @@ __device__ __forceinline__ void mixed_run(const unsigned char *p, size_t stride,
         // room for a second point in flight; one point at a time spills less
         // (P = 25: 1984 -> 1148 bytes) and runs faster (z and dz/df, N = 2000,
         // 1e6 frequencies: P = 25 27.7 -> 15.0 ms, P = 23 11.74 -> 11.36 ms;
-        // P = 21 kept the two points: 9.51 against 9.62 ms)
+        // narrower bases keep the two points: one at a time lost 1% at P = 21
+        // and 3-11% at P = 9-19)
         for (int j = 0; j < m; ++j) {
             MixedPoint<P, NSET> pc;
             mixed_load<P, SEED, NSET>(rec(j), tab, j0, pc);
